@@ -1,0 +1,139 @@
+"""FP64 CPU oracle for the neighbourhood graph (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It shares no code with the CUDA library: the
+arithmetic lives in ``oracle.c`` (plain C, double precision, OpenMP) and this
+module only marshals numpy arrays through ctypes.
+
+Functions and the definitions they follow (paper, Methods: "Custom GPU
+kernels" for the distances, "Implementation" for following scanpy, whose
+neighbours step uses the UMAP smooth-kNN / fuzzy-union construction):
+
+* ``knn``          -- brute-force exact kNN, ties broken by ascending index.
+* ``smooth_knn``   -- rho, sigma (64-step bisection to log2 k) and weights.
+* ``fuzzy_union``  -- G = A + A^T - A o A^T as CSR with sorted columns.
+* ``connectivities`` -- smooth_knn followed by fuzzy_union.
+
+Parity is pinned by tests/test_oracle_pins.py (brute force on tiny inputs,
+closed forms, a library kNN, invariants).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+EUCLIDEAN, COSINE = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_lib/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            vp = ctypes.c_void_p
+            lib.oracle_knn.argtypes = [vp, i64, i32, vp, i64, i32, i32, vp, vp, vp]
+            lib.oracle_knn.restype = i32
+            lib.oracle_smooth_knn.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp]
+            lib.oracle_smooth_knn.restype = i32
+            lib.oracle_fuzzy_union.argtypes = [vp, vp, i64, i32, vp, vp, vp, i64]
+            lib.oracle_fuzzy_union.restype = i32
+            lib.oracle_num_threads.argtypes = []
+            lib.oracle_num_threads.restype = i32
+            _ = dbl
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def knn(X: np.ndarray, k: int, metric: int = EUCLIDEAN, queries=None):
+    """Exact kNN of `queries` (row ids, default all rows) against all rows.
+
+    Returns (idx int32 [nq, k], dist float64 [nq, k], next float64 [nq]) where
+    ``next`` is the (k+1)-th distance, for judging ties at the boundary.
+    Euclidean distances are metric (square-rooted); cosine is 1 - cos.
+    """
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n, d = X.shape
+    q = None if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    nq = n if q is None else len(q)
+    idx = np.empty((nq, k), dtype=np.int32)
+    dist = np.empty((nq, k), dtype=np.float64)
+    nxt = np.empty(nq, dtype=np.float64)
+    rc = _load().oracle_knn(_ptr(X), n, d, _ptr(q), nq, k, metric, _ptr(idx), _ptr(dist), _ptr(nxt))
+    if rc != 0:
+        raise ValueError(f"oracle_knn failed with status {rc}")
+    return idx, dist, nxt
+
+
+def smooth_knn(idx: np.ndarray, dist: np.ndarray):
+    """Per-row rho, sigma, directed weights and bisection diagnostics."""
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    dist = np.ascontiguousarray(dist, dtype=np.float64)
+    n, k = idx.shape
+    out = {
+        "rho": np.empty(n), "sigma": np.empty(n), "weights": np.empty((n, k)),
+        "iters": np.empty(n, dtype=np.int32), "stop_margin": np.empty(n),
+        "floored": np.empty(n, dtype=np.int32), "converged": np.empty(n, dtype=np.int32),
+    }
+    rc = _load().oracle_smooth_knn(_ptr(idx), _ptr(dist), n, k, _ptr(out["rho"]), _ptr(out["sigma"]),
+                                   _ptr(out["weights"]), _ptr(out["iters"]), _ptr(out["stop_margin"]),
+                                   _ptr(out["floored"]), _ptr(out["converged"]))
+    if rc != 0:
+        raise ValueError(f"oracle_smooth_knn failed with status {rc}")
+    return out
+
+
+def fuzzy_union(idx: np.ndarray, weights: np.ndarray):
+    """CSR (indptr int64, indices int32, data float64) of A + A^T - A o A^T."""
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    weights = np.ascontiguousarray(weights, dtype=np.float64)
+    n, k = idx.shape
+    cap = 2 * n * k
+    indptr = np.empty(n + 1, dtype=np.int64)
+    indices = np.empty(cap, dtype=np.int32)
+    data = np.empty(cap, dtype=np.float64)
+    rc = _load().oracle_fuzzy_union(_ptr(idx), _ptr(weights), n, k, _ptr(indptr), _ptr(indices), _ptr(data), cap)
+    if rc != 0:
+        raise ValueError(f"oracle_fuzzy_union failed with status {rc}")
+    nnz = int(indptr[-1])
+    return indptr, indices[:nnz].copy(), data[:nnz].copy()
+
+
+def connectivities(idx: np.ndarray, dist: np.ndarray):
+    """smooth_knn then fuzzy_union; returns the smooth_knn dict plus the CSR."""
+    s = smooth_knn(idx, dist)
+    indptr, indices, data = fuzzy_union(idx, s["weights"])
+    s.update(indptr=indptr, indices=indices, data=data)
+    return s
