@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Neighbourhood-graph benchmark (exact kNN + fuzzy connectivities).
+
+One step = rsc_knn (prep, candidate search, exact FP32 re-rank) followed by
+rsc_connectivities (rho/sigma/weights, fuzzy union, CSR) over the whole
+1,000,000-cell x 50-PC workload, inputs resident in HBM.  Prints one JSON
+line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own
+seeded input (the graph step has no exchange): weak scaling, value = all
+cells / max-over-ranks time.  ``--impl reference`` times the FP64 CPU oracle
+on bounded query samples of the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "neighbors graph cells/s (50 PCs, k=15): BF16+rerank vs FP32 at recall@15≥0.999"
+WORKLOAD = ("1,000,000 cells x 50 PCs fp32, 100-cluster Gaussian mixture (means ~N(0,4I), "
+            "PC variance 1/t), euclidean, k=15")
+
+# DRAM traffic per launch of the candidate-search kernel from an ncu capture
+# (profiles/), valid only while the kernel source is unchanged.
+TRAFFIC = {}
+
+# Kernels this library launches per step (rsc_knn: column sums, column means,
+# prep, candidate search, re-rank; rsc_connectivities: 10 phases).
+LAUNCHES_PER_STEP = {"euclidean": 5 + 10, "cosine": 3 + 10}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["auto", "fp32", "bf16"], default="auto")
+    p.add_argument("--n", type=int, default=1_000_000)
+    p.add_argument("--k", type=int, default=15)
+    p.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the plain FP32 path for comparison")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _kernel_sha(name):
+    src = os.path.join(ROOT, "paper_2603_02402_gb300", "csrc", name)
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def setup_dist(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed on bounded query samples."""
+    world, rank, _ = setup_dist(args)
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2603_02402_gb300 import synth
+    oracle.build()
+    X = synth.mixture(args.n, 50, n_comp=100, seed=0)
+    per_step = max(16, int(os.environ.get("RSC_REF_QUERIES", "0")) or 0)
+    # size each step so W + K steps fit in about two minutes
+    t0 = time.perf_counter()
+    oracle.knn(X, args.k, queries=synth.query_sample(args.n, 16, seed=99))
+    t16 = time.perf_counter() - t0
+    budget = 120.0 / max(1, args.warmup + args.steps)
+    per_step = max(per_step, int(16 * budget / max(t16, 1e-3)))
+    per_step = min(per_step, args.n)
+    times = []
+    for s in range(args.warmup + args.steps):
+        q = synth.query_sample(args.n, per_step, seed=1000 + s)
+        t0 = time.perf_counter()
+        oracle.knn(X, args.k, queries=q)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step / (ms / 1e3)
+    cores = oracle.num_threads()
+    sample = f"{per_step} seeded query rows per step against all {args.n} rows (kNN stage; FP64, {cores} threads)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "d": 50, "k": args.k, "sample_queries": per_step},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_02402_gb300 import rsc, synth
+
+    world, rank, local = setup_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    rsc.lib()
+    n, d, k = args.n, 50, args.k
+    metric = "euclidean"
+
+    X = synth.mixture(n, d, n_comp=100, seed=rank)
+    X_pin = torch.from_numpy(X).pin_memory()
+    Xd = X_pin.to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    precision = args.precision
+    if precision == "auto":
+        try:
+            rsc.rsc_knn_workspace_size(n, d, k, metric, "bf16")
+            precision = "bf16"
+        except rsc.RscError:
+            precision = "fp32"
+
+    def buffers(prec):
+        ws_knn = torch.empty(rsc.rsc_knn_workspace_size(n, d, k, metric, prec), dtype=torch.uint8, device=dev)
+        return ws_knn
+
+    cap = rsc.rsc_connectivities_max_nnz(n, k)
+    ws_conn = torch.empty(rsc.rsc_connectivities_workspace_size(n, k), dtype=torch.uint8, device=dev)
+    idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    dst = torch.empty((n, k), dtype=torch.float32, device=dev)
+    indptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    indices = torch.empty(cap, dtype=torch.int32, device=dev)
+    data = torch.empty(cap, dtype=torch.float32, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    sigma = torch.empty(n, dtype=torch.float32, device=dev)
+
+    def make_events(count):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(count)]
+        for e in evs:
+            e.record(stream)     # materialise the underlying cudaEvent_t
+        torch.cuda.synchronize(dev)
+        return evs
+
+    def step(prec, ws_knn, ev=None):
+        arr = None
+        if ev is not None:
+            arr = (ctypes.c_void_p * 4)(*[e.cuda_event for e in ev])
+        rsc.rsc_knn(Xd, k, metric, prec, workspace=ws_knn, out=(idx, dst), phase_events=arr)
+        rsc.rsc_connectivities(idx, dst, nnz_capacity=cap, workspace=ws_conn,
+                               out=(indptr, indices, data, rho, sigma))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(prec, steps, warmup, clocks=False):
+        ws_knn = buffers(prec)
+        for _ in range(warmup):
+            step(prec, ws_knn)
+        torch.cuda.synchronize(dev)
+        phase = [make_events(4) for _ in range(steps)]
+        start, end = make_events(2)
+        sampler = ClockSampler(_smi_id(dev)) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for s in range(steps):
+            step(prec, ws_knn, phase[s])
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        if sampler:
+            sampler.__exit__()
+        if rsc.rsc_workspace_status(ws_knn) != rsc.RSC_OK or rsc.rsc_workspace_status(ws_conn) != rsc.RSC_OK:
+            raise RuntimeError("a kernel recorded a failure status")
+        ms = max_over_ranks(start.elapsed_time(end) / steps)
+        search = [p[1].elapsed_time(p[2]) for p in phase]
+        rerank = [p[2].elapsed_time(p[3]) for p in phase]
+        prep = [p[0].elapsed_time(p[1]) for p in phase]
+        return ms, {"search_ms": statistics.mean(search), "rerank_ms": statistics.mean(rerank),
+                    "prep_ms": statistics.mean(prep)}, (sampler.summary() if sampler else None), ws_knn
+
+    ms, phases, clocks, ws_knn = timed(precision, args.steps, args.warmup, clocks=True)
+    nnz = int(indptr[-1].item())
+    idx_main = idx.clone()
+    dist_main = dst.clone()
+
+    # end to end through the public API: pinned host X in, graph out to pinned host memory
+    out_host = {
+        "idx": torch.empty((n, k), dtype=torch.int32).pin_memory(),
+        "dist": torch.empty((n, k), dtype=torch.float32).pin_memory(),
+        "indptr": torch.empty(n + 1, dtype=torch.int64).pin_memory(),
+        "indices": torch.empty(nnz, dtype=torch.int32).pin_memory(),
+        "data": torch.empty(nnz, dtype=torch.float32).pin_memory(),
+    }
+
+    def e2e_step():
+        Xd.copy_(X_pin, non_blocking=True)
+        step(precision, ws_knn)
+        out_host["idx"].copy_(idx, non_blocking=True)
+        out_host["dist"].copy_(dst, non_blocking=True)
+        out_host["indptr"].copy_(indptr, non_blocking=True)
+        out_host["indices"].copy_(indices[:nnz], non_blocking=True)
+        out_host["data"].copy_(data[:nnz], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e_start, e_end = make_events(2)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    e_start.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = max_over_ranks(e_start.elapsed_time(e_end) / e2e_steps)
+    h2d = X_pin.numel() * 4
+    d2h = sum(t.numel() * t.element_size() for t in out_host.values())
+
+    fp32 = None
+    if precision != "fp32" and args.fp32_steps > 0:
+        f_ms, f_ph, _, _ = timed("fp32", args.fp32_steps, 1)
+        fp32 = {"value": world * n / (f_ms / 1e3), "ms_per_step": f_ms, "search_ms": f_ph["search_ms"]}
+
+    # roofline of the dominant kernel (candidate search): algorithmic flops =
+    # 2 * d per (query, database row) pair, n^2 pairs per launch
+    flops = 2.0 * d * float(n) * float(n)
+    peaks = _peaks()
+    search_s = phases["search_ms"] / 1e3
+    achieved = flops / search_s / 1e12
+    if precision == "bf16":
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        bound, src = "tensor", "bf16_tflops_sustained of measured" if peaks else "fallback 1.7 PFLOP/s"
+        kname = "knn_tc.cu"
+    else:
+        smc = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * 2 * smc * 1e6 / 1e12       # FP32 FFMA lanes x 2 flops x max SM clock
+        bound, src = "alu", f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {smc:.0f} MHz"
+        kname = "knn_simt.cuh"
+    tr = TRAFFIC.get(kname)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_sha") == _kernel_sha(kname) else None
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kname, "peak_source": src,
+                "algorithmic": "2*d flops per (query, row) pair, n^2 pairs per launch"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(X, idx_main.cpu().numpy(), dist_main.cpu().numpy(), k, args.cpu_seconds)
+
+    if rank == 0:
+        value = world * n / (ms / 1e3)
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if precision == "bf16" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "d": d, "k": k,
+                       "precision": f"{precision} candidates + fp32 exact re-rank",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (X 200 MB, operands re-streamed from HBM/L2 each step)",
+                       "nnz": nnz},
+            "phases_ms": phases,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": LAUNCHES_PER_STEP[metric] * args.steps,
+            "clocks": clocks,
+        }
+        if fp32:
+            line["fp32_path"] = fp32
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _smi_id(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return dev.index
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(X, gpu_idx, gpu_dist, k, seconds):
+    """The FP64 oracle on a bounded query sample, plus recall of the GPU rows."""
+    import numpy as np
+    import oracle
+    from paper_2603_02402_gb300 import synth
+    oracle.build()
+    n = len(X)
+    t0 = time.perf_counter()
+    oracle.knn(X, k, queries=synth.query_sample(n, 16, seed=77))
+    t16 = time.perf_counter() - t0
+    m = int(min(n, max(64, 16 * seconds / max(t16, 1e-3))))
+    q = synth.query_sample(n, m, seed=5)
+    t0 = time.perf_counter()
+    oi, od, _ = oracle.knn(X, k, queries=q)
+    dt = time.perf_counter() - t0
+    gi = gpu_idx[q]
+    # recall@k (tie-tolerant): a returned id counts when its oracle distance is within the k-th
+    Xq = X[q].astype(np.float64)
+    dex = np.sqrt(((Xq[:, None, :] - X[gi].astype(np.float64)) ** 2).sum(-1))
+    good = dex <= od[:, -1:] * (1 + 1e-6)
+    rel = np.abs(gpu_dist[q] - dex) / np.maximum(dex, 1e-30)
+    return {"value": m / dt, "unit": "cells/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{m} seeded query rows against all {n} rows (kNN stage, FP64 brute force)",
+            "recall_at_k": float(good.mean()), "id_exact": float((gi == oi).mean()),
+            "max_rel_dist_err": float(np.where(dex > 0, rel, 0).max())}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

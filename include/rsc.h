@@ -1,0 +1,167 @@
+/*
+ * rsc.h -- C ABI of the GB300 neighbourhood-graph library.
+ *
+ * The library computes the neighbourhood-graph step of a scanpy-style
+ * single-cell workflow on one GPU:
+ *   1. exact k-nearest neighbours of every cell over its principal
+ *      components (Euclidean or cosine distance; paper, Methods, "Custom GPU
+ *      kernels", which defines the two distances, and "Dimensionality
+ *      reduction and graph analysis", where the kNN graph feeds UMAP and
+ *      Leiden), and
+ *   2. the fuzzy connectivities graph built from those lists: per-cell rho and
+ *      sigma of the smooth-kNN equation, directed weights, and the union
+ *      G = A + A^T - A o A^T stored as CSR (paper, Methods,
+ *      "Implementation": results follow scanpy, whose neighbours step builds
+ *      this graph; "Dimensionality reduction and graph analysis": the graph is
+ *      stored in .obsp for UMAP and Leiden).
+ *
+ * Conventions shared by every entry point
+ *   - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *     argument's comment says "host".  Matrices are row-major and contiguous.
+ *   - The library allocates no device memory: each call that needs scratch
+ *     space takes a caller-provided `workspace` whose minimum size the matching
+ *     *_workspace_size() returns.  Workspace pointers must be 256-byte aligned.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) unless documented otherwise.  Argument errors are found
+ *     on the host before anything is launched.
+ *   - Errors: a non-zero rsc_status is returned and rsc_last_error() gives a
+ *     thread-local message.  Outputs are unspecified after an error.
+ *   - Bounded waits: kernels that wait on in-kernel barriers give up after a
+ *     fixed budget and record RSC_ERR_TIMEOUT in the workspace's status word;
+ *     rsc_workspace_status() reads it back (it synchronises the stream).
+ *   - Indices are int32 (n < 2^31 rows); CSR row pointers are int64.
+ */
+#ifndef RSC_H
+#define RSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RSC_OK = 0,
+    RSC_ERR_INVALID_ARG = 1,   /* bad size, pointer, alignment or option        */
+    RSC_ERR_CUDA = 2,          /* a CUDA runtime/driver call failed             */
+    RSC_ERR_WORKSPACE = 3,     /* workspace missing or smaller than required    */
+    RSC_ERR_TIMEOUT = 4,       /* an in-kernel wait exceeded its budget         */
+    RSC_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement   */
+    RSC_ERR_CAPACITY = 6       /* CSR output capacity smaller than nnz          */
+} rsc_status;
+
+typedef enum {
+    RSC_EUCLIDEAN = 0,         /* sqrt(sum_t (x_t - y_t)^2)                      */
+    RSC_COSINE = 1             /* 1 - x.y / (|x| |y|); 0 between two all-zero
+                                  rows, 1 between an all-zero row and any other */
+} rsc_metric;
+
+typedef enum {
+    RSC_FP32 = 0,              /* FP32 SIMT distances for candidate selection   */
+    RSC_BF16 = 1               /* BF16 tcgen05 tensor-core distances (FP32
+                                  accumulate) for candidate selection            */
+} rsc_precision;
+
+/* Options of rsc_knn.  Zero-initialise and set what you need. */
+typedef struct {
+    int32_t precision;   /* rsc_precision used to select candidates          */
+    int32_t candidates;  /* candidates kept per query before the exact FP32
+                            re-rank; 0 = default (k + 8 for FP32, 2k for BF16);
+                            rounded up to a supported width (16, 32, 64)  */
+    int32_t db_splits;   /* split the database into this many ranges handled
+                            by separate CTAs (small n); 0 = automatic          */
+    int32_t reserved;    /* must be 0                                           */
+    void *stream;        /* cudaStream_t                                        */
+    void *phase_events;  /* optional host array of 4 cudaEvent_t owned by the
+                            caller, recorded on `stream` before the prep pass,
+                            before the candidate search, before the exact
+                            re-rank and after it (per-phase timing); NULL = off */
+} rsc_knn_opts;
+
+/* Library version string (static storage). */
+const char *rsc_version(void);
+
+/* Thread-local message describing the last error returned on this thread. */
+const char *rsc_last_error(void);
+
+/*
+ * Reads and clears the status word that kernels write into `workspace`
+ * (first 4 bytes).  Synchronises `stream`.  Returns RSC_OK when no kernel
+ * recorded a failure, else the recorded rsc_status.
+ */
+rsc_status rsc_workspace_status(void *workspace, void *stream);
+
+/*
+ * Minimum workspace for rsc_knn with these arguments (host query; no GPU
+ * work).  `opts` may be NULL (defaults).  Result in *bytes (host).
+ */
+rsc_status rsc_knn_workspace_size(int64_t n, int32_t d, int32_t k, int32_t metric,
+                                  const rsc_knn_opts *opts, size_t *bytes);
+
+/*
+ * Exact k-nearest neighbours of every row of X among all rows of X.
+ *   X        [n, d] float32 cells x principal components.
+ *   n, d     1 <= n < 2^31, 1 <= d <= 64.
+ *   k        1 <= k <= min(n, 64); for RSC_BF16 also 2k <= 64 by default.
+ *   metric   rsc_metric.
+ *   idx      [n, k] int32 out: neighbour row ids, self included, ordered by
+ *            (distance, id) ascending.
+ *   dist     [n, k] float32 out: Euclidean distance (not squared) or 1 - cos.
+ * Method: candidates are selected with the precision in opts (FP32 SIMT or
+ * BF16 tensor cores, the n x n distance matrix is never stored), then every
+ * candidate is re-scored exactly in FP32 by direct difference and the k best
+ * are kept.  Ties in the final order are broken by ascending id.
+ */
+rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metric,
+                   int32_t *idx, float *dist, const rsc_knn_opts *opts,
+                   void *workspace, size_t workspace_bytes);
+
+/*
+ * Minimum workspace for rsc_connectivities / rsc_connectivities_nnz.
+ */
+rsc_status rsc_connectivities_workspace_size(int64_t n, int32_t k, size_t *bytes);
+
+/*
+ * Upper bound on the number of stored entries of the connectivities graph:
+ * 2 * n * (k - 1) (every directed non-self edge stored twice).
+ */
+int64_t rsc_connectivities_max_nnz(int64_t n, int32_t k);
+
+/*
+ * Fuzzy connectivities of a kNN graph (UMAP smooth-kNN + fuzzy union).
+ *   idx, dist  [n, k] as returned by rsc_knn (each row ascending by
+ *              distance; slots with idx < 0 are ignored).  2 <= k <= 256.
+ *   indptr     [n + 1] int64 out; indptr[n] = nnz.
+ *   indices    [nnz_capacity] int32 out, ascending within each row.
+ *   data       [nnz_capacity] float32 out.
+ *   rho, sigma [n] float32 out, or NULL.
+ * Per row i: rho_i = first non-zero distance; sigma_i solves
+ *   sum_{c=1}^{k-1} exp(-max(0, d_ic - rho_i) / sigma_i) = log2(k)
+ * by at most 64 bisection steps (stop within 1e-5), then is floored at
+ * 1e-3 * mean row distance (1e-3 * mean of all distances when rho_i = 0);
+ * w_ic = 0 for the row itself, 1 when d_ic <= rho_i, else
+ * exp(-(d_ic - rho_i) / sigma_i).  G = A + A^T - A o A^T without the diagonal
+ * or zeros.  All arithmetic is FP32.
+ * If nnz_capacity >= rsc_connectivities_max_nnz(n, k) the call is
+ * asynchronous; otherwise it synchronises once to compare nnz with the
+ * capacity and returns RSC_ERR_CAPACITY (indptr valid) when it does not fit.
+ */
+rsc_status rsc_connectivities(const int32_t *idx, const float *dist, int64_t n, int32_t k,
+                              int64_t *indptr, int32_t *indices, float *data,
+                              int64_t nnz_capacity, float *rho, float *sigma,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Number of stored entries rsc_connectivities would produce, written to
+ * *nnz (host).  Synchronises `stream`.
+ */
+rsc_status rsc_connectivities_nnz(const int32_t *idx, const float *dist, int64_t n, int32_t k,
+                                  int64_t *nnz, void *workspace, size_t workspace_bytes,
+                                  void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSC_H */

@@ -1,0 +1,287 @@
+// C ABI entry points (include/rsc.h): argument checks, workspace layout and
+// launch sequences.  Everything numeric happens in the kernels.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsc {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+rsc_status fail(rsc_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+int sm_count() {
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+// ------------------------------------------------------------------ kNN plan
+
+namespace {
+
+constexpr int kSupportedKC[] = {16, 32, 64};
+
+struct KnnPlan {
+    int precision = RSC_FP32;
+    int DP = 0;         // padded FP32 row length
+    int KC = 0;         // candidates per query per split
+    int splits = 1;     // database splits
+    int64_t split_len = 0;
+};
+
+struct KnnLayout {
+    unsigned int *status;
+    float *Y;
+    float *ny;
+    float *prep_scratch;
+    int32_t *cand;
+};
+
+rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_knn_opts *o,
+                    KnnPlan *p) {
+    rsc_knn_opts def = {};
+    if (!o) o = &def;
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(RSC_ERR_INVALID_ARG, "n=%lld out of [1, 2^31)", (long long)n);
+    if (metric != RSC_EUCLIDEAN && metric != RSC_COSINE) return fail(RSC_ERR_INVALID_ARG, "unknown metric %d", metric);
+    const int dmax = (metric == RSC_COSINE) ? 63 : 64;
+    if (d < 1 || d > dmax) return fail(RSC_ERR_INVALID_ARG, "d=%d out of [1, %d]", d, dmax);
+    if (k < 1 || k > 64 || k > n) return fail(RSC_ERR_INVALID_ARG, "k=%d out of [1, min(n, 64)]", k);
+    if (o->precision != RSC_FP32 && o->precision != RSC_BF16)
+        return fail(RSC_ERR_INVALID_ARG, "unknown precision %d", o->precision);
+    if (o->candidates < 0 || o->db_splits < 0) return fail(RSC_ERR_INVALID_ARG, "negative option");
+    if (o->reserved != 0) return fail(RSC_ERR_INVALID_ARG, "reserved option field must be 0");
+    p->precision = o->precision;
+    if (p->precision == RSC_BF16) return fail(RSC_ERR_UNSUPPORTED, "BF16 candidate search not built yet");
+    p->DP = ((d + (metric == RSC_COSINE ? 1 : 0) + 7) / 8) * 8;
+    int want = o->candidates;
+    if (want == 0) want = (p->precision == RSC_FP32) ? k + 8 : 2 * k;
+    if (want < k) return fail(RSC_ERR_INVALID_ARG, "candidates=%d smaller than k=%d", want, k);
+    if (want > 64) {
+        if (o->candidates != 0) return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 64", want);
+        want = 64;
+    }
+    p->KC = 0;
+    for (int c : kSupportedKC)
+        if (c >= want) { p->KC = c; break; }
+    // database splits: enough CTAs to fill the GPU when there are few queries
+    const int64_t qblocks = ceil_div(n, 128);
+    int splits = o->db_splits;
+    if (splits == 0) splits = (int)std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(1024, qblocks)));
+    while (splits > 1 && splits * p->KC > 1024) --splits;
+    if (splits * p->KC > 1024) return fail(RSC_ERR_INVALID_ARG, "db_splits * candidates above 1024");
+    p->split_len = ((ceil_div(n, splits) + 31) / 32) * 32;
+    p->splits = (int)ceil_div(n, p->split_len);
+    if (!knn_simt_supported(p->DP, p->KC)) return fail(RSC_ERR_UNSUPPORTED, "no SIMT kernel for DP=%d KC=%d", p->DP, p->KC);
+    return RSC_OK;
+}
+
+KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
+    Carve cv(ws);
+    KnnLayout L;
+    L.status = cv.take<unsigned int>(kStatusBytes / sizeof(unsigned int));
+    L.Y = cv.take<float>((size_t)n * p.DP);
+    L.ny = cv.take<float>((size_t)n);
+    L.prep_scratch = cv.take<float>(prep_scratch_floats());
+    L.cand = cv.take<int32_t>((size_t)p.splits * n * p.KC);
+    if (bytes) *bytes = cv.used;
+    return L;
+}
+
+rsc_status check_ws(void *ws, size_t have, size_t need) {
+    if (!ws) return fail(RSC_ERR_WORKSPACE, "workspace is NULL (%zu bytes needed)", need);
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(RSC_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    if (have < need) return fail(RSC_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", have, need);
+    return RSC_OK;
+}
+
+// ------------------------------------------------------- connectivities plan
+
+struct ConnLayout {
+    ConnWork w;
+    int64_t *indptr_tmp;
+    int32_t *zeroed;       // in_cnt, cursor, long_count (2n + 1 int32)
+};
+
+ConnLayout carve_conn(void *ws, int64_t n, int k, size_t *bytes) {
+    Carve cv(ws);
+    ConnLayout L;
+    L.w.status = cv.take<unsigned int>(kStatusBytes / sizeof(unsigned int));
+    L.w.partials = cv.take<float>(kMeanBlocks);
+    L.w.mean_all = cv.take<float>(1);
+    L.w.rho = cv.take<float>((size_t)n);
+    L.w.sigma = cv.take<float>((size_t)n);
+    L.w.scol = cv.take<int32_t>((size_t)n * k);
+    L.w.sw = cv.take<float>((size_t)n * k);
+    L.w.gv = cv.take<float>((size_t)n * k);
+    L.w.own_cnt = cv.take<int32_t>((size_t)n);
+    L.zeroed = cv.take<int32_t>((size_t)2 * n + 1);
+    L.w.in_cnt = L.zeroed;
+    L.w.cursor = L.zeroed ? L.zeroed + n : nullptr;
+    L.w.long_count = L.zeroed ? L.zeroed + 2 * n : nullptr;
+    L.w.long_rows = cv.take<int32_t>((size_t)n);
+    L.w.scan_part = cv.take<int64_t>(conn_scan_blocks(n));
+    L.indptr_tmp = cv.take<int64_t>((size_t)n + 1);
+    if (bytes) *bytes = cv.used;
+    return L;
+}
+
+rsc_status check_conn_args(const int32_t *idx, const float *dist, int64_t n, int32_t k) {
+    if (!idx || !dist) return fail(RSC_ERR_INVALID_ARG, "idx/dist is NULL");
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(RSC_ERR_INVALID_ARG, "n=%lld out of [1, 2^31)", (long long)n);
+    if (k < 1 || k > 256) return fail(RSC_ERR_INVALID_ARG, "k=%d out of [1, 256]", k);
+    return RSC_OK;
+}
+
+rsc_status conn_count_phase(const int32_t *idx, const float *dist, int64_t n, int32_t k,
+                            int64_t *indptr, float *rho, float *sigma, ConnLayout &L,
+                            cudaStream_t st) {
+    if (rho) L.w.rho = rho;
+    if (sigma) L.w.sigma = sigma;
+    RSC_CUDA_TRY(cudaMemsetAsync(L.w.status, 0, sizeof(unsigned int), st));
+    RSC_CUDA_TRY(cudaMemsetAsync(L.zeroed, 0, sizeof(int32_t) * (2 * n + 1), st));
+    RSC_CUDA_TRY(launch_conn_count(idx, dist, n, k, indptr, L.w, st));
+    return RSC_OK;
+}
+
+}  // namespace
+}  // namespace rsc
+
+using namespace rsc;
+
+extern "C" {
+
+const char *rsc_version(void) { return "rsc-gb300 0.1 (sm_103a)"; }
+
+const char *rsc_last_error(void) { return g_err; }
+
+rsc_status rsc_workspace_status(void *workspace, void *stream) {
+    if (!workspace) return fail(RSC_ERR_INVALID_ARG, "workspace is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int word = 0;
+    RSC_CUDA_TRY(cudaMemcpyAsync(&word, workspace, sizeof(word), cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    RSC_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(word), st));
+    if (word != 0) return fail((rsc_status)word, "a kernel recorded status %u", word);
+    return RSC_OK;
+}
+
+rsc_status rsc_knn_workspace_size(int64_t n, int32_t d, int32_t k, int32_t metric,
+                                  const rsc_knn_opts *opts, size_t *bytes) {
+    if (!bytes) return fail(RSC_ERR_INVALID_ARG, "bytes is NULL");
+    KnnPlan p;
+    rsc_status s = plan_knn(n, d, k, metric, opts, &p);
+    if (s != RSC_OK) return s;
+    carve_knn(nullptr, n, p, bytes);
+    return RSC_OK;
+}
+
+rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metric, int32_t *idx,
+                   float *dist, const rsc_knn_opts *opts, void *workspace, size_t workspace_bytes) {
+    if (!X || !idx || !dist) return fail(RSC_ERR_INVALID_ARG, "X/idx/dist is NULL");
+    KnnPlan p;
+    rsc_status s = plan_knn(n, d, k, metric, opts, &p);
+    if (s != RSC_OK) return s;
+    size_t need = 0;
+    carve_knn(nullptr, n, p, &need);
+    if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
+    KnnLayout L = carve_knn(workspace, n, p, nullptr);
+    cudaStream_t st = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+    cudaEvent_t *ev = opts ? static_cast<cudaEvent_t *>(opts->phase_events) : nullptr;
+    RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
+    if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[0], st));
+    RSC_CUDA_TRY(launch_prep_fp32(X, n, d, p.DP, metric, L.Y, L.ny, L.prep_scratch, st));
+    if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
+    RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
+    if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[2], st));
+    // exact re-rank reads the caller's rows (Euclidean) or the normalised rows (cosine)
+    const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
+    const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC, p.splits, k, idx, dist, st));
+    if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[3], st));
+    return RSC_OK;
+}
+
+int64_t rsc_connectivities_max_nnz(int64_t n, int32_t k) {
+    if (n < 1 || k < 1) return 0;
+    return 2 * n * (int64_t)(k - 1);
+}
+
+rsc_status rsc_connectivities_workspace_size(int64_t n, int32_t k, size_t *bytes) {
+    if (!bytes) return fail(RSC_ERR_INVALID_ARG, "bytes is NULL");
+    if (n < 1 || k < 1 || k > 256) return fail(RSC_ERR_INVALID_ARG, "bad n/k");
+    carve_conn(nullptr, n, k, bytes);
+    return RSC_OK;
+}
+
+rsc_status rsc_connectivities(const int32_t *idx, const float *dist, int64_t n, int32_t k,
+                              int64_t *indptr, int32_t *indices, float *data, int64_t nnz_capacity,
+                              float *rho, float *sigma, void *workspace, size_t workspace_bytes,
+                              void *stream) {
+    rsc_status s = check_conn_args(idx, dist, n, k);
+    if (s != RSC_OK) return s;
+    if (!indptr) return fail(RSC_ERR_INVALID_ARG, "indptr is NULL");
+    if (nnz_capacity < 0) return fail(RSC_ERR_INVALID_ARG, "negative capacity");
+    if (nnz_capacity > 0 && (!indices || !data)) return fail(RSC_ERR_INVALID_ARG, "indices/data is NULL");
+    size_t need = 0;
+    carve_conn(nullptr, n, k, &need);
+    if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
+    ConnLayout L = carve_conn(workspace, n, k, nullptr);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((s = conn_count_phase(idx, dist, n, k, indptr, rho, sigma, L, st)) != RSC_OK) return s;
+    if (nnz_capacity < rsc_connectivities_max_nnz(n, k)) {
+        int64_t nnz = 0;
+        RSC_CUDA_TRY(cudaMemcpyAsync(&nnz, indptr + n, sizeof(nnz), cudaMemcpyDeviceToHost, st));
+        RSC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (nnz > nnz_capacity)
+            return fail(RSC_ERR_CAPACITY, "nnz=%lld exceeds capacity %lld", (long long)nnz, (long long)nnz_capacity);
+    }
+    RSC_CUDA_TRY(launch_conn_fill(n, k, indptr, indices, data, nnz_capacity, L.w, st));
+    return RSC_OK;
+}
+
+rsc_status rsc_connectivities_nnz(const int32_t *idx, const float *dist, int64_t n, int32_t k,
+                                  int64_t *nnz, void *workspace, size_t workspace_bytes,
+                                  void *stream) {
+    rsc_status s = check_conn_args(idx, dist, n, k);
+    if (s != RSC_OK) return s;
+    if (!nnz) return fail(RSC_ERR_INVALID_ARG, "nnz is NULL");
+    size_t need = 0;
+    carve_conn(nullptr, n, k, &need);
+    if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
+    ConnLayout L = carve_conn(workspace, n, k, nullptr);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((s = conn_count_phase(idx, dist, n, k, L.indptr_tmp, nullptr, nullptr, L, st)) != RSC_OK) return s;
+    RSC_CUDA_TRY(cudaMemcpyAsync(nnz, L.indptr_tmp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    return RSC_OK;
+}
+
+}  // extern "C"

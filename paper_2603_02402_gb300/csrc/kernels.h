@@ -1,0 +1,63 @@
+// Launchers of the library's kernels (internal; the public ABI is rsc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsc {
+
+// ---- prep.cu --------------------------------------------------------------
+// Y [n, DP] float32: the rows of X minus the column means (Euclidean) or
+// X / |X| (cosine), zero padded to DP columns; for cosine, column d holds 1
+// for an all-zero row.  ny [n]: sum_t Y_t^2 in FP32 (Euclidean) or 0 (cosine).
+// scratch: prep_scratch_floats() floats.
+size_t prep_scratch_floats();
+cudaError_t launch_prep_fp32(const float *X, int64_t n, int d, int DP, int metric,
+                             float *Y, float *ny, float *scratch, cudaStream_t st);
+
+// ---- knn_simt.cu ----------------------------------------------------------
+// FP32 SIMT candidate search: for every query row and database split s,
+// cand[(s * n + q) * KC + c] = the KC columns with the smallest
+// ny_j - 2 * Y_q . Y_j inside the split (ties keep the earlier column).
+bool knn_simt_supported(int DP, int KC);
+cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, int KC,
+                            int splits, int64_t split_len, int32_t *cand, cudaStream_t st);
+
+// ---- rerank.cu ------------------------------------------------------------
+// Exact re-rank: every candidate of query q (splits * KC ids, split s at
+// cand[(s * n + q) * KC]) is re-scored by direct difference in FP32 over the
+// rows R (row stride rs: the caller's X for Euclidean, the normalised Y for
+// cosine, whose column d is the zero-row flag), sorted by (distance, id) and
+// the first k written to idx/dist (Euclidean sqrt, cosine d^2 / 2 with the
+// zero-row convention).  splits * KC <= 1024.
+cudaError_t launch_rerank(const float *R, int64_t rs, int64_t n, int d, int metric,
+                          const int32_t *cand, int KC, int splits, int k, int32_t *idx,
+                          float *dist, cudaStream_t st);
+
+// ---- connectivities.cu -------------------------------------------------------
+struct ConnWork {
+    float *partials;     // [kMeanBlocks]
+    float *mean_all;     // [1]
+    float *rho, *sigma;  // [n]
+    int32_t *scol;       // [n, k] row's columns, ascending (INT32_MAX pads)
+    float *sw;           // [n, k] directed weights in scol order
+    float *gv;           // [n, k] union value of each own entry (negative: also
+                         //        emit the transposed entry)
+    int32_t *own_cnt;    // [n]
+    int32_t *in_cnt;     // [n]   (zeroed by the launcher)
+    int32_t *cursor;     // [n]   (zeroed by the launcher)
+    int32_t *long_rows;  // [n]
+    int32_t *long_count; // [1]   (zeroed by the launcher)
+    int64_t *scan_part;  // [scan blocks]
+    unsigned int *status;
+};
+constexpr int kMeanBlocks = 512;
+size_t conn_scan_blocks(int64_t n);
+// Phases: rho/sigma/weights + in-degree counts + row pointers.
+cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, int k,
+                              int64_t *indptr, const ConnWork &w, cudaStream_t st);
+// Phases: CSR fill and per-row column sort.
+cudaError_t launch_conn_fill(int64_t n, int k, const int64_t *indptr, int32_t *indices,
+                             float *data, int64_t cap, const ConnWork &w, cudaStream_t st);
+
+}  // namespace rsc

@@ -1,0 +1,122 @@
+// Prep pass: one read of X, one write of the padded FP32 operand rows.
+//
+// Euclidean rows are centred on the column means first: distances do not
+// change, but |y|^2 shrinks, and with it the cancellation in the expansion
+// form |y|^2 - 2 x.y that the candidate search ranks by.  Cosine distance
+// (paper, Methods, "Custom GPU kernels": 1 - x.y/(|x||y|)) is computed on rows
+// normalised here, so later steps work with unit vectors:
+// 1 - cos = |x^ - y^|^2 / 2.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsc {
+
+namespace {
+
+constexpr int kRowsPerWarp = 32;
+constexpr int kWarps = 4;
+constexpr int kColBlocks = 256;
+
+// Column sums, deterministic: block b owns a fixed row range; thread (g, c)
+// adds column c of rows g, g + 4, ... with Kahan compensation.
+__global__ void __launch_bounds__(256)
+colsum_partials_kernel(const float *__restrict__ X, int64_t n, int d, float *__restrict__ part) {
+    __shared__ float red[4][64];
+    const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
+    const int64_t chunk = ceil_div(n, gridDim.x);
+    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+    float s = 0.f, comp = 0.f;
+    if (c < d) {
+        for (int64_t r = r0 + g; r < r1; r += 4) {
+            const float y = X[r * d + c] - comp;
+            const float t = s + y;
+            comp = (t - s) - y;
+            s = t;
+        }
+    }
+    red[g][c] = s - comp;
+    __syncthreads();
+    if (g == 0 && c < d) part[(int64_t)blockIdx.x * 64 + c] = (red[0][c] + red[1][c]) + (red[2][c] + red[3][c]);
+}
+
+__global__ void colmean_final_kernel(const float *__restrict__ part, int nb, int64_t n, int d,
+                                     float *__restrict__ mu) {
+    const int c = threadIdx.x;
+    if (c >= d) return;
+    float s = 0.f, comp = 0.f;
+    for (int b = 0; b < nb; ++b) {
+        const float y = part[b * 64 + c] - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
+    mu[c] = (float)((double)(s - comp) / (double)n);
+}
+
+// A warp stages 32 consecutive rows (contiguous in X) through shared memory so
+// that both the read of X and the write of Y are coalesced; lane r then
+// handles row r on its own.
+__global__ void __launch_bounds__(kWarps * 32)
+prep_fp32_kernel(const float *__restrict__ X, int64_t n, int d, int DP, int metric,
+                 const float *__restrict__ mu, float *__restrict__ Y, float *__restrict__ ny) {
+    extern __shared__ float stage[];   // [kWarps][32][DP + 1]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ld = DP + 1;             // odd stride: lane-per-row access is conflict free
+    float *s = stage + (size_t)warp * kRowsPerWarp * ld;
+    const int64_t row0 = ((int64_t)blockIdx.x * kWarps + warp) * kRowsPerWarp;
+    if (row0 >= n) return;
+    const int rows = (n - row0 < kRowsPerWarp) ? (int)(n - row0) : kRowsPerWarp;
+
+    const float *src = X + row0 * d;
+    for (int e = lane; e < rows * d; e += 32) s[(e / d) * ld + (e % d)] = src[e];
+    __syncwarp();
+
+    if (lane < rows) {
+        float *r = s + lane * ld;
+        float sum = 0.f;
+        for (int t = 0; t < d; ++t) sum = fmaf(r[t], r[t], sum);
+        if (metric == RSC_COSINE) {
+            if (sum > 0.f) {
+                const float nrm = sqrtf(sum);
+                for (int t = 0; t < d; ++t) r[t] = r[t] / nrm;
+            }
+            for (int t = d; t < DP; ++t) r[t] = 0.f;
+            r[d] = (sum > 0.f) ? 0.f : 1.f;   // all-zero row flag
+            ny[row0 + lane] = 0.f;
+        } else {
+            float cs = 0.f;
+            for (int t = 0; t < d; ++t) {
+                r[t] = r[t] - mu[t];
+                cs = fmaf(r[t], r[t], cs);
+            }
+            for (int t = d; t < DP; ++t) r[t] = 0.f;
+            ny[row0 + lane] = cs;
+        }
+    }
+    __syncwarp();
+
+    float *dst = Y + row0 * DP;
+    for (int e = lane; e < rows * DP; e += 32) dst[e] = s[(e / DP) * ld + (e % DP)];
+}
+
+}  // namespace
+
+size_t prep_scratch_floats() { return (size_t)kColBlocks * 64 + 64; }
+
+cudaError_t launch_prep_fp32(const float *X, int64_t n, int d, int DP, int metric,
+                             float *Y, float *ny, float *scratch, cudaStream_t st) {
+    float *mu = scratch + (size_t)kColBlocks * 64;
+    if (metric == RSC_EUCLIDEAN) {
+        colsum_partials_kernel<<<kColBlocks, 256, 0, st>>>(X, n, d, scratch);
+        colmean_final_kernel<<<1, 64, 0, st>>>(scratch, kColBlocks, n, d, mu);
+    }
+    const int64_t rows_per_block = (int64_t)kWarps * kRowsPerWarp;
+    const int64_t blocks = ceil_div(n, rows_per_block);
+    const size_t smem = sizeof(float) * kWarps * kRowsPerWarp * (DP + 1);
+    prep_fp32_kernel<<<(unsigned)blocks, kWarps * 32, smem, st>>>(X, n, d, DP, metric, mu, Y, ny);
+    return cudaGetLastError();
+}
+
+}  // namespace rsc

@@ -1,0 +1,194 @@
+"""Thin Python binding of the C ABI in include/rsc.h (ctypes + torch tensors).
+
+Argument marshalling only: every step of the neighbourhood graph runs in the
+CUDA library (librsc.so).  torch provides device memory and streams.  The
+functions carry the C names; outputs and the workspace are allocated here
+with torch and handed to the library as raw device pointers.
+
+If the library has not been built, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "librsc.so")
+
+RSC_OK, RSC_ERR_INVALID_ARG, RSC_ERR_CUDA, RSC_ERR_WORKSPACE, RSC_ERR_TIMEOUT, \
+    RSC_ERR_UNSUPPORTED, RSC_ERR_CAPACITY = range(7)
+RSC_EUCLIDEAN, RSC_COSINE = 0, 1
+RSC_FP32, RSC_BF16 = 0, 1
+
+_METRICS = {"euclidean": RSC_EUCLIDEAN, "cosine": RSC_COSINE}
+_PRECISIONS = {"fp32": RSC_FP32, "bf16": RSC_BF16}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RscError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"rsc status {status}: {message}")
+        self.status = status
+
+
+class rsc_knn_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("db_splits", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("phase_events", ctypes.c_void_p)]
+
+
+# name -> (restype, argtypes); the full exported surface of include/rsc.h
+_vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+SIGNATURES = {
+    "rsc_version": (ctypes.c_char_p, []),
+    "rsc_last_error": (ctypes.c_char_p, []),
+    "rsc_workspace_status": (_i32, [_vp, _vp]),
+    "rsc_knn_workspace_size": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(_sz)]),
+    "rsc_knn": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(rsc_knn_opts), _vp, _sz]),
+    "rsc_connectivities_workspace_size": (_i32, [_i64, _i32, ctypes.POINTER(_sz)]),
+    "rsc_connectivities_max_nnz": (_i64, [_i64, _i32]),
+    "rsc_connectivities": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "rsc_connectivities_nnz": (_i32, [_vp, _vp, _i64, _i32, ctypes.POINTER(_i64), _vp, _sz, _vp]),
+}
+
+
+def lib():
+    """Load librsc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                                   "(the CUDA library is required; there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != RSC_OK:
+        raise RscError(status, lib().rsc_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _workspace(nbytes: int, device, workspace=None):
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        return workspace
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def rsc_version() -> str:
+    return lib().rsc_version().decode()
+
+
+def rsc_workspace_status(workspace: torch.Tensor, stream=None) -> int:
+    """Status word recorded by kernels in `workspace` (synchronises)."""
+    return int(lib().rsc_workspace_status(_ptr(workspace), _stream(stream)))
+
+
+def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_events=None) -> rsc_knn_opts:
+    """Option struct; `phase_events` is a ctypes array of 4 raw cudaEvent_t."""
+    o = rsc_knn_opts()
+    o.phase_events = ctypes.cast(phase_events, ctypes.c_void_p).value if phase_events is not None else None
+    o.precision = _PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.candidates = int(candidates)
+    o.db_splits = int(db_splits)
+    o.stream = _stream(stream).value
+    return o
+
+
+def rsc_knn_workspace_size(n, d, k, metric="euclidean", precision="fp32", candidates=0, db_splits=0) -> int:
+    o = knn_opts(precision, candidates, db_splits, stream=None) if torch.cuda.is_available() else rsc_knn_opts(
+        _PRECISIONS[precision], candidates, db_splits, 0, None, None)
+    out = _sz(0)
+    _check(lib().rsc_knn_workspace_size(n, d, k, _METRICS.get(metric, metric), ctypes.byref(o), ctypes.byref(out)))
+    return int(out.value)
+
+
+def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candidates=0, db_splits=0,
+            stream=None, workspace=None, out=None, phase_events=None):
+    """Exact kNN of every row of X (float32 [n, d] on the GPU).
+
+    Returns (idx int32 [n, k], dist float32 [n, k]) on X's device.
+    """
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()):
+        raise ValueError("X must be a contiguous float32 [n, d] CUDA tensor")
+    n, d = X.shape
+    m = _METRICS[metric] if isinstance(metric, str) else int(metric)
+    o = knn_opts(precision, candidates, db_splits, stream, phase_events)
+    need = _sz(0)
+    _check(lib().rsc_knn_workspace_size(n, d, k, m, ctypes.byref(o), ctypes.byref(need)))
+    ws = _workspace(need.value, X.device, workspace)
+    if out is None:
+        idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
+        dist = torch.empty((n, k), dtype=torch.float32, device=X.device)
+    else:
+        idx, dist = out
+    _check(lib().rsc_knn(_ptr(X), n, d, k, m, _ptr(idx), _ptr(dist), ctypes.byref(o), _ptr(ws),
+                         ws.numel()))
+    return idx, dist
+
+
+def rsc_connectivities_workspace_size(n: int, k: int) -> int:
+    out = _sz(0)
+    _check(lib().rsc_connectivities_workspace_size(n, k, ctypes.byref(out)))
+    return int(out.value)
+
+
+def rsc_connectivities_max_nnz(n: int, k: int) -> int:
+    return int(lib().rsc_connectivities_max_nnz(n, k))
+
+
+def rsc_connectivities(idx: torch.Tensor, dist: torch.Tensor, nnz_capacity=None, stream=None,
+                       workspace=None, out=None, with_rho_sigma=True):
+    """Fuzzy connectivities CSR of a kNN graph.
+
+    Returns (indptr int64 [n+1], indices int32 [cap], data float32 [cap], rho, sigma)
+    with the first indptr[n] entries of indices/data valid.
+    """
+    if not (idx.is_cuda and dist.is_cuda and idx.dtype == torch.int32 and dist.dtype == torch.float32):
+        raise ValueError("idx int32 / dist float32 CUDA tensors expected")
+    idx, dist = idx.contiguous(), dist.contiguous()
+    n, k = idx.shape
+    cap = rsc_connectivities_max_nnz(n, k) if nnz_capacity is None else int(nnz_capacity)
+    ws = _workspace(rsc_connectivities_workspace_size(n, k), idx.device, workspace)
+    if out is None:
+        indptr = torch.empty(n + 1, dtype=torch.int64, device=idx.device)
+        indices = torch.empty(max(cap, 1), dtype=torch.int32, device=idx.device)
+        data = torch.empty(max(cap, 1), dtype=torch.float32, device=idx.device)
+        rho = torch.empty(n, dtype=torch.float32, device=idx.device) if with_rho_sigma else None
+        sigma = torch.empty(n, dtype=torch.float32, device=idx.device) if with_rho_sigma else None
+    else:
+        indptr, indices, data, rho, sigma = out
+    _check(lib().rsc_connectivities(_ptr(idx), _ptr(dist), n, k, _ptr(indptr), _ptr(indices), _ptr(data), cap,
+                                    _ptr(rho), _ptr(sigma), _ptr(ws), ws.numel(), _stream(stream)))
+    return indptr, indices, data, rho, sigma
+
+
+def rsc_connectivities_nnz(idx: torch.Tensor, dist: torch.Tensor, stream=None, workspace=None) -> int:
+    n, k = idx.shape
+    ws = _workspace(rsc_connectivities_workspace_size(n, k), idx.device, workspace)
+    out = _i64(0)
+    _check(lib().rsc_connectivities_nnz(_ptr(idx), _ptr(dist), n, k, ctypes.byref(out), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
+    return int(out.value)

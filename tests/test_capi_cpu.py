@@ -1,0 +1,102 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads,
+exports every function include/rsc.h declares, and rejects bad arguments on
+the host before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2603_02402_gb300 import build as build_lib
+from paper_2603_02402_gb300 import rsc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build_lib()
+    return rsc.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rsc_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    declared = _declared()
+    assert "rsc_knn" in declared and "rsc_connectivities" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(rsc.SIGNATURES) == declared
+
+
+def test_version(L):
+    assert "sm_103a" in rsc.rsc_version()
+
+
+def test_workspace_size_is_host_only_and_grows(L):
+    a = rsc.rsc_knn_workspace_size(10_000, 50, 15)
+    b = rsc.rsc_knn_workspace_size(20_000, 50, 15)
+    assert 0 < a < b
+    c = rsc.rsc_connectivities_workspace_size(10_000, 15)
+    assert c > 10_000 * 15 * 12
+    assert rsc.rsc_connectivities_max_nnz(10, 15) == 2 * 10 * 14
+
+
+@pytest.mark.parametrize("args,code", [
+    ((0, 50, 15, 0), rsc.RSC_ERR_INVALID_ARG),        # n = 0
+    ((100, 0, 15, 0), rsc.RSC_ERR_INVALID_ARG),       # d = 0
+    ((100, 65, 15, 0), rsc.RSC_ERR_INVALID_ARG),      # d too large
+    ((100, 64, 15, 1), rsc.RSC_ERR_INVALID_ARG),      # cosine needs d <= 63
+    ((100, 50, 0, 0), rsc.RSC_ERR_INVALID_ARG),       # k = 0
+    ((10, 50, 11, 0), rsc.RSC_ERR_INVALID_ARG),       # k > n
+    ((100, 50, 65, 0), rsc.RSC_ERR_INVALID_ARG),      # k > 64
+    ((100, 50, 15, 7), rsc.RSC_ERR_INVALID_ARG),      # metric
+])
+def test_knn_argument_errors(L, args, code):
+    n, d, k, m = args
+    out = ctypes.c_size_t(0)
+    o = rsc.rsc_knn_opts(0, 0, 0, 0, None, None)
+    st = L.rsc_knn_workspace_size(n, d, k, m, ctypes.byref(o), ctypes.byref(out))
+    assert st == code
+    assert L.rsc_last_error()
+
+
+def test_knn_rejects_missing_workspace_before_launch(L):
+    o = rsc.rsc_knn_opts(0, 0, 0, 0, None, None)
+    fake = ctypes.c_void_p(256)   # never dereferenced: the workspace check fails first
+    st = L.rsc_knn(fake, 1000, 50, 15, 0, fake, fake, ctypes.byref(o), None, 0)
+    assert st == rsc.RSC_ERR_WORKSPACE
+    st = L.rsc_knn(fake, 1000, 50, 15, 0, fake, fake, ctypes.byref(o), ctypes.c_void_p(512), 16)
+    assert st == rsc.RSC_ERR_WORKSPACE
+    st = L.rsc_knn(fake, 1000, 50, 15, 0, fake, fake, ctypes.byref(o), ctypes.c_void_p(100), 1 << 40)
+    assert st == rsc.RSC_ERR_INVALID_ARG   # misaligned
+
+
+def test_candidate_option_errors(L):
+    out = ctypes.c_size_t(0)
+    o = rsc.rsc_knn_opts(0, 10, 0, 0, None, None)      # fewer candidates than k
+    assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.rsc_knn_opts(0, 80, 0, 0, None, None)      # above the widest list
+    assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.rsc_knn_opts(9, 0, 0, 0, None, None)       # unknown precision
+    assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.rsc_knn_opts(0, 0, 0, 1, None, None)       # reserved field set
+    assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+
+
+def test_connectivities_argument_errors(L):
+    fake = ctypes.c_void_p(256)
+    assert L.rsc_connectivities(None, fake, 10, 5, fake, fake, fake, 100, None, None, fake, 1 << 30, None) \
+        == rsc.RSC_ERR_INVALID_ARG
+    assert L.rsc_connectivities(fake, fake, 10, 0, fake, fake, fake, 100, None, None, fake, 1 << 30, None) \
+        == rsc.RSC_ERR_INVALID_ARG
+    assert L.rsc_connectivities(fake, fake, 10, 5, fake, fake, fake, 100, None, None, None, 0, None) \
+        == rsc.RSC_ERR_WORKSPACE
