@@ -51,6 +51,7 @@ constexpr int kSupportedKC[] = {16, 32, 64};
 
 struct KnnPlan {
     int precision = RSC_FP32;
+    int d = 0, metric = 0;
     int DP = 0;         // padded FP32 row length
     int KC = 0;         // candidates per query per split
     int splits = 1;     // database splits
@@ -62,6 +63,7 @@ struct KnnLayout {
     float *Y;
     float *ny;
     float *prep_scratch;
+    void *Qb, *Db;       // BF16 operands (tensor-core path only)
     int32_t *cand;
 };
 
@@ -79,7 +81,8 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     if (o->candidates < 0 || o->db_splits < 0) return fail(RSC_ERR_INVALID_ARG, "negative option");
     if (o->reserved != 0) return fail(RSC_ERR_INVALID_ARG, "reserved option field must be 0");
     p->precision = o->precision;
-    if (p->precision == RSC_BF16) return fail(RSC_ERR_UNSUPPORTED, "BF16 candidate search not built yet");
+    p->d = d;
+    p->metric = metric;
     p->DP = ((d + (metric == RSC_COSINE ? 1 : 0) + 7) / 8) * 8;
     int want = o->candidates;
     if (want == 0) want = (p->precision == RSC_FP32) ? k + 8 : 2 * k;
@@ -92,14 +95,23 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     for (int c : kSupportedKC)
         if (c >= want) { p->KC = c; break; }
     // database splits: enough CTAs to fill the GPU when there are few queries
-    const int64_t qblocks = ceil_div(n, 128);
+    const bool tc = p->precision == RSC_BF16;
+    const int64_t qrows = tc ? 256 : 128;            // query rows per CTA work unit
+    const int64_t target = tc ? 152 : 1024;          // work units wanted (persistent CTAs / blocks)
+    const int64_t align = tc ? knn_tc_split_align() : 32;
+    const int64_t qblocks = ceil_div(n, qrows);
     int splits = o->db_splits;
-    if (splits == 0) splits = (int)std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(1024, qblocks)));
+    if (splits == 0) splits = (int)std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(target, qblocks)));
     while (splits > 1 && splits * p->KC > 1024) --splits;
     if (splits * p->KC > 1024) return fail(RSC_ERR_INVALID_ARG, "db_splits * candidates above 1024");
-    p->split_len = ((ceil_div(n, splits) + 31) / 32) * 32;
+    p->split_len = ceil_div(ceil_div(n, splits), align) * align;
     p->splits = (int)ceil_div(n, p->split_len);
-    if (!knn_simt_supported(p->DP, p->KC)) return fail(RSC_ERR_UNSUPPORTED, "no SIMT kernel for DP=%d KC=%d", p->DP, p->KC);
+    if (tc) {
+        if (!knn_tc_supported(d, metric, p->KC))
+            return fail(RSC_ERR_UNSUPPORTED, "no tensor-core kernel for d=%d KC=%d", d, p->KC);
+    } else if (!knn_simt_supported(p->DP, p->KC)) {
+        return fail(RSC_ERR_UNSUPPORTED, "no SIMT kernel for DP=%d KC=%d", p->DP, p->KC);
+    }
     return RSC_OK;
 }
 
@@ -110,6 +122,11 @@ KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
     L.Y = cv.take<float>((size_t)n * p.DP);
     L.ny = cv.take<float>((size_t)n);
     L.prep_scratch = cv.take<float>(prep_scratch_floats());
+    L.Qb = L.Db = nullptr;
+    if (p.precision == RSC_BF16) {
+        L.Qb = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
+        L.Db = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
+    }
     L.cand = cv.take<int32_t>((size_t)p.splits * n * p.KC);
     if (bytes) *bytes = cv.used;
     return L;
@@ -218,8 +235,14 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[0], st));
     RSC_CUDA_TRY(launch_prep_fp32(X, n, d, p.DP, metric, L.Y, L.ny, L.prep_scratch, st));
-    if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
-    RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
+    if (p.precision == RSC_BF16) {
+        RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.Qb, L.Db, st));
+        if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
+        RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, p.KC, p.splits, p.split_len, L.cand, L.status, st));
+    } else {
+        if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
+        RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
+    }
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[2], st));
     // exact re-rank reads the caller's rows (Euclidean) or the normalised rows (cosine)
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;

@@ -23,6 +23,19 @@ bool knn_simt_supported(int DP, int KC);
 cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, int KC,
                             int splits, int64_t split_len, int32_t *cand, cudaStream_t st);
 
+// ---- knn_tc.cu ------------------------------------------------------------
+// BF16 tensor-core candidate search.  Qb/Db: [n, 64 * tc_kb(d, metric)] bf16
+// operand rows built by launch_prep_bf16 from the FP32 prep rows Y; cand as
+// for the SIMT search.  Database splits must be multiples of
+// knn_tc_split_align() rows.  Bounded waits record RSC_ERR_TIMEOUT in *status.
+int tc_kb(int d, int metric);
+bool knn_tc_supported(int d, int metric, int KC);
+int64_t knn_tc_split_align();
+cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, void *Qb, void *Db,
+                             cudaStream_t st);
+cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, int KC, int splits,
+                          int64_t split_len, int32_t *cand, unsigned int *status, cudaStream_t st);
+
 // ---- rerank.cu ------------------------------------------------------------
 // Exact re-rank: every candidate of query q (splits * KC ids, split s at
 // cand[(s * n + q) * KC]) is re-scored by direct difference in FP32 over the

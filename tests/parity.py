@@ -103,8 +103,12 @@ def check_csr_structure(indptr, indices, data, n):
     return ind, dat
 
 
-def compare_graphs(gpu, ref, n, exclude_rows=(), atol=W_ABS):
-    """Dense-on-union comparison; returns (max error, entries compared)."""
+def compare_graphs(gpu, ref, n, exclude_rows=(), atol=W_ABS, row_slack=None):
+    """Dense-on-union comparison; returns (max error, entries compared).
+
+    `row_slack[i]` (optional) widens the tolerance of entries in row or
+    column i by that amount (first-order effect of input perturbations).
+    """
     G = dense_from_csr(*gpu, n)
     R = dense_from_csr(*ref, n)
     ex = set(int(r) for r in exclude_rows)
@@ -113,13 +117,28 @@ def compare_graphs(gpu, ref, n, exclude_rows=(), atol=W_ABS):
         if key[0] in ex or key[1] in ex:
             continue
         e = abs(G.get(key, 0.0) - R.get(key, 0.0))
+        tol = atol if row_slack is None else atol + row_slack[key[0]] + row_slack[key[1]]
         worst = max(worst, e)
         cnt += 1
-        assert e <= atol, f"entry {key}: gpu {G.get(key)} oracle {R.get(key)}"
+        assert e <= tol, f"entry {key}: gpu {G.get(key)} oracle {R.get(key)} tol {tol}"
     return worst, cnt
+
+
+def distance_slack(ref, dist, rel_err):
+    """Per-row first-order change of the weights when every distance moves by
+    up to rel_err relative: |dw| <= w * (|dd| + |drho|) / sigma, doubled for
+    the induced change of sigma.  Used when the two sides' distances are not
+    the same float32 values (end-to-end comparisons)."""
+    w, rho, sig = ref["weights"], ref["rho"], ref["sigma"]
+    sens = w * (np.abs(dist) + rho[:, None]) / np.maximum(sig, 1e-30)[:, None]
+    return 2.0 * rel_err * sens.max(axis=1)
 
 
 def near_branch_rows(ref, margin=1e-6):
     """Rows whose FP64 bisection came within `margin` of flipping its stop
-    test; FP32 may legitimately stop one step earlier or later there."""
+    test (|psum - log2 k| within margin of 1e-5 at some step).  The FP32
+    psum (compensated sum of 2-ulp exps) is accurate to about 1e-6, so FP32
+    may stop one step earlier or later on exactly these rows; about 13% of
+    rows of a Gaussian-mixture graph qualify, because the last step's error
+    is spread over [0, 1e-5).  They are compared at 5e-5 instead of 1e-5."""
     return np.nonzero(ref["stop_margin"] < margin)[0]

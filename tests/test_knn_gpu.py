@@ -31,6 +31,8 @@ def run_knn(rsc, X, k, metric="euclidean", precision="fp32", **kw):
 
 
 PRECISIONS = ["fp32", "bf16"]
+# BF16 candidate search + exact re-rank targets recall@k >= 0.999; FP32 is exact
+MISS = {"fp32": 0.0, "bf16": 1e-3}
 
 
 def _maybe(rsc, fn):
@@ -48,7 +50,7 @@ def test_10k_mixture_full_parity(rsc, precision):
     X = synth.mixture(10_000, 50, n_comp=20, seed=0)
     oi, od, on = oracle.knn(X, 15)
     gi, gd = _maybe(rsc, lambda: run_knn(rsc, X, 15, precision=precision))
-    stats = check_knn(X, gi, gd, oi, od, on)
+    stats = check_knn(X, gi, gd, oi, od, on, allow_miss=MISS[precision])
     assert stats["id_exact"] > 0.999
 
 
@@ -62,7 +64,7 @@ def test_shapes_and_ragged_tails(rsc, precision, n, d, k):
     X = synth.mixture(n, d, n_comp=5, seed=n + d)
     oi, od, on = oracle.knn(X, k)
     gi, gd = _maybe(rsc, lambda: run_knn(rsc, X, k, precision=precision))
-    check_knn(X, gi, gd, oi, od, on)
+    check_knn(X, gi, gd, oi, od, on, allow_miss=MISS[precision])
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
@@ -71,7 +73,7 @@ def test_database_splits(rsc, precision, splits):
     X = synth.mixture(3000, 50, n_comp=10, seed=3)
     oi, od, on = oracle.knn(X, 15)
     gi, gd = _maybe(rsc, lambda: run_knn(rsc, X, 15, precision=precision, db_splits=splits))
-    check_knn(X, gi, gd, oi, od, on)
+    check_knn(X, gi, gd, oi, od, on, allow_miss=MISS[precision])
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
@@ -80,7 +82,7 @@ def test_cosine_with_zero_rows(rsc, precision):
     X[[7, 100, 4999]] = 0.0          # all-zero rows: distance 0 between them, 1 to others
     oi, od, on = oracle.knn(X, 30, metric=oracle.COSINE)
     gi, gd = _maybe(rsc, lambda: run_knn(rsc, X, 30, metric="cosine", precision=precision))
-    check_knn(X, gi, gd, oi, od, on, metric="cosine")
+    check_knn(X, gi, gd, oi, od, on, metric="cosine", allow_miss=MISS[precision])
     assert gi[7].tolist()[:3] == [7, 100, 4999]
 
 
@@ -96,7 +98,7 @@ def test_exact_ties_and_duplicates_integer_grid(rsc, precision):
         np.testing.assert_array_equal(gi, oi)
         np.testing.assert_array_equal(gd, od.astype(np.float32))
     else:
-        check_knn(X, gi, gd, oi, od, on)
+        check_knn(X, gi, gd, oi, od, on, allow_miss=MISS[precision])
 
 
 def test_large_offset_is_translation_invariant(rsc):
@@ -108,10 +110,11 @@ def test_large_offset_is_translation_invariant(rsc):
     check_knn(X, gi, gd, oi, od, on)
 
 
-def test_query_sample_of_large_input(rsc):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_query_sample_of_large_input(rsc, precision):
     # 200,000 cells: compare a seeded sample of rows with the oracle
     X = synth.mixture(200_000, 50, n_comp=100, seed=1)
     q = synth.query_sample(len(X), 200, seed=1)
     oi, od, on = oracle.knn(X, 15, queries=q)
-    gi, gd = run_knn(rsc, X, 15)
-    check_knn(X, gi[q], gd[q], oi, od, on, rows=q)
+    gi, gd = _maybe(rsc, lambda: run_knn(rsc, X, 15, precision=precision))
+    check_knn(X, gi[q], gd[q], oi, od, on, rows=q, allow_miss=MISS[precision])
