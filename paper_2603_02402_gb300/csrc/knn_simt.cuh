@@ -23,7 +23,7 @@ namespace simt {
 constexpr int kThreads = 128;
 constexpr int kTileRows = 32;   // database rows per shared-memory tile
 constexpr int kChunk = 16;      // values per threshold test
-constexpr int kCap = 24;        // candidate buffer entries per thread
+constexpr int kCap = 24;        // candidate buffer entries per thread (>= 16)
 
 template <int DP, int KC>
 __global__ void __launch_bounds__(kThreads)
@@ -79,7 +79,7 @@ knn_simt_kernel(const float *__restrict__ Y, const float *__restrict__ ny, int64
     __syncthreads();
     for (int64_t j0 = j_begin; j0 < j_end; j0 += kTileRows) {
         if (j0 + kTileRows < j_end) stage(buf ^ 1, j0 + kTileRows);   // prefetch next tile
-        if (active) {
+        {   // every lane computes (rows past n on zeros) so the top-k stays warp-synchronous
 #pragma unroll
             for (int h = 0; h < kTileRows / kChunk; ++h) {
                 float v[kChunk];
@@ -97,15 +97,14 @@ knn_simt_kernel(const float *__restrict__ Y, const float *__restrict__ ny, int64
                     }
                     v[i] = fmaf(-2.f, acc, ns[buf][h * kChunk + i]);
                 }
-                tk.template offer<kChunk>(v, (int)(j0 + h * kChunk));
+                tk.offer16(v, (int)(j0 + h * kChunk));
             }
-            if (tk.cnt > 0) tk.flush();
         }
         __syncthreads();
         buf ^= 1;
     }
+    tk.flush();
     if (active) {
-        tk.flush();
         int32_t *out = cand + ((int64_t)split * n + q) * KC;
 #pragma unroll
         for (int c = 0; c < KC; ++c) out[c] = tk.list.id[c];

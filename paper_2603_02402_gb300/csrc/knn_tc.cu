@@ -289,7 +289,6 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
         const int et = threadIdx.x - 64;
         BufferedTopK<KC, kCap> tk;
         tk.init(bkey, bid, et, kEpiThreads);
-        constexpr int LPW = (KC <= 32) ? 2 : 1;   // 32-column loads per wait
 
         uint32_t gt = 0;
         bool ok = true;
@@ -297,8 +296,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             const int qt = it / splits, sp = it - qt * splits;
             const int64_t j_begin = (int64_t)sp * split_len;
             const int64_t j_end = min(n, j_begin + split_len);
-            tk.list.init();
-            tk.cnt = 0;
+            tk.reset();
             for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
                 const uint32_t b = gt & 1, v = gt >> 1;
                 ok = wait(&acc_full[b], v & 1);
@@ -307,38 +305,32 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 tc::tc_fence_after();
                 const uint32_t tbase = tmem_base + lane_bits + (b * QT + g) * BN;
                 const int valid = (j_end - j0 < BN) ? (int)(j_end - j0) : BN;
-#pragma unroll
-                for (int c0 = 0; c0 < BN; c0 += 32 * LPW) {
-                    float vv[LPW][32];
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float vv[32];
                     __syncwarp();
-#pragma unroll
-                    for (int h = 0; h < LPW; ++h) tc::tmem_ld32(tbase + c0 + 32 * h, vv[h]);
+                    tc::tmem_ld32(tbase + c0, vv);
                     tc::tmem_wait_ld();
-                    if (c0 + 32 * LPW == BN) {
+                    if (c0 == BN - 32) {
                         // last load of this accumulator: hand it back to the MMA warp
                         tc::tc_fence_before();
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
                     }
+                    if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
 #pragma unroll
-                    for (int h = 0; h < LPW; ++h) {
-                        const int cb = c0 + 32 * h;
-                        if (valid < cb + 32) {   // ragged end of the range (uniform)
-#pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                if (cb + i >= valid) vv[h][i] = INFINITY;
-                        }
-                        float lo[16], hi[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            lo[i] = vv[h][i];
-                            hi[i] = vv[h][16 + i];
-                        }
-                        tk.template offer<kChunk>(lo, (int)(j0 + cb));
-                        tk.template offer<kChunk>(hi, (int)(j0 + cb + 16));
+                        for (int i = 0; i < 32; ++i)
+                            if (c0 + i >= valid) vv[i] = INFINITY;
                     }
+                    float lo[16], hi[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        lo[i] = vv[i];
+                        hi[i] = vv[16 + i];
+                    }
+                    tk.offer16(lo, (int)(j0 + c0));
+                    tk.offer16(hi, (int)(j0 + c0 + 16));
                 }
-                if (tk.cnt > 0) tk.flush();
             }
             if (!ok) break;
             tk.flush();

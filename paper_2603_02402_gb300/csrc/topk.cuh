@@ -2,12 +2,11 @@
 //
 // Each thread keeps the KC smallest (key, column) pairs of its query row in
 // registers, sorted ascending; the threshold is the KC-th key.  Values arrive
-// in chunks of CH.  A chunk whose minimum is not below the threshold (the
-// common case once the list has filled) costs one min tree and one compare.
-// Otherwise the chunk's qualifying values are appended to a per-thread
-// shared-memory buffer; the buffer is merged into the register list when it
-// could overflow and at tile boundaries, so the costly sorted insertions of a
-// warp's lanes run side by side rather than one lane at a time.
+// in chunks of 16.  A chunk whose minimum is not below the threshold (the
+// common case once the list has filled) costs a 3-input min tree and one
+// compare.  Otherwise the chunk's qualifying values are appended to a
+// per-thread shared-memory buffer, merged into the register list only when
+// some lane's buffer could overflow (and at the end of a row's scan).
 #pragma once
 
 #include <math.h>
@@ -52,6 +51,13 @@ struct RowTopK {
 // Shared-memory candidate buffer of one thread: entry e lives at
 // base[e * stride]; with stride = threads per block, lanes of a warp always
 // hit distinct banks whatever their fill levels.
+//
+// All calls are warp-synchronous (every lane of the warp calls them
+// together): the decision to merge buffers into the register lists is taken
+// for the whole warp, so the lanes' sorted insertions run side by side
+// instead of one lane at a time.  A lane's threshold is only refreshed at
+// merges; a stale (higher) threshold admits extra candidates but never drops
+// one of the KC best, because thresholds only decrease.
 template <int KC, int CAP>
 struct BufferedTopK {
     RowTopK<KC> list;
@@ -68,30 +74,46 @@ struct BufferedTopK {
         cnt = 0;
     }
 
+    __device__ __forceinline__ void reset() {
+        list.init();
+        cnt = 0;
+    }
+
+    // Merge every lane's buffer into its list (warp-synchronous).
     __device__ __forceinline__ void flush() {
-        for (int e = 0; e < cnt; ++e) {
-            const float v = bkey[e * stride];
-            if (v < list.thr()) list.insert(v, bid[e * stride]);
+        const int rounds = __reduce_max_sync(0xffffffffu, cnt);
+        for (int e = 0; e < rounds; ++e) {
+            if (e < cnt) {
+                const float v = bkey[e * stride];
+                if (v < list.thr()) list.insert(v, bid[e * stride]);
+            }
         }
         cnt = 0;
     }
 
-    // Offer CH values of columns j0 .. j0 + CH - 1.
-    template <int CH>
-    __device__ __forceinline__ void offer(const float (&v)[CH], int j0) {
-        static_assert(CH <= CAP, "buffer smaller than a chunk");
-        const float m = min_of<CH>(v);
-        if (m < list.thr()) {
-            if (cnt > CAP - CH) flush();
-            const float t = list.thr();
+    template <int G>
+    __device__ __forceinline__ void append(const float *v, int j0, float t) {
 #pragma unroll
-            for (int i = 0; i < CH; ++i) {
-                if (v[i] < t) {
-                    bkey[cnt * stride] = v[i];
-                    bid[cnt * stride] = j0 + i;
-                    ++cnt;
-                }
+        for (int i = 0; i < G; ++i) {
+            if (v[i] < t) {
+                bkey[cnt * stride] = v[i];
+                bid[cnt * stride] = j0 + i;
+                ++cnt;
             }
+        }
+    }
+
+    // Offer CH = 16 values of columns j0 .. j0 + 15 (warp-synchronous).
+    __device__ __forceinline__ void offer16(const float (&v)[16], int j0) {
+        static_assert(CAP >= 16, "buffer smaller than a chunk");
+        const float m_lo = fmin3(fmin3(v[0], v[1], v[2]), fmin3(v[3], v[4], v[5]), fminf(v[6], v[7]));
+        const float m_hi = fmin3(fmin3(v[8], v[9], v[10]), fmin3(v[11], v[12], v[13]), fminf(v[14], v[15]));
+        const bool hit = fminf(m_lo, m_hi) < list.thr();
+        if (__any_sync(0xffffffffu, hit)) {
+            if (__any_sync(0xffffffffu, hit && cnt > CAP - 16)) flush();
+            const float t = list.thr();
+            if (m_lo < t) append<8>(v, j0, t);
+            if (m_hi < t) append<8>(v + 8, j0 + 8, t);
         }
     }
 };
