@@ -127,7 +127,7 @@ KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
         L.Qb = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
         L.Db = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
     }
-    L.cand = cv.take<int32_t>((size_t)p.splits * n * p.KC);
+    L.cand = cv.take<int32_t>((size_t)p.splits * n * p.KC);   // splits x parts x (KC / parts)
     if (bytes) *bytes = cv.used;
     return L;
 }
@@ -247,7 +247,8 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     // exact re-rank reads the caller's rows (Euclidean) or the normalised rows (cosine)
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC, p.splits, k, idx, dist, st));
+    const int parts = (p.precision == RSC_BF16) ? knn_tc_parts(p.KC) : 1;
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC / parts, p.splits * parts, k, idx, dist, st));
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[3], st));
     return RSC_OK;
 }

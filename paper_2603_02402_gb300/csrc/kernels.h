@@ -29,6 +29,9 @@ cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, 
 // for the SIMT search.  Database splits must be multiples of
 // knn_tc_split_align() rows.  Bounded waits record RSC_ERR_TIMEOUT in *status.
 int tc_kb(int d, int metric);
+// The KC candidates of a row come in knn_tc_parts(KC) lists of KC / parts
+// (one per column part): cand holds splits * parts lists per query.
+int knn_tc_parts(int KC);
 bool knn_tc_supported(int d, int metric, int KC);
 int64_t knn_tc_split_align();
 cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, void *Qb, void *Db,

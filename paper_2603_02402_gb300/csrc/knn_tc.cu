@@ -49,21 +49,28 @@ constexpr int QT = 2;                // accumulators per work item
 constexpr int ITEM_ROWS = BM * QT;   // 256 query rows per item
 constexpr int BN = 128;              // database rows per stage
 constexpr int BLK = 128 * 128;       // bytes of one 128-row x 64-element bf16 block
-constexpr int kThreads = 320;
-constexpr int kEpiThreads = 256;
 constexpr int kChunk = 16;
-constexpr int kCap = 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks
 
-template <int KB>
+// EG epilogue warpgroups: each accumulator (128 rows x BN columns) is read by
+// EG / 2 warpgroups, each owning BN / (EG / 2) of its columns; a query row
+// therefore has EG / 2 threads, each keeping its own top-KC list.
+template <int KB, int KC, int EG>
 struct Cfg {
-    static constexpr int kStages = (KB == 1) ? 6 : 3;
+    static constexpr int kHC = EG / 2;                       // column parts per row
+    static constexpr int kCols = BN / kHC;                   // columns per thread per tile
+    static constexpr int kEpiThreads = EG * 128;
+    static constexpr int kThreads = 64 + kEpiThreads;
+    static constexpr int kCap = (EG == 4) ? 24 : 32;         // buffer entries per thread
     static constexpr int kQBytes = QT * KB * BLK;
     static constexpr int kStageBytes = KB * BLK;
     static constexpr int kBufBytes = kCap * kEpiThreads * 8;
+    static constexpr int kBudget = 224 * 1024 - kQBytes - kBufBytes;
+    static constexpr int kStages = (kBudget / kStageBytes) > 6 ? 6 : (kBudget / kStageBytes);
     static constexpr int kBarOff = kQBytes + kStages * kStageBytes + kBufBytes;
-    static constexpr int kSmem = kBarOff + 256 + 1024;   // barriers + alignment slack
+    static constexpr int kSmem = kBarOff + 256 + 1024;       // barriers + alignment slack
+    static_assert(kStages >= 2, "shared memory too small for two stages");
 };
 
 __global__ void __launch_bounds__(256)
@@ -125,28 +132,29 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>(a);
 }
 
-template <int KB, int KC>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int KB, int KC, int EG>
+__global__ void __launch_bounds__(Cfg<KB, KC, EG>::kThreads, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmD, int64_t n,
               int splits, int64_t split_len, int n_items, int32_t *__restrict__ cand,
               unsigned int *status) {
-    using C = Cfg<KB>;
+    using C = Cfg<KB, KC, EG>;
     constexpr int S = C::kStages;
+    constexpr int HC = C::kHC;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint8_t *sQ = smem;
     uint8_t *sD = smem + C::kQBytes;
     float *bkey = reinterpret_cast<float *>(sD + S * C::kStageBytes);
-    int *bid = reinterpret_cast<int *>(bkey + kCap * kEpiThreads);
+    int *bid = reinterpret_cast<int *>(bkey + C::kCap * C::kEpiThreads);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kBarOff);
-    uint64_t *full = bars;
-    uint64_t *empty = bars + S;
-    uint64_t *acc_full = bars + 2 * S;
-    uint64_t *acc_empty = bars + 2 * S + 2;
-    uint64_t *q_full = bars + 2 * S + 4;
-    uint64_t *q_empty = bars + 2 * S + 5;
-    uint64_t *mma_done = bars + 2 * S + 6;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 7);
+    uint64_t *full = bars;                      // [S]  database stage loaded
+    uint64_t *empty = bars + S;                 // [S]  database stage consumed
+    uint64_t *acc_full = bars + 2 * S;          // [2][QT] accumulator ready
+    uint64_t *acc_empty = bars + 2 * S + 4;     // [2][QT] accumulator drained
+    uint64_t *q_full = bars + 2 * S + 8;
+    uint64_t *q_empty = bars + 2 * S + 9;
+    uint64_t *mma_done = bars + 2 * S + 10;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 11);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -156,9 +164,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&acc_full[b], 1);
-            tc::mbar_init(&acc_empty[b], kEpiThreads / 32);
+        for (int a = 0; a < 2 * QT; ++a) {
+            tc::mbar_init(&acc_full[a], 1);
+            tc::mbar_init(&acc_empty[a], 4 * HC);   // the warps reading that accumulator
         }
         tc::mbar_init(q_full, 1);
         tc::mbar_init(q_empty, 1);
@@ -249,15 +257,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 const int64_t j_end = min(n, j_begin + split_len);
                 if (!(ok = wait(q_full, item_no & 1))) break;
                 tc::tc_fence_after();
-                for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
+                for (int64_t j0 = j_begin; j0 < j_end && ok; j0 += BN, ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
                     const uint32_t b = gt & 1, v = gt >> 1;
-                    if (!(ok = wait(&acc_empty[b], (v & 1) ^ 1))) break;
                     if (!(ok = wait(&full[s], u & 1))) break;
-                    tc::tc_fence_after();
 #pragma unroll
                     for (int g = 0; g < QT; ++g) {
+                        if (!(ok = wait(&acc_empty[b * QT + g], (v & 1) ^ 1))) break;
+                        tc::tc_fence_after();
                         const uint32_t d_tmem = tmem_base + (b * QT + g) * BN;
 #pragma unroll
                         for (int kb = 0; kb < KB; ++kb) {
@@ -269,12 +277,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                                              tc::smem_desc_sw128(b_addr + kk * 32), idesc, (kb | kk) != 0);
                             }
                         }
+                        tc::mma_commit(&acc_full[b * QT + g]);   // this accumulator is ready
                     }
-                    tc::mma_commit(&empty[s]);      // stage reusable once these MMAs finish
-                    tc::mma_commit(&acc_full[b]);   // accumulators ready for the epilogue
+                    if (!ok) break;
+                    tc::mma_commit(&empty[s]);                   // stage reusable once these MMAs finish
                 }
                 if (!ok) break;
-                tc::mma_commit(q_empty);            // query tile reusable
+                tc::mma_commit(q_empty);                         // query tile reusable
             }
             tc::mma_commit(mma_done);
             drain(mma_done, 0);
@@ -282,13 +291,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     } else {
         // ---------------------------------------------------- epilogue
         const int e = warp - 2;
-        const int g = e >> 2;                 // accumulator (query sub-tile) of this warp
+        const int G = e >> 2;                 // epilogue warpgroup
+        const int g = G / HC;                 // accumulator (query sub-tile) it reads
+        const int part = G - g * HC;          // which column part of the accumulator
         const int quarter = warp & 3;         // TMEM lane quarter this warp may access
         const int r = quarter * 32 + lane;    // query row within the sub-tile
         const uint32_t lane_bits = (uint32_t)(quarter * 32) << 16;
         const int et = threadIdx.x - 64;
-        BufferedTopK<KC, kCap> tk;
-        tk.init(bkey, bid, et, kEpiThreads);
+        BufferedTopK<KC, C::kCap> tk;
+        tk.init(bkey, bid, et, C::kEpiThreads);
 
         uint32_t gt = 0;
         bool ok = true;
@@ -299,23 +310,24 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             tk.reset();
             for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
                 const uint32_t b = gt & 1, v = gt >> 1;
-                ok = wait(&acc_full[b], v & 1);
+                ok = wait(&acc_full[b * QT + g], v & 1);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc::tc_fence_after();
-                const uint32_t tbase = tmem_base + lane_bits + (b * QT + g) * BN;
-                const int valid = (j_end - j0 < BN) ? (int)(j_end - j0) : BN;
+                const int cbeg = part * C::kCols;
+                const uint32_t tbase = tmem_base + lane_bits + (b * QT + g) * BN + cbeg;
+                const int valid = ((j_end - j0 < BN) ? (int)(j_end - j0) : BN) - cbeg;
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 32) {
+                for (int c0 = 0; c0 < C::kCols; c0 += 32) {
                     float vv[32];
                     __syncwarp();
                     tc::tmem_ld32(tbase + c0, vv);
                     tc::tmem_wait_ld();
-                    if (c0 == BN - 32) {
-                        // last load of this accumulator: hand it back to the MMA warp
+                    if (c0 + 32 == C::kCols) {
+                        // last load of this accumulator part: hand it back to the MMA warp
                         tc::tc_fence_before();
                         __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+                        if (lane == 0) tc::mbar_arrive(&acc_empty[b * QT + g]);
                     }
                     if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
 #pragma unroll
@@ -328,15 +340,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                         lo[i] = vv[i];
                         hi[i] = vv[16 + i];
                     }
-                    tk.offer16(lo, (int)(j0 + c0));
-                    tk.offer16(hi, (int)(j0 + c0 + 16));
+                    tk.offer16(lo, (int)(j0 + cbeg + c0));
+                    tk.offer16(hi, (int)(j0 + cbeg + c0 + 16));
                 }
             }
             if (!ok) break;
             tk.flush();
             const int64_t q = (int64_t)qt * ITEM_ROWS + g * BM + r;
             if (q < n) {
-                int32_t *out = cand + ((int64_t)sp * n + q) * KC;
+                int32_t *out = cand + ((int64_t)(sp * HC + part) * n + q) * KC;
 #pragma unroll
                 for (int c = 0; c < KC; ++c) out[c] = tk.list.id[c];
             }
@@ -382,15 +394,16 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int KB, int KC>
+template <int KB, int KC, int EG>
 cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, int64_t n, int splits, int64_t split_len,
                           int32_t *cand, unsigned int *status, cudaStream_t st) {
-    const int smem = Cfg<KB>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel<KB, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    using C = Cfg<KB, KC, EG>;
+    auto kern = knn_tc_kernel<KB, KC, EG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return e;
     const int64_t items = ceil_div(n, ITEM_ROWS) * splits;
     const int grid = (int)std::min<int64_t>(items, sm_count());
-    knn_tc_kernel<KB, KC><<<grid, kThreads, smem, st>>>(mq, md, n, splits, split_len, (int)items, cand, status);
+    kern<<<grid, C::kThreads, C::kSmem, st>>>(mq, md, n, splits, split_len, (int)items, cand, status);
     return cudaGetLastError();
 }
 
@@ -413,6 +426,8 @@ cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metri
     return cudaGetLastError();
 }
 
+int knn_tc_parts(int KC) { return KC <= 32 ? 2 : 1; }
+
 cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, int KC, int splits,
                           int64_t split_len, int32_t *cand, unsigned int *status, cudaStream_t st) {
     const int KB = tc_kb(d, metric);
@@ -420,19 +435,24 @@ cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int 
     cudaError_t e = tck::make_map(&mq, Qb, n, KB);
     if (e != cudaSuccess) return e;
     if ((e = tck::make_map(&md, Db, n, KB)) != cudaSuccess) return e;
+    // KC candidates per row: two threads per row with KC / 2 each (four
+    // epilogue warpgroups) up to 32, one thread with KC (two warpgroups) above
+#define RSC_TC_CASE(kb, kc, eg) \
+    return tck::launch_kernel<kb, kc, eg>(mq, md, n, splits, split_len, cand, status, st)
     if (KB == 1) {
         switch (KC) {
-            case 16: return tck::launch_kernel<1, 16>(mq, md, n, splits, split_len, cand, status, st);
-            case 32: return tck::launch_kernel<1, 32>(mq, md, n, splits, split_len, cand, status, st);
-            case 64: return tck::launch_kernel<1, 64>(mq, md, n, splits, split_len, cand, status, st);
+            case 16: RSC_TC_CASE(1, 8, 4);
+            case 32: RSC_TC_CASE(1, 16, 4);
+            case 64: RSC_TC_CASE(1, 64, 2);
         }
     } else {
         switch (KC) {
-            case 16: return tck::launch_kernel<2, 16>(mq, md, n, splits, split_len, cand, status, st);
-            case 32: return tck::launch_kernel<2, 32>(mq, md, n, splits, split_len, cand, status, st);
-            case 64: return tck::launch_kernel<2, 64>(mq, md, n, splits, split_len, cand, status, st);
+            case 16: RSC_TC_CASE(2, 8, 4);
+            case 32: RSC_TC_CASE(2, 16, 4);
+            case 64: RSC_TC_CASE(2, 64, 2);
         }
     }
+#undef RSC_TC_CASE
     return cudaErrorInvalidValue;
 }
 
