@@ -53,7 +53,8 @@ struct KnnPlan {
     int precision = RSC_FP32;
     int d = 0, metric = 0;
     int DP = 0;         // padded FP32 row length
-    int KC = 0;         // candidates per query per split
+    int KC = 0;         // ids per candidate list
+    int parts = 1;      // candidate lists per query per split
     int splits = 1;     // database splits
     int64_t split_len = 0;
 };
@@ -88,30 +89,39 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     if (want == 0) want = (p->precision == RSC_FP32) ? k + 8 : 2 * k;
     if (want < k) return fail(RSC_ERR_INVALID_ARG, "candidates=%d smaller than k=%d", want, k);
     if (want > 64) {
-        if (o->candidates != 0) return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 64", want);
-        want = 64;
+        if (o->candidates != 0 && p->precision == RSC_FP32)
+            return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 64", want);
+        if (o->candidates > 128) return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 128", want);
+        if (o->candidates == 0) want = 64;
     }
-    p->KC = 0;
-    for (int c : kSupportedKC)
-        if (c >= want) { p->KC = c; break; }
-    // database splits: enough CTAs to fill the GPU when there are few queries
+    // candidates per row: FP32 lists of KC; tensor-core rows as parts x list
     const bool tc = p->precision == RSC_BF16;
-    const int64_t qrows = tc ? 256 : 128;            // query rows per CTA work unit
-    const int64_t target = tc ? 152 : 1024;          // work units wanted (persistent CTAs / blocks)
+    p->KC = 0;
+    p->parts = 1;
+    if (tc) {
+        if (!knn_tc_supported(d, metric)) return fail(RSC_ERR_UNSUPPORTED, "no tensor-core kernel for d=%d", d);
+        TcShape sh = knn_tc_shape(d, metric, k, want);
+        if (sh.parts == 0) return fail(RSC_ERR_UNSUPPORTED, "no tensor-core list shape for k=%d candidates=%d", k, want);
+        p->parts = sh.parts;
+        p->KC = sh.list;
+    } else {
+        for (int c : kSupportedKC)
+            if (c >= want) { p->KC = c; break; }
+        if (!knn_simt_supported(p->DP, p->KC))
+            return fail(RSC_ERR_UNSUPPORTED, "no SIMT kernel for DP=%d KC=%d", p->DP, p->KC);
+    }
+    // database splits: enough CTAs to fill the GPU when there are few queries
+    const int64_t qrows = 128;                        // query rows per CTA work unit
+    const int64_t target = tc ? 152 : 1024;           // work units wanted (persistent CTAs / blocks)
     const int64_t align = tc ? knn_tc_split_align() : 32;
     const int64_t qblocks = ceil_div(n, qrows);
+    const int per_split = p->parts * p->KC;           // candidate ids per row and split
     int splits = o->db_splits;
     if (splits == 0) splits = (int)std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(target, qblocks)));
-    while (splits > 1 && splits * p->KC > 1024) --splits;
-    if (splits * p->KC > 1024) return fail(RSC_ERR_INVALID_ARG, "db_splits * candidates above 1024");
+    while (splits > 1 && splits * per_split > 1024) --splits;
+    if (splits * per_split > 1024) return fail(RSC_ERR_INVALID_ARG, "db_splits * candidates above 1024");
     p->split_len = ceil_div(ceil_div(n, splits), align) * align;
     p->splits = (int)ceil_div(n, p->split_len);
-    if (tc) {
-        if (!knn_tc_supported(d, metric, p->KC))
-            return fail(RSC_ERR_UNSUPPORTED, "no tensor-core kernel for d=%d KC=%d", d, p->KC);
-    } else if (!knn_simt_supported(p->DP, p->KC)) {
-        return fail(RSC_ERR_UNSUPPORTED, "no SIMT kernel for DP=%d KC=%d", p->DP, p->KC);
-    }
     return RSC_OK;
 }
 
@@ -127,7 +137,7 @@ KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
         L.Qb = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
         L.Db = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
     }
-    L.cand = cv.take<int32_t>((size_t)p.splits * n * p.KC);   // splits x parts x (KC / parts)
+    L.cand = cv.take<int32_t>((size_t)p.splits * p.parts * n * p.KC);
     if (bytes) *bytes = cv.used;
     return L;
 }
@@ -238,7 +248,8 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     if (p.precision == RSC_BF16) {
         RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.Qb, L.Db, st));
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
-        RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, p.KC, p.splits, p.split_len, L.cand, L.status, st));
+        RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, TcShape{p.parts, p.KC}, p.splits, p.split_len,
+                                   L.cand, L.status, st));
     } else {
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
         RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
@@ -247,8 +258,7 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     // exact re-rank reads the caller's rows (Euclidean) or the normalised rows (cosine)
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    const int parts = (p.precision == RSC_BF16) ? knn_tc_parts(p.KC) : 1;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC / parts, p.splits * parts, k, idx, dist, st));
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC, p.splits * p.parts, k, idx, dist, st));
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[3], st));
     return RSC_OK;
 }

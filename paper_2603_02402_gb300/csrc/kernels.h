@@ -25,18 +25,23 @@ cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, 
 
 // ---- knn_tc.cu ------------------------------------------------------------
 // BF16 tensor-core candidate search.  Qb/Db: [n, 64 * tc_kb(d, metric)] bf16
-// operand rows built by launch_prep_bf16 from the FP32 prep rows Y; cand as
-// for the SIMT search.  Database splits must be multiples of
-// knn_tc_split_align() rows.  Bounded waits record RSC_ERR_TIMEOUT in *status.
+// operand rows built by launch_prep_bf16 from the FP32 prep rows Y.  Each
+// row's candidates come in sh.parts lists of sh.list ids (one list per column
+// part of the database tiles): cand holds splits * parts lists per query, list
+// (s * parts + p) of query q at cand[((s * parts + p) * n + q) * list].
+// Database splits must be multiples of knn_tc_split_align() rows.  Bounded
+// waits record RSC_ERR_TIMEOUT in *status.
+struct TcShape {
+    int parts;   // lists per row and split (0: no kernel for this request)
+    int list;    // ids per list
+};
 int tc_kb(int d, int metric);
-// The KC candidates of a row come in knn_tc_parts(KC) lists of KC / parts
-// (one per column part): cand holds splits * parts lists per query.
-int knn_tc_parts(int KC);
-bool knn_tc_supported(int d, int metric, int KC);
+TcShape knn_tc_shape(int d, int metric, int k, int want);
+bool knn_tc_supported(int d, int metric);
 int64_t knn_tc_split_align();
 cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, void *Qb, void *Db,
                              cudaStream_t st);
-cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, int KC, int splits,
+cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int splits,
                           int64_t split_len, int32_t *cand, unsigned int *status, cudaStream_t st);
 
 // ---- rerank.cu ------------------------------------------------------------

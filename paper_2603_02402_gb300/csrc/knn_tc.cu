@@ -17,15 +17,20 @@
 // distances; this pass only has to bring the true neighbours into the
 // per-row candidate list.
 //
-// One persistent CTA per SM; a work item is 256 query rows (two M = 128
-// accumulators) against one database range:
-//   warp 0      TMA producer: query tile once per item, then 128-row database
+// One persistent CTA per SM; a work item is 128 query rows (one M = 128
+// accumulator) against one database range:
+//   warp 0      TMA producer: query tile once per item, then 256-row database
 //               tiles through a ring of shared-memory stages
-//   warp 1      MMA issuer: per database tile, 2 x (K/16) tcgen05.mma into one
-//               of two double-buffered TMEM accumulator pairs (512 columns)
-//   warps 2..9  epilogue: thread = query row; tcgen05.ld 32 columns at a time,
-//               3-input min tree per 16 values, threshold test against the
-//               row's register top-k, rare appends to a shared-memory buffer
+//   warp 1      MMA issuer: per database tile, K/16 tcgen05.mma of
+//               M = 128, N = 256 (the largest single-CTA shape: the issuing
+//               thread and the per-tile barrier round trips, not the tensor
+//               pipe, limit smaller shapes) into one of two 256-column TMEM
+//               accumulators (2 x 256 = 512 columns)
+//   epilogue    EG warpgroups, each owning 256 / EG columns of every tile; a
+//               thread owns one query row's part: tcgen05.ld 32 columns at a
+//               time, 3-input min tree per 16 values, threshold test against
+//               its register top-k, rare appends to a shared-memory buffer.
+//               The row's EG per-part lists together form its candidates.
 // Every wait is bounded; on timeout the CTA records RSC_ERR_TIMEOUT, drains
 // its in-flight copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
@@ -44,27 +49,24 @@ namespace rsc {
 
 namespace tck {
 
-constexpr int BM = 128;              // query rows per accumulator (TMEM lanes)
-constexpr int QT = 2;                // accumulators per work item
-constexpr int ITEM_ROWS = BM * QT;   // 256 query rows per item
-constexpr int BN = 128;              // database rows per stage
-constexpr int BLK = 128 * 128;       // bytes of one 128-row x 64-element bf16 block
-constexpr int kChunk = 16;
+constexpr int BM = 128;              // query rows per item (TMEM lanes)
+constexpr int BN = 256;              // database rows per stage = accumulator columns
+constexpr int NBUF = 2;              // accumulators (NBUF x BN = 512 TMEM columns)
+constexpr int QBLK = BM * 128;       // bytes of one 128-row x 64-element bf16 query block
+constexpr int DBLK = BN * 128;       // bytes of one 256-row x 64-element bf16 database block
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks
 
-// EG epilogue warpgroups: each accumulator (128 rows x BN columns) is read by
-// EG / 2 warpgroups, each owning BN / (EG / 2) of its columns; a query row
-// therefore has EG / 2 threads, each keeping its own top-KC list.
-template <int KB, int KC, int EG>
+// EG epilogue warpgroups, each owning kCols = BN / EG columns of every tile;
+// KCP = top-k list length per (row, part).
+template <int KB, int KCP, int EG>
 struct Cfg {
-    static constexpr int kHC = EG / 2;                       // column parts per row
-    static constexpr int kCols = BN / kHC;                   // columns per thread per tile
+    static constexpr int kCols = BN / EG;
     static constexpr int kEpiThreads = EG * 128;
     static constexpr int kThreads = 64 + kEpiThreads;
     static constexpr int kCap = (EG == 4) ? 24 : 32;         // buffer entries per thread
-    static constexpr int kQBytes = QT * KB * BLK;
-    static constexpr int kStageBytes = KB * BLK;
+    static constexpr int kQBytes = KB * QBLK;
+    static constexpr int kStageBytes = KB * DBLK;
     static constexpr int kBufBytes = kCap * kEpiThreads * 8;
     static constexpr int kBudget = 224 * 1024 - kQBytes - kBufBytes;
     static constexpr int kStages = (kBudget / kStageBytes) > 6 ? 6 : (kBudget / kStageBytes);
@@ -132,14 +134,13 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>(a);
 }
 
-template <int KB, int KC, int EG>
-__global__ void __launch_bounds__(Cfg<KB, KC, EG>::kThreads, 1)
+template <int KB, int KCP, int EG>
+__global__ void __launch_bounds__(Cfg<KB, KCP, EG>::kThreads, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmD, int64_t n,
               int splits, int64_t split_len, int n_items, int32_t *__restrict__ cand,
               unsigned int *status) {
-    using C = Cfg<KB, KC, EG>;
+    using C = Cfg<KB, KCP, EG>;
     constexpr int S = C::kStages;
-    constexpr int HC = C::kHC;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint8_t *sQ = smem;
@@ -147,14 +148,14 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     float *bkey = reinterpret_cast<float *>(sD + S * C::kStageBytes);
     int *bid = reinterpret_cast<int *>(bkey + C::kCap * C::kEpiThreads);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kBarOff);
-    uint64_t *full = bars;                      // [S]  database stage loaded
-    uint64_t *empty = bars + S;                 // [S]  database stage consumed
-    uint64_t *acc_full = bars + 2 * S;          // [2][QT] accumulator ready
-    uint64_t *acc_empty = bars + 2 * S + 4;     // [2][QT] accumulator drained
-    uint64_t *q_full = bars + 2 * S + 8;
-    uint64_t *q_empty = bars + 2 * S + 9;
-    uint64_t *mma_done = bars + 2 * S + 10;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 11);
+    uint64_t *full = bars;                     // [S]     database stage loaded
+    uint64_t *empty = bars + S;                // [S]     database stage consumed
+    uint64_t *acc_full = bars + 2 * S;         // [NBUF]  accumulator ready
+    uint64_t *acc_empty = acc_full + NBUF;     // [NBUF]  accumulator drained
+    uint64_t *q_full = acc_empty + NBUF;
+    uint64_t *q_empty = q_full + 1;
+    uint64_t *mma_done = q_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(q_full + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -164,9 +165,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        for (int a = 0; a < 2 * QT; ++a) {
+        for (int a = 0; a < NBUF; ++a) {
             tc::mbar_init(&acc_full[a], 1);
-            tc::mbar_init(&acc_empty[a], 4 * HC);   // the warps reading that accumulator
+            tc::mbar_init(&acc_empty[a], C::kEpiThreads / 32);
         }
         tc::mbar_init(q_full, 1);
         tc::mbar_init(q_empty, 1);
@@ -222,9 +223,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 const int64_t j_end = min(n, j_begin + split_len);
                 if (!(ok = wait(q_empty, (item_no & 1) ^ 1))) break;
                 tc::mbar_arrive_expect_tx(q_full, C::kQBytes);
-                for (int g = 0; g < QT; ++g)
-                    for (int kb = 0; kb < KB; ++kb)
-                        tc::tma_load_2d(sQ + (g * KB + kb) * BLK, &tmQ, kb * 64, qt * ITEM_ROWS + g * BM, q_full);
+                for (int kb = 0; kb < KB; ++kb)
+                    tc::tma_load_2d(sQ + kb * QBLK, &tmQ, kb * 64, qt * BM, q_full);
                 q_issued = true;
                 q_parity = item_no & 1;
                 for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
@@ -233,7 +233,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                     if (!(ok = wait(&empty[s], (u & 1) ^ 1))) break;
                     tc::mbar_arrive_expect_tx(&full[s], C::kStageBytes);
                     for (int kb = 0; kb < KB; ++kb)
-                        tc::tma_load_2d(sD + (s * KB + kb) * BLK, &tmD, kb * 64, (int)j0, &full[s]);
+                        tc::tma_load_2d(sD + (s * KB + kb) * DBLK, &tmD, kb * 64, (int)j0, &full[s]);
                 }
             }
             if (!ok) {
@@ -257,33 +257,29 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 const int64_t j_end = min(n, j_begin + split_len);
                 if (!(ok = wait(q_full, item_no & 1))) break;
                 tc::tc_fence_after();
-                for (int64_t j0 = j_begin; j0 < j_end && ok; j0 += BN, ++gt) {
+                for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
-                    const uint32_t b = gt & 1, v = gt >> 1;
+                    const uint32_t b = gt % NBUF, v = gt / NBUF;
+                    if (!(ok = wait(&acc_empty[b], (v & 1) ^ 1))) break;
                     if (!(ok = wait(&full[s], u & 1))) break;
+                    tc::tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + b * BN;
 #pragma unroll
-                    for (int g = 0; g < QT; ++g) {
-                        if (!(ok = wait(&acc_empty[b * QT + g], (v & 1) ^ 1))) break;
-                        tc::tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (b * QT + g) * BN;
+                    for (int kb = 0; kb < KB; ++kb) {
+                        const uint32_t a_addr = tc::smem_u32(sQ + kb * QBLK);
+                        const uint32_t b_addr = tc::smem_u32(sD + (s * KB + kb) * DBLK);
 #pragma unroll
-                        for (int kb = 0; kb < KB; ++kb) {
-                            const uint32_t a_addr = tc::smem_u32(sQ + (g * KB + kb) * BLK);
-                            const uint32_t b_addr = tc::smem_u32(sD + (s * KB + kb) * BLK);
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                tc::mma_bf16(d_tmem, tc::smem_desc_sw128(a_addr + kk * 32),
-                                             tc::smem_desc_sw128(b_addr + kk * 32), idesc, (kb | kk) != 0);
-                            }
+                        for (int kk = 0; kk < 4; ++kk) {
+                            tc::mma_bf16(d_tmem, tc::smem_desc_sw128(a_addr + kk * 32),
+                                         tc::smem_desc_sw128(b_addr + kk * 32), idesc, (kb | kk) != 0);
                         }
-                        tc::mma_commit(&acc_full[b * QT + g]);   // this accumulator is ready
                     }
-                    if (!ok) break;
-                    tc::mma_commit(&empty[s]);                   // stage reusable once these MMAs finish
+                    tc::mma_commit(&acc_full[b]);   // accumulator ready for the epilogue
+                    tc::mma_commit(&empty[s]);      // stage reusable once these MMAs finish
                 }
                 if (!ok) break;
-                tc::mma_commit(q_empty);                         // query tile reusable
+                tc::mma_commit(q_empty);            // query tile reusable
             }
             tc::mma_commit(mma_done);
             drain(mma_done, 0);
@@ -291,14 +287,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     } else {
         // ---------------------------------------------------- epilogue
         const int e = warp - 2;
-        const int G = e >> 2;                 // epilogue warpgroup
-        const int g = G / HC;                 // accumulator (query sub-tile) it reads
-        const int part = G - g * HC;          // which column part of the accumulator
+        const int part = e >> 2;              // column part of every tile this warp reads
         const int quarter = warp & 3;         // TMEM lane quarter this warp may access
-        const int r = quarter * 32 + lane;    // query row within the sub-tile
+        const int r = quarter * 32 + lane;    // query row within the item
         const uint32_t lane_bits = (uint32_t)(quarter * 32) << 16;
         const int et = threadIdx.x - 64;
-        BufferedTopK<KC, C::kCap> tk;
+        const int cbeg = part * C::kCols;
+        BufferedTopK<KCP, C::kCap> tk;
         tk.init(bkey, bid, et, C::kEpiThreads);
 
         uint32_t gt = 0;
@@ -309,13 +304,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             const int64_t j_end = min(n, j_begin + split_len);
             tk.reset();
             for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
-                const uint32_t b = gt & 1, v = gt >> 1;
-                ok = wait(&acc_full[b * QT + g], v & 1);
+                const uint32_t b = gt % NBUF, v = gt / NBUF;
+                ok = wait(&acc_full[b], v & 1);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc::tc_fence_after();
-                const int cbeg = part * C::kCols;
-                const uint32_t tbase = tmem_base + lane_bits + (b * QT + g) * BN + cbeg;
+                const uint32_t tbase = tmem_base + lane_bits + b * BN + cbeg;
                 const int valid = ((j_end - j0 < BN) ? (int)(j_end - j0) : BN) - cbeg;
 #pragma unroll 1
                 for (int c0 = 0; c0 < C::kCols; c0 += 32) {
@@ -327,7 +321,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                         // last load of this accumulator part: hand it back to the MMA warp
                         tc::tc_fence_before();
                         __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&acc_empty[b * QT + g]);
+                        if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
                     }
                     if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
 #pragma unroll
@@ -346,11 +340,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             }
             if (!ok) break;
             tk.flush();
-            const int64_t q = (int64_t)qt * ITEM_ROWS + g * BM + r;
+            const int64_t q = (int64_t)qt * BM + r;
             if (q < n) {
-                int32_t *out = cand + ((int64_t)(sp * HC + part) * n + q) * KC;
+                int32_t *out = cand + ((int64_t)(sp * EG + part) * n + q) * KCP;
 #pragma unroll
-                for (int c = 0; c < KC; ++c) out[c] = tk.list.id[c];
+                for (int c = 0; c < KCP; ++c) out[c] = tk.list.id[c];
             }
         }
     }
@@ -380,13 +374,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// [rows, 64 * KB] bf16, 128 x 64-element boxes, 128-byte swizzle
-cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB) {
+// [rows, 64 * KB] bf16, box_rows x 64-element boxes, 128-byte swizzle
+cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     cuuint64_t dims[2] = {(cuuint64_t)(64 * KB), (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(128 * KB)};
-    cuuint32_t box[2] = {64, 128};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -394,14 +388,14 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int KB, int KC, int EG>
+template <int KB, int KCP, int EG>
 cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, int64_t n, int splits, int64_t split_len,
                           int32_t *cand, unsigned int *status, cudaStream_t st) {
-    using C = Cfg<KB, KC, EG>;
-    auto kern = knn_tc_kernel<KB, KC, EG>;
+    using C = Cfg<KB, KCP, EG>;
+    auto kern = knn_tc_kernel<KB, KCP, EG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return e;
-    const int64_t items = ceil_div(n, ITEM_ROWS) * splits;
+    const int64_t items = ceil_div(n, BM) * splits;
     const int grid = (int)std::min<int64_t>(items, sm_count());
     kern<<<grid, C::kThreads, C::kSmem, st>>>(mq, md, n, splits, split_len, (int)items, cand, status);
     return cudaGetLastError();
@@ -411,10 +405,16 @@ cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, int64_t 
 
 int tc_kb(int d, int metric) { return (d + (metric == RSC_EUCLIDEAN ? 3 : 1) <= 64) ? 1 : 2; }
 
-bool knn_tc_supported(int d, int metric, int KC) {
-    const bool kc_ok = KC == 16 || KC == 32 || KC == 64;
-    return kc_ok && d >= 1 && d + (metric == RSC_EUCLIDEAN ? 3 : 1) <= 128;
+TcShape knn_tc_shape(int d, int metric, int k, int want) {
+    // each part's list must be able to hold the whole top-k (all of it may
+    // fall in one part), and parts x list >= the requested candidate count
+    if (tc_kb(d, metric) == 1 && k <= 16 && want <= 64) return TcShape{4, 16};
+    for (int list : {16, 32, 64})
+        if (list >= k && 2 * list >= want) return TcShape{2, list};
+    return TcShape{0, 0};
 }
+
+bool knn_tc_supported(int d, int metric) { return d >= 1 && d + (metric == RSC_EUCLIDEAN ? 3 : 1) <= 128; }
 
 int64_t knn_tc_split_align() { return tck::BN; }
 
@@ -426,32 +426,22 @@ cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metri
     return cudaGetLastError();
 }
 
-int knn_tc_parts(int KC) { return KC <= 32 ? 2 : 1; }
-
-cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, int KC, int splits,
+cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int splits,
                           int64_t split_len, int32_t *cand, unsigned int *status, cudaStream_t st) {
     const int KB = tc_kb(d, metric);
     CUtensorMap mq, md;
-    cudaError_t e = tck::make_map(&mq, Qb, n, KB);
+    cudaError_t e = tck::make_map(&mq, Qb, n, KB, tck::BM);
     if (e != cudaSuccess) return e;
-    if ((e = tck::make_map(&md, Db, n, KB)) != cudaSuccess) return e;
-    // KC candidates per row: two threads per row with KC / 2 each (four
-    // epilogue warpgroups) up to 32, one thread with KC (two warpgroups) above
-#define RSC_TC_CASE(kb, kc, eg) \
-    return tck::launch_kernel<kb, kc, eg>(mq, md, n, splits, split_len, cand, status, st)
-    if (KB == 1) {
-        switch (KC) {
-            case 16: RSC_TC_CASE(1, 8, 4);
-            case 32: RSC_TC_CASE(1, 16, 4);
-            case 64: RSC_TC_CASE(1, 64, 2);
-        }
-    } else {
-        switch (KC) {
-            case 16: RSC_TC_CASE(2, 8, 4);
-            case 32: RSC_TC_CASE(2, 16, 4);
-            case 64: RSC_TC_CASE(2, 64, 2);
-        }
-    }
+    if ((e = tck::make_map(&md, Db, n, KB, tck::BN)) != cudaSuccess) return e;
+#define RSC_TC_CASE(kb, kcp, eg) \
+    return tck::launch_kernel<kb, kcp, eg>(mq, md, n, splits, split_len, cand, status, st)
+    if (KB == 1 && sh.parts == 4 && sh.list == 16) RSC_TC_CASE(1, 16, 4);
+    if (KB == 1 && sh.parts == 2 && sh.list == 16) RSC_TC_CASE(1, 16, 2);
+    if (KB == 1 && sh.parts == 2 && sh.list == 32) RSC_TC_CASE(1, 32, 2);
+    if (KB == 1 && sh.parts == 2 && sh.list == 64) RSC_TC_CASE(1, 64, 2);
+    if (KB == 2 && sh.parts == 2 && sh.list == 16) RSC_TC_CASE(2, 16, 2);
+    if (KB == 2 && sh.parts == 2 && sh.list == 32) RSC_TC_CASE(2, 32, 2);
+    if (KB == 2 && sh.parts == 2 && sh.list == 64) RSC_TC_CASE(2, 64, 2);
 #undef RSC_TC_CASE
     return cudaErrorInvalidValue;
 }
