@@ -118,6 +118,44 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
                    void *workspace, size_t workspace_bytes);
 
 /*
+ * Minimum workspace for rsc_knn_batched (host query; no GPU work).
+ */
+rsc_status rsc_knn_batched_workspace_size(int64_t n, int32_t d, const int64_t *sample_offsets,
+                                          int32_t n_samples, int32_t k_within, int32_t k_cross,
+                                          int32_t metric, const rsc_knn_opts *opts, size_t *bytes);
+
+/*
+ * Batched exact kNN over samples (for batch-aware graphs).
+ *   X               [n, d] float32; the cells of sample s are rows
+ *                   sample_offsets[s] .. sample_offsets[s+1]-1.
+ *   sample_offsets  HOST array of n_samples + 1 ascending int64, [0] = 0,
+ *                   [n_samples] = n; every sample needs >= k_within cells.
+ *   k_within        1 <= k_within <= 16: neighbours inside the cell's own
+ *                   sample (self included).
+ *   k_cross         1 <= k_cross <= min(4, k_within): neighbours taken from
+ *                   EVERY sample, own sample included.
+ *   idx_within, dist_within  [n, k_within] out, as rsc_knn restricted to the
+ *                   cell's sample (global row ids, ordered by (distance, id)).
+ *   idx_cross, dist_cross    [n, n_samples * k_cross] out: the k_cross nearest
+ *                   cells of each sample, the whole row ordered by
+ *                   (distance, id); n_samples * k_cross <= 1024.
+ * Candidates come from one persistent BF16 tensor-core launch over
+ * (query tile, sample) work items and are re-scored exactly in FP32 (the
+ * precision option must be RSC_BF16).  With a non-NULL stream the launch
+ * sequence is captured once into a CUDA graph (cached per argument set, up
+ * to 8 entries per process) and replayed; the first call for an argument set
+ * synchronises the stream.  d + 3 <= 64 (Euclidean) or d + 1 <= 64 (cosine).
+ * Paper: per-group kernels over category offsets (Methods, "Perturbation
+ * distance computation"); kNN graph construction (Methods, "Dimensionality
+ * reduction and graph analysis").
+ */
+rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *sample_offsets,
+                           int32_t n_samples, int32_t k_within, int32_t k_cross, int32_t metric,
+                           int32_t *idx_within, float *dist_within, int32_t *idx_cross,
+                           float *dist_cross, const rsc_knn_opts *opts, void *workspace,
+                           size_t workspace_bytes);
+
+/*
  * Minimum workspace for rsc_connectivities / rsc_connectivities_nnz.
  */
 rsc_status rsc_connectivities_workspace_size(int64_t n, int32_t k, size_t *bytes);

@@ -10,6 +10,8 @@ kernels" for the distances, "Implementation" for following scanpy, whose
 neighbours step uses the UMAP smooth-kNN / fuzzy-union construction):
 
 * ``knn``          -- brute-force exact kNN, ties broken by ascending index.
+* ``knn_qd``       -- the same for external queries against a row set.
+* ``batched_knn``  -- per-sample kNN and k_cross nearest from every sample.
 * ``smooth_knn``   -- rho, sigma (64-step bisection to log2 k) and weights.
 * ``fuzzy_union``  -- G = A + A^T - A o A^T as CSR with sorted columns.
 * ``connectivities`` -- smooth_knn followed by fuzzy_union.
@@ -58,6 +60,8 @@ def _load():
             vp = ctypes.c_void_p
             lib.oracle_knn.argtypes = [vp, i64, i32, vp, i64, i32, i32, vp, vp, vp]
             lib.oracle_knn.restype = i32
+            lib.oracle_knn_qd.argtypes = [vp, i64, vp, i64, i32, i32, i32, vp, vp, vp]
+            lib.oracle_knn_qd.restype = i32
             lib.oracle_smooth_knn.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp]
             lib.oracle_smooth_knn.restype = i32
             lib.oracle_fuzzy_union.argtypes = [vp, vp, i64, i32, vp, vp, vp, i64]
@@ -95,6 +99,49 @@ def knn(X: np.ndarray, k: int, metric: int = EUCLIDEAN, queries=None):
     if rc != 0:
         raise ValueError(f"oracle_knn failed with status {rc}")
     return idx, dist, nxt
+
+
+def knn_qd(Q: np.ndarray, D: np.ndarray, k: int, metric: int = EUCLIDEAN):
+    """Exact kNN of the rows of Q among the rows of D (ids index D)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    D = np.ascontiguousarray(D, dtype=np.float32)
+    nq, d = Q.shape
+    idx = np.empty((nq, k), dtype=np.int32)
+    dist = np.empty((nq, k), dtype=np.float64)
+    nxt = np.empty(nq, dtype=np.float64)
+    rc = _load().oracle_knn_qd(_ptr(Q), nq, _ptr(D), len(D), d, k, metric, _ptr(idx), _ptr(dist), _ptr(nxt))
+    if rc != 0:
+        raise ValueError(f"oracle_knn_qd failed with status {rc}")
+    return idx, dist, nxt
+
+
+def batched_knn(X: np.ndarray, offsets, k_within: int, k_cross: int, metric: int = EUCLIDEAN):
+    """Per-sample kNN and cross-sample lists, by definition.
+
+    within: rows of sample s against rows of sample s (global ids);
+    cross: for every sample t the k_cross nearest rows of t, the row's
+    n_samples * k_cross entries ordered by (distance, id).
+    """
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    off = np.asarray(offsets, dtype=np.int64)
+    S, n = len(off) - 1, len(X)
+    wi = np.empty((n, k_within), dtype=np.int32)
+    wd = np.empty((n, k_within))
+    xi = np.empty((n, S * k_cross), dtype=np.int64)
+    xd = np.empty((n, S * k_cross))
+    for s in range(S):
+        a, b = off[s], off[s + 1]
+        i, d_, _ = knn_qd(X[a:b], X[a:b], k_within, metric)
+        wi[a:b], wd[a:b] = i + a, d_
+    for t in range(S):
+        a, b = off[t], off[t + 1]
+        i, d_, _ = knn_qd(X, X[a:b], k_cross, metric)
+        xi[:, t * k_cross:(t + 1) * k_cross] = i + a
+        xd[:, t * k_cross:(t + 1) * k_cross] = d_
+    order = np.lexsort((xi, xd), axis=1)
+    xi = np.take_along_axis(xi, order, axis=1).astype(np.int32)
+    xd = np.take_along_axis(xd, order, axis=1)
+    return wi, wd, xi, xd
 
 
 def smooth_knn(idx: np.ndarray, dist: np.ndarray):

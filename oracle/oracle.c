@@ -129,6 +129,54 @@ int oracle_knn(const float *X, int64_t n, int d, const int64_t *queries, int64_t
 }
 
 /*
+ * Exact kNN of nq external query rows Q against the nd rows of D (both
+ * row-major float32 with d columns); ids index D.  Same order and tie rule
+ * as oracle_knn.  Used for neighbours restricted to one sample of a batch.
+ */
+int oracle_knn_qd(const float *Q, int64_t nq, const float *D, int64_t nd, int d, int k, int metric,
+                  int32_t *idx, double *dist, double *next) {
+    if (!Q || !D || nq < 0 || nd <= 0 || d <= 0 || k <= 0 || k > nd || (metric != 0 && metric != 1))
+        return ORC_BAD_ARG;
+    int kk = (k < nd) ? k + 1 : k;
+    int bad = 0;
+#pragma omp parallel
+    {
+        double *bd = (double *)malloc(sizeof(double) * (size_t)kk);
+        int64_t *bj = (int64_t *)malloc(sizeof(int64_t) * (size_t)kk);
+        if (!bd || !bj) {
+#pragma omp atomic write
+            bad = 1;
+        } else {
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t qi = 0; qi < nq; ++qi) {
+                const float *xi = Q + (size_t)qi * (size_t)d;
+                int cnt = 0;
+                for (int64_t j = 0; j < nd; ++j) {
+                    double dj = pair_distance(xi, D + (size_t)j * (size_t)d, d, metric);
+                    if (cnt == kk && !before(dj, j, bd[kk - 1], bj[kk - 1])) continue;
+                    int p = (cnt < kk) ? cnt++ : kk - 1;
+                    while (p > 0 && before(dj, j, bd[p - 1], bj[p - 1])) {
+                        bd[p] = bd[p - 1];
+                        bj[p] = bj[p - 1];
+                        --p;
+                    }
+                    bd[p] = dj;
+                    bj[p] = j;
+                }
+                for (int c = 0; c < k; ++c) {
+                    idx[(size_t)qi * k + c] = (int32_t)bj[c];
+                    dist[(size_t)qi * k + c] = bd[c];
+                }
+                if (next) next[qi] = (kk > k) ? bd[k] : INFINITY;
+            }
+        }
+        free(bd);
+        free(bj);
+    }
+    return bad ? ORC_NO_MEM : ORC_OK;
+}
+
+/*
  * Per-row rho, sigma and directed weights (smooth kNN distances).
  * idx [n, k] int32, dist [n, k] double (ascending per row, as kNN returns).
  * Outputs rho[n], sigma[n], w[n, k]; iters[n] = bisection steps taken;

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -198,6 +199,98 @@ rsc_status conn_count_phase(const int32_t *idx, const float *dist, int64_t n, in
     return RSC_OK;
 }
 
+// ------------------------------------------------------------- batched plan
+
+struct BatchedPlan {
+    int64_t n = 0;
+    int d = 0, S = 0, kw = 0, kx = 0, metric = 0, DP = 0;
+    int64_t T = 0;
+};
+
+struct BatchedLayout {
+    unsigned int *status;
+    float *Y, *ny, *prep_scratch;
+    void *Qb, *Db;
+    void *tables;
+    int32_t *cand_w, *cand_x;
+};
+
+rsc_status plan_batched(int64_t n, int32_t d, const int64_t *off, int32_t S, int32_t kw, int32_t kx,
+                        int32_t metric, const rsc_knn_opts *o, BatchedPlan *p) {
+    rsc_knn_opts def = {};
+    if (!o) o = &def;
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(RSC_ERR_INVALID_ARG, "n=%lld out of [1, 2^31)", (long long)n);
+    if (metric != RSC_EUCLIDEAN && metric != RSC_COSINE) return fail(RSC_ERR_INVALID_ARG, "unknown metric %d", metric);
+    if (d < 1 || d + (metric == RSC_EUCLIDEAN ? 3 : 1) > 64)
+        return fail(d < 1 ? RSC_ERR_INVALID_ARG : RSC_ERR_UNSUPPORTED, "d=%d not supported by the batched search", d);
+    if (!off || S < 1) return fail(RSC_ERR_INVALID_ARG, "sample_offsets / n_samples");
+    if (kw < 1 || kw > kBatchedList) return fail(RSC_ERR_INVALID_ARG, "k_within=%d out of [1, %d]", kw, kBatchedList);
+    if (kx < 1 || kx > kBatchedShort || kx > kw)
+        return fail(RSC_ERR_INVALID_ARG, "k_cross=%d out of [1, min(%d, k_within)]", kx, kBatchedShort);
+    if ((int64_t)S * kx > 1024) return fail(RSC_ERR_INVALID_ARG, "n_samples * k_cross above 1024");
+    if (o->precision != RSC_BF16) return fail(RSC_ERR_UNSUPPORTED, "batched search runs BF16 candidates only");
+    if (o->reserved != 0) return fail(RSC_ERR_INVALID_ARG, "reserved option field must be 0");
+    if (off[0] != 0 || off[S] != n) return fail(RSC_ERR_INVALID_ARG, "sample_offsets must run from 0 to n");
+    for (int s = 0; s < S; ++s)
+        if (off[s + 1] - off[s] < kw) return fail(RSC_ERR_INVALID_ARG, "sample %d has fewer than k_within cells", s);
+    p->n = n;
+    p->d = d;
+    p->S = S;
+    p->kw = kw;
+    p->kx = kx;
+    p->metric = metric;
+    p->DP = ((d + (metric == RSC_COSINE ? 1 : 0) + 7) / 8) * 8;
+    p->T = batched_query_tiles(off, S);
+    if (p->T * S >= (int64_t(1) << 31)) return fail(RSC_ERR_UNSUPPORTED, "too many (tile, sample) work items");
+    return RSC_OK;
+}
+
+BatchedLayout carve_batched(void *ws, const BatchedPlan &p, size_t *bytes) {
+    Carve cv(ws);
+    BatchedLayout L;
+    L.status = cv.take<unsigned int>(kStatusBytes / sizeof(unsigned int));
+    L.Y = cv.take<float>((size_t)p.n * p.DP);
+    L.ny = cv.take<float>((size_t)p.n);
+    L.prep_scratch = cv.take<float>(prep_scratch_floats());
+    L.Qb = cv.take<uint16_t>((size_t)p.n * 64);
+    L.Db = cv.take<uint16_t>((size_t)p.n * 64);
+    L.tables = cv.take<uint8_t>(batched_tables_bytes((int)p.T, p.S));
+    L.cand_w = cv.take<int32_t>((size_t)kBatchedParts * p.n * kBatchedList);
+    L.cand_x = cv.take<int32_t>((size_t)p.n * p.S * kBatchedParts * kBatchedShort);
+    if (bytes) *bytes = cv.used;
+    return L;
+}
+
+rsc_status enqueue_batched(const float *X, const BatchedPlan &p, const BatchedLayout &L, const void *tables_host,
+                           int32_t *iw, float *dw, int32_t *ix, float *dx, cudaStream_t st) {
+    const int64_t n = p.n;
+    const int d = p.d, metric = p.metric;
+    RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
+    RSC_CUDA_TRY(cudaMemcpyAsync(L.tables, tables_host, batched_tables_bytes((int)p.T, p.S), cudaMemcpyHostToDevice, st));
+    RSC_CUDA_TRY(launch_prep_fp32(X, n, d, p.DP, metric, L.Y, L.ny, L.prep_scratch, st));
+    RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.Qb, L.Db, st));
+    RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, L.tables, L.cand_w, L.cand_x,
+                                       L.status, st));
+    const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
+    const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, kBatchedParts, p.kw, iw, dw, st));
+    RSC_CUDA_TRY(launch_rerank_cross(R, rs, n, d, metric, L.tables, p.S, (int)p.T, L.cand_x, iw, dw, p.kw, p.kx,
+                                     ix, dx, st));
+    return RSC_OK;
+}
+
+// CUDA graphs of the batched launch sequence, one per argument set.  The
+// host copy of the work tables lives in pinned memory owned by the entry so
+// that every replay re-uploads them (the workspace may have been reused).
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    void *tables_pinned = nullptr;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+constexpr size_t kMaxGraphs = 8;
+
 }  // namespace
 }  // namespace rsc
 
@@ -260,6 +353,92 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
     RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC, p.splits * p.parts, k, idx, dist, st));
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[3], st));
+    return RSC_OK;
+}
+
+rsc_status rsc_knn_batched_workspace_size(int64_t n, int32_t d, const int64_t *sample_offsets,
+                                          int32_t n_samples, int32_t k_within, int32_t k_cross,
+                                          int32_t metric, const rsc_knn_opts *opts, size_t *bytes) {
+    if (!bytes) return fail(RSC_ERR_INVALID_ARG, "bytes is NULL");
+    BatchedPlan p;
+    rsc_status s = plan_batched(n, d, sample_offsets, n_samples, k_within, k_cross, metric, opts, &p);
+    if (s != RSC_OK) return s;
+    carve_batched(nullptr, p, bytes);
+    return RSC_OK;
+}
+
+rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *sample_offsets,
+                           int32_t n_samples, int32_t k_within, int32_t k_cross, int32_t metric,
+                           int32_t *idx_within, float *dist_within, int32_t *idx_cross,
+                           float *dist_cross, const rsc_knn_opts *opts, void *workspace,
+                           size_t workspace_bytes) {
+    if (!X || !idx_within || !dist_within || !idx_cross || !dist_cross)
+        return fail(RSC_ERR_INVALID_ARG, "NULL array argument");
+    BatchedPlan p;
+    rsc_status s = plan_batched(n, d, sample_offsets, n_samples, k_within, k_cross, metric, opts, &p);
+    if (s != RSC_OK) return s;
+    size_t need = 0;
+    carve_batched(nullptr, p, &need);
+    if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
+    BatchedLayout L = carve_batched(workspace, p, nullptr);
+    cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+    const size_t tb = batched_tables_bytes((int)p.T, p.S);
+    if (st == nullptr) {   // legacy default stream cannot be captured: launch directly
+        std::vector<uint8_t> host(tb);
+        batched_fill_tables(sample_offsets, n_samples, host.data());
+        s = enqueue_batched(X, p, L, host.data(), idx_within, dist_within, idx_cross, dist_cross, st);
+        if (s == RSC_OK) RSC_CUDA_TRY(cudaStreamSynchronize(st));   // host table buffer goes out of scope
+        return s;
+    }
+    std::vector<uint64_t> key = {(uint64_t)X, (uint64_t)n, (uint64_t)d, (uint64_t)n_samples, (uint64_t)k_within,
+                                 (uint64_t)k_cross, (uint64_t)metric, (uint64_t)idx_within, (uint64_t)dist_within,
+                                 (uint64_t)idx_cross, (uint64_t)dist_cross, (uint64_t)workspace};
+    for (int i = 0; i <= n_samples; ++i) key.push_back((uint64_t)sample_offsets[i]);
+    int dev = 0;
+    RSC_CUDA_TRY(cudaGetDevice(&dev));
+    key.push_back((uint64_t)dev);
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto &g : g_graphs) {
+        if (g.key == key) {
+            RSC_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+            return RSC_OK;
+        }
+    }
+    GraphEntry e;
+    e.key = key;
+    RSC_CUDA_TRY(cudaHostAlloc(&e.tables_pinned, tb, cudaHostAllocDefault));
+    batched_fill_tables(sample_offsets, n_samples, e.tables_pinned);
+    RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {   // e.g. the caller is capturing this stream already
+        cudaGetLastError();
+        s = enqueue_batched(X, p, L, e.tables_pinned, idx_within, dist_within, idx_cross, dist_cross, st);
+        cudaStreamSynchronize(st);
+        cudaFreeHost(e.tables_pinned);
+        return s;
+    }
+    s = enqueue_batched(X, p, L, e.tables_pinned, idx_within, dist_within, idx_cross, dist_cross, st);
+    ce = cudaStreamEndCapture(st, &graph);
+    if (s != RSC_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaFreeHost(e.tables_pinned);
+        return s != RSC_OK ? s : fail(RSC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        cudaFreeHost(e.tables_pinned);
+        return fail(RSC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    }
+    if (g_graphs.size() >= kMaxGraphs) {   // evict the oldest entry
+        cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        cudaFreeHost(g_graphs.front().tables_pinned);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(e);
+    RSC_CUDA_TRY(cudaGraphLaunch(e.exec, st));
     return RSC_OK;
 }
 

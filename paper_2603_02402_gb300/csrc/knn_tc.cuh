@@ -1,0 +1,295 @@
+// Tensor-core candidate search kernel, shared by the whole-matrix and the
+// batched launches (the work-item policy decides what a CTA scans and
+// where it writes).  See knn_tc.cu for the design.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+#include "topk.cuh"
+
+namespace rsc {
+namespace tck {
+
+
+constexpr int BM = 128;              // query rows per item (TMEM lanes)
+constexpr int BN = 256;              // database rows per stage = accumulator columns
+constexpr int NBUF = 2;              // accumulators (NBUF x BN = 512 TMEM columns)
+constexpr int QBLK = BM * 128;       // bytes of one 128-row x 64-element bf16 query block
+constexpr int DBLK = BN * 128;       // bytes of one 256-row x 64-element bf16 database block
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks
+
+// EG epilogue warpgroups, each owning kCols = BN / EG columns of every tile;
+// KCP = top-k list length per (row, part).
+template <int KB, int KCP, int EG>
+struct Cfg {
+    static constexpr int kCols = BN / EG;
+    static constexpr int kEpiThreads = EG * 128;
+    static constexpr int kThreads = 64 + kEpiThreads;
+    static constexpr int kCap = (EG == 4) ? 24 : 32;         // buffer entries per thread
+    static constexpr int kQBytes = KB * QBLK;
+    static constexpr int kStageBytes = KB * DBLK;
+    static constexpr int kBufBytes = kCap * kEpiThreads * 8;
+    static constexpr int kBudget = 224 * 1024 - kQBytes - kBufBytes;
+    static constexpr int kStages = (kBudget / kStageBytes) > 6 ? 6 : (kBudget / kStageBytes);
+    static constexpr int kBarOff = kQBytes + kStages * kStageBytes + kBufBytes;
+    static constexpr int kSmem = kBarOff + 256 + 1024;       // barriers + alignment slack
+    static_assert(kStages >= 2, "shared memory too small for two stages");
+};
+
+// One work item: query rows [q0, q_end) (at most BM) against database rows
+// [j_begin, j_end).  short_list: only the best Work::kShort of each list are
+// needed (the threshold is the kShort-th key).
+struct WorkItem {
+    int64_t q0, q_end, j_begin, j_end;
+    int tag;
+    bool short_list;
+};
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023);
+    return reinterpret_cast<uint8_t *>(a);
+}
+
+template <int KB, int KCP, int EG, class Work>
+__global__ void __launch_bounds__(Cfg<KB, KCP, EG>::kThreads, 1)
+knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmD,
+              const Work work, unsigned int *status) {
+    using C = Cfg<KB, KCP, EG>;
+    constexpr int S = C::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    uint8_t *sQ = smem;
+    uint8_t *sD = smem + C::kQBytes;
+    float *bkey = reinterpret_cast<float *>(sD + S * C::kStageBytes);
+    int *bid = reinterpret_cast<int *>(bkey + C::kCap * C::kEpiThreads);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kBarOff);
+    uint64_t *full = bars;                     // [S]     database stage loaded
+    uint64_t *empty = bars + S;                // [S]     database stage consumed
+    uint64_t *acc_full = bars + 2 * S;         // [NBUF]  accumulator ready
+    uint64_t *acc_empty = acc_full + NBUF;     // [NBUF]  accumulator drained
+    uint64_t *q_full = acc_empty + NBUF;
+    uint64_t *q_empty = q_full + 1;
+    uint64_t *mma_done = q_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(q_full + 3);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_items = work.count();
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < NBUF; ++a) {
+            tc::mbar_init(&acc_full[a], 1);
+            tc::mbar_init(&acc_empty[a], C::kEpiThreads / 32);
+        }
+        tc::mbar_init(q_full, 1);
+        tc::mbar_init(q_empty, 1);
+        tc::mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tc::prefetch_tensormap(&tmQ);
+        tc::prefetch_tensormap(&tmD);
+    }
+    if (warp == 1) tc::tmem_alloc<kTmemCols>(tmem_slot);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    // bounded wait: false on timeout (recorded) or when another role aborted
+    auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        const long long t0 = clock64();
+        while (true) {
+            if (tc::mbar_try_wait(bar, parity)) return true;
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kWaitBudget) {
+                *abort_flag = 1;
+                record_status(status, RSC_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    };
+    // bounded wait that ignores the abort flag (draining in-flight work)
+    auto drain = [&](uint64_t *bar, uint32_t parity) {
+        const long long t0 = clock64();
+        while (!tc::mbar_try_wait(bar, parity)) {
+            if (clock64() - t0 > kWaitBudget) {
+                record_status(status, RSC_ERR_TIMEOUT);
+                return;
+            }
+        }
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------ TMA producer
+            uint32_t gt = 0;
+            int item_no = 0;
+            bool ok = true, q_issued = false;
+            uint32_t q_parity = 0;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++item_no) {
+                const WorkItem wi = work.get(it);
+                const int64_t j_begin = wi.j_begin, j_end = wi.j_end;
+                if (!(ok = wait(q_empty, (item_no & 1) ^ 1))) break;
+                tc::mbar_arrive_expect_tx(q_full, C::kQBytes);
+                for (int kb = 0; kb < KB; ++kb)
+                    tc::tma_load_2d(sQ + kb * QBLK, &tmQ, kb * 64, (int)wi.q0, q_full);
+                q_issued = true;
+                q_parity = item_no & 1;
+                for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
+                    const int s = gt % S;
+                    const uint32_t u = gt / S;
+                    if (!(ok = wait(&empty[s], (u & 1) ^ 1))) break;
+                    tc::mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+                    for (int kb = 0; kb < KB; ++kb)
+                        tc::tma_load_2d(sD + (s * KB + kb) * DBLK, &tmD, kb * 64, (int)j0, &full[s]);
+                }
+            }
+            if (!ok) {
+                // let every copy this thread started land before the CTA exits
+                const uint32_t first = gt > (uint32_t)S ? gt - S : 0;
+                for (uint32_t t = first; t < gt; ++t) drain(&full[t % S], (t / S) & 1);
+                if (q_issued) drain(q_full, q_parity);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------------------------ MMA issuer
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            uint32_t gt = 0;
+            int item_no = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++item_no) {
+                const WorkItem wi = work.get(it);
+                const int64_t j_begin = wi.j_begin, j_end = wi.j_end;
+                if (!(ok = wait(q_full, item_no & 1))) break;
+                tc::tc_fence_after();
+                for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
+                    const int s = gt % S;
+                    const uint32_t u = gt / S;
+                    const uint32_t b = gt % NBUF, v = gt / NBUF;
+                    if (!(ok = wait(&acc_empty[b], (v & 1) ^ 1))) break;
+                    if (!(ok = wait(&full[s], u & 1))) break;
+                    tc::tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + b * BN;
+#pragma unroll
+                    for (int kb = 0; kb < KB; ++kb) {
+                        const uint32_t a_addr = tc::smem_u32(sQ + kb * QBLK);
+                        const uint32_t b_addr = tc::smem_u32(sD + (s * KB + kb) * DBLK);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            tc::mma_bf16(d_tmem, tc::smem_desc_sw128(a_addr + kk * 32),
+                                         tc::smem_desc_sw128(b_addr + kk * 32), idesc, (kb | kk) != 0);
+                        }
+                    }
+                    tc::mma_commit(&acc_full[b]);   // accumulator ready for the epilogue
+                    tc::mma_commit(&empty[s]);      // stage reusable once these MMAs finish
+                }
+                if (!ok) break;
+                tc::mma_commit(q_empty);            // query tile reusable
+            }
+            tc::mma_commit(mma_done);
+            drain(mma_done, 0);
+        }
+    } else {
+        // ---------------------------------------------------- epilogue
+        const int e = warp - 2;
+        const int part = e >> 2;              // column part of every tile this warp reads
+        const int quarter = warp & 3;         // TMEM lane quarter this warp may access
+        const int r = quarter * 32 + lane;    // query row within the item
+        const uint32_t lane_bits = (uint32_t)(quarter * 32) << 16;
+        const int et = threadIdx.x - 64;
+        const int cbeg = part * C::kCols;
+        BufferedTopK<KCP, C::kCap, Work::kShort> tk;
+        tk.init(bkey, bid, et, C::kEpiThreads);
+
+        uint32_t gt = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const WorkItem wi = work.get(it);
+            const int64_t j_begin = wi.j_begin, j_end = wi.j_end;
+            tk.reset();
+            tk.shortl = wi.short_list;
+            for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
+                const uint32_t b = gt % NBUF, v = gt / NBUF;
+                ok = wait(&acc_full[b], v & 1);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc::tc_fence_after();
+                const uint32_t tbase = tmem_base + lane_bits + b * BN + cbeg;
+                const int valid = ((j_end - j0 < BN) ? (int)(j_end - j0) : BN) - cbeg;
+#pragma unroll 1
+                for (int c0 = 0; c0 < C::kCols; c0 += 32) {
+                    float vv[32];
+                    __syncwarp();
+                    tc::tmem_ld32(tbase + c0, vv);
+                    tc::tmem_wait_ld();
+                    if (c0 + 32 == C::kCols) {
+                        // last load of this accumulator part: hand it back to the MMA warp
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+                    }
+                    if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (c0 + i >= valid) vv[i] = INFINITY;
+                    }
+                    float lo[16], hi[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        lo[i] = vv[i];
+                        hi[i] = vv[16 + i];
+                    }
+                    tk.offer16(lo, (int)(j0 + cbeg + c0));
+                    tk.offer16(hi, (int)(j0 + cbeg + c0 + 16));
+                }
+            }
+            if (!ok) break;
+            tk.flush();
+            const int64_t q = wi.q0 + r;
+            if (q < wi.q_end) work.template emit<EG>(wi, part, q, tk.list);
+        }
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tc::tmem_dealloc<kTmemCols>(tmem_base);
+    }
+}
+
+template <int KB, int KCP, int EG, class Work>
+cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, const Work &work, unsigned int *status,
+                          cudaStream_t st) {
+    using C = Cfg<KB, KCP, EG>;
+    auto kern = knn_tc_kernel<KB, KCP, EG, Work>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t items = work.count_host();
+    if (items <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>(items, sm_count());
+    kern<<<grid, C::kThreads, C::kSmem, st>>>(mq, md, work, status);
+    return cudaGetLastError();
+}
+
+cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB, int box_rows);
+
+}  // namespace tck
+}  // namespace rsc

@@ -58,13 +58,17 @@ struct RowTopK {
 // instead of one lane at a time.  A lane's threshold is only refreshed at
 // merges; a stale (higher) threshold admits extra candidates but never drops
 // one of the KC best, because thresholds only decrease.
-template <int KC, int CAP>
+//
+// SHORT > 0: when `shortl` is set only the best SHORT entries are wanted, so
+// the filtering threshold is the SHORT-th key (the list still keeps KC).
+template <int KC, int CAP, int SHORT = 0>
 struct BufferedTopK {
     RowTopK<KC> list;
     float *bkey;
     int *bid;
     int stride;
     int cnt;
+    bool shortl;
 
     __device__ __forceinline__ void init(float *keys, int *ids, int thread, int nthreads) {
         list.init();
@@ -72,11 +76,17 @@ struct BufferedTopK {
         bid = ids + thread;
         stride = nthreads;
         cnt = 0;
+        shortl = false;
     }
 
     __device__ __forceinline__ void reset() {
         list.init();
         cnt = 0;
+    }
+
+    __device__ __forceinline__ float bound() const {
+        if constexpr (SHORT > 0 && SHORT < KC) return shortl ? list.key[SHORT - 1] : list.key[KC - 1];
+        else return list.thr();
     }
 
     // Merge every lane's buffer into its list (warp-synchronous).
@@ -85,7 +95,7 @@ struct BufferedTopK {
         for (int e = 0; e < rounds; ++e) {
             if (e < cnt) {
                 const float v = bkey[e * stride];
-                if (v < list.thr()) list.insert(v, bid[e * stride]);
+                if (v < bound()) list.insert(v, bid[e * stride]);
             }
         }
         cnt = 0;
@@ -108,10 +118,10 @@ struct BufferedTopK {
         static_assert(CAP >= 16, "buffer smaller than a chunk");
         const float m_lo = fmin3(fmin3(v[0], v[1], v[2]), fmin3(v[3], v[4], v[5]), fminf(v[6], v[7]));
         const float m_hi = fmin3(fmin3(v[8], v[9], v[10]), fmin3(v[11], v[12], v[13]), fminf(v[14], v[15]));
-        const bool hit = fminf(m_lo, m_hi) < list.thr();
+        const bool hit = fminf(m_lo, m_hi) < bound();
         if (__any_sync(0xffffffffu, hit)) {
             if (__any_sync(0xffffffffu, hit && cnt > CAP - 16)) flush();
-            const float t = list.thr();
+            const float t = bound();
             if (m_lo < t) append<8>(v, j0, t);
             if (m_hi < t) append<8>(v + 8, j0 + 8, t);
         }

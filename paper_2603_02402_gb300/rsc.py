@@ -50,6 +50,10 @@ SIGNATURES = {
     "rsc_workspace_status": (_i32, [_vp, _vp]),
     "rsc_knn_workspace_size": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(_sz)]),
     "rsc_knn": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(rsc_knn_opts), _vp, _sz]),
+    "rsc_knn_batched_workspace_size": (_i32, [_i64, _i32, _vp, _i32, _i32, _i32, _i32,
+                                               ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(_sz)]),
+    "rsc_knn_batched": (_i32, [_vp, _i64, _i32, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
+                                ctypes.POINTER(rsc_knn_opts), _vp, _sz]),
     "rsc_connectivities_workspace_size": (_i32, [_i64, _i32, ctypes.POINTER(_sz)]),
     "rsc_connectivities_max_nnz": (_i64, [_i64, _i32]),
     "rsc_connectivities": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
@@ -147,6 +151,51 @@ def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candi
     _check(lib().rsc_knn(_ptr(X), n, d, k, m, _ptr(idx), _ptr(dist), ctypes.byref(o), _ptr(ws),
                          ws.numel()))
     return idx, dist
+
+
+def _offsets_host(sample_offsets):
+    import numpy as np
+    off = np.ascontiguousarray(np.asarray(sample_offsets, dtype=np.int64))
+    return off, off.ctypes.data_as(ctypes.c_void_p)
+
+
+def rsc_knn_batched_workspace_size(n, d, sample_offsets, k_within, k_cross, metric="euclidean",
+                                   precision="bf16") -> int:
+    off, optr = _offsets_host(sample_offsets)
+    o = rsc_knn_opts(_PRECISIONS[precision], 0, 0, 0, None, None)
+    out = _sz(0)
+    _check(lib().rsc_knn_batched_workspace_size(n, d, optr, len(off) - 1, k_within, k_cross,
+                                                _METRICS.get(metric, metric), ctypes.byref(o), ctypes.byref(out)))
+    return int(out.value)
+
+
+def rsc_knn_batched(X: torch.Tensor, sample_offsets, k_within: int, k_cross: int, metric="euclidean",
+                    precision="bf16", stream=None, workspace=None, out=None):
+    """Per-sample kNN and k_cross nearest from every sample (host offsets).
+
+    Returns (idx_within [n, k_within], dist_within, idx_cross [n, S * k_cross], dist_cross).
+    """
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()):
+        raise ValueError("X must be a contiguous float32 [n, d] CUDA tensor")
+    n, d = X.shape
+    off, optr = _offsets_host(sample_offsets)
+    S = len(off) - 1
+    m = _METRICS[metric] if isinstance(metric, str) else int(metric)
+    o = knn_opts(precision, 0, 0, stream)
+    need = _sz(0)
+    _check(lib().rsc_knn_batched_workspace_size(n, d, optr, S, k_within, k_cross, m, ctypes.byref(o),
+                                                ctypes.byref(need)))
+    ws = _workspace(need.value, X.device, workspace)
+    if out is None:
+        iw = torch.empty((n, k_within), dtype=torch.int32, device=X.device)
+        dw = torch.empty((n, k_within), dtype=torch.float32, device=X.device)
+        ix = torch.empty((n, S * k_cross), dtype=torch.int32, device=X.device)
+        dx = torch.empty((n, S * k_cross), dtype=torch.float32, device=X.device)
+    else:
+        iw, dw, ix, dx = out
+    _check(lib().rsc_knn_batched(_ptr(X), n, d, optr, S, k_within, k_cross, m, _ptr(iw), _ptr(dw), _ptr(ix),
+                                 _ptr(dx), ctypes.byref(o), _ptr(ws), ws.numel()))
+    return iw, dw, ix, dx
 
 
 def rsc_connectivities_workspace_size(n: int, k: int) -> int:

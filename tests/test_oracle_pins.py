@@ -301,3 +301,37 @@ def test_union_hub_row():
     deg = np.diff(s["indptr"])
     assert deg[0] == 40
     assert (s["indices"][:40] == np.arange(1, 41)).all()
+
+
+def test_knn_qd_matches_kdtree_and_self_join():
+    X = synth.mixture(2500, 50, n_comp=10, seed=21)
+    Q = synth.mixture(300, 50, n_comp=10, seed=22)
+    idx, dist, nxt = oracle.knn_qd(Q, X, 9)
+    tree = scipy_spatial.cKDTree(X.astype(np.float64))
+    dd, ii = tree.query(Q.astype(np.float64), k=10)
+    np.testing.assert_array_equal(idx, ii[:, :9])
+    np.testing.assert_allclose(dist, dd[:, :9], rtol=1e-12)
+    # querying a set against itself is the self-join
+    si, sd, _ = oracle.knn(X, 9)
+    qi, qd, _ = oracle.knn_qd(X, X, 9)
+    np.testing.assert_array_equal(si, qi)
+    np.testing.assert_array_equal(sd, qd)
+
+
+def test_batched_oracle_by_brute_force():
+    X = synth.mixture(120, 5, n_comp=3, seed=23)
+    off = np.array([0, 30, 70, 120])
+    wi, wd, xi, xd = oracle.batched_knn(X, off, 4, 2)
+    D = np.sqrt(((X[:, None, :].astype(np.float64) - X[None, :, :]) ** 2).sum(-1))
+    for q in range(len(X)):
+        s = np.searchsorted(off, q, side="right") - 1
+        cols = np.arange(off[s], off[s + 1])
+        order = cols[np.lexsort((cols, D[q, cols]))][:4]
+        assert wi[q].tolist() == order.tolist()
+        exp = []
+        for t in range(3):
+            c = np.arange(off[t], off[t + 1])
+            exp += c[np.lexsort((c, D[q, c]))][:2].tolist()
+        exp = sorted(exp, key=lambda j: (D[q, j], j))
+        assert xi[q].tolist() == exp
+        np.testing.assert_allclose(xd[q], D[q, exp], rtol=1e-12)
