@@ -88,3 +88,35 @@ def test_batched_legacy_stream_and_k_limits(rsc):
         rsc.rsc_knn_batched(torch.from_numpy(X).cuda(), off, 15, 5)
     with pytest.raises(rsc.RscError):
         rsc.rsc_knn_batched(torch.from_numpy(X).cuda(), [0, 10, len(X)], 15, 3)   # sample smaller than k
+
+
+def test_batched_full_size_sampled(rsc):
+    # the 64-sample, ~3M-cell workload: a seeded sample of rows against the oracle
+    sizes = synth.batched_sizes(64, seed=0)
+    X, off = synth.batched(sizes, d=50, n_comp=30, seed=0)
+    n = len(X)
+    Xd = torch.from_numpy(X).cuda()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        gi, gd, gxi, gxd = [t.cpu().numpy() for t in rsc.rsc_knn_batched(Xd, off, 15, 3, stream=stream)]
+    q = synth.query_sample(n, 60, seed=3)
+    samp = np.searchsorted(off, q, side="right") - 1
+    OI = np.empty((len(q), 15), dtype=np.int32)
+    OD = np.empty((len(q), 15))
+    for i, (r, s) in enumerate(zip(q, samp)):
+        a, b = off[s], off[s + 1]
+        oi, od, _ = oracle.knn_qd(X[r:r + 1], X[a:b], 15)
+        OI[i], OD[i] = oi[0] + a, od[0]
+    check_knn(X, gi[q], gd[q], OI, OD, np.full(len(q), np.inf), rows=q, allow_miss=1e-3)
+    # cross lists of the sample rows, from every sample
+    exp_d = []
+    for t in range(64):
+        a, b = off[t], off[t + 1]
+        _, od, _ = oracle.knn_qd(X[q], X[a:b], 3)
+        exp_d.append(od)
+    exp_d = np.sort(np.concatenate(exp_d, axis=1), axis=1)
+    assert _recall(gxi[q], gxd[q], None, exp_d) >= 0.999
+    dex = exact_distances(X, q, gxi[q], "euclidean")
+    np.testing.assert_allclose(gxd[q], dex, rtol=1e-5, atol=1e-6)
+    row_ok = np.all(np.abs(gxd[q] - exp_d) <= 1e-5 * exp_d + 1e-6, axis=1)
+    assert row_ok.mean() >= 0.95
