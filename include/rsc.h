@@ -191,6 +191,31 @@ rsc_status rsc_connectivities(const int32_t *idx, const float *dist, int64_t n, 
                               void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * rsc_connectivities without a caller workspace and without allocating.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot hand out device memory when they build the graph, such as a host
+ * application whose own pool has reserved the device's memory and offers
+ * plug-ins no allocation hook, or a service with a fixed device-memory budget
+ * that may not grow after start-up.  Same arguments and results as
+ * rsc_connectivities, except:
+ *   - scratch comes from a 32 MiB array declared by the library (held by
+ *     every GPU that loads the library until the process exits); problems
+ *     whose rsc_connectivities_workspace_size exceeds 32 MiB are rejected
+ *     with RSC_ERR_WORKSPACE (k = 15: up to about 150,000 rows);
+ *   - nnz_capacity must be at least rsc_connectivities_max_nnz(n, k), so the
+ *     call never synchronises to check the size;
+ *   - the first call on a device looks up the array's device address (a
+ *     host-side query, done once per device).
+ * All calls share the one array: calls whose work overlaps on the GPU (on
+ * different streams, or from different host threads) race and corrupt each
+ * other's results.  Issue them on one stream, or order them.  The call itself
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+rsc_status rsc_connectivities_static(const int32_t *idx, const float *dist, int64_t n, int32_t k,
+                                     int64_t *indptr, int32_t *indices, float *data,
+                                     int64_t nnz_capacity, float *rho, float *sigma, void *stream);
+
+/*
  * Number of stored entries rsc_connectivities would produce, written to
  * *nnz (host).  Synchronises `stream`.
  */

@@ -58,6 +58,7 @@ SIGNATURES = {
     "rsc_connectivities_max_nnz": (_i64, [_i64, _i32]),
     "rsc_connectivities": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rsc_connectivities_nnz": (_i32, [_vp, _vp, _i64, _i32, ctypes.POINTER(_i64), _vp, _sz, _vp]),
+    "rsc_connectivities_static": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
 }
 
 
@@ -241,3 +242,26 @@ def rsc_connectivities_nnz(idx: torch.Tensor, dist: torch.Tensor, stream=None, w
     _check(lib().rsc_connectivities_nnz(_ptr(idx), _ptr(dist), n, k, ctypes.byref(out), _ptr(ws), ws.numel(),
                                         _stream(stream)))
     return int(out.value)
+
+
+def rsc_connectivities_static(idx: torch.Tensor, dist: torch.Tensor, stream=None, out=None):
+    """rsc_connectivities with the library's fixed 32 MiB scratch (no workspace,
+    no allocation inside the call; outputs are allocated here unless given).
+
+    Returns (indptr, indices, data, rho, sigma) like rsc_connectivities.
+    """
+    if not (idx.is_cuda and dist.is_cuda and idx.dtype == torch.int32 and dist.dtype == torch.float32):
+        raise ValueError("idx int32 / dist float32 CUDA tensors expected")
+    idx, dist = idx.contiguous(), dist.contiguous()
+    n, k = idx.shape
+    cap = rsc_connectivities_max_nnz(n, k)
+    if out is None:
+        out = (torch.empty(n + 1, dtype=torch.int64, device=idx.device),
+               torch.empty(max(cap, 1), dtype=torch.int32, device=idx.device),
+               torch.empty(max(cap, 1), dtype=torch.float32, device=idx.device),
+               torch.empty(n, dtype=torch.float32, device=idx.device),
+               torch.empty(n, dtype=torch.float32, device=idx.device))
+    indptr, indices, data, rho, sigma = out
+    _check(lib().rsc_connectivities_static(_ptr(idx), _ptr(dist), n, k, _ptr(indptr), _ptr(indices), _ptr(data),
+                                           cap, _ptr(rho), _ptr(sigma), _stream(stream)))
+    return indptr, indices, data, rho, sigma
