@@ -71,7 +71,8 @@ typedef struct {
                             rounded up to a supported width (16, 32, 64)  */
     int32_t db_splits;   /* split the database into this many ranges handled
                             by separate CTAs (small n); 0 = automatic          */
-    int32_t reserved;    /* must be 0                                           */
+    int32_t tc_parts;    /* tensor-core path: threads (column parts) per query
+                            row, 2 or 4; 0 = automatic                          */
     void *stream;        /* cudaStream_t                                        */
     void *phase_events;  /* optional host array of 4 cudaEvent_t owned by the
                             caller, recorded on `stream` before the prep pass,
@@ -116,6 +117,52 @@ rsc_status rsc_knn_workspace_size(int64_t n, int32_t d, int32_t k, int32_t metri
 rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metric,
                    int32_t *idx, float *dist, const rsc_knn_opts *opts,
                    void *workspace, size_t workspace_bytes);
+
+/*
+ * Autotuner.  Options left at 0 (db_splits, candidates, tc_parts) are
+ * "automatic": rsc_knn and rsc_knn_batched then look up a process-wide table
+ * of tuned choices keyed by (entry point, precision, metric, d, k, k_cross,
+ * floor(log2 n)), and fall back to built-in defaults when it has no entry.
+ * The rsc_autotune_* calls fill that table by timing the candidate
+ * configurations (database splits, column parts per row, candidate list
+ * widths; every candidate keeps the result exact by construction) on the
+ * caller's own data with CUDA events on opts->stream, keeping the fastest.
+ * They synchronise the stream and leave the result of the last timed run in
+ * the output arrays.
+ */
+
+/* Workspace large enough for every configuration rsc_autotune_knn tries. */
+rsc_status rsc_autotune_workspace_size(int64_t n, int32_t d, int32_t k, int32_t metric,
+                                       int32_t precision, size_t *bytes);
+
+/*
+ * Tune rsc_knn for (n, d, k, metric, opts->precision): `trials` timed runs
+ * per configuration (>= 1).  On return *best (host) holds the chosen options
+ * (stream and precision copied from opts) and *best_ms (host, may be NULL)
+ * its time; the choice is stored in the table.
+ */
+rsc_status rsc_autotune_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metric,
+                            const rsc_knn_opts *opts, int32_t trials, int32_t *idx, float *dist,
+                            rsc_knn_opts *best, float *best_ms, void *workspace,
+                            size_t workspace_bytes);
+
+/*
+ * Tune rsc_knn_batched (column parts per row) the same way; the workspace is
+ * sized by rsc_knn_batched_workspace_size with automatic options.
+ */
+rsc_status rsc_autotune_knn_batched(const float *X, int64_t n, int32_t d,
+                                    const int64_t *sample_offsets, int32_t n_samples,
+                                    int32_t k_within, int32_t k_cross, int32_t metric,
+                                    const rsc_knn_opts *opts, int32_t trials,
+                                    int32_t *idx_within, float *dist_within, int32_t *idx_cross,
+                                    float *dist_cross, rsc_knn_opts *best, float *best_ms,
+                                    void *workspace, size_t workspace_bytes);
+
+/* Persist / restore / empty the tuned table (plain text, one entry per line;
+ * host only). */
+rsc_status rsc_autotune_save(const char *path);
+rsc_status rsc_autotune_load(const char *path);
+rsc_status rsc_autotune_clear(void);
 
 /*
  * Minimum workspace for rsc_knn_batched (host query; no GPU work).

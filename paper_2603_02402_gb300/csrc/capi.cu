@@ -81,7 +81,19 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     if (o->precision != RSC_FP32 && o->precision != RSC_BF16)
         return fail(RSC_ERR_INVALID_ARG, "unknown precision %d", o->precision);
     if (o->candidates < 0 || o->db_splits < 0) return fail(RSC_ERR_INVALID_ARG, "negative option");
-    if (o->reserved != 0) return fail(RSC_ERR_INVALID_ARG, "reserved option field must be 0");
+    if (o->tc_parts != 0 && o->tc_parts != 2 && o->tc_parts != 4)
+        return fail(RSC_ERR_INVALID_ARG, "tc_parts=%d (0, 2 or 4)", o->tc_parts);
+    rsc_knn_opts tuned;
+    if (o->db_splits == 0 && o->candidates == 0 && o->tc_parts == 0) {   // automatic: tuned table first
+        TunedChoice c;
+        if (tuned_lookup(0, o->precision, metric, d, k, 0, n, &c)) {
+            tuned = *o;
+            tuned.db_splits = c.db_splits;
+            tuned.candidates = c.candidates;
+            tuned.tc_parts = c.tc_parts;
+            o = &tuned;
+        }
+    }
     p->precision = o->precision;
     p->d = d;
     p->metric = metric;
@@ -101,7 +113,7 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     p->parts = 1;
     if (tc) {
         if (!knn_tc_supported(d, metric)) return fail(RSC_ERR_UNSUPPORTED, "no tensor-core kernel for d=%d", d);
-        TcShape sh = knn_tc_shape(d, metric, k, want);
+        TcShape sh = knn_tc_shape(d, metric, k, want, o->tc_parts);
         if (sh.parts == 0) return fail(RSC_ERR_UNSUPPORTED, "no tensor-core list shape for k=%d candidates=%d", k, want);
         p->parts = sh.parts;
         p->KC = sh.list;
@@ -204,6 +216,7 @@ rsc_status conn_count_phase(const int32_t *idx, const float *dist, int64_t n, in
 struct BatchedPlan {
     int64_t n = 0;
     int d = 0, S = 0, kw = 0, kx = 0, metric = 0, DP = 0;
+    int parts = 4;      // threads (column parts) per query row
     int64_t T = 0;
 };
 
@@ -229,7 +242,13 @@ rsc_status plan_batched(int64_t n, int32_t d, const int64_t *off, int32_t S, int
         return fail(RSC_ERR_INVALID_ARG, "k_cross=%d out of [1, min(%d, k_within)]", kx, kBatchedShort);
     if ((int64_t)S * kx > 1024) return fail(RSC_ERR_INVALID_ARG, "n_samples * k_cross above 1024");
     if (o->precision != RSC_BF16) return fail(RSC_ERR_UNSUPPORTED, "batched search runs BF16 candidates only");
-    if (o->reserved != 0) return fail(RSC_ERR_INVALID_ARG, "reserved option field must be 0");
+    if (o->tc_parts != 0 && o->tc_parts != 2 && o->tc_parts != 4)
+        return fail(RSC_ERR_INVALID_ARG, "tc_parts=%d (0, 2 or 4)", o->tc_parts);
+    p->parts = o->tc_parts;
+    if (p->parts == 0) {
+        TunedChoice c;
+        p->parts = tuned_lookup(1, o->precision, metric, d, kw, kx, n, &c) ? c.tc_parts : 4;
+    }
     if (off[0] != 0 || off[S] != n) return fail(RSC_ERR_INVALID_ARG, "sample_offsets must run from 0 to n");
     for (int s = 0; s < S; ++s)
         if (off[s + 1] - off[s] < kw) return fail(RSC_ERR_INVALID_ARG, "sample %d has fewer than k_within cells", s);
@@ -255,6 +274,7 @@ BatchedLayout carve_batched(void *ws, const BatchedPlan &p, size_t *bytes) {
     L.Qb = cv.take<uint16_t>((size_t)p.n * 64);
     L.Db = cv.take<uint16_t>((size_t)p.n * 64);
     L.tables = cv.take<uint8_t>(batched_tables_bytes((int)p.T, p.S));
+    // sized for the widest part count, so a tuned choice always fits
     L.cand_w = cv.take<int32_t>((size_t)kBatchedParts * p.n * kBatchedList);
     L.cand_x = cv.take<int32_t>((size_t)p.n * p.S * kBatchedParts * kBatchedShort);
     if (bytes) *bytes = cv.used;
@@ -269,13 +289,13 @@ rsc_status enqueue_batched(const float *X, const BatchedPlan &p, const BatchedLa
     RSC_CUDA_TRY(cudaMemcpyAsync(L.tables, tables_host, batched_tables_bytes((int)p.T, p.S), cudaMemcpyHostToDevice, st));
     RSC_CUDA_TRY(launch_prep_fp32(X, n, d, p.DP, metric, L.Y, L.ny, L.prep_scratch, st));
     RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.Qb, L.Db, st));
-    RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, L.tables, L.cand_w, L.cand_x,
-                                       L.status, st));
+    RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.parts, L.tables, L.cand_w,
+                                       L.cand_x, L.status, st));
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, kBatchedParts, p.kw, iw, dw, st));
-    RSC_CUDA_TRY(launch_rerank_cross(R, rs, n, d, metric, L.tables, p.S, (int)p.T, L.cand_x, iw, dw, p.kw, p.kx,
-                                     ix, dx, st));
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, p.parts, p.kw, iw, dw, st));
+    RSC_CUDA_TRY(launch_rerank_cross(R, rs, n, d, metric, L.tables, p.S, (int)p.T, p.parts, L.cand_x, iw, dw, p.kw,
+                                     p.kx, ix, dx, st));
     return RSC_OK;
 }
 
@@ -392,7 +412,8 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
     }
     std::vector<uint64_t> key = {(uint64_t)X, (uint64_t)n, (uint64_t)d, (uint64_t)n_samples, (uint64_t)k_within,
                                  (uint64_t)k_cross, (uint64_t)metric, (uint64_t)idx_within, (uint64_t)dist_within,
-                                 (uint64_t)idx_cross, (uint64_t)dist_cross, (uint64_t)workspace};
+                                 (uint64_t)idx_cross, (uint64_t)dist_cross, (uint64_t)workspace,
+                                 (uint64_t)p.parts};
     for (int i = 0; i <= n_samples; ++i) key.push_back((uint64_t)sample_offsets[i]);
     int dev = 0;
     RSC_CUDA_TRY(cudaGetDevice(&dev));

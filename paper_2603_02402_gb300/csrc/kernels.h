@@ -36,7 +36,7 @@ struct TcShape {
     int list;    // ids per list
 };
 int tc_kb(int d, int metric);
-TcShape knn_tc_shape(int d, int metric, int k, int want);
+TcShape knn_tc_shape(int d, int metric, int k, int want, int parts_req);
 bool knn_tc_supported(int d, int metric);
 int64_t knn_tc_split_align();
 cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, void *Qb, void *Db,
@@ -46,8 +46,9 @@ cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int 
 
 // ---- knn_tc_batched.cu ---------------------------------------------------------
 // Batched search: one launch over (query tile of a sample) x (database sample)
-// items.  Within lists: [4, N, kBatchedList] (re-ranked by launch_rerank with
-// 4 splits); cross lists: [N, S, 16] (re-ranked by launch_rerank_cross).
+// items, parts (2 or 4) threads per query row.  Within lists:
+// [parts, N, kBatchedList] (re-ranked by launch_rerank with parts splits);
+// cross lists: [N, S, parts * kBatchedShort] (re-ranked by launch_rerank_cross).
 constexpr int kBatchedList = 16;      // within-sample ids per (row, part); k_within <= 16
 constexpr int kBatchedShort = 4;      // cross-sample ids per (row, sample, part); k_cross <= 4
 constexpr int kBatchedParts = 4;
@@ -55,11 +56,20 @@ size_t batched_tables_bytes(int T, int S);
 int64_t batched_query_tiles(const int64_t *offsets_host, int S);
 void batched_fill_tables(const int64_t *offsets_host, int S, void *host_buf);
 cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                  const void *tables_dev, int32_t *cand_w, int32_t *cand_x, unsigned int *status,
-                                  cudaStream_t st);
+                                  int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
+                                  unsigned int *status, cudaStream_t st);
 cudaError_t launch_rerank_cross(const float *R, int64_t rs, int64_t N, int d, int metric, const void *tables_dev,
-                                int S, int T, const int32_t *cand_x, const int32_t *idx_w, const float *dist_w,
-                                int k_within, int k_cross, int32_t *idx_x, float *dist_x, cudaStream_t st);
+                                int S, int T, int parts, const int32_t *cand_x, const int32_t *idx_w,
+                                const float *dist_w, int k_within, int k_cross, int32_t *idx_x, float *dist_x,
+                                cudaStream_t st);
+
+// ---- autotune.cu --------------------------------------------------------------
+// Tuned-choice table consulted when options are automatic (all zero).
+struct TunedChoice {
+    int db_splits, candidates, tc_parts;
+};
+bool tuned_lookup(int kind, int precision, int metric, int d, int k, int kx, int64_t n, TunedChoice *out);
+void tuned_store(int kind, int precision, int metric, int d, int k, int kx, int64_t n, const TunedChoice &c);
 
 // ---- rerank.cu ------------------------------------------------------------
 // Exact re-rank: every candidate of query q (splits * KC ids, split s at

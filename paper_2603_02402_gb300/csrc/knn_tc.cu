@@ -164,10 +164,13 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB, int
 
 int tc_kb(int d, int metric) { return (d + (metric == RSC_EUCLIDEAN ? 3 : 1) <= 64) ? 1 : 2; }
 
-TcShape knn_tc_shape(int d, int metric, int k, int want) {
+TcShape knn_tc_shape(int d, int metric, int k, int want, int parts_req) {
     // each part's list must be able to hold the whole top-k (all of it may
     // fall in one part), and parts x list >= the requested candidate count
-    if (tc_kb(d, metric) == 1 && k <= 16 && want <= 64) return TcShape{4, 16};
+    const bool four_ok = tc_kb(d, metric) == 1 && k <= 16 && want <= 64;
+    if (parts_req == 4) return four_ok ? TcShape{4, 16} : TcShape{0, 0};
+    if (parts_req == 0 && four_ok) return TcShape{4, 16};
+    if (parts_req != 0 && parts_req != 2) return TcShape{0, 0};
     for (int list : {16, 32, 64})
         if (list >= k && 2 * list >= want) return TcShape{2, list};
     return TcShape{0, 0};

@@ -66,7 +66,6 @@ struct BatchedWork {
 namespace {
 
 constexpr int kXWarps = 4;
-constexpr int kXCand = 4 * tck::BatchedWork::kShort;   // candidates per (query, sample): parts x kShort
 
 __device__ __forceinline__ bool pair_gt(float ka, int ia, float kb, int ib) {
     return ka > kb || (ka == kb && ia > ib);
@@ -80,7 +79,8 @@ __global__ void __launch_bounds__(kXWarps * 32)
 rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, int metric,
                     const int64_t *__restrict__ samp_off, int S, const int32_t *__restrict__ cand_x,
                     const int32_t *__restrict__ idx_w, const float *__restrict__ dist_w, int k_within,
-                    int k_cross, int L2, int32_t *__restrict__ idx_x, float *__restrict__ dist_x) {
+                    int k_cross, int L2, int parts, int32_t *__restrict__ idx_x, float *__restrict__ dist_x) {
+    const int n_cand = parts * tck::BatchedWork::kShort;   // candidates per (query, sample)
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int XQ = 65;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -107,13 +107,14 @@ rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, i
     __syncwarp();
     const bool fq = cosine && xq[d] != 0.f;
     // two samples per pass: lanes 0-15 sample t, lanes 16-31 sample t + 1
+    // (lanes past n_cand hold +inf)
     const int half = lane >> 4, hl = lane & 15;
     for (int t0 = 0; t0 < S; t0 += 2) {
         const int t = t0 + half;
         float key = INFINITY;
         int id = INT_MAX;
-        if (t < S && t != own) {
-            const int32_t j = cand_x[((int64_t)q * S + t) * kXCand + hl];
+        if (t < S && t != own && hl < n_cand) {
+            const int32_t j = cand_x[((int64_t)q * S + t) * n_cand + hl];
             if (j >= 0) {
                 const float *yr = R + (int64_t)j * rs;
                 float acc = 0.f;
@@ -215,8 +216,8 @@ void batched_fill_tables(const int64_t *offsets_host, int S, void *host_buf) {
 }
 
 cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                  const void *tables_dev, int32_t *cand_w, int32_t *cand_x, unsigned int *status,
-                                  cudaStream_t st) {
+                                  int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
+                                  unsigned int *status, cudaStream_t st) {
     if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
     CUtensorMap mq, md;
     cudaError_t e = tck::make_map(&mq, Qb, N, 1, tck::BM);
@@ -227,12 +228,16 @@ cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int
     const int64_t *samp_off = tile_end + T;
     const int32_t *tile_samp = reinterpret_cast<const int32_t *>(samp_off + S + 1);
     tck::BatchedWork work{T, S, tile_row, tile_end, tile_samp, samp_off, N, cand_w, cand_x};
-    return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
+    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
+    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_rerank_cross(const float *R, int64_t rs, int64_t N, int d, int metric, const void *tables_dev,
-                                int S, int T, const int32_t *cand_x, const int32_t *idx_w, const float *dist_w,
-                                int k_within, int k_cross, int32_t *idx_x, float *dist_x, cudaStream_t st) {
+                                int S, int T, int parts, const int32_t *cand_x, const int32_t *idx_w,
+                                const float *dist_w, int k_within, int k_cross, int32_t *idx_x, float *dist_x,
+                                cudaStream_t st) {
+    if (parts != 2 && parts != 4) return cudaErrorInvalidValue;
     const int64_t *samp_off = static_cast<const int64_t *>(tables_dev) + 2 * (int64_t)T;
     int L2 = 32;
     while (L2 < S * k_cross) L2 <<= 1;
@@ -240,7 +245,7 @@ cudaError_t launch_rerank_cross(const float *R, int64_t rs, int64_t N, int d, in
     constexpr int XQ = 65;
     const size_t smem = sizeof(float) * kXWarps * XQ + (sizeof(float) + sizeof(int)) * kXWarps * L2;
     rerank_cross_kernel<<<(unsigned)ceil_div(N, kXWarps), kXWarps * 32, smem, st>>>(
-        R, rs, N, d, metric, samp_off, S, cand_x, idx_w, dist_w, k_within, k_cross, L2, idx_x, dist_x);
+        R, rs, N, d, metric, samp_off, S, cand_x, idx_w, dist_w, k_within, k_cross, L2, parts, idx_x, dist_x);
     return cudaGetLastError();
 }
 

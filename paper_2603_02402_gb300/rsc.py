@@ -38,7 +38,7 @@ class RscError(RuntimeError):
 
 class rsc_knn_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("candidates", ctypes.c_int32),
-                ("db_splits", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("db_splits", ctypes.c_int32), ("tc_parts", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("phase_events", ctypes.c_void_p)]
 
 
@@ -59,6 +59,15 @@ SIGNATURES = {
     "rsc_connectivities": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rsc_connectivities_nnz": (_i32, [_vp, _vp, _i64, _i32, ctypes.POINTER(_i64), _vp, _sz, _vp]),
     "rsc_connectivities_static": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "rsc_autotune_workspace_size": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_sz)]),
+    "rsc_autotune_knn": (_i32, [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts), _i32, _vp, _vp,
+                                 ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(ctypes.c_float), _vp, _sz]),
+    "rsc_autotune_knn_batched": (_i32, [_vp, _i64, _i32, _vp, _i32, _i32, _i32, _i32,
+                                         ctypes.POINTER(rsc_knn_opts), _i32, _vp, _vp, _vp, _vp,
+                                         ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(ctypes.c_float), _vp, _sz]),
+    "rsc_autotune_save": (_i32, [ctypes.c_char_p]),
+    "rsc_autotune_load": (_i32, [ctypes.c_char_p]),
+    "rsc_autotune_clear": (_i32, []),
 }
 
 
@@ -265,3 +274,59 @@ def rsc_connectivities_static(idx: torch.Tensor, dist: torch.Tensor, stream=None
     _check(lib().rsc_connectivities_static(_ptr(idx), _ptr(dist), n, k, _ptr(indptr), _ptr(indices), _ptr(data),
                                            cap, _ptr(rho), _ptr(sigma), _stream(stream)))
     return indptr, indices, data, rho, sigma
+
+
+def rsc_autotune_knn(X: torch.Tensor, k: int, metric="euclidean", precision="bf16", trials=2, stream=None):
+    """Time rsc_knn's configurations on X, remember the fastest for automatic
+    options, and return (chosen option dict, best ms, idx, dist)."""
+    n, d = X.shape
+    m = _METRICS[metric] if isinstance(metric, str) else int(metric)
+    p = _PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    need = _sz(0)
+    _check(lib().rsc_autotune_workspace_size(n, d, k, m, p, ctypes.byref(need)))
+    ws = _workspace(need.value, X.device)
+    idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((n, k), dtype=torch.float32, device=X.device)
+    o = knn_opts(precision, 0, 0, stream)
+    best = rsc_knn_opts()
+    ms = ctypes.c_float(0)
+    _check(lib().rsc_autotune_knn(_ptr(X), n, d, k, m, ctypes.byref(o), trials, _ptr(idx), _ptr(dist),
+                                  ctypes.byref(best), ctypes.byref(ms), _ptr(ws), ws.numel()))
+    return ({"db_splits": best.db_splits, "candidates": best.candidates, "tc_parts": best.tc_parts},
+            float(ms.value), idx, dist)
+
+
+def rsc_autotune_knn_batched(X: torch.Tensor, sample_offsets, k_within: int, k_cross: int, metric="euclidean",
+                             trials=2, stream=None):
+    """Tune rsc_knn_batched's column parts; returns (tc_parts, best ms, outputs)."""
+    n, d = X.shape
+    off, optr = _offsets_host(sample_offsets)
+    S = len(off) - 1
+    m = _METRICS[metric] if isinstance(metric, str) else int(metric)
+    o = knn_opts("bf16", 0, 0, stream)
+    need = _sz(0)
+    _check(lib().rsc_knn_batched_workspace_size(n, d, optr, S, k_within, k_cross, m, ctypes.byref(o),
+                                                ctypes.byref(need)))
+    ws = _workspace(need.value, X.device)
+    outs = (torch.empty((n, k_within), dtype=torch.int32, device=X.device),
+            torch.empty((n, k_within), dtype=torch.float32, device=X.device),
+            torch.empty((n, S * k_cross), dtype=torch.int32, device=X.device),
+            torch.empty((n, S * k_cross), dtype=torch.float32, device=X.device))
+    best = rsc_knn_opts()
+    ms = ctypes.c_float(0)
+    _check(lib().rsc_autotune_knn_batched(_ptr(X), n, d, optr, S, k_within, k_cross, m, ctypes.byref(o), trials,
+                                          *[_ptr(t) for t in outs], ctypes.byref(best), ctypes.byref(ms), _ptr(ws),
+                                          ws.numel()))
+    return int(best.tc_parts), float(ms.value), outs
+
+
+def rsc_autotune_save(path: str):
+    _check(lib().rsc_autotune_save(path.encode()))
+
+
+def rsc_autotune_load(path: str):
+    _check(lib().rsc_autotune_load(path.encode()))
+
+
+def rsc_autotune_clear():
+    _check(lib().rsc_autotune_clear())

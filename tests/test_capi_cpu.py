@@ -88,7 +88,7 @@ def test_candidate_option_errors(L):
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
     o = rsc.rsc_knn_opts(9, 0, 0, 0, None, None)       # unknown precision
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
-    o = rsc.rsc_knn_opts(0, 0, 0, 1, None, None)       # reserved field set
+    o = rsc.rsc_knn_opts(1, 0, 0, 3, None, None)       # tc_parts must be 0, 2 or 4
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
 
 
@@ -100,3 +100,27 @@ def test_connectivities_argument_errors(L):
         == rsc.RSC_ERR_INVALID_ARG
     assert L.rsc_connectivities(fake, fake, 10, 5, fake, fake, fake, 100, None, None, None, 0, None) \
         == rsc.RSC_ERR_WORKSPACE
+
+
+def test_autotune_table_save_load_roundtrip(L, tmp_path):
+    rsc.rsc_autotune_clear()
+    src = tmp_path / "tuned.txt"
+    src.write_text("# kind precision metric d k k_cross log2n db_splits candidates tc_parts\n"
+                   "0 1 0 50 15 0 19 2 0 4\n"
+                   "1 1 0 50 15 3 21 0 0 2\n")
+    rsc.rsc_autotune_load(str(src))
+    # an automatic rsc_knn request of that key now plans with 2 database splits
+    auto = rsc.rsc_knn_workspace_size(600_000, 50, 15, "euclidean", "bf16")
+    explicit = ctypes.c_size_t(0)
+    o = rsc.rsc_knn_opts(1, 0, 2, 4, None, None)
+    assert L.rsc_knn_workspace_size(600_000, 50, 15, 0, ctypes.byref(o), ctypes.byref(explicit)) == 0
+    assert auto == explicit.value
+    out = tmp_path / "saved.txt"
+    rsc.rsc_autotune_save(str(out))
+    rows = [l.split() for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert sorted(rows) == sorted([l.split() for l in src.read_text().splitlines() if not l.startswith("#")])
+    bad = tmp_path / "bad.txt"
+    bad.write_text("0 1 0 50 15 0 19 2 0 3\n")    # tc_parts 3 is not a valid choice
+    with pytest.raises(rsc.RscError):
+        rsc.rsc_autotune_load(str(bad))
+    rsc.rsc_autotune_clear()
