@@ -15,6 +15,7 @@ neighbours step uses the UMAP smooth-kNN / fuzzy-union construction):
 * ``smooth_knn``   -- rho, sigma (64-step bisection to log2 k) and weights.
 * ``fuzzy_union``  -- G = A + A^T - A o A^T as CSR with sorted columns.
 * ``connectivities`` -- smooth_knn followed by fuzzy_union.
+* ``mlp_loss_grad`` -- the partitioner MLP's soft cross-entropy and gradients.
 
 Parity is pinned by tests/test_oracle_pins.py (brute force on tiny inputs,
 closed forms, a library kNN, invariants).
@@ -66,6 +67,8 @@ def _load():
             lib.oracle_smooth_knn.restype = i32
             lib.oracle_fuzzy_union.argtypes = [vp, vp, i64, i32, vp, vp, vp, i64]
             lib.oracle_fuzzy_union.restype = i32
+            lib.oracle_mlp_loss_grad.argtypes = [vp, vp, i64, i32, i32, i32, i32, vp, i32, vp, vp]
+            lib.oracle_mlp_loss_grad.restype = i32
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i32
             _ = dbl
@@ -184,3 +187,24 @@ def connectivities(idx: np.ndarray, dist: np.ndarray):
     indptr, indices, data = fuzzy_union(idx, s["weights"])
     s.update(indptr=indptr, indices=indices, data=data)
     return s
+
+
+def mlp_param_count(D, H1, H2, P):
+    return H1 * D + H1 + H2 * H1 + H2 + P * H2 + P
+
+
+def mlp_loss_grad(X, T, params, dims, bf16=False, need_grad=True):
+    """Loss and gradient (double) of the MLP relu(W1 x+b1) -> relu(W2 .+b2) ->
+    W3 .+b3 with soft-target cross-entropy, params flat [W1, b1, W2, b2, W3, b3]."""
+    D, H1, H2, P = dims
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    assert params.size == mlp_param_count(D, H1, H2, P)
+    loss = ctypes.c_double(0)
+    grad = np.empty(params.size, dtype=np.float64) if need_grad else None
+    rc = _load().oracle_mlp_loss_grad(_ptr(X), _ptr(T), len(X), D, H1, H2, P, _ptr(params), int(bf16),
+                                      ctypes.byref(loss), _ptr(grad))
+    if rc != 0:
+        raise ValueError(f"oracle_mlp_loss_grad failed with status {rc}")
+    return loss.value, grad

@@ -336,3 +336,115 @@ int oracle_fuzzy_union(const int32_t *idx, const double *w, int64_t n, int k,
     free(fill);
     return status;
 }
+
+/* ------------------------------------------------------------------------
+ * Partitioner MLP (reference for the GPU training kernels).
+ *
+ * Layers: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), z = W3 h2 + b3;
+ * loss = mean over the batch of -sum_p t_p log softmax(z)_p (soft targets).
+ * W1 [H1, D], W2 [H2, H1], W3 [P, H2] row-major (out x in).  With bf16 != 0
+ * every GEMM operand that is a weight or an activation (x, h1, h2) is first
+ * rounded to bfloat16 (round to nearest, ties to even), as the GPU does; the
+ * arithmetic itself is double.  Gradients are of the loss with respect to
+ * the (unrounded) parameters, treating the rounding as the identity
+ * (straight-through), which is what the GPU backward computes.
+ * ---------------------------------------------------------------------- */
+static double round_bf16(double v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof(u));
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;   /* inf / nan unchanged */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, sizeof(f));
+    return (double)f;
+}
+
+static double rd(double v, int bf16) { return bf16 ? round_bf16(v) : v; }
+
+int oracle_mlp_loss_grad(const float *X, const float *T, int64_t B, int D, int H1, int H2, int P,
+                         const float *params, int bf16, double *loss, double *grad) {
+    if (!X || !T || !params || B <= 0 || D <= 0 || H1 <= 0 || H2 <= 0 || P <= 0) return ORC_BAD_ARG;
+    const float *W1 = params, *b1 = W1 + (size_t)H1 * D;
+    const float *W2 = b1 + H1, *b2 = W2 + (size_t)H2 * H1;
+    const float *W3 = b2 + H2, *b3 = W3 + (size_t)P * H2;
+    size_t np = (size_t)H1 * D + H1 + (size_t)H2 * H1 + H2 + (size_t)P * H2 + P;
+    double *g = grad;
+    if (g) memset(g, 0, sizeof(double) * np);
+    double *gW1 = g, *gb1 = g ? g + (size_t)H1 * D : NULL;
+    double *gW2 = g ? gb1 + H1 : NULL, *gb2 = g ? gW2 + (size_t)H2 * H1 : NULL;
+    double *gW3 = g ? gb2 + H2 : NULL, *gb3 = g ? gW3 + (size_t)P * H2 : NULL;
+    double *z1 = malloc(sizeof(double) * H1), *h1 = malloc(sizeof(double) * H1);
+    double *z2 = malloc(sizeof(double) * H2), *h2 = malloc(sizeof(double) * H2);
+    double *z3 = malloc(sizeof(double) * P), *dz3 = malloc(sizeof(double) * P);
+    double *dh2 = malloc(sizeof(double) * H2), *dz2 = malloc(sizeof(double) * H2);
+    double *dh1 = malloc(sizeof(double) * H1), *dz1 = malloc(sizeof(double) * H1);
+    double *xr = malloc(sizeof(double) * D);
+    if (!z1 || !h1 || !z2 || !h2 || !z3 || !dz3 || !dh2 || !dz2 || !dh1 || !dz1 || !xr) {
+        free(z1); free(h1); free(z2); free(h2); free(z3); free(dz3); free(dh2); free(dz2); free(dh1); free(dz1); free(xr);
+        return ORC_NO_MEM;
+    }
+    double total = 0.0;
+    for (int64_t b = 0; b < B; ++b) {
+        const float *x = X + (size_t)b * D;
+        const float *t = T + (size_t)b * P;
+        for (int i = 0; i < D; ++i) xr[i] = rd(x[i], bf16);
+        for (int o = 0; o < H1; ++o) {
+            double s = 0.0;
+            for (int i = 0; i < D; ++i) s += rd(W1[(size_t)o * D + i], bf16) * xr[i];
+            z1[o] = s + b1[o];
+            h1[o] = z1[o] > 0.0 ? z1[o] : 0.0;
+        }
+        for (int o = 0; o < H2; ++o) {
+            double s = 0.0;
+            for (int i = 0; i < H1; ++i) s += rd(W2[(size_t)o * H1 + i], bf16) * rd(h1[i], bf16);
+            z2[o] = s + b2[o];
+            h2[o] = z2[o] > 0.0 ? z2[o] : 0.0;
+        }
+        double zmax = -INFINITY;
+        for (int o = 0; o < P; ++o) {
+            double s = 0.0;
+            for (int i = 0; i < H2; ++i) s += rd(W3[(size_t)o * H2 + i], bf16) * rd(h2[i], bf16);
+            z3[o] = s + b3[o];
+            if (z3[o] > zmax) zmax = z3[o];
+        }
+        double se = 0.0;
+        for (int o = 0; o < P; ++o) se += exp(z3[o] - zmax);
+        const double lse = zmax + log(se);
+        double lb = 0.0;
+        for (int o = 0; o < P; ++o) lb -= (double)t[o] * (z3[o] - lse);
+        total += lb;
+        if (!g) continue;
+        double tsum = 0.0;
+        for (int o = 0; o < P; ++o) tsum += (double)t[o];
+        for (int o = 0; o < P; ++o) dz3[o] = (exp(z3[o] - lse) * tsum - (double)t[o]) / (double)B;
+        for (int o = 0; o < P; ++o) {
+            gb3[o] += dz3[o];
+            for (int i = 0; i < H2; ++i) gW3[(size_t)o * H2 + i] += dz3[o] * rd(h2[i], bf16);
+        }
+        for (int i = 0; i < H2; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < P; ++o) s += dz3[o] * rd(W3[(size_t)o * H2 + i], bf16);
+            dh2[i] = s;
+            dz2[i] = z2[i] > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < H2; ++o) {
+            gb2[o] += dz2[o];
+            for (int i = 0; i < H1; ++i) gW2[(size_t)o * H1 + i] += dz2[o] * rd(h1[i], bf16);
+        }
+        for (int i = 0; i < H1; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < H2; ++o) s += dz2[o] * rd(W2[(size_t)o * H1 + i], bf16);
+            dh1[i] = s;
+            dz1[i] = z1[i] > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < H1; ++o) {
+            gb1[o] += dz1[o];
+            for (int i = 0; i < D; ++i) gW1[(size_t)o * D + i] += dz1[o] * xr[i];
+        }
+    }
+    *loss = total / (double)B;
+    free(z1); free(h1); free(z2); free(h2); free(z3); free(dz3); free(dh2); free(dz2); free(dh1); free(dz1); free(xr);
+    return ORC_OK;
+}
