@@ -203,6 +203,93 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
                            size_t workspace_bytes);
 
 /*
+ * Learned partitioner (candidate pruning for the exact search).
+ *
+ * A handle owns a small network d -> hidden -> hidden -> n_parts (ReLU; FP32
+ * master weights, bfloat16-rounded weights and activations in every GEMM when
+ * bf16_weights != 0, FP32 accumulation), n_parts k-means centroids and, once
+ * built, an index of one database: its rows counting-sorted by the part the
+ * network ranks first.  The handle is the one object of this library that
+ * allocates device memory (create, build_index); destroy frees it.
+ * rsc_knn_partitioned answers a query by scanning only the n_probe parts the
+ * network ranks highest (or, with routing = 1, the n_probe nearest centroids:
+ * the same parts and budget without the network), scoring candidates with
+ * the BF16 tensor-core search and re-scoring them exactly in FP32: the result
+ * is exact inside the probed parts and approximate overall (recall < 1).
+ * The paper does not describe this component; its kNN is cuVS on the GPU and
+ * PyNNDescent on the CPU (Methods, "Benchmarking").  Euclidean only, k <= 16,
+ * d <= 61, n_parts in [8, 1024], hidden in [8, 1024].
+ */
+typedef struct rsc_partitioner rsc_partitioner;
+
+rsc_status rsc_partitioner_create(int32_t d, int32_t n_parts, int32_t hidden, int32_t bf16_weights,
+                                  uint64_t seed, rsc_partitioner **out);
+rsc_status rsc_partitioner_destroy(rsc_partitioner *p);
+
+/* Network parameters as one FP32 host array [W1 (hidden x d), b1, W2 (hidden x
+ * hidden), b2, W3 (n_parts x hidden), b3], weights row-major out x in. */
+rsc_status rsc_partitioner_param_count(const rsc_partitioner *p, int64_t *count);
+rsc_status rsc_partitioner_get_params(const rsc_partitioner *p, float *host_out);
+rsc_status rsc_partitioner_set_params(rsc_partitioner *p, const float *host_in);   /* resets Adam */
+
+/*
+ * Soft-target cross-entropy of a batch and its gradient (one forward and
+ * backward pass of the training kernels, no update): loss = mean over rows of
+ * -sum_p T[b, p] log softmax(z_b)_p.  Xb [batch, d], T [batch, n_parts] and
+ * grad [param_count] are device arrays (grad may be NULL); *loss_host is
+ * written after synchronising the stream.
+ */
+rsc_status rsc_partitioner_loss_grad_workspace_size(const rsc_partitioner *p, int32_t batch, size_t *bytes);
+rsc_status rsc_partitioner_loss_grad(rsc_partitioner *p, const float *Xb, const float *T, int32_t batch,
+                                     float *loss_host, float *grad, void *workspace,
+                                     size_t workspace_bytes, void *stream);
+
+/* Workspace for build_index / train (n_train rows, k) / rsc_knn_partitioned
+ * (n_queries, n_probe); pass 0 for what a call does not use. */
+rsc_status rsc_partitioner_workspace_size(const rsc_partitioner *p, int64_t n, int64_t n_train,
+                                          int32_t k, int64_t n_queries, int32_t n_probe,
+                                          size_t *bytes);
+
+/*
+ * Fit the partitioner on X [n, d] (device) and index X:
+ *   1. k-means (kmeans_iters Lloyd steps) on the training rows train_rows
+ *      (device int32 [n_train], n_parts <= n_train <= n; initial centroids =
+ *      the first n_parts training rows); every row's label = nearest centroid;
+ *   2. exact k nearest neighbours of each training row among all n rows;
+ *   3. `epochs` passes of minibatch Adam (lr; betas 0.9, 0.999; eps 1e-8) on
+ *      the soft target "histogram of the labels of my k neighbours";
+ *   4. rsc_partitioner_build_index(X).
+ * Synchronises the stream; *final_loss (host, nullable) = last epoch's loss.
+ */
+rsc_status rsc_partitioner_train(rsc_partitioner *p, const float *X, int64_t n,
+                                 const int32_t *train_rows, int64_t n_train, int32_t k,
+                                 int32_t kmeans_iters, int32_t epochs, int32_t batch, float lr,
+                                 float *final_loss, void *workspace, size_t workspace_bytes,
+                                 void *stream);
+
+/* Assign every row of X to its network top-1 part and sort (re-allocates the
+ * handle's index when n changes). */
+rsc_status rsc_partitioner_build_index(rsc_partitioner *p, const float *X, int64_t n,
+                                       void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * k nearest neighbours (Euclidean, ids of X, self included when probed,
+ * ordered by (distance, id)) of query_rows (device int32 [n_queries]; NULL =
+ * every row, n_queries ignored) among the rows of the indexed X, probing
+ * n_probe in {1, 2, 4, 8} parts per query.  routing: 0 = the network's
+ * top parts, 1 = nearest centroids.  idx/dist [n_queries, k].
+ */
+rsc_status rsc_knn_partitioned(rsc_partitioner *p, const float *X, int64_t n, int32_t k,
+                               int32_t n_probe, int32_t routing, const int32_t *query_rows,
+                               int64_t n_queries, int32_t *idx, float *dist, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
+/* Network parameters and centroids to / from a binary file (host only; the
+ * index is rebuilt with build_index after loading). */
+rsc_status rsc_partitioner_save(const rsc_partitioner *p, const char *path);
+rsc_status rsc_partitioner_load(const char *path, rsc_partitioner **out);
+
+/*
  * Minimum workspace for rsc_connectivities / rsc_connectivities_nnz.
  */
 rsc_status rsc_connectivities_workspace_size(int64_t n, int32_t k, size_t *bytes);

@@ -68,6 +68,20 @@ SIGNATURES = {
     "rsc_autotune_save": (_i32, [ctypes.c_char_p]),
     "rsc_autotune_load": (_i32, [ctypes.c_char_p]),
     "rsc_autotune_clear": (_i32, []),
+    "rsc_partitioner_create": (_i32, [_i32, _i32, _i32, _i32, ctypes.c_uint64, ctypes.POINTER(_vp)]),
+    "rsc_partitioner_destroy": (_i32, [_vp]),
+    "rsc_partitioner_param_count": (_i32, [_vp, ctypes.POINTER(_i64)]),
+    "rsc_partitioner_get_params": (_i32, [_vp, _vp]),
+    "rsc_partitioner_set_params": (_i32, [_vp, _vp]),
+    "rsc_partitioner_loss_grad_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "rsc_partitioner_loss_grad": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_float), _vp, _vp, _sz, _vp]),
+    "rsc_partitioner_workspace_size": (_i32, [_vp, _i64, _i64, _i32, _i64, _i32, ctypes.POINTER(_sz)]),
+    "rsc_partitioner_train": (_i32, [_vp, _vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, ctypes.c_float,
+                                      ctypes.POINTER(ctypes.c_float), _vp, _sz, _vp]),
+    "rsc_partitioner_build_index": (_i32, [_vp, _vp, _i64, _vp, _sz, _vp]),
+    "rsc_knn_partitioned": (_i32, [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "rsc_partitioner_save": (_i32, [_vp, ctypes.c_char_p]),
+    "rsc_partitioner_load": (_i32, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
 }
 
 
@@ -330,3 +344,105 @@ def rsc_autotune_load(path: str):
 
 def rsc_autotune_clear():
     _check(lib().rsc_autotune_clear())
+
+
+class Partitioner:
+    """Owning wrapper of an rsc_partitioner handle (see include/rsc.h)."""
+
+    def __init__(self, d=50, n_parts=1024, hidden=256, bf16_weights=True, seed=0, _handle=None):
+        self._h = _vp()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            _check(lib().rsc_partitioner_create(d, n_parts, hidden, int(bf16_weights), seed, ctypes.byref(self._h)))
+        self.d, self.n_parts, self.hidden = d, n_parts, hidden
+
+    def close(self):
+        if self._h:
+            lib().rsc_partitioner_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def param_count(self) -> int:
+        c = _i64(0)
+        _check(lib().rsc_partitioner_param_count(self._h, ctypes.byref(c)))
+        return int(c.value)
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.param_count, dtype=np.float32)
+        _check(lib().rsc_partitioner_get_params(self._h, out.ctypes.data_as(_vp)))
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.param_count
+        _check(lib().rsc_partitioner_set_params(self._h, a.ctypes.data_as(_vp)))
+
+    def loss_grad(self, Xb: torch.Tensor, T: torch.Tensor, stream=None):
+        B = Xb.shape[0]
+        need = _sz(0)
+        _check(lib().rsc_partitioner_loss_grad_workspace_size(self._h, B, ctypes.byref(need)))
+        ws = _workspace(need.value, Xb.device)
+        grad = torch.empty(self.param_count, dtype=torch.float32, device=Xb.device)
+        loss = ctypes.c_float(0)
+        _check(lib().rsc_partitioner_loss_grad(self._h, _ptr(Xb), _ptr(T), B, ctypes.byref(loss), _ptr(grad),
+                                               _ptr(ws), ws.numel(), _stream(stream)))
+        return float(loss.value), grad
+
+    def workspace_size(self, n, n_train=0, k=15, n_queries=0, n_probe=8) -> int:
+        need = _sz(0)
+        _check(lib().rsc_partitioner_workspace_size(self._h, n, n_train, k, n_queries, n_probe, ctypes.byref(need)))
+        return int(need.value)
+
+    def train(self, X: torch.Tensor, train_rows: torch.Tensor, k=15, kmeans_iters=10, epochs=10, batch=1024,
+              lr=1e-3, stream=None, workspace=None) -> float:
+        n = X.shape[0]
+        ws = _workspace(self.workspace_size(n, len(train_rows), k, 1, 1), X.device, workspace)
+        loss = ctypes.c_float(0)
+        _check(lib().rsc_partitioner_train(self._h, _ptr(X), n, _ptr(train_rows), len(train_rows), k, kmeans_iters,
+                                           epochs, batch, lr, ctypes.byref(loss), _ptr(ws), ws.numel(),
+                                           _stream(stream)))
+        return float(loss.value)
+
+    def build_index(self, X: torch.Tensor, stream=None, workspace=None):
+        n = X.shape[0]
+        ws = _workspace(self.workspace_size(n, 0, 1, 1, 1), X.device, workspace)
+        _check(lib().rsc_partitioner_build_index(self._h, _ptr(X), n, _ptr(ws), ws.numel(), _stream(stream)))
+
+    def knn(self, X: torch.Tensor, k=15, n_probe=8, routing="network", query_rows=None, stream=None,
+            workspace=None, out=None):
+        """kNN of query_rows (int32 CUDA tensor; None = all rows) by probing n_probe parts."""
+        n = X.shape[0]
+        nq = n if query_rows is None else len(query_rows)
+        ws = _workspace(self.workspace_size(n, 0, k, nq, n_probe), X.device, workspace)
+        if out is None:
+            idx = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+            dist = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+        else:
+            idx, dist = out
+        r = {"network": 0, "centroids": 1}[routing]
+        _check(lib().rsc_knn_partitioned(self._h, _ptr(X), n, k, n_probe, r, _ptr(query_rows), nq, _ptr(idx),
+                                         _ptr(dist), _ptr(ws), ws.numel(), _stream(stream)))
+        return idx, dist
+
+    def save(self, path: str):
+        _check(lib().rsc_partitioner_save(self._h, path.encode()))
+
+    @classmethod
+    def load(cls, path: str):
+        h = _vp()
+        _check(lib().rsc_partitioner_load(path.encode(), ctypes.byref(h)))
+        obj = cls.__new__(cls)
+        obj._h = h
+        params = _i64(0)
+        _check(lib().rsc_partitioner_param_count(h, ctypes.byref(params)))
+        obj.d = obj.n_parts = obj.hidden = None
+        return obj

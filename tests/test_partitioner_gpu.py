@@ -1,0 +1,89 @@
+"""GPU tests of the learned partitioner: training-kernel gradients against the
+FP64 oracle, recall of the partitioned search against the exact oracle, and
+the gain of the network over nearest-centroid routing with the same parts and
+probe budget."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_02402_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_02402_gb300 import rsc as mod
+    mod.lib()
+    return mod
+
+
+def _batch(seed, B, d, P):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = rng.standard_normal((B, d)).astype(np.float32)
+    T = rng.uniform(size=(B, P)).astype(np.float32)
+    T /= T.sum(axis=1, keepdims=True)
+    return X, T
+
+
+@pytest.mark.parametrize("bf16,rtol", [(False, 2e-4), (True, 1e-2)])
+def test_loss_and_gradient_match_oracle(rsc, bf16, rtol):
+    d, P, H, B = 12, 16, 24, 37
+    part = rsc.Partitioner(d, P, H, bf16_weights=bf16, seed=3)
+    params = (np.random.Generator(np.random.PCG64(4)).standard_normal(part.param_count) * 0.3).astype(np.float32)
+    part.set_params(params)
+    X, T = _batch(5, B, d, P)
+    loss, grad = part.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    grad = grad.cpu().numpy().astype(np.float64)
+    ref_loss, ref_grad = oracle.mlp_loss_grad(X, T, params, (d, H, H, P), bf16=bf16)
+    assert abs(loss - ref_loss) <= rtol * abs(ref_loss)
+    scale = np.abs(ref_grad).max()
+    # per-element agreement relative to the gradient's scale
+    np.testing.assert_allclose(grad, ref_grad, rtol=0, atol=rtol * scale)
+    assert np.dot(grad, ref_grad) / (np.linalg.norm(grad) * np.linalg.norm(ref_grad)) > 1 - rtol
+
+
+def _recall(gi, oi, gd, od):
+    ok = gd <= od[:, -1:] * (1 + 1e-6)
+    return float(ok.mean())
+
+
+def test_partitioned_search_recall_and_gain(rsc):
+    n, d, k = 60_000, 50, 15
+    X = synth.anisotropic(n, d, n_comp=40, seed=7)
+    Xd = torch.from_numpy(X).cuda()
+    rng = np.random.Generator(np.random.PCG64(8))
+    perm = rng.permutation(n)
+    train = torch.from_numpy(np.sort(perm[:8000]).astype(np.int32)).cuda()
+    queries = np.sort(perm[8000:9000]).astype(np.int32)
+    part = rsc.Partitioner(d, n_parts=64, hidden=64, bf16_weights=True, seed=9)
+    loss = part.train(Xd, train, k=k, kmeans_iters=8, epochs=8, batch=512, lr=2e-3)
+    assert np.isfinite(loss) and loss > 0
+    q = torch.from_numpy(queries).cuda()
+    oi, od, _ = oracle.knn(X, k, queries=queries)
+    res = {}
+    for routing in ("network", "centroids"):
+        gi, gd = part.knn(Xd, k=k, n_probe=4, routing=routing, query_rows=q)
+        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+        assert (np.diff(gd, axis=1) >= 0).all()
+        # every returned distance is exact for its id
+        ex = np.sqrt(((X[queries][:, None, :].astype(np.float64) - X[gi].astype(np.float64)) ** 2).sum(-1))
+        np.testing.assert_allclose(gd, ex, rtol=1e-5, atol=1e-6)
+        res[routing] = _recall(gi, oi, gd, od)
+    print("recall@15", res)
+    assert res["network"] >= 0.9
+    # probing every part is the exact search
+    gi, gd = part.knn(Xd, k=k, n_probe=8, routing="network", query_rows=q)
+    assert _recall(gi.cpu().numpy(), oi, gd.cpu().numpy(), od) >= res["network"]
+
+
+def test_save_load_roundtrip(rsc, tmp_path):
+    part = rsc.Partitioner(10, 16, 16, seed=11)
+    p0 = part.get_params()
+    path = str(tmp_path / "part.bin")
+    part.save(path)
+    other = rsc.Partitioner.load(path)
+    np.testing.assert_array_equal(other.get_params(), p0)
