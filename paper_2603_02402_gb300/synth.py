@@ -91,7 +91,10 @@ def anisotropic(n: int, d: int = 50, n_comp: int = 200, seed: int = 0,
         e = min(n, s + _CHUNK)
         comp = rng.integers(0, n_comp, size=e - s)
         z = rng.standard_normal((e - s, d))
-        x = means[comp] + np.einsum("nij,nj->ni", factors[comp], z)
+        x = np.empty((e - s, d))
+        for c in np.unique(comp):                      # one matrix product per component
+            m = comp == c
+            x[m] = means[c] + z[m] @ factors[c].T
         out[s:e] = x.astype(np.float32)
     return out
 
