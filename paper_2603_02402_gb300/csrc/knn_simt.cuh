@@ -32,8 +32,7 @@ knn_simt_kernel(const float *__restrict__ Y, const float *__restrict__ ny, int64
     static_assert(DP % 8 == 0, "DP multiple of 8");
     __shared__ __align__(16) float ys[2][kTileRows][DP];
     __shared__ float ns[2][kTileRows];
-    __shared__ float bkey[kCap * kThreads];
-    __shared__ int bid[kCap * kThreads];
+    __shared__ float bkey[2 * kCap * kThreads];   // keys, then ids
 
     const int tid = threadIdx.x;
     const int64_t q = (int64_t)blockIdx.x * kThreads + tid;
@@ -58,8 +57,8 @@ knn_simt_kernel(const float *__restrict__ Y, const float *__restrict__ ny, int64
         for (int t = 0; t < DP; ++t) x[t] = 0.f;
     }
 
-    BufferedTopK<KC, kCap> tk;
-    tk.init(bkey, bid, tid, kThreads);
+    BufferedTopK<KC, kCap, kThreads> tk;
+    tk.init(bkey, tid);
 
     // stage tile `buf` with rows j0 .. j0 + kTileRows - 1 (zeros / +inf past the split)
     auto stage = [&](int buf, int64_t j0) {

@@ -120,6 +120,7 @@ struct PlainWork {
         w.j_end = min(n, w.j_begin + split_len);
         w.tag = sp;
         w.short_list = false;
+        w.win_lo = w.win_hi = 0;
         return w;
     }
     template <int EG, int KCP>

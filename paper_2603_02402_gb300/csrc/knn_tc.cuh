@@ -20,11 +20,13 @@ namespace tck {
 
 constexpr int BM = 128;              // query rows per item (TMEM lanes)
 constexpr int BN = 256;              // database rows per stage = accumulator columns
-constexpr int NBUF = 2;              // accumulators (NBUF x BN = 512 TMEM columns)
+constexpr int NBUF = 2;              // accumulators (NBUF x BN = 512 TMEM columns); the
+                                     // buffer of tile g is g & 1, its phase (g >> 1) & 1
 constexpr int QBLK = BM * 128;       // bytes of one 128-row x 64-element bf16 query block
 constexpr int DBLK = BN * 128;       // bytes of one 256-row x 64-element bf16 database block
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks
+constexpr uint32_t kSleepNs = 100000;             // suspend limit of one try_wait (ns)
 
 // EG epilogue warpgroups, each owning kCols = BN / EG columns of every tile;
 // KCP = top-k list length per (row, part).
@@ -51,6 +53,41 @@ struct WorkItem {
     int64_t q0, q_end, j_begin, j_end;
     int tag;
     bool short_list;
+    int win_lo, win_hi;   // database tiles [win_lo, win_hi) (counted from j_begin) are scanned first
+};
+
+// Visiting order of an item's T database tiles: the window [wlo, whi) first,
+// then [0, wlo), then [whi, T); every tile exactly once.  A tile costs one
+// increment and one compare; the range switch runs three times per item.
+// Requires 0 <= wlo <= whi <= T.
+struct TileSeq {
+    int m, end, T, wlo, whi, phase;
+
+    __device__ __forceinline__ void init(int T_, int wlo_, int whi_) {
+        T = T_;
+        wlo = wlo_;
+        whi = whi_;
+        m = wlo;
+        end = whi;
+        phase = 0;
+        settle();
+    }
+    __device__ __forceinline__ void settle() {
+        while (m == end && phase < 2) {
+            if (phase == 0) {
+                m = 0;
+                end = wlo;
+            } else {
+                m = whi;
+                end = T;
+            }
+            ++phase;
+        }
+    }
+    __device__ __forceinline__ bool done() const { return m >= end; }
+    __device__ __forceinline__ void next() {
+        if (++m == end) settle();
+    }
 };
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
@@ -68,8 +105,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     uint8_t *smem = align1024(smem_raw);
     uint8_t *sQ = smem;
     uint8_t *sD = smem + C::kQBytes;
-    float *bkey = reinterpret_cast<float *>(sD + S * C::kStageBytes);
-    int *bid = reinterpret_cast<int *>(bkey + C::kCap * C::kEpiThreads);
+    float *bkey = reinterpret_cast<float *>(sD + S * C::kStageBytes);   // keys, then ids
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kBarOff);
     uint64_t *full = bars;                     // [S]     database stage loaded
     uint64_t *empty = bars + S;                // [S]     database stage consumed
@@ -114,7 +150,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
         if (tc::mbar_try_wait(bar, parity)) return true;
         const long long t0 = clock64();
         while (true) {
-            if (tc::mbar_try_wait(bar, parity)) return true;
+            if (tc::mbar_try_wait_sleep(bar, parity, kSleepNs)) return true;
             if (*abort_flag) return false;
             if (clock64() - t0 > kWaitBudget) {
                 *abort_flag = 1;
@@ -150,13 +186,16 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                     tc::tma_load_2d(sQ + kb * QBLK, &tmQ, kb * 64, (int)wi.q0, q_full);
                 q_issued = true;
                 q_parity = item_no & 1;
-                for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
+                const int jb = (int)j_begin, T = (int)((j_end - j_begin + BN - 1) / BN);
+                TileSeq sq;
+                for (sq.init(T, wi.win_lo, wi.win_hi); !sq.done(); sq.next(), ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
                     if (!(ok = wait(&empty[s], (u & 1) ^ 1))) break;
                     tc::mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+                    const int j0 = jb + sq.m * BN;
                     for (int kb = 0; kb < KB; ++kb)
-                        tc::tma_load_2d(sD + (s * KB + kb) * DBLK, &tmD, kb * 64, (int)j0, &full[s]);
+                        tc::tma_load_2d(sD + (s * KB + kb) * DBLK, &tmD, kb * 64, j0, &full[s]);
                 }
             }
             if (!ok) {
@@ -178,10 +217,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 const int64_t j_begin = wi.j_begin, j_end = wi.j_end;
                 if (!(ok = wait(q_full, item_no & 1))) break;
                 tc::tc_fence_after();
-                for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
+                const int T = (int)((j_end - j_begin + BN - 1) / BN);
+                TileSeq sq;
+                for (sq.init(T, wi.win_lo, wi.win_hi); !sq.done(); sq.next(), ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
-                    const uint32_t b = gt % NBUF, v = gt / NBUF;
+                    const uint32_t b = gt & 1u, v = gt >> 1;
                     if (!(ok = wait(&acc_empty[b], (v & 1) ^ 1))) break;
                     if (!(ok = wait(&full[s], u & 1))) break;
                     tc::tc_fence_after();
@@ -214,50 +255,69 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
         const uint32_t lane_bits = (uint32_t)(quarter * 32) << 16;
         const int et = threadIdx.x - 64;
         const int cbeg = part * C::kCols;
-        BufferedTopK<KCP, C::kCap, Work::kShort> tk;
-        tk.init(bkey, bid, et, C::kEpiThreads);
+        BufferedTopK<KCP, C::kCap, C::kEpiThreads, Work::kShort> tk;
+        tk.init(bkey, et);
 
+        const uint32_t tb0 = tmem_base + lane_bits + cbeg;
         uint32_t gt = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const WorkItem wi = work.get(it);
-            const int64_t j_begin = wi.j_begin, j_end = wi.j_end;
+            const int jb = (int)wi.j_begin, len = (int)(wi.j_end - wi.j_begin);
+            const int T = (len + BN - 1) / BN;
+            const int tail = len - (T - 1) * BN;            // columns of the last tile
+            const int t_rag = tail < BN ? T - 1 : -1;       // the last tile, when it is partial
             tk.reset();
             tk.shortl = wi.short_list;
-            for (int64_t j0 = j_begin; j0 < j_end; j0 += BN, ++gt) {
-                const uint32_t b = gt % NBUF, v = gt / NBUF;
-                ok = wait(&acc_full[b], v & 1);
+            TileSeq sq;
+            for (sq.init(T, wi.win_lo, wi.win_hi); !sq.done(); sq.next(), ++gt) {
+                const uint32_t b = gt & 1u;
+                ok = wait(&acc_full[b], (gt >> 1) & 1u);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc::tc_fence_after();
-                const uint32_t tbase = tmem_base + lane_bits + b * BN + cbeg;
-                const int valid = ((j_end - j0 < BN) ? (int)(j_end - j0) : BN) - cbeg;
+                const uint32_t tb = tb0 + b * BN;
+                // fast path: minimum of this thread's kCols values, one vote per tile
+                float mn = INFINITY;
 #pragma unroll 1
                 for (int c0 = 0; c0 < C::kCols; c0 += 32) {
                     float vv[32];
                     __syncwarp();
-                    tc::tmem_ld32(tbase + c0, vv);
+                    tc::tmem_ld32(tb + c0, vv);
                     tc::tmem_wait_ld();
-                    if (c0 + 32 == C::kCols) {
-                        // last load of this accumulator part: hand it back to the MMA warp
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
-                    }
-                    if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (c0 + i >= valid) vv[i] = INFINITY;
-                    }
-                    float lo[16], hi[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        lo[i] = vv[i];
-                        hi[i] = vv[16 + i];
-                    }
-                    tk.offer16(lo, (int)(j0 + cbeg + c0));
-                    tk.offer16(hi, (int)(j0 + cbeg + c0 + 16));
+                    mn = fminf(mn, min_of(vv));
                 }
+                const bool rag = sq.m == t_rag;
+                if (__any_sync(0xffffffffu, rag || mn < tk.bound())) {
+                    // some lane may improve its list (or the tile is partial): read
+                    // the accumulator again and offer every value
+                    const int j0 = jb + sq.m * BN + cbeg;
+                    const int valid = rag ? tail - cbeg : C::kCols;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < C::kCols; c0 += 32) {
+                        float vv[32];
+                        __syncwarp();
+                        tc::tmem_ld32(tb + c0, vv);
+                        tc::tmem_wait_ld();
+                        if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (c0 + i >= valid) vv[i] = INFINITY;
+                        }
+                        float lo[16], hi[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            lo[i] = vv[i];
+                            hi[i] = vv[16 + i];
+                        }
+                        tk.offer16(lo, j0 + c0);
+                        tk.offer16(hi, j0 + c0 + 16);
+                    }
+                }
+                // hand the accumulator part back to the MMA warp
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
             }
             if (!ok) break;
             tk.flush();

@@ -45,6 +45,7 @@ struct BatchedWork {
         w.j_end = samp_off[t + 1];
         w.tag = t;
         w.short_list = tile_samp[qt] != t;
+        w.win_lo = w.win_hi = 0;
         return w;
     }
     template <int EG, int KCP>

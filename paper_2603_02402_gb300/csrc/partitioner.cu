@@ -511,6 +511,7 @@ struct ProbeWork {
         w.j_end = doff[lo + 1];
         w.tag = lo;
         w.short_list = false;
+        w.win_lo = w.win_hi = 0;
         return w;
     }
     template <int EG, int KCP>

@@ -48,9 +48,11 @@ struct RowTopK {
     }
 };
 
-// Shared-memory candidate buffer of one thread: entry e lives at
-// base[e * stride]; with stride = threads per block, lanes of a warp always
-// hit distinct banks whatever their fill levels.
+// Shared-memory candidate buffer of one thread: keys of entry e at
+// keys[e * STRIDE], ids at keys[(CAP + e) * STRIDE] (the id block follows the
+// key block); with STRIDE = threads per block, lanes of a warp always hit
+// distinct banks whatever their fill levels.  The buffer is addressed by its
+// 32-bit shared-window address, which keeps the register cost at one word.
 //
 // All calls are warp-synchronous (every lane of the warp calls them
 // together): the decision to merge buffers into the register lists is taken
@@ -61,20 +63,19 @@ struct RowTopK {
 //
 // SHORT > 0: when `shortl` is set only the best SHORT entries are wanted, so
 // the filtering threshold is the SHORT-th key (the list still keeps KC).
-template <int KC, int CAP, int SHORT = 0>
+template <int KC, int CAP, int STRIDE, int SHORT = 0>
 struct BufferedTopK {
+    static constexpr uint32_t kEntry = 4u * STRIDE;          // bytes between entries
+    static constexpr uint32_t kIds = 4u * STRIDE * CAP;      // bytes from keys to ids
     RowTopK<KC> list;
-    float *bkey;
-    int *bid;
-    int stride;
+    uint32_t sbase;   // shared address of this thread's key 0
     int cnt;
     bool shortl;
 
-    __device__ __forceinline__ void init(float *keys, int *ids, int thread, int nthreads) {
+    // `keys`: the block's buffer (2 * CAP * STRIDE words); thread < STRIDE.
+    __device__ __forceinline__ void init(float *keys, int thread) {
         list.init();
-        bkey = keys + thread;
-        bid = ids + thread;
-        stride = nthreads;
+        sbase = (uint32_t)__cvta_generic_to_shared(keys + thread);
         cnt = 0;
         shortl = false;
     }
@@ -89,13 +90,29 @@ struct BufferedTopK {
         else return list.thr();
     }
 
+    __device__ __forceinline__ void put(int e, float v, int j) const {
+        const uint32_t a = sbase + (uint32_t)e * kEntry;
+        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(a + kIds), "r"(j) : "memory");
+    }
+    __device__ __forceinline__ float key_at(int e) const {
+        float v;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(sbase + (uint32_t)e * kEntry) : "memory");
+        return v;
+    }
+    __device__ __forceinline__ int id_at(int e) const {
+        int j;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(j) : "r"(sbase + (uint32_t)e * kEntry + kIds) : "memory");
+        return j;
+    }
+
     // Merge every lane's buffer into its list (warp-synchronous).
     __device__ __forceinline__ void flush() {
         const int rounds = __reduce_max_sync(0xffffffffu, cnt);
         for (int e = 0; e < rounds; ++e) {
             if (e < cnt) {
-                const float v = bkey[e * stride];
-                if (v < bound()) list.insert(v, bid[e * stride]);
+                const float v = key_at(e);
+                if (v < bound()) list.insert(v, id_at(e));
             }
         }
         cnt = 0;
@@ -106,8 +123,7 @@ struct BufferedTopK {
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             if (v[i] < t) {
-                bkey[cnt * stride] = v[i];
-                bid[cnt * stride] = j0 + i;
+                put(cnt, v[i], j0 + i);
                 ++cnt;
             }
         }
