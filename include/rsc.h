@@ -78,6 +78,11 @@ typedef struct {
                             caller, recorded on `stream` before the prep pass,
                             before the candidate search, before the exact
                             re-rank and after it (per-phase timing); NULL = off */
+    int32_t locality;    /* tensor-core path: group rows by a coarse k-means
+                            before the search and let every query tile scan its
+                            own neighbourhood first (fewer top-k updates; the
+                            result is unchanged).  0 = automatic (on for
+                            n >= 16384), 1 = off, 2 = on                        */
 } rsc_knn_opts;
 
 /* Library version string (static storage). */

@@ -58,6 +58,7 @@ struct KnnPlan {
     int parts = 1;      // candidate lists per query per split
     int splits = 1;     // database splits
     int64_t split_len = 0;
+    bool order = false; // locality ordering before the tensor-core search
 };
 
 struct KnnLayout {
@@ -67,6 +68,8 @@ struct KnnLayout {
     float *prep_scratch;
     void *Qb, *Db;       // BF16 operands (tensor-core path only)
     int32_t *cand;
+    int32_t *perm;       // locality order (sorted position -> row), when planned
+    void *order_scratch;
 };
 
 rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_knn_opts *o,
@@ -83,6 +86,7 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     if (o->candidates < 0 || o->db_splits < 0) return fail(RSC_ERR_INVALID_ARG, "negative option");
     if (o->tc_parts != 0 && o->tc_parts != 2 && o->tc_parts != 4)
         return fail(RSC_ERR_INVALID_ARG, "tc_parts=%d (0, 2 or 4)", o->tc_parts);
+    if (o->locality < 0 || o->locality > 2) return fail(RSC_ERR_INVALID_ARG, "locality=%d (0, 1 or 2)", o->locality);
     rsc_knn_opts tuned;
     if (o->db_splits == 0 && o->candidates == 0 && o->tc_parts == 0) {   // automatic: tuned table first
         TunedChoice c;
@@ -97,6 +101,7 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     p->precision = o->precision;
     p->d = d;
     p->metric = metric;
+    p->order = o->precision == RSC_BF16 && (o->locality == 2 || (o->locality == 0 && n >= kOrderMinRows));
     p->DP = ((d + (metric == RSC_COSINE ? 1 : 0) + 7) / 8) * 8;
     int want = o->candidates;
     if (want == 0) want = (p->precision == RSC_FP32) ? k + 8 : 2 * k;
@@ -151,6 +156,12 @@ KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
         L.Db = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
     }
     L.cand = cv.take<int32_t>((size_t)p.splits * p.parts * n * p.KC);
+    L.perm = nullptr;
+    L.order_scratch = nullptr;
+    if (p.order) {
+        L.perm = cv.take<int32_t>((size_t)n);
+        L.order_scratch = cv.take<uint8_t>(order_scratch_bytes(n, p.DP));
+    }
     if (bytes) *bytes = cv.used;
     return L;
 }
@@ -288,12 +299,12 @@ rsc_status enqueue_batched(const float *X, const BatchedPlan &p, const BatchedLa
     RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
     RSC_CUDA_TRY(cudaMemcpyAsync(L.tables, tables_host, batched_tables_bytes((int)p.T, p.S), cudaMemcpyHostToDevice, st));
     RSC_CUDA_TRY(launch_prep_fp32(X, n, d, p.DP, metric, L.Y, L.ny, L.prep_scratch, st));
-    RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.Qb, L.Db, st));
+    RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, nullptr, L.Qb, L.Db, st));
     RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.parts, L.tables, L.cand_w,
                                        L.cand_x, L.status, st));
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, p.parts, p.kw, iw, dw, st));
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, p.parts, p.kw, nullptr, iw, dw, st));
     RSC_CUDA_TRY(launch_rerank_cross(R, rs, n, d, metric, L.tables, p.S, (int)p.T, p.parts, L.cand_x, iw, dw, p.kw,
                                      p.kx, ix, dx, st));
     return RSC_OK;
@@ -359,10 +370,11 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[0], st));
     RSC_CUDA_TRY(launch_prep_fp32(X, n, d, p.DP, metric, L.Y, L.ny, L.prep_scratch, st));
     if (p.precision == RSC_BF16) {
-        RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.Qb, L.Db, st));
+        if (p.order) RSC_CUDA_TRY(launch_locality_order(L.Y, n, p.DP, kOrderIters, L.perm, L.order_scratch, st));
+        RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.perm, L.Qb, L.Db, st));
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
         RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, TcShape{p.parts, p.KC}, p.splits, p.split_len,
-                                   L.cand, L.status, st));
+                                   p.order ? kOrderWindow : 0, L.cand, L.status, st));
     } else {
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
         RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
@@ -371,7 +383,7 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     // exact re-rank reads the caller's rows (Euclidean) or the normalised rows (cosine)
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC, p.splits * p.parts, k, idx, dist, st));
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC, p.splits * p.parts, k, L.perm, idx, dist, st));
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[3], st));
     return RSC_OK;
 }

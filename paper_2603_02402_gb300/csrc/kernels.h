@@ -39,10 +39,31 @@ int tc_kb(int d, int metric);
 TcShape knn_tc_shape(int d, int metric, int k, int want, int parts_req);
 bool knn_tc_supported(int d, int metric);
 int64_t knn_tc_split_align();
-cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, void *Qb, void *Db,
-                             cudaStream_t st);
+// perm (nullable): operand row i is built from Y row perm[i].
+cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, const int32_t *perm, void *Qb,
+                             void *Db, cudaStream_t st);
+// window > 0: each query tile first scans the `window` database tiles on
+// either side of its own position (rows in locality order), then the rest.
 cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int splits,
-                          int64_t split_len, int32_t *cand, unsigned int *status, cudaStream_t st);
+                          int64_t split_len, int window, int32_t *cand, unsigned int *status, cudaStream_t st);
+
+// ---- order.cu -------------------------------------------------------------------
+// Locality ordering: coarse k-means (C centroids, Lloyd on a strided sample
+// of m = n / step rows), then a stable counting sort of all rows by centroid.
+constexpr int kOrderMaxCentroids = 512;
+constexpr int kOrderIters = 4;
+constexpr int64_t kOrderMinRows = 16384;   // automatic ordering from this many rows
+constexpr int kOrderWindow = 2;            // database tiles on each side scanned first
+struct OrderShape {
+    int C;
+    int64_t m, step;
+    int nchunk;
+};
+OrderShape order_shape(int64_t n);
+size_t order_scratch_bytes(int64_t n, int DP);
+// perm[sorted position] = original row, for the FP32 prep rows Y [n, DP].
+cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, int32_t *perm, void *scratch,
+                                  cudaStream_t st);
 
 // ---- knn_tc_batched.cu ---------------------------------------------------------
 // Batched search: one launch over (query tile of a sample) x (database sample)
@@ -78,8 +99,11 @@ void tuned_store(int kind, int precision, int metric, int d, int k, int kx, int6
 // cosine, whose column d is the zero-row flag), sorted by (distance, id) and
 // the first k written to idx/dist (Euclidean sqrt, cosine d^2 / 2 with the
 // zero-row convention).  splits * KC <= 1024.
+// perm (nullable): candidate lists are indexed by sorted position i, whose
+// original row is perm[i]; ids in the lists are sorted positions too.  The
+// output is always by original row and holds original ids.
 cudaError_t launch_rerank(const float *R, int64_t rs, int64_t n, int d, int metric,
-                          const int32_t *cand, int KC, int splits, int k, int32_t *idx,
+                          const int32_t *cand, int KC, int splits, int k, const int32_t *perm, int32_t *idx,
                           float *dist, cudaStream_t st);
 
 // ---- connectivities.cu -------------------------------------------------------

@@ -48,10 +48,10 @@ namespace tck {
 
 __global__ void __launch_bounds__(256)
 prep_bf16_kernel(const float *__restrict__ Y, int64_t n, int d, int DP, int metric, int KB,
-                 __nv_bfloat16 *__restrict__ Qb, __nv_bfloat16 *__restrict__ Db) {
+                 const int32_t *__restrict__ perm, __nv_bfloat16 *__restrict__ Qb, __nv_bfloat16 *__restrict__ Db) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float *y = Y + i * DP;
+    const float *y = Y + (perm ? (int64_t)perm[i] : i) * DP;
     const int W = 64 * KB;
     float nrm = 0.f;
     for (int t = 0; t < d; ++t) {
@@ -108,6 +108,7 @@ struct PlainWork {
     int64_t split_len;
     int32_t *cand;    // [splits * EG, n, KCP]
     int n_items;
+    int window;       // tiles on either side of the query tile scanned first (0: none)
 
     int64_t count_host() const { return n_items; }
     __device__ __forceinline__ int count() const { return n_items; }
@@ -121,6 +122,12 @@ struct PlainWork {
         w.tag = sp;
         w.short_list = false;
         w.win_lo = w.win_hi = 0;
+        if (window > 0 && w.q0 >= w.j_begin && w.q0 < w.j_end) {
+            const int T = (int)((w.j_end - w.j_begin + BN - 1) / BN);
+            const int tq = (int)((w.q0 - w.j_begin) / BN);
+            w.win_lo = max(0, tq - window);
+            w.win_hi = min(T, tq + window + 1);
+        }
         return w;
     }
     template <int EG, int KCP>
@@ -181,22 +188,22 @@ bool knn_tc_supported(int d, int metric) { return d >= 1 && d + (metric == RSC_E
 
 int64_t knn_tc_split_align() { return tck::BN; }
 
-cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, void *Qb, void *Db,
-                             cudaStream_t st) {
+cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, const int32_t *perm, void *Qb,
+                             void *Db, cudaStream_t st) {
     const int KB = tc_kb(d, metric);
     tck::prep_bf16_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
-        Y, n, d, DP, metric, KB, static_cast<__nv_bfloat16 *>(Qb), static_cast<__nv_bfloat16 *>(Db));
+        Y, n, d, DP, metric, KB, perm, static_cast<__nv_bfloat16 *>(Qb), static_cast<__nv_bfloat16 *>(Db));
     return cudaGetLastError();
 }
 
 cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int splits,
-                          int64_t split_len, int32_t *cand, unsigned int *status, cudaStream_t st) {
+                          int64_t split_len, int window, int32_t *cand, unsigned int *status, cudaStream_t st) {
     const int KB = tc_kb(d, metric);
     CUtensorMap mq, md;
     cudaError_t e = tck::make_map(&mq, Qb, n, KB, tck::BM);
     if (e != cudaSuccess) return e;
     if ((e = tck::make_map(&md, Db, n, KB, tck::BN)) != cudaSuccess) return e;
-    tck::PlainWork work{n, splits, split_len, cand, (int)(ceil_div(n, tck::BM) * splits)};
+    tck::PlainWork work{n, splits, split_len, cand, (int)(ceil_div(n, tck::BM) * splits), window};
 #define RSC_TC_CASE(kb, kcp, eg) return tck::launch_kernel<kb, kcp, eg>(mq, md, work, status, st)
     if (KB == 1 && sh.parts == 4 && sh.list == 16) RSC_TC_CASE(1, 16, 4);
     if (KB == 1 && sh.parts == 2 && sh.list == 16) RSC_TC_CASE(1, 16, 2);

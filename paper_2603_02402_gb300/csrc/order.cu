@@ -1,0 +1,306 @@
+// Locality ordering of the rows for the tensor-core candidate search.
+//
+// The search keeps, per (query row, column part), the best list seen so far
+// and admits a tile's values only when one beats the list's threshold.  Rows
+// that arrive in random order keep improving the lists for the whole scan
+// (about KC * ln(n / KC) improvements per list), and each improvement sends
+// the whole warp through the slow insertion path.  When a query first meets
+// its own neighbourhood, its thresholds are nearly final after a few tiles
+// and the rest of the scan is a pure min-and-compare.
+//
+// So, before the search, rows are grouped by a coarse k-means:
+//   1. C centroids start at strided rows; Lloyd iterations run on a strided
+//      sample of the rows;
+//   2. every row is assigned to its nearest centroid;
+//   3. a stable counting sort by centroid gives perm (sorted position ->
+//      original row).
+// The search then runs on the permuted operands and each query tile scans
+// the database tiles around its own position first.  The ordering changes
+// only the order in which candidates are met, never the set of distances
+// scanned: the result is still the exact scan's, and the FP32 re-rank maps
+// positions back to the original row ids and orders ties by them.
+//
+// Every step is deterministic: centroid sums run over each cluster's rows in
+// row order (after the stable sort) instead of atomics.
+#include <limits.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsc {
+
+namespace {
+
+constexpr int kCentTile = 64;        // centroids staged in shared memory per pass
+constexpr int kAssignThreads = 128;
+constexpr int kChunk = 8192;         // rows per warp in the counting sort
+constexpr int kSortWarps = 4;
+
+// Nearest centroid (squared distance |c|^2 - 2 x.c, ties to the lower index)
+// of rows i * step, i < m.  Thread per row; DP = padded row length.
+template <int DP>
+__global__ void __launch_bounds__(kAssignThreads)
+assign_kernel(const float *__restrict__ Y, int64_t m, int64_t step, const float *__restrict__ cent,
+              const float *__restrict__ cnorm, int C, int32_t *__restrict__ lab) {
+    __shared__ __align__(16) float cs[kCentTile][DP];
+    __shared__ float cn[kCentTile];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < m;
+    float x[DP];
+    const float4 *xr = reinterpret_cast<const float4 *>(Y + (active ? i * step : 0) * DP);
+#pragma unroll
+    for (int t4 = 0; t4 < DP / 4; ++t4) {
+        const float4 v = active ? xr[t4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[4 * t4] = v.x;
+        x[4 * t4 + 1] = v.y;
+        x[4 * t4 + 2] = v.z;
+        x[4 * t4 + 3] = v.w;
+    }
+    float best = INFINITY;
+    int bi = 0;
+    for (int c0 = 0; c0 < C; c0 += kCentTile) {
+        const int nc = min(kCentTile, C - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nc * DP; e += blockDim.x) cs[e / DP][e % DP] = cent[(int64_t)c0 * DP + e];
+        for (int e = threadIdx.x; e < nc; e += blockDim.x) cn[e] = cnorm[c0 + e];
+        __syncthreads();
+        for (int c = 0; c < nc; ++c) {
+            const float4 *cr = reinterpret_cast<const float4 *>(cs[c]);
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int t4 = 0; t4 < DP / 4; t4 += 2) {
+                const float4 u = cr[t4];
+                a0 = fmaf(x[4 * t4], u.x, a0);
+                a0 = fmaf(x[4 * t4 + 1], u.y, a0);
+                a0 = fmaf(x[4 * t4 + 2], u.z, a0);
+                a0 = fmaf(x[4 * t4 + 3], u.w, a0);
+                const float4 w = cr[t4 + 1];   // DP is a multiple of 8
+                a1 = fmaf(x[4 * t4 + 4], w.x, a1);
+                a1 = fmaf(x[4 * t4 + 5], w.y, a1);
+                a1 = fmaf(x[4 * t4 + 6], w.z, a1);
+                a1 = fmaf(x[4 * t4 + 7], w.w, a1);
+            }
+            const float s = fmaf(-2.f, a0 + a1, cn[c]);
+            if (s < best) {   // strict: the lower index wins ties
+                best = s;
+                bi = c0 + c;
+            }
+        }
+    }
+    if (active) lab[i] = bi;
+}
+
+// Centroid c <- row (c * n) / C; its squared norm alongside.
+__global__ void init_centroids_kernel(const float *__restrict__ Y, int64_t n, int DP, int C, float *__restrict__ cent,
+                                      float *__restrict__ cnorm) {
+    const int c = blockIdx.x;
+    const int64_t row = ((int64_t)c * n) / C;
+    float s = 0.f;
+    for (int t = threadIdx.x; t < DP; t += 32) {
+        const float v = Y[row * DP + t];
+        cent[(int64_t)c * DP + t] = v;
+        s = fmaf(v, v, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) cnorm[c] = s;
+}
+
+// Per-chunk label counts: warp w of the grid counts rows
+// [w * kChunk, (w + 1) * kChunk) into cnt[label * nchunk + w].
+__global__ void __launch_bounds__(kSortWarps * 32)
+chunk_hist_kernel(const int32_t *__restrict__ lab, int64_t m, int C, int nchunk, int32_t *__restrict__ cnt) {
+    extern __shared__ int32_t hs[];   // [kSortWarps][C]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * kSortWarps + warp;
+    int32_t *h = hs + warp * C;
+    for (int c = lane; c < C; c += 32) h[c] = 0;
+    __syncwarp();
+    if (ch < nchunk) {
+        const int64_t b = (int64_t)ch * kChunk, e = min(m, b + kChunk);
+        for (int64_t r = b + lane; r < e; r += 32) atomicAdd(&h[lab[r]], 1);
+        __syncwarp();
+        for (int c = lane; c < C; c += 32) cnt[(int64_t)c * nchunk + ch] = h[c];
+    }
+}
+
+// Exclusive scan of cnt[0 .. N) into off (one block; coalesced 1024-wide
+// tiles with a running carry).  off[N] = total.
+__global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int32_t *__restrict__ cnt, int64_t N,
+                                                              int32_t *__restrict__ off) {
+    __shared__ int32_t ws[32];
+    __shared__ int32_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < N; base += 1024) {
+        const int64_t i = base + tid;
+        const int32_t v = i < N ? cnt[i] : 0;
+        int32_t x = v;   // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t w = ws[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            ws[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const int32_t carry = carry_s;
+        const int32_t incl = x + (warp > 0 ? ws[warp - 1] : 0);
+        if (i < N) off[i] = carry + incl - v;
+        __syncthreads();
+        if (tid == 1023) carry_s = carry + incl;
+        __syncthreads();
+    }
+    if (tid == 0) off[N] = carry_s;
+}
+
+// Stable scatter: warp w walks its chunk in row order, 32 rows a step; rows
+// with equal labels within a step are ranked by lane (match_any), and a
+// per-label cursor carries the count across steps.  out[pos] = row * step.
+__global__ void __launch_bounds__(kSortWarps * 32)
+chunk_scatter_kernel(const int32_t *__restrict__ lab, int64_t m, int64_t step, int C, int nchunk,
+                     const int32_t *__restrict__ off, int32_t *__restrict__ out) {
+    extern __shared__ int32_t cur_s[];   // [kSortWarps][C]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * kSortWarps + warp;
+    int32_t *cur = cur_s + warp * C;
+    if (ch >= nchunk) return;
+    for (int c = lane; c < C; c += 32) cur[c] = off[(int64_t)c * nchunk + ch];
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t b = (int64_t)ch * kChunk, e = min(m, b + kChunk);
+    for (int64_t r0 = b; r0 < e; r0 += 32) {
+        const int64_t r = r0 + lane;
+        const bool act = r < e;
+        const int c = act ? lab[r] : -1 - lane;   // inactive lanes match nobody
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (act) {
+            const int pos = cur[c] + __popc(peers & lt);
+            out[pos] = (int32_t)(r * step);
+        }
+        __syncwarp();
+        if (act && (peers & lt) == 0) cur[c] += __popc(peers);   // the lowest lane of each label advances it
+        __syncwarp();
+    }
+}
+
+// Centroid c <- mean of its rows (sorted positions [off[c * nchunk],
+// off[(c + 1) * nchunk])), summed in row order; an empty cluster keeps its
+// centroid.  Warp per centroid.
+__global__ void centroid_mean_kernel(const float *__restrict__ Y, int DP, const int32_t *__restrict__ sorted_rows,
+                                     const int32_t *__restrict__ off, int nchunk, int C, float *__restrict__ cent,
+                                     float *__restrict__ cnorm) {
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= C) return;
+    const int32_t b = off[(int64_t)c * nchunk], e = off[(int64_t)(c + 1) * nchunk];
+    if (e == b) return;
+    float s0 = 0.f, s1 = 0.f;
+    for (int32_t p = b; p < e; ++p) {
+        const float *y = Y + (int64_t)sorted_rows[p] * DP;
+        if (lane < DP) s0 += y[lane];
+        if (lane + 32 < DP) s1 += y[lane + 32];
+    }
+    const float inv = 1.f / (float)(e - b);
+    s0 *= inv;
+    s1 *= inv;
+    if (lane < DP) cent[(int64_t)c * DP + lane] = s0;
+    if (lane + 32 < DP) cent[(int64_t)c * DP + lane + 32] = s1;
+    float q = (lane < DP ? s0 * s0 : 0.f) + (lane + 32 < DP ? s1 * s1 : 0.f);
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) cnorm[c] = q;
+}
+
+cudaError_t launch_assign(const float *Y, int DP, int64_t m, int64_t step, const float *cent, const float *cnorm,
+                          int C, int32_t *lab, cudaStream_t st) {
+    const unsigned blocks = (unsigned)ceil_div(m, kAssignThreads);
+#define RSC_ASSIGN(dp) \
+    case dp: assign_kernel<dp><<<blocks, kAssignThreads, 0, st>>>(Y, m, step, cent, cnorm, C, lab); break
+    switch (DP) {
+        RSC_ASSIGN(8);
+        RSC_ASSIGN(16);
+        RSC_ASSIGN(24);
+        RSC_ASSIGN(32);
+        RSC_ASSIGN(40);
+        RSC_ASSIGN(48);
+        RSC_ASSIGN(56);
+        RSC_ASSIGN(64);
+        default: return cudaErrorInvalidValue;
+    }
+#undef RSC_ASSIGN
+    return cudaGetLastError();
+}
+
+// Stable counting sort of labels lab[0 .. m) -> out (positions hold row * step).
+cudaError_t counting_sort(const int32_t *lab, int64_t m, int64_t step, int C, int32_t *cnt, int32_t *off,
+                          int32_t *out, cudaStream_t st) {
+    const int nchunk = (int)ceil_div(m, kChunk);
+    const unsigned blocks = (unsigned)ceil_div(nchunk, kSortWarps);
+    const size_t sm = sizeof(int32_t) * kSortWarps * C;
+    chunk_hist_kernel<<<blocks, kSortWarps * 32, sm, st>>>(lab, m, C, nchunk, cnt);
+    exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt, (int64_t)C * nchunk, off);
+    chunk_scatter_kernel<<<blocks, kSortWarps * 32, sm, st>>>(lab, m, step, C, nchunk, off, out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+OrderShape order_shape(int64_t n) {
+    OrderShape s;
+    s.C = (int)std::min<int64_t>(kOrderMaxCentroids, std::max<int64_t>(2, n / 4096));
+    s.m = std::min<int64_t>(n, (int64_t)s.C * 64);
+    s.step = n / s.m;
+    s.m = n / s.step;                       // rows i * step, i < m, all inside [0, n)
+    s.nchunk = (int)ceil_div(n, kChunk);    // the full sort has the most chunks
+    return s;
+}
+
+size_t order_scratch_bytes(int64_t n, int DP) {
+    const OrderShape s = order_shape(n);
+    const size_t cnt = (size_t)s.C * s.nchunk;
+    return 256 * 6 + sizeof(float) * ((size_t)s.C * DP + s.C)   // centroids, norms
+           + sizeof(int32_t) * (size_t)n                        // labels
+           + sizeof(int32_t) * (2 * cnt + 1)                    // counts, offsets
+           + sizeof(int32_t) * (size_t)s.m;                     // sorted sample rows
+}
+
+cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, int32_t *perm, void *scratch,
+                                  cudaStream_t st) {
+    const OrderShape s = order_shape(n);
+    if (DP % 8 != 0 || DP > 64) return cudaErrorInvalidValue;
+    Carve cv(scratch);
+    float *cent = cv.take<float>((size_t)s.C * DP);
+    float *cnorm = cv.take<float>((size_t)s.C);
+    int32_t *lab = cv.take<int32_t>((size_t)n);
+    const size_t ncnt = (size_t)s.C * s.nchunk;
+    int32_t *cnt = cv.take<int32_t>(ncnt);
+    int32_t *off = cv.take<int32_t>(ncnt + 1);
+    int32_t *srows = cv.take<int32_t>((size_t)s.m);
+    cudaError_t e;
+    init_centroids_kernel<<<s.C, 32, 0, st>>>(Y, n, DP, s.C, cent, cnorm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int mean_warps = 4;
+    for (int it = 0; it < iters; ++it) {   // Lloyd iterations on the sample
+        if ((e = launch_assign(Y, DP, s.m, s.step, cent, cnorm, s.C, lab, st)) != cudaSuccess) return e;
+        if ((e = counting_sort(lab, s.m, s.step, s.C, cnt, off, srows, st)) != cudaSuccess) return e;
+        // the sample sort used ceil(m / kChunk) chunks: offsets are indexed with that count
+        const int nch = (int)ceil_div(s.m, kChunk);
+        centroid_mean_kernel<<<(unsigned)ceil_div(s.C, mean_warps), mean_warps * 32, 0, st>>>(Y, DP, srows, off, nch,
+                                                                                           s.C, cent, cnorm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = launch_assign(Y, DP, n, 1, cent, cnorm, s.C, lab, st)) != cudaSuccess) return e;
+    return counting_sort(lab, n, 1, s.C, cnt, off, perm, st);
+}
+
+}  // namespace rsc

@@ -890,7 +890,7 @@ int round_probe(int R) { return R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8; }
 rsc_status prep_operands(const rsc_partitioner *p, cudaStream_t st, const float *X, int64_t n, const PartLayout &L) {
     const int DP = ((p->d + 7) / 8) * 8;
     RSC_CUDA_TRY(launch_prep_fp32(X, n, p->d, DP, RSC_EUCLIDEAN, L.Y, L.ny, L.prep_scratch, st));
-    RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, p->d, DP, RSC_EUCLIDEAN, L.Qb, L.Db, st));
+    RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, p->d, DP, RSC_EUCLIDEAN, nullptr, L.Qb, L.Db, st));
     return RSC_OK;
 }
 

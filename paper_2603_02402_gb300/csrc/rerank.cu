@@ -25,7 +25,7 @@ __device__ __forceinline__ bool pair_gt(float ka, int ia, float kb, int ib) {
 
 __global__ void __launch_bounds__(kWarps * 32)
 rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int metric,
-              const int32_t *__restrict__ cand, int KC, int C, int C2, int k,
+              const int32_t *__restrict__ cand, int KC, int C, int C2, int k, const int32_t *__restrict__ perm,
               int32_t *__restrict__ idx, float *__restrict__ dist) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -34,12 +34,13 @@ rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int met
     float *skey = reinterpret_cast<float *>(smem) + kWarps * XQ + warp * C2;
     int *sid = reinterpret_cast<int *>(reinterpret_cast<float *>(smem) + kWarps * XQ + kWarps * C2) + warp * C2;
 
-    const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t q = (int64_t)blockIdx.x * kWarps + warp;   // position in the candidate lists
     if (q >= n) return;
+    const int64_t qo = perm ? (int64_t)perm[q] : q;            // original row
 
     const bool cosine = metric == RSC_COSINE;
     const int width = cosine ? d + 1 : d;
-    for (int t = lane; t < width; t += 32) xq[t] = R[q * rs + t];
+    for (int t = lane; t < width; t += 32) xq[t] = R[qo * rs + t];
     __syncwarp();
     const bool fq = cosine && xq[d] != 0.f;
 
@@ -48,8 +49,9 @@ rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int met
         int id = INT_MAX;
         if (c < C) {
             const int s = c / KC, slot = c - s * KC;
-            const int32_t j = cand[((int64_t)s * n + q) * KC + slot];
+            int32_t j = cand[((int64_t)s * n + q) * KC + slot];
             if (j >= 0) {
+                if (perm) j = perm[j];
                 const float *yr = R + (int64_t)j * rs;
                 float acc = 0.f;
                 for (int t = 0; t < d; ++t) {
@@ -94,15 +96,15 @@ rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int met
         const int id = sid[c];
         const float key = skey[c];
         const bool valid = id != INT_MAX;
-        idx[q * k + c] = valid ? id : -1;
-        dist[q * k + c] = valid ? (cosine ? 0.5f * key : sqrtf(key)) : INFINITY;
+        idx[qo * k + c] = valid ? id : -1;
+        dist[qo * k + c] = valid ? (cosine ? 0.5f * key : sqrtf(key)) : INFINITY;
     }
 }
 
 }  // namespace
 
 cudaError_t launch_rerank(const float *R, int64_t rs, int64_t n, int d, int metric,
-                          const int32_t *cand, int KC, int splits, int k, int32_t *idx,
+                          const int32_t *cand, int KC, int splits, int k, const int32_t *perm, int32_t *idx,
                           float *dist, cudaStream_t st) {
     const int C = KC * splits;
     int C2 = 32;
@@ -111,7 +113,7 @@ cudaError_t launch_rerank(const float *R, int64_t rs, int64_t n, int d, int metr
     constexpr int XQ = 65;
     const size_t smem = sizeof(float) * kWarps * XQ + (sizeof(float) + sizeof(int)) * kWarps * C2;
     const unsigned blocks = (unsigned)ceil_div(n, kWarps);
-    rerank_kernel<<<blocks, kWarps * 32, smem, st>>>(R, rs, n, d, metric, cand, KC, C, C2, k, idx, dist);
+    rerank_kernel<<<blocks, kWarps * 32, smem, st>>>(R, rs, n, d, metric, cand, KC, C, C2, k, perm, idx, dist);
     return cudaGetLastError();
 }
 

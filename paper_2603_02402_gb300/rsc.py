@@ -39,7 +39,8 @@ class RscError(RuntimeError):
 class rsc_knn_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("candidates", ctypes.c_int32),
                 ("db_splits", ctypes.c_int32), ("tc_parts", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("phase_events", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("phase_events", ctypes.c_void_p),
+                ("locality", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); the full exported surface of include/rsc.h
@@ -134,9 +135,14 @@ def rsc_workspace_status(workspace: torch.Tensor, stream=None) -> int:
     return int(lib().rsc_workspace_status(_ptr(workspace), _stream(stream)))
 
 
-def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_events=None) -> rsc_knn_opts:
+_LOCALITY = {"auto": 0, "off": 1, "on": 2}
+
+
+def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_events=None,
+             locality="auto") -> rsc_knn_opts:
     """Option struct; `phase_events` is a ctypes array of 4 raw cudaEvent_t."""
     o = rsc_knn_opts()
+    o.locality = _LOCALITY[locality] if isinstance(locality, str) else int(locality)
     o.phase_events = ctypes.cast(phase_events, ctypes.c_void_p).value if phase_events is not None else None
     o.precision = _PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.candidates = int(candidates)
@@ -145,16 +151,17 @@ def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_eve
     return o
 
 
-def rsc_knn_workspace_size(n, d, k, metric="euclidean", precision="fp32", candidates=0, db_splits=0) -> int:
-    o = knn_opts(precision, candidates, db_splits, stream=None) if torch.cuda.is_available() else rsc_knn_opts(
-        _PRECISIONS[precision], candidates, db_splits, 0, None, None)
+def rsc_knn_workspace_size(n, d, k, metric="euclidean", precision="fp32", candidates=0, db_splits=0,
+                           locality="auto") -> int:
+    o = knn_opts(precision, candidates, db_splits, stream=None, locality=locality) if torch.cuda.is_available() \
+        else rsc_knn_opts(_PRECISIONS[precision], candidates, db_splits, 0, None, None, _LOCALITY[locality])
     out = _sz(0)
     _check(lib().rsc_knn_workspace_size(n, d, k, _METRICS.get(metric, metric), ctypes.byref(o), ctypes.byref(out)))
     return int(out.value)
 
 
 def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candidates=0, db_splits=0,
-            stream=None, workspace=None, out=None, phase_events=None):
+            stream=None, workspace=None, out=None, phase_events=None, locality="auto"):
     """Exact kNN of every row of X (float32 [n, d] on the GPU).
 
     Returns (idx int32 [n, k], dist float32 [n, k]) on X's device.
@@ -163,7 +170,7 @@ def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candi
         raise ValueError("X must be a contiguous float32 [n, d] CUDA tensor")
     n, d = X.shape
     m = _METRICS[metric] if isinstance(metric, str) else int(metric)
-    o = knn_opts(precision, candidates, db_splits, stream, phase_events)
+    o = knn_opts(precision, candidates, db_splits, stream, phase_events, locality)
     need = _sz(0)
     _check(lib().rsc_knn_workspace_size(n, d, k, m, ctypes.byref(o), ctypes.byref(need)))
     ws = _workspace(need.value, X.device, workspace)

@@ -90,6 +90,25 @@ def test_candidate_option_errors(L):
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
     o = rsc.rsc_knn_opts(1, 0, 0, 3, None, None)       # tc_parts must be 0, 2 or 4
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.rsc_knn_opts(1, 0, 0, 0, None, None, 3)    # locality must be 0, 1 or 2
+    assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+
+
+def _ws(L, n, precision, locality):
+    out = ctypes.c_size_t(0)
+    o = rsc.rsc_knn_opts(precision, 0, 0, 0, None, None, locality)
+    assert L.rsc_knn_workspace_size(n, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_OK
+    return out.value
+
+
+def test_locality_workspace(L):
+    # the ordering adds a permutation (4 bytes per row) and its k-means scratch
+    # to the BF16 workspace; automatic from 16,384 rows; no effect on FP32
+    n = 100_000
+    off, on, auto = (_ws(L, n, 1, v) for v in (1, 2, 0))
+    assert on >= off + 4 * n and auto == on
+    assert _ws(L, 10_000, 1, 0) == _ws(L, 10_000, 1, 1) < _ws(L, 10_000, 1, 2)
+    assert _ws(L, n, 0, 2) == _ws(L, n, 0, 1)
 
 
 def test_connectivities_argument_errors(L):

@@ -22,7 +22,8 @@ def rsc():
 def run_knn(rsc, X, k, metric="euclidean", precision="fp32", **kw):
     Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
     ws = torch.empty(rsc.rsc_knn_workspace_size(*X.shape, k, metric, precision,
-                                                kw.get("candidates", 0), kw.get("db_splits", 0)),
+                                                kw.get("candidates", 0), kw.get("db_splits", 0),
+                                                kw.get("locality", "auto")),
                      dtype=torch.uint8, device="cuda")
     idx, dist = rsc.rsc_knn(Xd, k, metric, precision, workspace=ws, **kw)
     assert rsc.rsc_workspace_status(ws) == rsc.RSC_OK
@@ -118,3 +119,47 @@ def test_query_sample_of_large_input(rsc, precision):
     oi, od, on = oracle.knn(X, 15, queries=q)
     gi, gd = _maybe(rsc, lambda: run_knn(rsc, X, 15, precision=precision))
     check_knn(X, gi[q], gd[q], oi, od, on, rows=q, allow_miss=MISS[precision])
+
+
+# ---- locality ordering (coarse k-means + stable sort, window-first scan)
+
+@pytest.mark.parametrize("n,d,k,splits", [
+    (300, 50, 15, 0), (2049, 50, 15, 0), (5000, 50, 15, 3), (9001, 50, 30, 0), (4097, 16, 7, 2),
+    (20000, 50, 15, 0),
+])
+def test_locality_order_parity(rsc, n, d, k, splits):
+    # forced ordering on several tiles, ragged tails and database splits: the
+    # oracle's neighbours, and the same output as the unordered scan
+    X = synth.mixture(n, d, n_comp=12, seed=n)
+    oi, od, on = oracle.knn(X, k)
+    gi, gd = run_knn(rsc, X, k, precision="bf16", db_splits=splits, locality="on")
+    check_knn(X, gi, gd, oi, od, on, allow_miss=MISS["bf16"])
+    ui, ud = run_knn(rsc, X, k, precision="bf16", db_splits=splits, locality="off")
+    np.testing.assert_array_equal(gi, ui)
+    np.testing.assert_array_equal(gd, ud)
+
+
+def test_locality_order_cosine_zero_rows(rsc):
+    X = synth.mixture(6000, 50, n_comp=20, seed=9)
+    X[[3, 2500, 5999]] = 0.0
+    oi, od, on = oracle.knn(X, 30, metric=oracle.COSINE)
+    gi, gd = run_knn(rsc, X, 30, metric="cosine", precision="bf16", locality="on")
+    check_knn(X, gi, gd, oi, od, on, metric="cosine", allow_miss=MISS["bf16"])
+    assert gi[3].tolist()[:3] == [3, 2500, 5999]
+
+
+def test_locality_order_integer_ties(rsc):
+    # exact FP32 distances with many ties: ties still break by original row id
+    g = np.stack(np.meshgrid(np.arange(16), np.arange(16), np.arange(12)), -1).reshape(-1, 3)
+    X = np.concatenate([g, g[:100]]).astype(np.float32)
+    oi, od, on = oracle.knn(X, 15)
+    gi, gd = run_knn(rsc, X, 15, precision="bf16", locality="on")
+    check_knn(X, gi, gd, oi, od, on, allow_miss=MISS["bf16"])
+
+
+def test_locality_order_is_deterministic(rsc):
+    X = synth.mixture(30000, 50, n_comp=40, seed=12)
+    a = run_knn(rsc, X, 15, precision="bf16", locality="on")
+    b = run_knn(rsc, X, 15, precision="bf16", locality="on")
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
