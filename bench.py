@@ -37,9 +37,22 @@ WORKLOAD = ("1,000,000 cells x 50 PCs fp32, 100-cluster Gaussian mixture (means 
 # (profiles/), valid only while the kernel source is unchanged.
 TRAFFIC = {}
 
-# Kernels this library launches per step (rsc_knn: column sums, column means,
-# prep, candidate search, re-rank; rsc_connectivities: 10 phases).
-LAUNCHES_PER_STEP = {"euclidean": 5 + 10, "cosine": 3 + 10}
+ORDER_MIN_ROWS = 16384   # automatic locality ordering from this many rows (BF16 path)
+
+
+def launches_per_step(metric, precision, n):
+    """Kernels this library launches per graph step.
+
+    rsc_knn: FP32 prep (column sums + column means + prep for Euclidean, prep
+    alone for cosine), the BF16 operand prep (tensor-core path), the locality
+    ordering (1 init + 4 Lloyd rounds x 5 + 4 for the final assignment and
+    sort, + 1 gather of the re-rank rows), the candidate search and the
+    re-rank; rsc_connectivities: 11.
+    """
+    knn = (3 if metric == "euclidean" else 1) + 2
+    if precision == "bf16":
+        knn += 1 + (26 if n >= ORDER_MIN_ROWS else 0)
+    return knn + 11
 
 
 def parse():
@@ -346,7 +359,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": LAUNCHES_PER_STEP[metric] * args.steps,
+            "gpu_launches": launches_per_step(metric, precision, n) * args.steps,
             "clocks": clocks,
         }
         if fp32:
@@ -585,6 +598,7 @@ def run_cosine(args):
             "roofline": {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops / (ms / 1e3) / 1e12 / peak, "traffic": None,
                          "note": "whole step timed; 2*d flops per (query, row) pair"},
+            "gpu_launches": launches_per_step("cosine", "bf16", n) * args.steps,
             "clocks": sampler.summary()}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle

@@ -70,6 +70,7 @@ struct KnnLayout {
     int32_t *cand;
     int32_t *perm;       // locality order (sorted position -> row), when planned
     void *order_scratch;
+    float *Rp;           // re-rank rows in sorted order, when planned
 };
 
 rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_knn_opts *o,
@@ -158,9 +159,11 @@ KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
     L.cand = cv.take<int32_t>((size_t)p.splits * p.parts * n * p.KC);
     L.perm = nullptr;
     L.order_scratch = nullptr;
+    L.Rp = nullptr;
     if (p.order) {
         L.perm = cv.take<int32_t>((size_t)n);
         L.order_scratch = cv.take<uint8_t>(order_scratch_bytes(n, p.DP));
+        L.Rp = cv.take<float>((size_t)n * (p.metric == RSC_EUCLIDEAN ? ceil_div(p.d, 4) * 4 : p.DP));
     }
     if (bytes) *bytes = cv.used;
     return L;
@@ -178,7 +181,7 @@ rsc_status check_ws(void *ws, size_t have, size_t need) {
 struct ConnLayout {
     ConnWork w;
     int64_t *indptr_tmp;
-    int32_t *zeroed;       // in_cnt, cursor, long_count (2n + 1 int32)
+    int32_t *zeroed;       // in_cnt, cursor, long_count, mid_count (2n + 2 int32)
 };
 
 ConnLayout carve_conn(void *ws, int64_t n, int k, size_t *bytes) {
@@ -189,15 +192,19 @@ ConnLayout carve_conn(void *ws, int64_t n, int k, size_t *bytes) {
     L.w.mean_all = cv.take<float>(1);
     L.w.rho = cv.take<float>((size_t)n);
     L.w.sigma = cv.take<float>((size_t)n);
-    L.w.scol = cv.take<int32_t>((size_t)n * k);
-    L.w.sw = cv.take<float>((size_t)n * k);
-    L.w.gv = cv.take<float>((size_t)n * k);
+    const size_t KP = (size_t)conn_stride(k);
+    L.w.scol = cv.take<int32_t>((size_t)n * KP);
+    L.w.sw = cv.take<float>((size_t)n * KP);
+    L.w.gv = cv.take<float>((size_t)n * KP);
+    L.w.tslot = cv.take<int32_t>(k <= 32 ? (size_t)n * KP : 1);
     L.w.own_cnt = cv.take<int32_t>((size_t)n);
-    L.zeroed = cv.take<int32_t>((size_t)2 * n + 1);
+    L.zeroed = cv.take<int32_t>((size_t)2 * n + 2);
     L.w.in_cnt = L.zeroed;
     L.w.cursor = L.zeroed ? L.zeroed + n : nullptr;
     L.w.long_count = L.zeroed ? L.zeroed + 2 * n : nullptr;
+    L.w.mid_count = L.zeroed ? L.zeroed + 2 * n + 1 : nullptr;
     L.w.long_rows = cv.take<int32_t>((size_t)n);
+    L.w.mid_rows = cv.take<int32_t>((size_t)n);
     L.w.scan_part = cv.take<int64_t>(conn_scan_blocks(n));
     L.indptr_tmp = cv.take<int64_t>((size_t)n + 1);
     if (bytes) *bytes = cv.used;
@@ -217,7 +224,7 @@ rsc_status conn_count_phase(const int32_t *idx, const float *dist, int64_t n, in
     if (rho) L.w.rho = rho;
     if (sigma) L.w.sigma = sigma;
     RSC_CUDA_TRY(cudaMemsetAsync(L.w.status, 0, sizeof(unsigned int), st));
-    RSC_CUDA_TRY(cudaMemsetAsync(L.zeroed, 0, sizeof(int32_t) * (2 * n + 1), st));
+    RSC_CUDA_TRY(cudaMemsetAsync(L.zeroed, 0, sizeof(int32_t) * (2 * n + 2), st));
     RSC_CUDA_TRY(launch_conn_count(idx, dist, n, k, indptr, L.w, st));
     return RSC_OK;
 }
@@ -304,7 +311,8 @@ rsc_status enqueue_batched(const float *X, const BatchedPlan &p, const BatchedLa
                                        L.cand_x, L.status, st));
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, p.parts, p.kw, nullptr, iw, dw, st));
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, p.parts, p.kw, nullptr, false, iw, dw,
+                               st));
     RSC_CUDA_TRY(launch_rerank_cross(R, rs, n, d, metric, L.tables, p.S, (int)p.T, p.parts, L.cand_x, iw, dw, p.kw,
                                      p.kx, ix, dx, st));
     return RSC_OK;
@@ -383,7 +391,14 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     // exact re-rank reads the caller's rows (Euclidean) or the normalised rows (cosine)
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
     const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand, p.KC, p.splits * p.parts, k, L.perm, idx, dist, st));
+    int64_t rsr = rs;
+    if (p.order) {   // rows in search order, 16-byte aligned: neighbouring queries share cache lines
+        rsr = (metric == RSC_EUCLIDEAN) ? ceil_div(d, 4) * 4 : p.DP;
+        RSC_CUDA_TRY(launch_gather_rows(R, rs, n, (int)rs, L.perm, L.Rp, rsr, st));
+        R = L.Rp;
+    }
+    RSC_CUDA_TRY(launch_rerank(R, rsr, n, d, metric, L.cand, p.KC, p.splits * p.parts, k, L.perm, p.order, idx, dist,
+                               st));
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[3], st));
     return RSC_OK;
 }

@@ -101,30 +101,41 @@ void tuned_store(int kind, int precision, int metric, int d, int k, int kx, int6
 // zero-row convention).  splits * KC <= 1024.
 // perm (nullable): candidate lists are indexed by sorted position i, whose
 // original row is perm[i]; ids in the lists are sorted positions too.  The
-// output is always by original row and holds original ids.
+// output is always by original row and holds original ids.  r_by_pos: R holds
+// the rows in sorted order (R row i = original row perm[i]), so the gathers of
+// neighbouring queries' candidates stay close in memory.
 cudaError_t launch_rerank(const float *R, int64_t rs, int64_t n, int d, int metric,
-                          const int32_t *cand, int KC, int splits, int k, const int32_t *perm, int32_t *idx,
-                          float *dist, cudaStream_t st);
+                          const int32_t *cand, int KC, int splits, int k, const int32_t *perm, bool r_by_pos,
+                          int32_t *idx, float *dist, cudaStream_t st);
+// dst row i <- src row perm[i] (width floats per row).
+cudaError_t launch_gather_rows(const float *src, int64_t src_stride, int64_t n, int width, const int32_t *perm,
+                               float *dst, int64_t dst_stride, cudaStream_t st);
 
 // ---- connectivities.cu -------------------------------------------------------
 struct ConnWork {
     float *partials;     // [kMeanBlocks]
     float *mean_all;     // [1]
     float *rho, *sigma;  // [n]
-    int32_t *scol;       // [n, k] row's columns, ascending (INT32_MAX pads)
-    float *sw;           // [n, k] directed weights in scol order
-    float *gv;           // [n, k] union value of each own entry (negative: also
+    int32_t *scol;       // [n, KP] row's columns, ascending (INT32_MAX pads)
+    float *sw;           // [n, KP] directed weights in scol order
+    float *gv;           // [n, KP] union value of each own entry (negative: also
                          //        emit the transposed entry)
+    int32_t *tslot;      // [n, KP] place of a transposed entry in its row (k <= 32)
     int32_t *own_cnt;    // [n]
     int32_t *in_cnt;     // [n]   (zeroed by the launcher)
     int32_t *cursor;     // [n]   (zeroed by the launcher)
     int32_t *long_rows;  // [n]
     int32_t *long_count; // [1]   (zeroed by the launcher)
+    int32_t *mid_rows;   // [n]
+    int32_t *mid_count;  // [1]   (zeroed by the launcher)
     int64_t *scan_part;  // [scan blocks]
     unsigned int *status;
 };
 constexpr int kMeanBlocks = 512;
 size_t conn_scan_blocks(int64_t n);
+// Row stride KP of scol / sw / gv: k rounded up to 4 (16-byte rows) when
+// k <= 32 (lane-per-entry kernels), else k.
+inline int conn_stride(int k) { return k <= 32 ? (k + 3) / 4 * 4 : k; }
 // Phases: rho/sigma/weights + in-degree counts + row pointers.
 cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, int k,
                               int64_t *indptr, const ConnWork &w, cudaStream_t st);
