@@ -45,13 +45,15 @@ def launches_per_step(metric, precision, n):
 
     rsc_knn: FP32 prep (column sums + column means + prep for Euclidean, prep
     alone for cosine), the BF16 operand prep (tensor-core path), the locality
-    ordering (1 init + 4 Lloyd rounds x 5 + 4 for the final assignment and
-    sort, + 1 gather of the re-rank rows), the candidate search and the
-    re-rank; rsc_connectivities: 11.
+    ordering (two k-means levels of 1 init + 4 Lloyd rounds x 5 + 4 for the
+    full assignment and sort, + 1 gather of the re-rank rows), the candidate
+    search (one launch, or 9 when pruned: window pass, 2 sphere passes, tau,
+    count, scan, fill, offsets, list pass) and the re-rank;
+    rsc_connectivities: 11.
     """
     knn = (3 if metric == "euclidean" else 1) + 2
     if precision == "bf16":
-        knn += 1 + (26 if n >= ORDER_MIN_ROWS else 0)
+        knn += 1 + (51 + 8 if n >= ORDER_MIN_ROWS else 0)
     return knn + 11
 
 

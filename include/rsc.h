@@ -67,7 +67,8 @@ typedef enum {
 typedef struct {
     int32_t precision;   /* rsc_precision used to select candidates          */
     int32_t candidates;  /* candidates kept per query before the exact FP32
-                            re-rank; 0 = default (k + 8 for FP32, 2k for BF16);
+                            re-rank; 0 = default (k + 8 for FP32, 2k for BF16
+                            Euclidean, 4k for BF16 cosine, at most 64 / 128);
                             rounded up to a supported width (16, 32, 64)  */
     int32_t db_splits;   /* split the database into this many ranges handled
                             by separate CTAs (small n); 0 = automatic          */
@@ -83,6 +84,13 @@ typedef struct {
                             own neighbourhood first (fewer top-k updates; the
                             result is unchanged).  0 = automatic (on for
                             n >= 16384), 1 = off, 2 = on                        */
+    int32_t prune;       /* tensor-core path with locality ordering: after a first
+                            pass over each query tile's neighbourhood, skip the
+                            database tiles whose bounding sphere is provably too
+                            far from the query tile's to improve any of its
+                            lists (exact: the candidates equal the full scan's).
+                            0 = automatic (on with the ordering, one database
+                            split, d + 3 <= 64), 1 = off, 2 = on               */
 } rsc_knn_opts;
 
 /* Library version string (static storage). */
@@ -122,6 +130,20 @@ rsc_status rsc_knn_workspace_size(int64_t n, int32_t d, int32_t k, int32_t metri
 rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metric,
                    int32_t *idx, float *dist, const rsc_knn_opts *opts,
                    void *workspace, size_t workspace_bytes);
+
+/*
+ * Work done by the candidate search of the last rsc_knn call that used
+ * `workspace` with these same arguments (a diagnostic; the paper has no
+ * counterpart).  Counts pairs of a 128-row query tile and a 256-row database
+ * tile: *pairs_total (host) = query tiles x database tiles, *pairs_scanned
+ * (host) = the pairs whose distances were computed (= total without
+ * pruning).  Reads the workspace after synchronising opts->stream.
+ * Errors: RSC_ERR_INVALID_ARG for NULL outputs or arguments rsc_knn would
+ * reject; RSC_ERR_WORKSPACE when the workspace is missing or too small.
+ */
+rsc_status rsc_knn_scan_stats(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_knn_opts *opts,
+                              void *workspace, size_t workspace_bytes, int64_t *pairs_scanned,
+                              int64_t *pairs_total);
 
 /*
  * Autotuner.  Options left at 0 (db_splits, candidates, tc_parts) are

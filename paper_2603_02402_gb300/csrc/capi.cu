@@ -59,6 +59,7 @@ struct KnnPlan {
     int splits = 1;     // database splits
     int64_t split_len = 0;
     bool order = false; // locality ordering before the tensor-core search
+    bool prune = false; // window pass + tile bounds + list pass instead of one full scan
 };
 
 struct KnnLayout {
@@ -71,6 +72,9 @@ struct KnnLayout {
     int32_t *perm;       // locality order (sorted position -> row), when planned
     void *order_scratch;
     float *Rp;           // re-rank rows in sorted order, when planned
+    float *st_key;       // saved lists of the pruned search [n, parts, KC]
+    int32_t *st_id;
+    void *prune_scratch;
 };
 
 rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_knn_opts *o,
@@ -88,6 +92,7 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     if (o->tc_parts != 0 && o->tc_parts != 2 && o->tc_parts != 4)
         return fail(RSC_ERR_INVALID_ARG, "tc_parts=%d (0, 2 or 4)", o->tc_parts);
     if (o->locality < 0 || o->locality > 2) return fail(RSC_ERR_INVALID_ARG, "locality=%d (0, 1 or 2)", o->locality);
+    if (o->prune < 0 || o->prune > 2) return fail(RSC_ERR_INVALID_ARG, "prune=%d (0, 1 or 2)", o->prune);
     rsc_knn_opts tuned;
     if (o->db_splits == 0 && o->candidates == 0 && o->tc_parts == 0) {   // automatic: tuned table first
         TunedChoice c;
@@ -105,13 +110,16 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     p->order = o->precision == RSC_BF16 && (o->locality == 2 || (o->locality == 0 && n >= kOrderMinRows));
     p->DP = ((d + (metric == RSC_COSINE ? 1 : 0) + 7) / 8) * 8;
     int want = o->candidates;
-    if (want == 0) want = (p->precision == RSC_FP32) ? k + 8 : 2 * k;
+    // BF16 candidates: 2k for Euclidean rows; unit-length cosine rows crowd
+    // their distances together, so BF16 rounding reorders more of them: 4k
+    if (want == 0) want = (p->precision == RSC_FP32) ? k + 8 : (metric == RSC_COSINE ? 4 * k : 2 * k);
     if (want < k) return fail(RSC_ERR_INVALID_ARG, "candidates=%d smaller than k=%d", want, k);
     if (want > 64) {
         if (o->candidates != 0 && p->precision == RSC_FP32)
             return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 64", want);
         if (o->candidates > 128) return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 128", want);
-        if (o->candidates == 0) want = 64;
+        if (o->candidates == 0)
+            want = (metric == RSC_COSINE && p->precision == RSC_BF16) ? std::min(want, 128) : 64;
     }
     // candidates per row: FP32 lists of KC; tensor-core rows as parts x list
     const bool tc = p->precision == RSC_BF16;
@@ -141,6 +149,11 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     if (splits * per_split > 1024) return fail(RSC_ERR_INVALID_ARG, "db_splits * candidates above 1024");
     p->split_len = ceil_div(ceil_div(n, splits), align) * align;
     p->splits = (int)ceil_div(n, p->split_len);
+    // pruning: rows in locality order, one database split, one 64-element K block
+    const bool prune_ok = p->order && p->splits == 1 && tc && tc_kb(d, metric) == 1;
+    if (o->prune == 2 && !prune_ok)
+        return fail(RSC_ERR_UNSUPPORTED, "prune needs BF16, the locality ordering, one database split and d + 3 <= 64");
+    p->prune = prune_ok && o->prune != 1;
     return RSC_OK;
 }
 
@@ -164,6 +177,14 @@ KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
         L.perm = cv.take<int32_t>((size_t)n);
         L.order_scratch = cv.take<uint8_t>(order_scratch_bytes(n, p.DP));
         L.Rp = cv.take<float>((size_t)n * (p.metric == RSC_EUCLIDEAN ? ceil_div(p.d, 4) * 4 : p.DP));
+    }
+    L.st_key = nullptr;
+    L.st_id = nullptr;
+    L.prune_scratch = nullptr;
+    if (p.prune) {
+        L.st_key = cv.take<float>((size_t)n * p.parts * p.KC);
+        L.st_id = cv.take<int32_t>((size_t)n * p.parts * p.KC);
+        L.prune_scratch = cv.take<uint8_t>(prune_scratch_bytes(n, knn_tc_bm(), knn_tc_bn()));
     }
     if (bytes) *bytes = cv.used;
     return L;
@@ -381,8 +402,19 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
         if (p.order) RSC_CUDA_TRY(launch_locality_order(L.Y, n, p.DP, kOrderIters, L.perm, L.order_scratch, st));
         RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.perm, L.Qb, L.Db, st));
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
-        RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, TcShape{p.parts, p.KC}, p.splits, p.split_len,
-                                   p.order ? kOrderWindow : 0, L.cand, L.status, st));
+        const TcShape sh{p.parts, p.KC};
+        if (p.prune) {
+            RSC_CUDA_TRY(launch_knn_tc_window(L.Qb, L.Db, n, d, metric, sh, kOrderWindow, L.st_key, L.st_id, L.status,
+                                              st));
+            PruneOut po;
+            RSC_CUDA_TRY(launch_prune_bounds(L.Qb, n, d, metric, knn_tc_bm(), knn_tc_bn(), kOrderWindow, L.st_key,
+                                             p.parts, p.KC, L.prune_scratch, &po, st));
+            RSC_CUDA_TRY(launch_knn_tc_list(L.Qb, L.Db, n, d, metric, sh, kOrderWindow, L.st_key, L.st_id, po.tiles,
+                                            po.tile_off, po.overflow, L.cand, L.status, st));
+        } else {
+            RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, sh, p.splits, p.split_len,
+                                       p.order ? kOrderWindow : 0, L.cand, L.status, st));
+        }
     } else {
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
         RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
@@ -400,6 +432,39 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
     RSC_CUDA_TRY(launch_rerank(R, rsr, n, d, metric, L.cand, p.KC, p.splits * p.parts, k, L.perm, p.order, idx, dist,
                                st));
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[3], st));
+    return RSC_OK;
+}
+
+rsc_status rsc_knn_scan_stats(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_knn_opts *opts,
+                              void *workspace, size_t workspace_bytes, int64_t *pairs_scanned,
+                              int64_t *pairs_total) {
+    if (!pairs_scanned || !pairs_total) return fail(RSC_ERR_INVALID_ARG, "NULL output");
+    KnnPlan p;
+    rsc_status s = plan_knn(n, d, k, metric, opts, &p);
+    if (s != RSC_OK) return s;
+    size_t need = 0;
+    carve_knn(nullptr, n, p, &need);
+    if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
+    const int BM = knn_tc_bm(), BN = p.precision == RSC_BF16 ? knn_tc_bn() : BM;
+    const int64_t qt = ceil_div(n, BM), dt = ceil_div(n, BN);
+    *pairs_total = qt * dt;
+    *pairs_scanned = *pairs_total;
+    if (!p.prune) return RSC_OK;
+    KnnLayout L = carve_knn(workspace, n, p, nullptr);
+    const PruneOut po = prune_outputs(L.prune_scratch, n, BM, BN);
+    cudaStream_t st = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+    int64_t kept = 0;
+    int32_t overflow = 0;
+    RSC_CUDA_TRY(cudaMemcpyAsync(&kept, po.tile_off + qt, sizeof(kept), cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaMemcpyAsync(&overflow, po.overflow, sizeof(overflow), cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (overflow) return RSC_OK;   // the list pass scanned every tile
+    int64_t window = 0;
+    for (int64_t q = 0; q < qt; ++q) {
+        const int64_t tq = q * BM / BN;
+        window += std::min<int64_t>(dt, tq + kOrderWindow + 1) - std::max<int64_t>(0, tq - kOrderWindow);
+    }
+    *pairs_scanned = window + kept;
     return RSC_OK;
 }
 

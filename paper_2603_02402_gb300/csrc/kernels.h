@@ -48,15 +48,18 @@ cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int 
                           int64_t split_len, int window, int32_t *cand, unsigned int *status, cudaStream_t st);
 
 // ---- order.cu -------------------------------------------------------------------
-// Locality ordering: coarse k-means (C centroids, Lloyd on a strided sample
-// of m = n / step rows), then a stable counting sort of all rows by centroid.
-constexpr int kOrderMaxCentroids = 512;
+// Locality ordering: two-level k-means (C1 coarse clusters, then C2 sub-
+// clusters inside each; Lloyd on strided samples), then a stable counting
+// sort of all rows by (coarse, sub) label.
+constexpr int kOrderSub = 16;           // sub-clusters per coarse cluster
+constexpr int kOrderLeafRows = 512;     // target rows per sub-cluster
+constexpr int kOrderMaxCoarse = 128;
 constexpr int kOrderIters = 4;
 constexpr int64_t kOrderMinRows = 16384;   // automatic ordering from this many rows
 constexpr int kOrderWindow = 2;            // database tiles on each side scanned first
 struct OrderShape {
-    int C;
-    int64_t m, step;
+    int C1, C2;
+    int64_t m1, step1, m2, step2;
     int nchunk;
 };
 OrderShape order_shape(int64_t n);
@@ -64,6 +67,36 @@ size_t order_scratch_bytes(int64_t n, int DP);
 // perm[sorted position] = original row, for the FP32 prep rows Y [n, DP].
 cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, int32_t *perm, void *scratch,
                                   cudaStream_t st);
+
+// ---- knn_tc_prune.cu / prune.cu ---------------------------------------------------
+// Pruned search on rows in locality order (one database split, KB = 1):
+// a window pass saves every (row, part) list (keys and ids, [n, parts, list]),
+// launch_prune_bounds keeps per query tile the database tiles that can still
+// improve one of its lists, and the list pass resumes the lists over them.
+constexpr int64_t kPruneListCap = int64_t(1) << 28;   // kept (query tile, tile) pairs stored at most
+struct PruneShape {
+    int qtiles, dtiles, nchunk;
+    int64_t cap;
+};
+struct PruneOut {
+    int64_t *tile_off;   // [qtiles + 1]
+    int32_t *tiles;      // [cap]
+    int32_t *overflow;   // [1]: more kept pairs than cap (the list pass then scans every tile)
+};
+PruneShape prune_shape(int64_t n, int BM, int BN);
+size_t prune_scratch_bytes(int64_t n, int BM, int BN);
+PruneOut prune_outputs(void *scratch, int64_t n, int BM, int BN);   // the launcher's output pointers
+cudaError_t launch_prune_bounds(const void *Qb, int64_t n, int d, int metric, int BM, int BN, int window,
+                                const float *st_key, int EG, int KCP, void *scratch, PruneOut *out,
+                                cudaStream_t st);
+cudaError_t launch_knn_tc_window(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh,
+                                 int window, float *st_key, int32_t *st_id, unsigned int *status, cudaStream_t st);
+cudaError_t launch_knn_tc_list(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int window,
+                               const float *st_key, const int32_t *st_id, const int32_t *tiles,
+                               const int64_t *tile_off, const int32_t *overflow, int32_t *cand, unsigned int *status,
+                               cudaStream_t st);
+int knn_tc_bm();   // query rows per tensor-core work item
+int knn_tc_bn();   // database rows per tensor-core tile
 
 // ---- knn_tc_batched.cu ---------------------------------------------------------
 // Batched search: one launch over (query tile of a sample) x (database sample)

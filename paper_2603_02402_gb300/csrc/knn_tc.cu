@@ -103,6 +103,7 @@ prep_bf16_kernel(const float *__restrict__ Y, int64_t n, int d, int DP, int metr
 // Whole-matrix work: query tile qt (BM rows) x database split sp.
 struct PlainWork {
     static constexpr int kShort = 0;   // never used (short_list is false)
+    static constexpr bool kResume = false;
     int64_t n;
     int splits;
     int64_t split_len;
@@ -122,6 +123,9 @@ struct PlainWork {
         w.tag = sp;
         w.short_list = false;
         w.win_lo = w.win_hi = 0;
+        w.tiles = nullptr;
+        w.n_tiles = 0;
+        w.skip_window = false;
         if (window > 0 && w.q0 >= w.j_begin && w.q0 < w.j_end) {
             const int T = (int)((w.j_end - w.j_begin + BN - 1) / BN);
             const int tq = (int)((w.q0 - w.j_begin) / BN);
@@ -187,6 +191,8 @@ TcShape knn_tc_shape(int d, int metric, int k, int want, int parts_req) {
 bool knn_tc_supported(int d, int metric) { return d >= 1 && d + (metric == RSC_EUCLIDEAN ? 3 : 1) <= 128; }
 
 int64_t knn_tc_split_align() { return tck::BN; }
+int knn_tc_bm() { return tck::BM; }
+int knn_tc_bn() { return tck::BN; }
 
 cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, const int32_t *perm, void *Qb,
                              void *Db, cudaStream_t st) {

@@ -48,27 +48,49 @@ struct Cfg {
 
 // One work item: query rows [q0, q_end) (at most BM) against database rows
 // [j_begin, j_end).  short_list: only the best Work::kShort of each list are
-// needed (the threshold is the kShort-th key).
+// needed (the threshold is the kShort-th key).  A Work with kResume starts
+// each (row, part) list from work.resume() instead of empty.
 struct WorkItem {
     int64_t q0, q_end, j_begin, j_end;
     int tag;
     bool short_list;
-    int win_lo, win_hi;   // database tiles [win_lo, win_hi) (counted from j_begin) are scanned first
+    int win_lo, win_hi;     // database tiles [win_lo, win_hi) (counted from j_begin) are scanned first
+    const int32_t *tiles;   // non-null: scan exactly these tiles (ascending), nothing else
+    int n_tiles;
+    bool skip_window;       // scan [0, win_lo) and [win_hi, T) only (the window is already done)
 };
 
 // Visiting order of an item's T database tiles: the window [wlo, whi) first,
 // then [0, wlo), then [whi, T); every tile exactly once.  A tile costs one
 // increment and one compare; the range switch runs three times per item.
-// Requires 0 <= wlo <= whi <= T.
+// Requires 0 <= wlo <= whi <= T.  With an explicit list the tiles are
+// lst[0 .. nl) instead, read kAhead entries ahead of use so the list's
+// global-memory latency overlaps the tiles in flight (the producer and MMA
+// roles; the epilogue, which waits for each accumulator anyway, reads one
+// ahead and keeps its registers).
+template <int kAhead>
 struct TileSeq {
     int m, end, T, wlo, whi, phase;
+    const int32_t *lst;
+    int pos, nl;
+    int q[kAhead];   // lst[pos + 1 .. pos + kAhead]
 
-    __device__ __forceinline__ void init(int T_, int wlo_, int whi_) {
+    __device__ __forceinline__ void init(int T_, int wlo_, int whi_, const int32_t *lst_ = nullptr, int nl_ = 0,
+                                         bool skip_window = false) {
+        lst = lst_;
+        if (lst) {
+            pos = 0;
+            nl = nl_;
+            m = nl > 0 ? lst[0] : 0;
+#pragma unroll
+            for (int a = 0; a < kAhead; ++a) q[a] = (1 + a < nl) ? lst[1 + a] : 0;
+            return;
+        }
         T = T_;
         wlo = wlo_;
         whi = whi_;
         m = wlo;
-        end = whi;
+        end = skip_window ? wlo : whi;   // an empty first range moves straight on
         phase = 0;
         settle();
     }
@@ -84,8 +106,16 @@ struct TileSeq {
             ++phase;
         }
     }
-    __device__ __forceinline__ bool done() const { return m >= end; }
+    __device__ __forceinline__ bool done() const { return lst ? pos >= nl : m >= end; }
     __device__ __forceinline__ void next() {
+        if (lst) {
+            ++pos;
+            m = q[0];
+#pragma unroll
+            for (int a = 0; a < kAhead - 1; ++a) q[a] = q[a + 1];
+            q[kAhead - 1] = (pos + kAhead < nl) ? lst[pos + kAhead] : 0;
+            return;
+        }
         if (++m == end) settle();
     }
 };
@@ -187,8 +217,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 q_issued = true;
                 q_parity = item_no & 1;
                 const int jb = (int)j_begin, T = (int)((j_end - j_begin + BN - 1) / BN);
-                TileSeq sq;
-                for (sq.init(T, wi.win_lo, wi.win_hi); !sq.done(); sq.next(), ++gt) {
+                TileSeq<4> sq;
+                for (sq.init(T, wi.win_lo, wi.win_hi, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
                     if (!(ok = wait(&empty[s], (u & 1) ^ 1))) break;
@@ -218,8 +248,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 if (!(ok = wait(q_full, item_no & 1))) break;
                 tc::tc_fence_after();
                 const int T = (int)((j_end - j_begin + BN - 1) / BN);
-                TileSeq sq;
-                for (sq.init(T, wi.win_lo, wi.win_hi); !sq.done(); sq.next(), ++gt) {
+                TileSeq<4> sq;
+                for (sq.init(T, wi.win_lo, wi.win_hi, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
                     const uint32_t b = gt & 1u, v = gt >> 1;
@@ -269,8 +299,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             const int t_rag = tail < BN ? T - 1 : -1;       // the last tile, when it is partial
             tk.reset();
             tk.shortl = wi.short_list;
-            TileSeq sq;
-            for (sq.init(T, wi.win_lo, wi.win_hi); !sq.done(); sq.next(), ++gt) {
+            if constexpr (Work::kResume) {   // continue lists saved by an earlier pass
+                const int64_t q = wi.q0 + r;
+                if (q < wi.q_end) work.template resume<EG>(wi, part, q, tk.list);
+            }
+            TileSeq<1> sq;
+            for (sq.init(T, wi.win_lo, wi.win_hi, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
                 const uint32_t b = gt & 1u;
                 ok = wait(&acc_full[b], (gt >> 1) & 1u);
                 ok = __all_sync(0xffffffffu, ok);

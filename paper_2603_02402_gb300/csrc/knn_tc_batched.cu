@@ -24,6 +24,7 @@ namespace tck {
 
 struct BatchedWork {
     static constexpr int kShort = 4;   // ids kept per (query, sample, part) for cross lists
+    static constexpr bool kResume = false;
     int T;                             // query tiles
     int S;                             // samples
     const int64_t *tile_row;           // [T] first row of the tile
@@ -46,6 +47,9 @@ struct BatchedWork {
         w.tag = t;
         w.short_list = tile_samp[qt] != t;
         w.win_lo = w.win_hi = 0;
+        w.tiles = nullptr;
+        w.n_tiles = 0;
+        w.skip_window = false;
         return w;
     }
     template <int EG, int KCP>

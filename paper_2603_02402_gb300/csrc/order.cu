@@ -164,12 +164,13 @@ __global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int32_t *__r
     if (tid == 0) off[N] = carry_s;
 }
 
-// Stable scatter: warp w walks its chunk in row order, 32 rows a step; rows
+// Stable scatter: warp w walks its chunk in key order, 32 keys a step; keys
 // with equal labels within a step are ranked by lane (match_any), and a
-// per-label cursor carries the count across steps.  out[pos] = row * step.
+// per-label cursor carries the count across steps.  out[pos] = the row of
+// key r: rows[r * step] (rows given) or r * step.
 __global__ void __launch_bounds__(kSortWarps * 32)
-chunk_scatter_kernel(const int32_t *__restrict__ lab, int64_t m, int64_t step, int C, int nchunk,
-                     const int32_t *__restrict__ off, int32_t *__restrict__ out) {
+chunk_scatter_kernel(const int32_t *__restrict__ lab, int64_t m, int64_t step, const int32_t *__restrict__ rows,
+                     int C, int nchunk, const int32_t *__restrict__ off, int32_t *__restrict__ out) {
     extern __shared__ int32_t cur_s[];   // [kSortWarps][C]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x * kSortWarps + warp;
@@ -186,7 +187,7 @@ chunk_scatter_kernel(const int32_t *__restrict__ lab, int64_t m, int64_t step, i
         const unsigned peers = __match_any_sync(0xffffffffu, c);
         if (act) {
             const int pos = cur[c] + __popc(peers & lt);
-            out[pos] = (int32_t)(r * step);
+            out[pos] = rows ? rows[r * step] : (int32_t)(r * step);
         }
         __syncwarp();
         if (act && (peers & lt) == 0) cur[c] += __popc(peers);   // the lowest lane of each label advances it
@@ -221,6 +222,100 @@ __global__ void centroid_mean_kernel(const float *__restrict__ Y, int DP, const 
     if (lane == 0) cnorm[c] = q;
 }
 
+// Sub-cluster assignment: key i is row rows[i * step] (rows given) or
+// i * step; its coarse cluster c1 = lab1[row]; label = c1 * C2 + the nearest
+// of c1's C2 sub-centroids (|c|^2 - 2 x.c, ties to the lower index), written
+// at out[row] (by_row) or out[i].  Thread per key; the C2 sub-centroids of a
+// coarse cluster are read through L1 (neighbouring keys share them).
+template <int DP>
+__global__ void __launch_bounds__(kAssignThreads)
+assign_sub_kernel(const float *__restrict__ Y, int64_t m, int64_t step, const int32_t *__restrict__ rows,
+                  const int32_t *__restrict__ lab1, const float *__restrict__ cent2, const float *__restrict__ cnorm2,
+                  int C2, bool by_row, int32_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t row = rows ? (int64_t)rows[i * step] : i * step;
+    float x[DP];
+    const float4 *xr = reinterpret_cast<const float4 *>(Y + row * DP);
+#pragma unroll
+    for (int t4 = 0; t4 < DP / 4; ++t4) {
+        const float4 v = xr[t4];
+        x[4 * t4] = v.x;
+        x[4 * t4 + 1] = v.y;
+        x[4 * t4 + 2] = v.z;
+        x[4 * t4 + 3] = v.w;
+    }
+    const int base = lab1[row] * C2;
+    float best = INFINITY;
+    int bi = 0;
+    for (int c = 0; c < C2; ++c) {
+        const float4 *cr = reinterpret_cast<const float4 *>(cent2 + (int64_t)(base + c) * DP);
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int t4 = 0; t4 < DP / 4; t4 += 2) {
+            const float4 u = __ldg(cr + t4), w = __ldg(cr + t4 + 1);
+            a0 = fmaf(x[4 * t4], u.x, a0);
+            a0 = fmaf(x[4 * t4 + 1], u.y, a0);
+            a0 = fmaf(x[4 * t4 + 2], u.z, a0);
+            a0 = fmaf(x[4 * t4 + 3], u.w, a0);
+            a1 = fmaf(x[4 * t4 + 4], w.x, a1);
+            a1 = fmaf(x[4 * t4 + 5], w.y, a1);
+            a1 = fmaf(x[4 * t4 + 6], w.z, a1);
+            a1 = fmaf(x[4 * t4 + 7], w.w, a1);
+        }
+        const float sv = fmaf(-2.f, a0 + a1, cnorm2[base + c]);
+        if (sv < best) {
+            best = sv;
+            bi = c;
+        }
+    }
+    out[by_row ? row : i] = base + bi;
+}
+
+// Sub-centroid s of coarse cluster c <- the row at position b + (s * size) /
+// C2 of the cluster's segment [b, b + size) of perm1 (the coarse centroid
+// when the cluster is empty).  Warp per sub-centroid.
+__global__ void init_sub_centroids_kernel(const float *__restrict__ Y, int DP, const int32_t *__restrict__ perm1,
+                                          const int32_t *__restrict__ off1, int nchunk1, int C2,
+                                          const float *__restrict__ cent1, float *__restrict__ cent2,
+                                          float *__restrict__ cnorm2) {
+    const int g = blockIdx.x, c = g / C2, sidx = g % C2;
+    const int32_t b = off1[(int64_t)c * nchunk1], e = off1[(int64_t)(c + 1) * nchunk1];
+    const float *src = (e > b) ? Y + (int64_t)perm1[b + ((int64_t)sidx * (e - b)) / C2] * DP : cent1 + (int64_t)c * DP;
+    float q = 0.f;
+    for (int t = threadIdx.x; t < DP; t += 32) {
+        const float v = src[t];
+        cent2[(int64_t)g * DP + t] = v;
+        q = fmaf(v, v, q);
+    }
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (threadIdx.x == 0) cnorm2[g] = q;
+}
+
+cudaError_t launch_assign_sub(const float *Y, int DP, int64_t m, int64_t step, const int32_t *rows,
+                              const int32_t *lab1, const float *cent2, const float *cnorm2, int C2, bool by_row,
+                              int32_t *out, cudaStream_t st) {
+    const unsigned blocks = (unsigned)ceil_div(m, kAssignThreads);
+#define RSC_ASSIGN(dp)                                                                                       \
+    case dp:                                                                                                 \
+        assign_sub_kernel<dp><<<blocks, kAssignThreads, 0, st>>>(Y, m, step, rows, lab1, cent2, cnorm2, C2, \
+                                                                 by_row, out);                               \
+        break
+    switch (DP) {
+        RSC_ASSIGN(8);
+        RSC_ASSIGN(16);
+        RSC_ASSIGN(24);
+        RSC_ASSIGN(32);
+        RSC_ASSIGN(40);
+        RSC_ASSIGN(48);
+        RSC_ASSIGN(56);
+        RSC_ASSIGN(64);
+        default: return cudaErrorInvalidValue;
+    }
+#undef RSC_ASSIGN
+    return cudaGetLastError();
+}
+
 cudaError_t launch_assign(const float *Y, int DP, int64_t m, int64_t step, const float *cent, const float *cnorm,
                           int C, int32_t *lab, cudaStream_t st) {
     const unsigned blocks = (unsigned)ceil_div(m, kAssignThreads);
@@ -241,15 +336,16 @@ cudaError_t launch_assign(const float *Y, int DP, int64_t m, int64_t step, const
     return cudaGetLastError();
 }
 
-// Stable counting sort of labels lab[0 .. m) -> out (positions hold row * step).
-cudaError_t counting_sort(const int32_t *lab, int64_t m, int64_t step, int C, int32_t *cnt, int32_t *off,
-                          int32_t *out, cudaStream_t st) {
+// Stable counting sort of labels lab[0 .. m) -> out (positions hold the row
+// of each key: rows[r * step] when rows is given, else r * step).
+cudaError_t counting_sort(const int32_t *lab, int64_t m, int64_t step, const int32_t *rows, int C, int32_t *cnt,
+                          int32_t *off, int32_t *out, cudaStream_t st) {
     const int nchunk = (int)ceil_div(m, kChunk);
     const unsigned blocks = (unsigned)ceil_div(nchunk, kSortWarps);
     const size_t sm = sizeof(int32_t) * kSortWarps * C;
     chunk_hist_kernel<<<blocks, kSortWarps * 32, sm, st>>>(lab, m, C, nchunk, cnt);
     exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt, (int64_t)C * nchunk, off);
-    chunk_scatter_kernel<<<blocks, kSortWarps * 32, sm, st>>>(lab, m, step, C, nchunk, off, out);
+    chunk_scatter_kernel<<<blocks, kSortWarps * 32, sm, st>>>(lab, m, step, rows, C, nchunk, off, out);
     return cudaGetLastError();
 }
 
@@ -257,50 +353,92 @@ cudaError_t counting_sort(const int32_t *lab, int64_t m, int64_t step, int C, in
 
 OrderShape order_shape(int64_t n) {
     OrderShape s;
-    s.C = (int)std::min<int64_t>(kOrderMaxCentroids, std::max<int64_t>(2, n / 4096));
-    s.m = std::min<int64_t>(n, (int64_t)s.C * 64);
-    s.step = n / s.m;
-    s.m = n / s.step;                       // rows i * step, i < m, all inside [0, n)
-    s.nchunk = (int)ceil_div(n, kChunk);    // the full sort has the most chunks
+    s.C2 = kOrderSub;
+    s.C1 = (int)std::min<int64_t>(kOrderMaxCoarse, std::max<int64_t>(1, ceil_div(n, (int64_t)kOrderSub * kOrderLeafRows)));
+    s.m1 = std::min<int64_t>(n, (int64_t)s.C1 * 64);
+    s.step1 = n / s.m1;
+    s.m1 = n / s.step1;                    // keys i * step1, i < m1, all inside [0, n)
+    s.m2 = std::min<int64_t>(n, (int64_t)s.C1 * s.C2 * 32);
+    s.step2 = n / s.m2;
+    s.m2 = n / s.step2;
+    s.nchunk = (int)ceil_div(n, kChunk);   // the full sorts have the most chunks
     return s;
 }
 
+namespace {
+
+struct OrderLayout {
+    float *cent1, *cnorm1, *cent2, *cnorm2;
+    int32_t *lab1, *lab, *perm1, *cnt, *off, *srows;
+};
+
+OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, size_t *bytes) {
+    Carve cv(scratch);
+    OrderLayout L;
+    const int C = s.C1 * s.C2;
+    L.cent1 = cv.take<float>((size_t)s.C1 * DP);
+    L.cnorm1 = cv.take<float>((size_t)s.C1);
+    L.cent2 = cv.take<float>((size_t)C * DP);
+    L.cnorm2 = cv.take<float>((size_t)C);
+    L.lab1 = cv.take<int32_t>((size_t)n);
+    L.lab = cv.take<int32_t>((size_t)n);
+    L.perm1 = cv.take<int32_t>((size_t)n);
+    const size_t ncnt = (size_t)C * s.nchunk;
+    L.cnt = cv.take<int32_t>(ncnt);
+    L.off = cv.take<int32_t>(ncnt + 1);
+    L.srows = cv.take<int32_t>((size_t)std::max(s.m1, s.m2));
+    if (bytes) *bytes = cv.used;
+    return L;
+}
+
+}  // namespace
+
 size_t order_scratch_bytes(int64_t n, int DP) {
-    const OrderShape s = order_shape(n);
-    const size_t cnt = (size_t)s.C * s.nchunk;
-    return 256 * 6 + sizeof(float) * ((size_t)s.C * DP + s.C)   // centroids, norms
-           + sizeof(int32_t) * (size_t)n                        // labels
-           + sizeof(int32_t) * (2 * cnt + 1)                    // counts, offsets
-           + sizeof(int32_t) * (size_t)s.m;                     // sorted sample rows
+    size_t bytes = 0;
+    order_layout(nullptr, n, DP, order_shape(n), &bytes);
+    return bytes;
 }
 
 cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, int32_t *perm, void *scratch,
                                   cudaStream_t st) {
     const OrderShape s = order_shape(n);
     if (DP % 8 != 0 || DP > 64) return cudaErrorInvalidValue;
-    Carve cv(scratch);
-    float *cent = cv.take<float>((size_t)s.C * DP);
-    float *cnorm = cv.take<float>((size_t)s.C);
-    int32_t *lab = cv.take<int32_t>((size_t)n);
-    const size_t ncnt = (size_t)s.C * s.nchunk;
-    int32_t *cnt = cv.take<int32_t>(ncnt);
-    int32_t *off = cv.take<int32_t>(ncnt + 1);
-    int32_t *srows = cv.take<int32_t>((size_t)s.m);
-    cudaError_t e;
-    init_centroids_kernel<<<s.C, 32, 0, st>>>(Y, n, DP, s.C, cent, cnorm);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const OrderLayout L = order_layout(scratch, n, DP, s, nullptr);
+    const int C = s.C1 * s.C2;
     const int mean_warps = 4;
-    for (int it = 0; it < iters; ++it) {   // Lloyd iterations on the sample
-        if ((e = launch_assign(Y, DP, s.m, s.step, cent, cnorm, s.C, lab, st)) != cudaSuccess) return e;
-        if ((e = counting_sort(lab, s.m, s.step, s.C, cnt, off, srows, st)) != cudaSuccess) return e;
-        // the sample sort used ceil(m / kChunk) chunks: offsets are indexed with that count
-        const int nch = (int)ceil_div(s.m, kChunk);
-        centroid_mean_kernel<<<(unsigned)ceil_div(s.C, mean_warps), mean_warps * 32, 0, st>>>(Y, DP, srows, off, nch,
-                                                                                           s.C, cent, cnorm);
+    cudaError_t e;
+    // level 1: coarse k-means (Lloyd on a strided sample), then every row
+    init_centroids_kernel<<<s.C1, 32, 0, st>>>(Y, n, DP, s.C1, L.cent1, L.cnorm1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int nch1 = (int)ceil_div(s.m1, kChunk);
+    for (int it = 0; it < iters; ++it) {
+        if ((e = launch_assign(Y, DP, s.m1, s.step1, L.cent1, L.cnorm1, s.C1, L.lab1, st)) != cudaSuccess) return e;
+        if ((e = counting_sort(L.lab1, s.m1, s.step1, nullptr, s.C1, L.cnt, L.off, L.srows, st)) != cudaSuccess)
+            return e;
+        centroid_mean_kernel<<<(unsigned)ceil_div(s.C1, mean_warps), mean_warps * 32, 0, st>>>(
+            Y, DP, L.srows, L.off, nch1, s.C1, L.cent1, L.cnorm1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = launch_assign(Y, DP, n, 1, cent, cnorm, s.C, lab, st)) != cudaSuccess) return e;
-    return counting_sort(lab, n, 1, s.C, cnt, off, perm, st);
+    if ((e = launch_assign(Y, DP, n, 1, L.cent1, L.cnorm1, s.C1, L.lab1, st)) != cudaSuccess) return e;
+    if ((e = counting_sort(L.lab1, n, 1, nullptr, s.C1, L.cnt, L.off, L.perm1, st)) != cudaSuccess) return e;
+    // level 2: C2 sub-clusters inside each coarse cluster (sample in coarse order)
+    init_sub_centroids_kernel<<<C, 32, 0, st>>>(Y, DP, L.perm1, L.off, s.nchunk, s.C2, L.cent1, L.cent2, L.cnorm2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int nch2 = (int)ceil_div(s.m2, kChunk);
+    for (int it = 0; it < iters; ++it) {
+        if ((e = launch_assign_sub(Y, DP, s.m2, s.step2, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, false, L.lab,
+                                   st)) != cudaSuccess)
+            return e;
+        if ((e = counting_sort(L.lab, s.m2, s.step2, L.perm1, C, L.cnt, L.off, L.srows, st)) != cudaSuccess) return e;
+        centroid_mean_kernel<<<(unsigned)ceil_div(C, mean_warps), mean_warps * 32, 0, st>>>(Y, DP, L.srows, L.off,
+                                                                                            nch2, C, L.cent2,
+                                                                                            L.cnorm2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // every row (walked in coarse order, so a block shares its sub-centroids), then the final sort
+    if ((e = launch_assign_sub(Y, DP, n, 1, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, true, L.lab, st)) != cudaSuccess)
+        return e;
+    return counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, perm, st);
 }
 
 }  // namespace rsc

@@ -489,6 +489,7 @@ namespace tck {
 // segment p = query slots [goff[p], goff[p+1]) x database rows [doff[p], doff[p+1]).
 struct ProbeWork {
     static constexpr int kShort = 0;
+    static constexpr bool kResume = false;
     int P;
     const int64_t *goff;
     const int64_t *doff;
@@ -512,6 +513,9 @@ struct ProbeWork {
         w.tag = lo;
         w.short_list = false;
         w.win_lo = w.win_hi = 0;
+        w.tiles = nullptr;
+        w.n_tiles = 0;
+        w.skip_window = false;
         return w;
     }
     template <int EG, int KCP>

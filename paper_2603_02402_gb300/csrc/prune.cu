@@ -1,0 +1,308 @@
+// Tile pruning bounds for the tensor-core search (rows in locality order).
+//
+// The accumulator of query row i and database row j holds, up to the
+// tensor core's FP32 accumulation error e_ij,
+//     acc_ij = |v_i - v_j|^2 - |v_i|^2 - beta |v_j|^2,
+// where v are the BF16-rounded operand rows (Euclidean: the centred row,
+// beta = 0, the |v_j|^2 term being folded into the MMA; cosine: the
+// normalised row plus its zero-row flag, beta = 1).  A list of row i accepts
+// acc_ij only below its threshold thr_i, i.e. only when
+//     |v_i - v_j|^2 < thr_i + |v_i|^2 + beta |v_j|^2 + e_ij.
+// With spheres (c_Q, r_Q) around the query tile's v and (c_t, r_t) around
+// database tile t's v, |v_i - v_j| >= |c_Q - c_t| - r_Q - r_t for every pair,
+// so tile t can be dropped for query tile Q when
+//     (|c_Q - c_t| - r_Q - r_t)^2 - beta N_t - margin > tau_Q,
+// tau_Q = max over the tile's rows and parts of (thr + |v_i|^2), N_t =
+// max |v_j|^2 over t, and margin bounds e_ij and the FP32 rounding of these
+// bounds: 2^-11 (N_Q + N_t), sixteen times the worst-case error of a K = 64
+// FP32 accumulation of terms summing to at most 2 (N_Q + N_t) in magnitude.
+// Radii are inflated by 2^-10 relative plus 1e-6 for their own rounding.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsc {
+
+namespace {
+
+constexpr int kCen = 64;           // centre stride (floats); v has at most 64 components
+constexpr int kChunkTiles = 256;   // database tiles per block in the bound passes
+constexpr int kBoundThreads = 128; // query tiles per block in the bound passes
+constexpr int kStage = 32;         // database tiles staged in shared memory at once
+
+__device__ __forceinline__ float bf(const uint16_t *p) {
+    return __uint_as_float((uint32_t)(*p) << 16);
+}
+
+// Warp per group of R consecutive rows of the BF16 query operand (row stride
+// W elements, v = the first dv of them): centre (mean of v), radius
+// (max |v - c|, inflated), max |v|^2; row_norm[i] = |v_i|^2 when requested.
+__global__ void tile_sphere_kernel(const uint16_t *__restrict__ Qb, int64_t n, int W, int dv, int R, int groups,
+                                   float *__restrict__ cen, float *__restrict__ rad, float *__restrict__ nmax,
+                                   float *__restrict__ row_norm) {
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= groups) return;
+    const int64_t r0 = (int64_t)g * R, r1 = min(n, r0 + R);
+    const bool a0 = lane < dv, a1 = lane + 32 < dv;
+    float s0 = 0.f, s1 = 0.f;
+    for (int64_t r = r0; r < r1; ++r) {
+        const uint16_t *row = Qb + r * W;
+        if (a0) s0 += bf(row + lane);
+        if (a1) s1 += bf(row + lane + 32);
+    }
+    const float inv = 1.f / (float)(r1 - r0);
+    const float c0 = s0 * inv, c1 = s1 * inv;
+    float md = 0.f, mn = 0.f;
+    for (int64_t r = r0; r < r1; ++r) {
+        const uint16_t *row = Qb + r * W;
+        const float v0 = a0 ? bf(row + lane) : 0.f, v1 = a1 ? bf(row + lane + 32) : 0.f;
+        float dd = (v0 - c0) * (v0 - c0) + (v1 - c1) * (v1 - c1);
+        float nn = v0 * v0 + v1 * v1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dd += __shfl_xor_sync(0xffffffffu, dd, o);
+            nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        }
+        md = fmaxf(md, dd);
+        mn = fmaxf(mn, nn);
+        if (row_norm && lane == 0) row_norm[r] = nn;
+    }
+    cen[(int64_t)g * kCen + lane] = a0 ? c0 : 0.f;
+    cen[(int64_t)g * kCen + lane + 32] = a1 ? c1 : 0.f;
+    if (lane == 0) {
+        rad[g] = sqrtf(md) * (1.f + 0x1p-10f) + 1e-6f;
+        nmax[g] = mn;
+    }
+}
+
+// tau_Q = max over the query tile's rows and parts of (saved threshold +
+// |v_i|^2); infinite while some list is not full.  Warp per query tile.
+__global__ void tile_tau_kernel(const float *__restrict__ st_key, int64_t n, int EG, int KCP,
+                                const float *__restrict__ row_norm, int qtiles, int BM, float *__restrict__ tau) {
+    const int qt = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (qt >= qtiles) return;
+    float m = -INFINITY;
+    const int64_t r0 = (int64_t)qt * BM, r1 = min(n, r0 + BM);
+    for (int64_t q = r0 + lane; q < r1; q += 32)
+        for (int p = 0; p < EG; ++p) m = fmaxf(m, st_key[(q * EG + p) * KCP + KCP - 1] + row_norm[q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) tau[qt] = m;
+}
+
+// Thread per query tile Q, block column = a chunk of kChunkTiles database
+// tiles.  FILL = false: count the kept tiles of (Q, chunk); FILL = true:
+// write them, ascending, from off[Q * nchunk + chunk].
+template <bool FILL>
+__global__ void __launch_bounds__(kBoundThreads)
+prune_tiles_kernel(int qtiles, int dtiles, int nchunk, int qpt, int window, float beta,
+                   const float *__restrict__ qcen, const float *__restrict__ qrad, const float *__restrict__ qn,
+                   const float *__restrict__ tau, const float *__restrict__ dcen, const float *__restrict__ drad,
+                   const float *__restrict__ dn, int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
+                   int32_t *__restrict__ tiles, int64_t cap) {
+    __shared__ __align__(16) float sc[kStage][kCen];
+    __shared__ float sr[kStage], sn[kStage];
+    const int Q = blockIdx.x * kBoundThreads + threadIdx.x;
+    const int chunk = blockIdx.y;
+    const bool active = Q < qtiles;
+    float c[kCen];
+    const float4 *qc = reinterpret_cast<const float4 *>(qcen + (int64_t)(active ? Q : 0) * kCen);
+#pragma unroll
+    for (int u = 0; u < kCen / 4; ++u) {
+        const float4 v = qc[u];
+        c[4 * u] = v.x;
+        c[4 * u + 1] = v.y;
+        c[4 * u + 2] = v.z;
+        c[4 * u + 3] = v.w;
+    }
+    const float rq = active ? qrad[Q] : 0.f, nq = active ? qn[Q] : 0.f, tq = active ? tau[Q] : INFINITY;
+    // the query tile's window (already scanned by the first pass)
+    const int tw = active ? Q / qpt : 0;
+    const int wlo = max(0, tw - window), whi = min(dtiles, tw + window + 1);
+    const int t0 = chunk * kChunkTiles, t1 = min(dtiles, t0 + kChunkTiles);
+    int kept = 0;
+    int64_t pos = (FILL && active) ? off[(int64_t)Q * nchunk + chunk] : 0;
+    for (int s0 = t0; s0 < t1; s0 += kStage) {
+        const int ns = min(kStage, t1 - s0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < ns * kCen; e += blockDim.x) sc[e / kCen][e % kCen] = dcen[(int64_t)s0 * kCen + e];
+        for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+            sr[e] = drad[s0 + e];
+            sn[e] = dn[s0 + e];
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int e = 0; e < ns; ++e) {
+            const int t = s0 + e;
+            if (t >= wlo && t < whi) continue;
+            const float4 *dc = reinterpret_cast<const float4 *>(sc[e]);
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int u = 0; u < kCen / 4; u += 2) {
+                const float4 x = dc[u], y = dc[u + 1];
+                float f;
+                f = c[4 * u] - x.x; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 1] - x.y; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 2] - x.z; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 3] - x.w; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 4] - y.x; a1 = fmaf(f, f, a1);
+                f = c[4 * u + 5] - y.y; a1 = fmaf(f, f, a1);
+                f = c[4 * u + 6] - y.z; a1 = fmaf(f, f, a1);
+                f = c[4 * u + 7] - y.w; a1 = fmaf(f, f, a1);
+            }
+            const float gap = sqrtf(a0 + a1) - rq - sr[e];
+            const float margin = 0x1p-11f * (nq + sn[e]);
+            const bool drop = gap > 0.f && gap * gap - beta * sn[e] - margin > tq;
+            if (!drop) {
+                if (FILL && pos < cap) tiles[pos] = t;
+                ++pos;
+                ++kept;
+            }
+        }
+    }
+    if (!FILL && active) cnt[(int64_t)Q * nchunk + chunk] = kept;
+}
+
+// Exclusive scan of int32 counts into int64 offsets (one block, coalesced
+// 1024-wide tiles with a running carry); off[N] = total; *overflow = total >
+// cap.
+__global__ void __launch_bounds__(1024) scan64_kernel(const int32_t *__restrict__ cnt, int64_t N,
+                                                      int64_t *__restrict__ off, int64_t cap,
+                                                      int32_t *__restrict__ overflow) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < N; base += 1024) {
+        const int64_t i = base + tid;
+        const int64_t v = i < N ? cnt[i] : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = ws[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            ws[lane] = w;
+        }
+        __syncthreads();
+        const int64_t carry = carry_s;
+        const int64_t incl = x + (warp > 0 ? ws[warp - 1] : 0);
+        if (i < N) off[i] = carry + incl - v;
+        __syncthreads();
+        if (tid == 1023) carry_s = carry + incl;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        off[N] = carry_s;
+        *overflow = carry_s > cap ? 1 : 0;
+    }
+}
+
+// tile_off[Q] = off[Q * nchunk] (the query tile's first chunk), tile_off[qtiles] = total.
+__global__ void tile_offsets_kernel(int qtiles, int nchunk, const int64_t *__restrict__ off,
+                                    int64_t *__restrict__ tile_off) {
+    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Q <= qtiles) tile_off[Q] = off[(int64_t)Q * nchunk];
+}
+
+}  // namespace
+
+PruneShape prune_shape(int64_t n, int BM, int BN) {
+    PruneShape s;
+    s.qtiles = (int)ceil_div(n, BM);
+    s.dtiles = (int)ceil_div(n, BN);
+    s.nchunk = (int)ceil_div(s.dtiles, kChunkTiles);
+    const int64_t all = (int64_t)s.qtiles * s.dtiles;
+    s.cap = std::min<int64_t>(all, kPruneListCap);
+    return s;
+}
+
+// Layout of the pruning scratch (shared by the launcher and prune_outputs).
+struct PruneLayout {
+    float *row_norm, *qcen, *qrad, *qn, *dcen, *drad, *dn, *tau;
+    int32_t *cnt;
+    int64_t *off;
+    PruneOut out;
+};
+
+PruneLayout prune_layout(void *scratch, int64_t n, const PruneShape &s, size_t *bytes = nullptr) {
+    Carve cv(scratch);
+    PruneLayout L;
+    L.row_norm = cv.take<float>((size_t)n);
+    L.qcen = cv.take<float>((size_t)s.qtiles * kCen);
+    L.qrad = cv.take<float>((size_t)s.qtiles);
+    L.qn = cv.take<float>((size_t)s.qtiles);
+    L.dcen = cv.take<float>((size_t)s.dtiles * kCen);
+    L.drad = cv.take<float>((size_t)s.dtiles);
+    L.dn = cv.take<float>((size_t)s.dtiles);
+    L.tau = cv.take<float>((size_t)s.qtiles);
+    const size_t ncnt = (size_t)s.qtiles * s.nchunk;
+    L.cnt = cv.take<int32_t>(ncnt);
+    L.off = cv.take<int64_t>(ncnt + 1);
+    L.out.tile_off = cv.take<int64_t>((size_t)s.qtiles + 1);
+    L.out.tiles = cv.take<int32_t>((size_t)s.cap);
+    L.out.overflow = cv.take<int32_t>(1);
+    if (bytes) *bytes = cv.used;
+    return L;
+}
+
+PruneOut prune_outputs(void *scratch, int64_t n, int BM, int BN) {
+    return prune_layout(scratch, n, prune_shape(n, BM, BN)).out;
+}
+
+size_t prune_scratch_bytes(int64_t n, int BM, int BN) {
+    size_t bytes = 0;
+    prune_layout(nullptr, n, prune_shape(n, BM, BN), &bytes);
+    return bytes;
+}
+
+cudaError_t launch_prune_bounds(const void *Qb, int64_t n, int d, int metric, int BM, int BN, int window,
+                                const float *st_key, int EG, int KCP, void *scratch, PruneOut *out,
+                                cudaStream_t st) {
+    const PruneShape s = prune_shape(n, BM, BN);
+    if (BN % BM != 0) return cudaErrorInvalidValue;
+    const PruneLayout PL = prune_layout(scratch, n, s);
+    float *row_norm = PL.row_norm, *qcen = PL.qcen, *qrad = PL.qrad, *qn = PL.qn;
+    float *dcen = PL.dcen, *drad = PL.drad, *dn = PL.dn, *tau = PL.tau;
+    int32_t *cnt = PL.cnt;
+    int64_t *off = PL.off;
+    *out = PL.out;
+    const size_t ncnt = (size_t)s.qtiles * s.nchunk;
+    const int W = 64 * tc_kb(d, metric);
+    const int dv = metric == RSC_COSINE ? d + 1 : d;
+    const float beta = metric == RSC_COSINE ? 1.f : 0.f;
+    const uint16_t *q16 = static_cast<const uint16_t *>(Qb);
+    tile_sphere_kernel<<<(unsigned)ceil_div((int64_t)s.qtiles * 32, 256), 256, 0, st>>>(q16, n, W, dv, BM, s.qtiles,
+                                                                                        qcen, qrad, qn, row_norm);
+    tile_sphere_kernel<<<(unsigned)ceil_div((int64_t)s.dtiles * 32, 256), 256, 0, st>>>(q16, n, W, dv, BN, s.dtiles,
+                                                                                        dcen, drad, dn, nullptr);
+    tile_tau_kernel<<<(unsigned)ceil_div((int64_t)s.qtiles * 32, 256), 256, 0, st>>>(st_key, n, EG, KCP, row_norm,
+                                                                                     s.qtiles, BM, tau);
+    const dim3 grid((unsigned)ceil_div(s.qtiles, kBoundThreads), (unsigned)s.nchunk);
+    const int qpt = BN / BM;
+    prune_tiles_kernel<false><<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen,
+                                                              qrad, qn, tau, dcen, drad, dn, cnt, nullptr, nullptr,
+                                                              s.cap);
+    scan64_kernel<<<1, 1024, 0, st>>>(cnt, (int64_t)ncnt, off, s.cap, out->overflow);
+    prune_tiles_kernel<true><<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen,
+                                                             qrad, qn, tau, dcen, drad, dn, nullptr, off, out->tiles,
+                                                             s.cap);
+    tile_offsets_kernel<<<(unsigned)ceil_div(s.qtiles + 1, 256), 256, 0, st>>>(s.qtiles, s.nchunk, off,
+                                                                               out->tile_off);
+    return cudaGetLastError();
+}
+
+}  // namespace rsc

@@ -40,7 +40,7 @@ class rsc_knn_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("candidates", ctypes.c_int32),
                 ("db_splits", ctypes.c_int32), ("tc_parts", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("phase_events", ctypes.c_void_p),
-                ("locality", ctypes.c_int32)]
+                ("locality", ctypes.c_int32), ("prune", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); the full exported surface of include/rsc.h
@@ -50,6 +50,8 @@ SIGNATURES = {
     "rsc_last_error": (ctypes.c_char_p, []),
     "rsc_workspace_status": (_i32, [_vp, _vp]),
     "rsc_knn_workspace_size": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(_sz)]),
+    "rsc_knn_scan_stats": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts), _vp, _sz,
+                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "rsc_knn": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(rsc_knn_opts), _vp, _sz]),
     "rsc_knn_batched_workspace_size": (_i32, [_i64, _i32, _vp, _i32, _i32, _i32, _i32,
                                                ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(_sz)]),
@@ -139,10 +141,11 @@ _LOCALITY = {"auto": 0, "off": 1, "on": 2}
 
 
 def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_events=None,
-             locality="auto") -> rsc_knn_opts:
+             locality="auto", prune="auto") -> rsc_knn_opts:
     """Option struct; `phase_events` is a ctypes array of 4 raw cudaEvent_t."""
     o = rsc_knn_opts()
     o.locality = _LOCALITY[locality] if isinstance(locality, str) else int(locality)
+    o.prune = _LOCALITY[prune] if isinstance(prune, str) else int(prune)
     o.phase_events = ctypes.cast(phase_events, ctypes.c_void_p).value if phase_events is not None else None
     o.precision = _PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.candidates = int(candidates)
@@ -152,16 +155,27 @@ def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_eve
 
 
 def rsc_knn_workspace_size(n, d, k, metric="euclidean", precision="fp32", candidates=0, db_splits=0,
-                           locality="auto") -> int:
-    o = knn_opts(precision, candidates, db_splits, stream=None, locality=locality) if torch.cuda.is_available() \
-        else rsc_knn_opts(_PRECISIONS[precision], candidates, db_splits, 0, None, None, _LOCALITY[locality])
+                           locality="auto", prune="auto") -> int:
+    o = knn_opts(precision, candidates, db_splits, stream=None, locality=locality, prune=prune) \
+        if torch.cuda.is_available() else rsc_knn_opts(_PRECISIONS[precision], candidates, db_splits, 0, None, None,
+                                                       _LOCALITY[locality], _LOCALITY[prune])
     out = _sz(0)
     _check(lib().rsc_knn_workspace_size(n, d, k, _METRICS.get(metric, metric), ctypes.byref(o), ctypes.byref(out)))
     return int(out.value)
 
 
+def rsc_knn_scan_stats(n, d, k, workspace, metric="euclidean", precision="fp32", candidates=0, db_splits=0,
+                       locality="auto", prune="auto", stream=None):
+    """(pairs scanned, pairs total) of the last rsc_knn on `workspace` with these options."""
+    o = knn_opts(precision, candidates, db_splits, stream, None, locality, prune)
+    a, b = _i64(0), _i64(0)
+    _check(lib().rsc_knn_scan_stats(n, d, k, _METRICS.get(metric, metric), ctypes.byref(o), _ptr(workspace),
+                                    workspace.numel(), ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
+
+
 def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candidates=0, db_splits=0,
-            stream=None, workspace=None, out=None, phase_events=None, locality="auto"):
+            stream=None, workspace=None, out=None, phase_events=None, locality="auto", prune="auto"):
     """Exact kNN of every row of X (float32 [n, d] on the GPU).
 
     Returns (idx int32 [n, k], dist float32 [n, k]) on X's device.
@@ -170,7 +184,7 @@ def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candi
         raise ValueError("X must be a contiguous float32 [n, d] CUDA tensor")
     n, d = X.shape
     m = _METRICS[metric] if isinstance(metric, str) else int(metric)
-    o = knn_opts(precision, candidates, db_splits, stream, phase_events, locality)
+    o = knn_opts(precision, candidates, db_splits, stream, phase_events, locality, prune)
     need = _sz(0)
     _check(lib().rsc_knn_workspace_size(n, d, k, m, ctypes.byref(o), ctypes.byref(need)))
     ws = _workspace(need.value, X.device, workspace)

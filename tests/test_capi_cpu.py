@@ -92,11 +92,15 @@ def test_candidate_option_errors(L):
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
     o = rsc.rsc_knn_opts(1, 0, 0, 0, None, None, 3)    # locality must be 0, 1 or 2
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.rsc_knn_opts(1, 0, 0, 0, None, None, 0, 5)  # prune must be 0, 1 or 2
+    assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.rsc_knn_opts(1, 0, 0, 0, None, None, 1, 2)  # pruning needs the locality ordering
+    assert L.rsc_knn_workspace_size(100_000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_UNSUPPORTED
 
 
-def _ws(L, n, precision, locality):
+def _ws(L, n, precision, locality, prune=1):
     out = ctypes.c_size_t(0)
-    o = rsc.rsc_knn_opts(precision, 0, 0, 0, None, None, locality)
+    o = rsc.rsc_knn_opts(precision, 0, 0, 0, None, None, locality, prune)
     assert L.rsc_knn_workspace_size(n, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_OK
     return out.value
 
@@ -109,6 +113,15 @@ def test_locality_workspace(L):
     assert on >= off + 4 * n and auto == on
     assert _ws(L, 10_000, 1, 0) == _ws(L, 10_000, 1, 1) < _ws(L, 10_000, 1, 2)
     assert _ws(L, n, 0, 2) == _ws(L, n, 0, 1)
+
+
+def test_prune_workspace(L):
+    # pruning saves every (row, part) list (keys and ids: 8 bytes per candidate)
+    # and the kept-tile lists on top of the ordered workspace
+    n = 100_000
+    base, pruned, auto = _ws(L, n, 1, 2, 1), _ws(L, n, 1, 2, 2), _ws(L, n, 1, 2, 0)
+    assert pruned >= base + 8 * n * 64 and auto == pruned
+    assert _ws(L, n, 1, 1, 0) == _ws(L, n, 1, 1, 1)      # no ordering: automatic pruning stays off
 
 
 def test_connectivities_argument_errors(L):
