@@ -27,6 +27,7 @@ constexpr int DBLK = BN * 128;       // bytes of one 256-row x 64-element bf16 d
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks
 constexpr uint32_t kSleepNs = 100000;             // suspend limit of one try_wait (ns)
+constexpr int kRing = 2;                          // item-index ring slots (dynamic works)
 
 // EG epilogue warpgroups, each owning kCols = BN / EG columns of every tile;
 // KCP = top-k list length per (row, part).
@@ -144,7 +145,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     uint64_t *q_full = acc_empty + NBUF;
     uint64_t *q_empty = q_full + 1;
     uint64_t *mma_done = q_full + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(q_full + 3);
+    uint64_t *item_full = q_full + 3;          // [kRing] next item index published
+    uint64_t *item_empty = item_full + kRing;  // [kRing] item index read by every consumer
+    volatile int32_t *item_ring = reinterpret_cast<volatile int32_t *>(item_empty + kRing);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(const_cast<int32_t *>(item_ring) + kRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -162,6 +166,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
         tc::mbar_init(q_full, 1);
         tc::mbar_init(q_empty, 1);
         tc::mbar_init(mma_done, 1);
+        for (int r = 0; r < kRing; ++r) {
+            tc::mbar_init(&item_full[r], 1);
+            tc::mbar_init(&item_empty[r], 1 + C::kEpiThreads / 32);
+        }
         *abort_flag = 0;
         tc::fence_barrier_init();
     }
@@ -189,6 +197,44 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             }
         }
     };
+    // Item sequence.  Static works: item blockIdx.x + seq * gridDim.x.
+    // Dynamic works (items of very uneven cost): the producer takes the next
+    // item from a global counter and publishes it through a kRing-slot ring;
+    // the MMA thread and every epilogue warp read the same sequence.  -1 ends
+    // it.  Returns false on timeout / abort.
+    auto publish_item = [&](int seq, int &it) -> bool {
+        if constexpr (!Work::kDynamic) {
+            it = blockIdx.x + seq * (int)gridDim.x;
+            if (it >= n_items) it = -1;
+            return true;
+        } else {
+            const int r = seq % kRing;
+            const uint32_t u = (uint32_t)(seq / kRing);
+            if (!wait(&item_empty[r], (u & 1) ^ 1)) return false;
+            it = atomicAdd(work.counter, 1);
+            if (it >= n_items) it = -1;
+            item_ring[r] = it;
+            tc::mbar_arrive(&item_full[r]);
+            return true;
+        }
+    };
+    auto read_item = [&](int seq, int &it, bool warp_wide) -> bool {
+        if constexpr (!Work::kDynamic) {
+            it = blockIdx.x + seq * (int)gridDim.x;
+            if (it >= n_items) it = -1;
+            return true;
+        } else {
+            const int r = seq % kRing;
+            const uint32_t u = (uint32_t)(seq / kRing);
+            bool ok_ = wait(&item_full[r], u & 1);
+            if (warp_wide) ok_ = __all_sync(0xffffffffu, ok_);
+            if (!ok_) return false;
+            it = item_ring[r];
+            if (warp_wide) __syncwarp();
+            if (!warp_wide || (threadIdx.x & 31) == 0) tc::mbar_arrive(&item_empty[r]);
+            return true;
+        }
+    };
     // bounded wait that ignores the abort flag (draining in-flight work)
     auto drain = [&](uint64_t *bar, uint32_t parity) {
         const long long t0 = clock64();
@@ -207,7 +253,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             int item_no = 0;
             bool ok = true, q_issued = false;
             uint32_t q_parity = 0;
-            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++item_no) {
+            for (;; ++item_no) {
+                int it;
+                if (!(ok = publish_item(item_no, it)) || it < 0) break;
                 const WorkItem wi = work.get(it);
                 const int64_t j_begin = wi.j_begin, j_end = wi.j_end;
                 if (!(ok = wait(q_empty, (item_no & 1) ^ 1))) break;
@@ -242,7 +290,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             uint32_t gt = 0;
             int item_no = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++item_no) {
+            for (;; ++item_no) {
+                int it;
+                if (!(ok = read_item(item_no, it, false)) || it < 0) break;
                 const WorkItem wi = work.get(it);
                 const int64_t j_begin = wi.j_begin, j_end = wi.j_end;
                 if (!(ok = wait(q_full, item_no & 1))) break;
@@ -291,7 +341,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
         const uint32_t tb0 = tmem_base + lane_bits + cbeg;
         uint32_t gt = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        for (int seq = 0;; ++seq) {
+            int it;
+            if (!(ok = read_item(seq, it, true)) || it < 0) break;
             const WorkItem wi = work.get(it);
             const int jb = (int)wi.j_begin, len = (int)(wi.j_end - wi.j_begin);
             const int T = (len + BN - 1) / BN;

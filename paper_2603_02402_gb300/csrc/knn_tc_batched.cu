@@ -25,6 +25,7 @@ namespace tck {
 struct BatchedWork {
     static constexpr int kShort = 4;   // ids kept per (query, sample, part) for cross lists
     static constexpr bool kResume = false;
+    static constexpr bool kDynamic = false;
     int T;                             // query tiles
     int S;                             // samples
     const int64_t *tile_row;           // [T] first row of the tile

@@ -23,6 +23,7 @@ namespace tck {
 struct WindowWork {
     static constexpr int kShort = 0;
     static constexpr bool kResume = false;
+    static constexpr bool kDynamic = false;   // every item scans the same few tiles
     int64_t n;
     int window;
     float *st_key;     // [n, EG, KCP]
@@ -65,6 +66,7 @@ struct WindowWork {
 struct ListWork {
     static constexpr int kShort = 0;
     static constexpr bool kResume = true;
+    static constexpr bool kDynamic = true;    // kept-tile counts differ widely between query tiles
     int64_t n;
     int window;
     const float *st_key;
@@ -74,6 +76,7 @@ struct ListWork {
     const int32_t *overflow;    // [1]
     int32_t *cand;              // [EG, n, KCP]
     int n_items;
+    int *counter;               // next item (zeroed before the launch)
 
     int64_t count_host() const { return n_items; }
     __device__ __forceinline__ int count() const { return n_items; }
@@ -139,14 +142,15 @@ cudaError_t launch_knn_tc_window(const void *Qb, const void *Db, int64_t n, int 
 
 cudaError_t launch_knn_tc_list(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int window,
                                const float *st_key, const int32_t *st_id, const int32_t *tiles,
-                               const int64_t *tile_off, const int32_t *overflow, int32_t *cand, unsigned int *status,
-                               cudaStream_t st) {
+                               const int64_t *tile_off, const int32_t *overflow, int32_t *cand, int *counter,
+                               unsigned int *status, cudaStream_t st) {
     if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
     CUtensorMap mq, md;
     cudaError_t e = tck::make_map(&mq, Qb, n, 1, tck::BM);
     if (e != cudaSuccess) return e;
     if ((e = tck::make_map(&md, Db, n, 1, tck::BN)) != cudaSuccess) return e;
-    tck::ListWork work{n, window, st_key, st_id, tiles, tile_off, overflow, cand, (int)ceil_div(n, tck::BM)};
+    tck::ListWork work{n, window, st_key, st_id, tiles, tile_off, overflow, cand, (int)ceil_div(n, tck::BM), counter};
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
 #define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg>(mq, md, work, status, st)
     if (sh.parts == 4 && sh.list == 16) RSC_TC_CASE(16, 4);
     if (sh.parts == 2 && sh.list == 16) RSC_TC_CASE(16, 2);

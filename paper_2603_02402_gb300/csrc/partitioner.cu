@@ -490,6 +490,7 @@ namespace tck {
 struct ProbeWork {
     static constexpr int kShort = 0;
     static constexpr bool kResume = false;
+    static constexpr bool kDynamic = false;
     int P;
     const int64_t *goff;
     const int64_t *doff;

@@ -255,6 +255,7 @@ PruneLayout prune_layout(void *scratch, int64_t n, const PruneShape &s, size_t *
     L.out.tile_off = cv.take<int64_t>((size_t)s.qtiles + 1);
     L.out.tiles = cv.take<int32_t>((size_t)s.cap);
     L.out.overflow = cv.take<int32_t>(1);
+    L.out.counter = cv.take<int32_t>(1);
     if (bytes) *bytes = cv.used;
     return L;
 }
