@@ -16,6 +16,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "knn_tc.cuh"
 
 namespace rsc {
@@ -25,7 +27,7 @@ namespace tck {
 struct BatchedWork {
     static constexpr int kShort = 4;   // ids kept per (query, sample, part) for cross lists
     static constexpr bool kResume = false;
-    static constexpr bool kDynamic = false;
+    static constexpr bool kDynamic = true;   // item cost follows its database sample's size
     int T;                             // query tiles
     int S;                             // samples
     const int64_t *tile_row;           // [T] first row of the tile
@@ -35,11 +37,14 @@ struct BatchedWork {
     int64_t N;
     int32_t *cand_w;                   // [EG, N, KCP]      within-sample lists
     int32_t *cand_x;                   // [N, S, EG, kShort] cross-sample lists
+    const int32_t *samp_order;         // [S] samples by decreasing size (largest items first)
+    int *counter;                      // next item (zeroed by the table upload)
 
     int64_t count_host() const { return (int64_t)T * S; }
     __device__ __forceinline__ int count() const { return T * S; }
     __device__ __forceinline__ WorkItem get(int it) const {
-        const int t = it / T, qt = it - t * T;
+        const int r = it / T, qt = it - r * T;
+        const int t = samp_order[r];
         WorkItem w;
         w.q0 = tile_row[qt];
         w.q_end = tile_end[qt];
@@ -192,8 +197,11 @@ rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, i
 
 }  // namespace
 
+// Host-built tables, uploaded once per call: tile_row[T], tile_end[T],
+// samp_off[S + 1] (int64), tile_samp[T], samp_order[S], item counter (int32,
+// uploaded as 0).
 size_t batched_tables_bytes(int T, int S) {
-    return sizeof(int64_t) * (2 * (size_t)T + S + 1) + sizeof(int32_t) * (size_t)T;
+    return sizeof(int64_t) * (2 * (size_t)T + S + 1) + sizeof(int32_t) * ((size_t)T + S + 1);
 }
 
 int64_t batched_query_tiles(const int64_t *offsets_host, int S) {
@@ -219,6 +227,12 @@ void batched_fill_tables(const int64_t *offsets_host, int S, void *host_buf) {
         }
     }
     for (int s = 0; s <= S; ++s) samp_off[s] = offsets_host[s];
+    int32_t *samp_order = tile_samp + T;
+    for (int s = 0; s < S; ++s) samp_order[s] = s;
+    std::stable_sort(samp_order, samp_order + S, [&](int32_t a, int32_t b) {
+        return offsets_host[a + 1] - offsets_host[a] > offsets_host[b + 1] - offsets_host[b];
+    });
+    samp_order[S] = 0;   // the item counter
 }
 
 cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
@@ -233,7 +247,9 @@ cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int
     const int64_t *tile_end = tile_row + T;
     const int64_t *samp_off = tile_end + T;
     const int32_t *tile_samp = reinterpret_cast<const int32_t *>(samp_off + S + 1);
-    tck::BatchedWork work{T, S, tile_row, tile_end, tile_samp, samp_off, N, cand_w, cand_x};
+    const int32_t *samp_order = tile_samp + T;
+    int *counter = const_cast<int *>(samp_order + S);
+    tck::BatchedWork work{T, S, tile_row, tile_end, tile_samp, samp_off, N, cand_w, cand_x, samp_order, counter};
     if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
     if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
     return cudaErrorInvalidValue;

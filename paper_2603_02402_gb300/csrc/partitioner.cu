@@ -490,12 +490,13 @@ namespace tck {
 struct ProbeWork {
     static constexpr int kShort = 0;
     static constexpr bool kResume = false;
-    static constexpr bool kDynamic = false;
+    static constexpr bool kDynamic = true;   // segments differ in size
     int P;
     const int64_t *goff;
     const int64_t *doff;
     const int32_t *item_off;   // [P + 1] first work item of each segment
     int32_t *cand;             // [slots, EG * KCP]
+    int *counter;              // next item (zeroed before the launch)
 
     int64_t count_host() const { return INT_MAX; }   // the grid is sized by the SM count
     __device__ __forceinline__ int count() const { return item_off[P]; }
@@ -761,6 +762,7 @@ struct PartLayout {
     int32_t *gcnt, *gcursor;        // [P] each
     int64_t *goff, *doff;           // [P + 1] each
     int32_t *items;                 // [P + 1]
+    int32_t *item_counter;          // [1] the probe search's dynamic item counter
     // search (per query chunk)
     int32_t *route;                 // [chunk, R]
     int32_t *gq;                    // [chunk * R]
@@ -806,6 +808,7 @@ PartLayout carve_part(void *ws, const rsc_partitioner *p, int64_t n, int64_t n_t
     L.goff = cv.take<int64_t>((size_t)p->P + 1);
     L.doff = cv.take<int64_t>((size_t)p->P + 1);
     L.items = cv.take<int32_t>((size_t)p->P + 1);
+    L.item_counter = cv.take<int32_t>(1);
     L.route = cv.take<int32_t>((size_t)chunk * R);
     L.gq = cv.take<int32_t>((size_t)slots);
     L.gpos = cv.take<int64_t>((size_t)slots);
@@ -827,8 +830,9 @@ rsc_status probe_search(cudaStream_t st, const void *Dop, int64_t n_db, int64_t 
     cudaError_t e = tck::make_map(&mq, L.Qg, std::max<int64_t>(n_slots, 1), 1, tck::BM);
     if (e == cudaSuccess) e = tck::make_map(&md, Dop, n_db, 1, tck::BN);
     if (e != cudaSuccess) return fail(RSC_ERR_CUDA, "tensor map: %s", cudaGetErrorString(e));
-    tck::ProbeWork work{P_seg, L.goff, doff, L.items, L.cand};
-    e = tck::launch_kernel<1, kSlotList, kSlotParts>(mq, md, work, L.status, st);
+    tck::ProbeWork work{P_seg, L.goff, doff, L.items, L.cand, L.item_counter};
+    e = cudaMemsetAsync(L.item_counter, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = tck::launch_kernel<1, kSlotList, kSlotParts>(mq, md, work, L.status, st);
     if (e != cudaSuccess) return fail(RSC_ERR_CUDA, "probe search launch: %s", cudaGetErrorString(e));
     return RSC_OK;
 }
