@@ -46,14 +46,14 @@ def launches_per_step(metric, precision, n):
     rsc_knn: FP32 prep (column sums + column means + prep for Euclidean, prep
     alone for cosine), the BF16 operand prep (tensor-core path), the locality
     ordering (two k-means levels of 1 init + 4 Lloyd rounds x 5 + 4 for the
-    full assignment and sort, + 1 gather of the re-rank rows), the candidate
+    full assignment and sort, 2 chain passes, + 1 gather of the re-rank rows), the candidate
     search (one launch, or 9 when pruned: window pass, 2 sphere passes, tau,
     count, scan, fill, offsets, list pass) and the re-rank;
     rsc_connectivities: 11.
     """
     knn = (3 if metric == "euclidean" else 1) + 2
     if precision == "bf16":
-        knn += 1 + (51 + 8 if n >= ORDER_MIN_ROWS else 0)
+        knn += 1 + (53 + 8 if n >= ORDER_MIN_ROWS else 0)
     return knn + 11
 
 
@@ -67,6 +67,10 @@ def parse():
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--k", type=int, default=15)
     p.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the plain FP32 path for comparison")
+    p.add_argument("--locality", choices=["auto", "on", "off"], default="auto",
+                   help="locality ordering of the BF16 search (graph workload)")
+    p.add_argument("--prune", choices=["auto", "on", "off"], default="auto",
+                   help="exact tile pruning of the BF16 search (graph workload)")
     p.add_argument("--full-scan-steps", type=int, default=2,
                    help="timed steps of the BF16 path with pruning off, for comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
@@ -210,9 +214,9 @@ def run_ours(args):
         except rsc.RscError:
             precision = "fp32"
 
-    def buffers(prec, prune="auto"):
-        ws_knn = torch.empty(rsc.rsc_knn_workspace_size(n, d, k, metric, prec, prune=prune), dtype=torch.uint8,
-                             device=dev)
+    def buffers(prec, prune=args.prune):
+        ws_knn = torch.empty(rsc.rsc_knn_workspace_size(n, d, k, metric, prec, locality=args.locality, prune=prune),
+                             dtype=torch.uint8, device=dev)
         return ws_knn
 
     cap = rsc.rsc_connectivities_max_nnz(n, k)
@@ -232,11 +236,12 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         return evs
 
-    def step(prec, ws_knn, ev=None, prune="auto"):
+    def step(prec, ws_knn, ev=None, prune=args.prune):
         arr = None
         if ev is not None:
             arr = (ctypes.c_void_p * 4)(*[e.cuda_event for e in ev])
-        rsc.rsc_knn(Xd, k, metric, prec, workspace=ws_knn, out=(idx, dst), phase_events=arr, prune=prune)
+        rsc.rsc_knn(Xd, k, metric, prec, workspace=ws_knn, out=(idx, dst), phase_events=arr, locality=args.locality,
+                    prune=prune)
         rsc.rsc_connectivities(idx, dst, nnz_capacity=cap, workspace=ws_conn,
                                out=(indptr, indices, data, rho, sigma))
 
@@ -251,7 +256,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed(prec, steps, warmup, clocks=False, prune="auto"):
+    def timed(prec, steps, warmup, clocks=False, prune=args.prune):
         ws_knn = buffers(prec, prune)
         for _ in range(warmup):
             step(prec, ws_knn, prune=prune)
@@ -281,7 +286,8 @@ def run_ours(args):
                     "prep_ms": statistics.mean(prep)}, (sampler.summary() if sampler else None), ws_knn
 
     ms, phases, clocks, ws_knn = timed(precision, args.steps, args.warmup, clocks=True)
-    scanned, pairs_total = rsc.rsc_knn_scan_stats(n, d, k, ws_knn, metric, precision)
+    scanned, pairs_total = rsc.rsc_knn_scan_stats(n, d, k, ws_knn, metric, precision, locality=args.locality,
+                                                  prune=args.prune)
     nnz = int(indptr[-1].item())
     idx_main = idx.clone()
     dist_main = dst.clone()

@@ -8,12 +8,15 @@
 // its own neighbourhood, its thresholds are nearly final after a few tiles
 // and the rest of the scan is a pure min-and-compare.
 //
-// So, before the search, rows are grouped by a coarse k-means:
-//   1. C centroids start at strided rows; Lloyd iterations run on a strided
-//      sample of the rows;
-//   2. every row is assigned to its nearest centroid;
-//   3. a stable counting sort by centroid gives perm (sorted position ->
-//      original row).
+// So, before the search, rows are grouped by a two-level k-means:
+//   1. C1 coarse centroids start at strided rows; Lloyd iterations run on a
+//      strided sample; every row goes to its nearest coarse centroid;
+//   2. inside each coarse cluster, C2 sub-centroids (Lloyd on a sample taken
+//      in coarse order), and every row goes to the nearest of its cluster's;
+//   3. greedy nearest-neighbour chains order the coarse centroids and each
+//      cluster's sub-centroids, so neighbouring clusters end up adjacent;
+//   4. a stable counting sort by (coarse rank, sub rank) gives perm (sorted
+//      position -> original row).
 // The search then runs on the permuted operands and each query tile scans
 // the database tiles around its own position first.  The ordering changes
 // only the order in which candidates are met, never the set of distances
@@ -231,7 +234,8 @@ template <int DP>
 __global__ void __launch_bounds__(kAssignThreads)
 assign_sub_kernel(const float *__restrict__ Y, int64_t m, int64_t step, const int32_t *__restrict__ rows,
                   const int32_t *__restrict__ lab1, const float *__restrict__ cent2, const float *__restrict__ cnorm2,
-                  int C2, bool by_row, int32_t *__restrict__ out) {
+                  int C2, bool by_row, const int32_t *__restrict__ rank1, const int32_t *__restrict__ rank2,
+                  int32_t *__restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int64_t row = rows ? (int64_t)rows[i * step] : i * step;
@@ -269,7 +273,9 @@ assign_sub_kernel(const float *__restrict__ Y, int64_t m, int64_t step, const in
             bi = c;
         }
     }
-    out[by_row ? row : i] = base + bi;
+    // ranked key (position of the coarse cluster, then of the sub-cluster,
+    // along their chains) for the final order; the plain label otherwise
+    out[by_row ? row : i] = rank1 ? rank1[base / C2] * C2 + rank2[base + bi] : base + bi;
 }
 
 // Sub-centroid s of coarse cluster c <- the row at position b + (s * size) /
@@ -292,14 +298,66 @@ __global__ void init_sub_centroids_kernel(const float *__restrict__ Y, int DP, c
     if (threadIdx.x == 0) cnorm2[g] = q;
 }
 
+// Greedy nearest-neighbour chain through each group of gsize consecutive
+// centroids (cent [groups * gsize, DP]), starting at the group's first:
+// rank[c] = position of centroid c along its group's chain (ties to the lower
+// index).  Consecutive clusters in the final order are then near each other,
+// so tiles that straddle a cluster boundary stay compact.  Warp per group,
+// gsize <= kChainMax.
+constexpr int kChainMax = 128;
+static_assert(kOrderMaxCoarse <= kChainMax && kOrderSub <= kChainMax, "chain groups fit the seen flags");
+__global__ void chain_kernel(const float *__restrict__ cent, int DP, int gsize, int32_t *__restrict__ rank) {
+    __shared__ bool seen[kChainMax];
+    const int g = blockIdx.x, lane = threadIdx.x;
+    const float *C = cent + (int64_t)g * gsize * DP;
+    for (int c = lane; c < gsize; c += 32) seen[c] = false;
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+        seen[0] = true;
+        rank[(int64_t)g * gsize] = 0;
+    }
+    __syncwarp();
+    for (int pos = 1; pos < gsize; ++pos) {
+        float best = INFINITY;
+        int bi = INT_MAX;
+        for (int c = lane; c < gsize; c += 32) {
+            if (seen[c]) continue;
+            float s = 0.f;
+            for (int t = 0; t < DP; ++t) {
+                const float df = C[(int64_t)c * DP + t] - C[(int64_t)last * DP + t];
+                s = fmaf(df, df, s);
+            }
+            if (s < best) {
+                best = s;
+                bi = c;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob < best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        last = bi;
+        if (lane == 0) {
+            seen[bi] = true;
+            rank[(int64_t)g * gsize + bi] = pos;
+        }
+        __syncwarp();
+    }
+}
+
 cudaError_t launch_assign_sub(const float *Y, int DP, int64_t m, int64_t step, const int32_t *rows,
                               const int32_t *lab1, const float *cent2, const float *cnorm2, int C2, bool by_row,
-                              int32_t *out, cudaStream_t st) {
+                              const int32_t *rank1, const int32_t *rank2, int32_t *out, cudaStream_t st) {
     const unsigned blocks = (unsigned)ceil_div(m, kAssignThreads);
 #define RSC_ASSIGN(dp)                                                                                       \
     case dp:                                                                                                 \
         assign_sub_kernel<dp><<<blocks, kAssignThreads, 0, st>>>(Y, m, step, rows, lab1, cent2, cnorm2, C2, \
-                                                                 by_row, out);                               \
+                                                                 by_row, rank1, rank2, out);                 \
         break
     switch (DP) {
         RSC_ASSIGN(8);
@@ -369,7 +427,7 @@ namespace {
 
 struct OrderLayout {
     float *cent1, *cnorm1, *cent2, *cnorm2;
-    int32_t *lab1, *lab, *perm1, *cnt, *off, *srows;
+    int32_t *lab1, *lab, *perm1, *cnt, *off, *srows, *rank1, *rank2;
 };
 
 OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, size_t *bytes) {
@@ -387,6 +445,8 @@ OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, 
     L.cnt = cv.take<int32_t>(ncnt);
     L.off = cv.take<int32_t>(ncnt + 1);
     L.srows = cv.take<int32_t>((size_t)std::max(s.m1, s.m2));
+    L.rank1 = cv.take<int32_t>((size_t)s.C1);
+    L.rank2 = cv.take<int32_t>((size_t)C);
     if (bytes) *bytes = cv.used;
     return L;
 }
@@ -426,8 +486,8 @@ cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nch2 = (int)ceil_div(s.m2, kChunk);
     for (int it = 0; it < iters; ++it) {
-        if ((e = launch_assign_sub(Y, DP, s.m2, s.step2, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, false, L.lab,
-                                   st)) != cudaSuccess)
+        if ((e = launch_assign_sub(Y, DP, s.m2, s.step2, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, false, nullptr,
+                                   nullptr, L.lab, st)) != cudaSuccess)
             return e;
         if ((e = counting_sort(L.lab, s.m2, s.step2, L.perm1, C, L.cnt, L.off, L.srows, st)) != cudaSuccess) return e;
         centroid_mean_kernel<<<(unsigned)ceil_div(C, mean_warps), mean_warps * 32, 0, st>>>(Y, DP, L.srows, L.off,
@@ -435,8 +495,13 @@ cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, 
                                                                                             L.cnorm2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // every row (walked in coarse order, so a block shares its sub-centroids), then the final sort
-    if ((e = launch_assign_sub(Y, DP, n, 1, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, true, L.lab, st)) != cudaSuccess)
+    // chains through the coarse centroids and through each cluster's sub-centroids
+    chain_kernel<<<1, 32, 0, st>>>(L.cent1, DP, s.C1, L.rank1);
+    chain_kernel<<<s.C1, 32, 0, st>>>(L.cent2, DP, s.C2, L.rank2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // every row (walked in coarse order, so a block shares its sub-centroids), keyed by its ranks; the final sort
+    if ((e = launch_assign_sub(Y, DP, n, 1, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, true, L.rank1, L.rank2, L.lab,
+                               st)) != cudaSuccess)
         return e;
     return counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, perm, st);
 }
