@@ -24,25 +24,24 @@ __device__ __forceinline__ bool pair_gt(float ka, int ia, float kb, int ib) {
 }
 
 // Squared distance sum_t (xq_t - y_t)^2 for t < d, accumulated in t order
-// (the same rounding whichever loader runs).  W4 > 0: the row is 16-byte
-// aligned and its first 4 * W4 floats are read as W4 independent float4
-// loads up front; W4 == 0: scalar loads.
-template <int W4>
-__device__ __forceinline__ float row_dist2(const float *xq, const float *__restrict__ yr, int d) {
+// (the same rounding whichever loader runs).  w4 > 0: the row is 16-byte
+// aligned and its first 4 * w4 floats (w4 <= 16) are read as independent
+// float4 loads up front; w4 == 0: scalar loads.
+__device__ __forceinline__ float row_dist2(const float *xq, const float *__restrict__ yr, int d, int w4) {
     float acc = 0.f;
-    if constexpr (W4 > 0) {
-        float y[4 * W4];
+    if (w4 > 0) {
+        float y[64];
         const float4 *y4 = reinterpret_cast<const float4 *>(yr);
 #pragma unroll
-        for (int u = 0; u < W4; ++u) {
-            const float4 v = __ldg(y4 + u);
+        for (int u = 0; u < 16; ++u) {
+            const float4 v = (u < w4) ? __ldg(y4 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
             y[4 * u] = v.x;
             y[4 * u + 1] = v.y;
             y[4 * u + 2] = v.z;
             y[4 * u + 3] = v.w;
         }
 #pragma unroll
-        for (int t = 0; t < 4 * W4; ++t) {
+        for (int t = 0; t < 64; ++t) {
             if (t < d) {
                 const float diff = xq[t] - y[t];
                 acc = fmaf(diff, diff, acc);
@@ -57,17 +56,19 @@ __device__ __forceinline__ float row_dist2(const float *xq, const float *__restr
     return acc;
 }
 
-template <int W4>
+// Warp per query; E = (candidate slots rounded up to a power of two) / 32
+// (key, id) pairs per lane, element v = e * 32 + lane.  The candidates are
+// scored, then sorted ascending by (key, id) with a bitonic network held in
+// registers: strides >= 32 compare a lane's own elements, smaller strides
+// exchange with lane ^ stride by shuffles.
+template <int E>
 __global__ void __launch_bounds__(kWarps * 32)
-rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int metric,
-              const int32_t *__restrict__ cand, int KC, int C, int C2, int k, const int32_t *__restrict__ perm,
+rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int metric, int w4,
+              const int32_t *__restrict__ cand, int KC, int C, int k, const int32_t *__restrict__ perm,
               bool r_by_pos, int32_t *__restrict__ idx, float *__restrict__ dist) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) float xq_s[kWarps][68];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int XQ = 65;   // query row (d <= 63 for cosine, so its flag fits) or d <= 64
-    float *xq = reinterpret_cast<float *>(smem) + warp * XQ;
-    float *skey = reinterpret_cast<float *>(smem) + kWarps * XQ + warp * C2;
-    int *sid = reinterpret_cast<int *>(reinterpret_cast<float *>(smem) + kWarps * XQ + kWarps * C2) + warp * C2;
+    float *xq = xq_s[warp];   // query row (d <= 63 for cosine, so its flag fits) or d <= 64
 
     const int64_t q = (int64_t)blockIdx.x * kWarps + warp;   // position in the candidate lists
     if (q >= n) return;
@@ -80,56 +81,79 @@ rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int met
     __syncwarp();
     const bool fq = cosine && xq[d] != 0.f;
 
-    for (int c = lane; c < C2; c += 32) {
-        float key = INFINITY;
-        int id = INT_MAX;
+    float key[E];
+    int id[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = e * 32 + lane;
+        key[e] = INFINITY;
+        id[e] = INT_MAX;
         if (c < C) {
             const int s = c / KC, slot = c - s * KC;
             const int32_t jp = cand[((int64_t)s * n + q) * KC + slot];
             if (jp >= 0) {
                 const int32_t j = perm ? perm[jp] : jp;                    // original id
                 const float *yr = R + (int64_t)(r_by_pos ? jp : j) * rs;
-                float acc = row_dist2<W4>(xq, yr, d);
+                float acc = row_dist2(xq, yr, d, w4);
                 if (cosine) {
                     const bool fy = __ldg(yr + d) != 0.f;
                     if (fq || fy) acc = (fq && fy) ? 0.f : 2.f;
                 }
-                key = acc;
-                id = j;
+                key[e] = acc;
+                id[e] = j;
             }
         }
-        skey[c] = key;
-        sid[c] = id;
     }
-    __syncwarp();
 
-    // bitonic sort of C2 (a power of two) pairs, ascending by (key, id)
-    for (int size = 2; size <= C2; size <<= 1) {
+    constexpr int P = 32 * E;
+#pragma unroll
+    for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < C2 / 2; i += 32) {
-                const int lo = (i / stride) * 2 * stride + (i % stride);
-                const int hi = lo + stride;
-                const bool asc = (lo & size) == 0;
-                const float ka = skey[lo], kb = skey[hi];
-                const int ia = sid[lo], ib = sid[hi];
-                const bool swap = asc ? pair_gt(ka, ia, kb, ib) : pair_gt(kb, ib, ka, ia);
-                if (swap) {
-                    skey[lo] = kb;
-                    skey[hi] = ka;
-                    sid[lo] = ib;
-                    sid[hi] = ia;
+            if (stride >= 32) {
+                const int es = stride >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int pe = e ^ es;
+                    if (pe > e) {
+                        const bool asc = (((e << 5) | lane) & size) == 0;
+                        const bool gt = pair_gt(key[e], id[e], key[pe], id[pe]);
+                        if (gt == asc) {
+                            const float tk = key[e];
+                            key[e] = key[pe];
+                            key[pe] = tk;
+                            const int ti = id[e];
+                            id[e] = id[pe];
+                            id[pe] = ti;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const float pk = __shfl_xor_sync(0xffffffffu, key[e], stride);
+                    const int pi = __shfl_xor_sync(0xffffffffu, id[e], stride);
+                    const bool asc = (((e << 5) | lane) & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    // the lower position of an ascending pair keeps the smaller pair
+                    const bool take = (lower == asc) ? pair_gt(key[e], id[e], pk, pi) : pair_gt(pk, pi, key[e], id[e]);
+                    if (take) {
+                        key[e] = pk;
+                        id[e] = pi;
+                    }
                 }
             }
-            __syncwarp();
         }
     }
 
-    for (int c = lane; c < k; c += 32) {
-        const int id = sid[c];
-        const float key = skey[c];
-        const bool valid = id != INT_MAX;
-        idx[qo * k + c] = valid ? id : -1;
-        dist[qo * k + c] = valid ? (cosine ? 0.5f * key : sqrtf(key)) : INFINITY;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = e * 32 + lane;
+        if (c < k) {
+            const bool valid = id[e] != INT_MAX;
+            idx[qo * k + c] = valid ? id[e] : -1;
+            dist[qo * k + c] = valid ? (cosine ? 0.5f * key[e] : sqrtf(key[e])) : INFINITY;
+        }
     }
 }
 
@@ -160,21 +184,18 @@ cudaError_t launch_rerank(const float *R, int64_t rs, int64_t n, int d, int metr
     int C2 = 32;
     while (C2 < C) C2 <<= 1;
     if (C2 > 1024 || k > C) return cudaErrorInvalidValue;
-    constexpr int XQ = 65;
-    const size_t smem = sizeof(float) * kWarps * XQ + (sizeof(float) + sizeof(int)) * kWarps * C2;
     const unsigned blocks = (unsigned)ceil_div(n, kWarps);
     // vector loads when every row starts on a 16-byte boundary
     const int width = metric == RSC_COSINE ? d + 1 : d;
     const bool vec = rs % 4 == 0 && reinterpret_cast<uintptr_t>(R) % 16 == 0 && width <= 64;
-    const int W4 = vec ? (width + 3) / 4 : 0;
-#define RSC_RR(w4)                                                                                              \
-    case w4:                                                                                                    \
-        rerank_kernel<w4><<<blocks, kWarps * 32, smem, st>>>(R, rs, n, d, metric, cand, KC, C, C2, k, perm,     \
-                                                             r_by_pos, idx, dist);                              \
+    const int w4 = vec ? (width + 3) / 4 : 0;
+#define RSC_RR(e)                                                                                                   \
+    case 32 * e:                                                                                                    \
+        rerank_kernel<e><<<blocks, kWarps * 32, 0, st>>>(R, rs, n, d, metric, w4, cand, KC, C, k, perm, r_by_pos, \
+                                                         idx, dist);                                                \
         break
-    switch (W4) {
-        RSC_RR(0); RSC_RR(1); RSC_RR(2); RSC_RR(3); RSC_RR(4); RSC_RR(5); RSC_RR(6); RSC_RR(7); RSC_RR(8);
-        RSC_RR(9); RSC_RR(10); RSC_RR(11); RSC_RR(12); RSC_RR(13); RSC_RR(14); RSC_RR(15); RSC_RR(16);
+    switch (C2) {
+        RSC_RR(1); RSC_RR(2); RSC_RR(4); RSC_RR(8); RSC_RR(16); RSC_RR(32);
         default: return cudaErrorInvalidValue;
     }
 #undef RSC_RR
