@@ -54,6 +54,7 @@ cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int 
 constexpr int kOrderSub = 16;           // sub-clusters per coarse cluster
 constexpr int kOrderLeafRows = 512;     // target rows per sub-cluster
 constexpr int kOrderMaxCoarse = 128;
+constexpr int kOrderMaxLeaves = kOrderMaxCoarse * kOrderSub;
 constexpr int kOrderIters = 4;
 constexpr int64_t kOrderMinRows = 16384;   // automatic ordering from this many rows
 constexpr int kOrderWindow = 2;            // database tiles on each side scanned first

@@ -39,8 +39,9 @@ namespace {
 
 constexpr int kCentTile = 64;        // centroids staged in shared memory per pass
 constexpr int kAssignThreads = 128;
-constexpr int kChunk = 8192;         // rows per warp in the counting sort
-constexpr int kSortWarps = 4;
+constexpr int kSortWarps = 8;        // warps per block in the counting sort
+constexpr int kSub = 1024;           // keys per warp slice
+constexpr int kChunk = kSortWarps * kSub;   // keys per block (one count column per chunk)
 
 // Nearest centroid (squared distance |c|^2 - 2 x.c, ties to the lower index)
 // of rows i * step, i < m.  Thread per row; DP = padded row length.
@@ -111,22 +112,18 @@ __global__ void init_centroids_kernel(const float *__restrict__ Y, int64_t n, in
     if (threadIdx.x == 0) cnorm[c] = s;
 }
 
-// Per-chunk label counts: warp w of the grid counts rows
-// [w * kChunk, (w + 1) * kChunk) into cnt[label * nchunk + w].
+// Per-chunk label counts: block b counts keys [b * kChunk, (b + 1) * kChunk)
+// into cnt[label * nchunk + b] (kSortWarps warps, shared-memory atomics).
 __global__ void __launch_bounds__(kSortWarps * 32)
 chunk_hist_kernel(const int32_t *__restrict__ lab, int64_t m, int C, int nchunk, int32_t *__restrict__ cnt) {
-    extern __shared__ int32_t hs[];   // [kSortWarps][C]
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = blockIdx.x * kSortWarps + warp;
-    int32_t *h = hs + warp * C;
-    for (int c = lane; c < C; c += 32) h[c] = 0;
-    __syncwarp();
-    if (ch < nchunk) {
-        const int64_t b = (int64_t)ch * kChunk, e = min(m, b + kChunk);
-        for (int64_t r = b + lane; r < e; r += 32) atomicAdd(&h[lab[r]], 1);
-        __syncwarp();
-        for (int c = lane; c < C; c += 32) cnt[(int64_t)c * nchunk + ch] = h[c];
-    }
+    extern __shared__ int32_t hs[];   // [C]
+    const int ch = blockIdx.x;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) hs[c] = 0;
+    __syncthreads();
+    const int64_t b = (int64_t)ch * kChunk, e = min(m, b + kChunk);
+    for (int64_t r = b + threadIdx.x; r < e; r += blockDim.x) atomicAdd(&hs[lab[r]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) cnt[(int64_t)c * nchunk + ch] = hs[c];
 }
 
 // Exclusive scan of cnt[0 .. N) into off (one block; coalesced 1024-wide
@@ -167,22 +164,35 @@ __global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int32_t *__r
     if (tid == 0) off[N] = carry_s;
 }
 
-// Stable scatter: warp w walks its chunk in key order, 32 keys a step; keys
-// with equal labels within a step are ranked by lane (match_any), and a
-// per-label cursor carries the count across steps.  out[pos] = the row of
-// key r: rows[r * step] (rows given) or r * step.
+// Stable scatter, block per chunk: warp w walks its kSub-key slice of the
+// chunk in key order, 32 keys a step; keys with equal labels within a step
+// are ranked by lane (match_any) and a per-(warp, label) cursor carries the
+// count across steps.  The cursors start at the chunk's offset plus the
+// slice histograms of the lower warps.  out[pos] = the row of key r:
+// rows[r * step] (rows given) or r * step.
 __global__ void __launch_bounds__(kSortWarps * 32)
 chunk_scatter_kernel(const int32_t *__restrict__ lab, int64_t m, int64_t step, const int32_t *__restrict__ rows,
                      int C, int nchunk, const int32_t *__restrict__ off, int32_t *__restrict__ out) {
     extern __shared__ int32_t cur_s[];   // [kSortWarps][C]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = blockIdx.x * kSortWarps + warp;
+    const int ch = blockIdx.x;
     int32_t *cur = cur_s + warp * C;
-    if (ch >= nchunk) return;
-    for (int c = lane; c < C; c += 32) cur[c] = off[(int64_t)c * nchunk + ch];
+    for (int c = lane; c < C; c += 32) cur[c] = 0;
     __syncwarp();
+    const int64_t b = (int64_t)ch * kChunk + (int64_t)warp * kSub, e = min(m, b + kSub);
+    for (int64_t r = b + lane; r < e; r += 32) atomicAdd(&cur[lab[r]], 1);
+    __syncthreads();
+    // exclusive prefix over the warps, per label, plus the chunk offset
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        int run = off[(int64_t)c * nchunk + ch];
+        for (int w = 0; w < kSortWarps; ++w) {
+            const int h = cur_s[w * C + c];
+            cur_s[w * C + c] = run;
+            run += h;
+        }
+    }
+    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t b = (int64_t)ch * kChunk, e = min(m, b + kChunk);
     for (int64_t r0 = b; r0 < e; r0 += 32) {
         const int64_t r = r0 + lane;
         const bool act = r < e;
@@ -399,11 +409,13 @@ cudaError_t launch_assign(const float *Y, int DP, int64_t m, int64_t step, const
 cudaError_t counting_sort(const int32_t *lab, int64_t m, int64_t step, const int32_t *rows, int C, int32_t *cnt,
                           int32_t *off, int32_t *out, cudaStream_t st) {
     const int nchunk = (int)ceil_div(m, kChunk);
-    const unsigned blocks = (unsigned)ceil_div(nchunk, kSortWarps);
     const size_t sm = sizeof(int32_t) * kSortWarps * C;
-    chunk_hist_kernel<<<blocks, kSortWarps * 32, sm, st>>>(lab, m, C, nchunk, cnt);
+    cudaError_t e = cudaFuncSetAttribute(chunk_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(int32_t) * kSortWarps * kOrderMaxLeaves));
+    if (e != cudaSuccess) return e;
+    chunk_hist_kernel<<<nchunk, kSortWarps * 32, sizeof(int32_t) * C, st>>>(lab, m, C, nchunk, cnt);
     exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt, (int64_t)C * nchunk, off);
-    chunk_scatter_kernel<<<blocks, kSortWarps * 32, sm, st>>>(lab, m, step, rows, C, nchunk, off, out);
+    chunk_scatter_kernel<<<nchunk, kSortWarps * 32, sm, st>>>(lab, m, step, rows, C, nchunk, off, out);
     return cudaGetLastError();
 }
 
