@@ -45,7 +45,7 @@ def launches_per_step(metric, precision, n):
 
     rsc_knn: FP32 prep (column sums + column means + prep for Euclidean, prep
     alone for cosine), the BF16 operand prep (tensor-core path), the locality
-    ordering (two k-means levels of 1 init + 4 Lloyd rounds x 5 + 4 for the
+    ordering (two k-means levels of 1 init + 2 Lloyd rounds x 5 + 4 for the
     full assignment and sort, 2 chain passes, + 1 gather of the re-rank rows), the candidate
     search (one launch, or 9 when pruned: window pass, 2 sphere passes, tau,
     count, scan, fill, offsets, list pass) and the re-rank;
@@ -53,7 +53,7 @@ def launches_per_step(metric, precision, n):
     """
     knn = (3 if metric == "euclidean" else 1) + 2
     if precision == "bf16":
-        knn += 1 + (53 + 8 if n >= ORDER_MIN_ROWS else 0)
+        knn += 1 + (33 + 8 if n >= ORDER_MIN_ROWS else 0)
     return knn + 11
 
 

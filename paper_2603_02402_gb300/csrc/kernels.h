@@ -55,7 +55,7 @@ constexpr int kOrderSub = 16;           // sub-clusters per coarse cluster
 constexpr int kOrderLeafRows = 512;     // target rows per sub-cluster
 constexpr int kOrderMaxCoarse = 128;
 constexpr int kOrderMaxLeaves = kOrderMaxCoarse * kOrderSub;
-constexpr int kOrderIters = 4;
+constexpr int kOrderIters = 2;
 constexpr int64_t kOrderMinRows = 16384;   // automatic ordering from this many rows
 constexpr int kOrderWindow = 2;            // database tiles on each side scanned first
 struct OrderShape {
