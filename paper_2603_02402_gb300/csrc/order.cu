@@ -316,10 +316,14 @@ __global__ void init_sub_centroids_kernel(const float *__restrict__ Y, int DP, c
 // gsize <= kChainMax.
 constexpr int kChainMax = 128;
 static_assert(kOrderMaxCoarse <= kChainMax && kOrderSub <= kChainMax, "chain groups fit the seen flags");
-__global__ void chain_kernel(const float *__restrict__ cent, int DP, int gsize, int32_t *__restrict__ rank) {
+__global__ void __launch_bounds__(32) chain_kernel(const float *__restrict__ cent, int DP, int gsize,
+                                                   int32_t *__restrict__ rank) {
+    extern __shared__ float cs[];   // [gsize][DP + 1] (padded against bank conflicts)
     __shared__ bool seen[kChainMax];
     const int g = blockIdx.x, lane = threadIdx.x;
+    const int W = DP + 1;
     const float *C = cent + (int64_t)g * gsize * DP;
+    for (int e = lane; e < gsize * DP; e += 32) cs[(e / DP) * W + e % DP] = C[e];
     for (int c = lane; c < gsize; c += 32) seen[c] = false;
     __syncwarp();
     int last = 0;
@@ -331,11 +335,13 @@ __global__ void chain_kernel(const float *__restrict__ cent, int DP, int gsize, 
     for (int pos = 1; pos < gsize; ++pos) {
         float best = INFINITY;
         int bi = INT_MAX;
+        const float *cl = cs + last * W;
         for (int c = lane; c < gsize; c += 32) {
             if (seen[c]) continue;
+            const float *cc = cs + c * W;
             float s = 0.f;
             for (int t = 0; t < DP; ++t) {
-                const float df = C[(int64_t)c * DP + t] - C[(int64_t)last * DP + t];
+                const float df = cc[t] - cl[t];
                 s = fmaf(df, df, s);
             }
             if (s < best) {
@@ -508,8 +514,8 @@ cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // chains through the coarse centroids and through each cluster's sub-centroids
-    chain_kernel<<<1, 32, 0, st>>>(L.cent1, DP, s.C1, L.rank1);
-    chain_kernel<<<s.C1, 32, 0, st>>>(L.cent2, DP, s.C2, L.rank2);
+    chain_kernel<<<1, 32, sizeof(float) * s.C1 * (DP + 1), st>>>(L.cent1, DP, s.C1, L.rank1);
+    chain_kernel<<<s.C1, 32, sizeof(float) * s.C2 * (DP + 1), st>>>(L.cent2, DP, s.C2, L.rank2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // every row (walked in coarse order, so a block shares its sub-centroids), keyed by its ranks; the final sort
     if ((e = launch_assign_sub(Y, DP, n, 1, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, true, L.rank1, L.rank2, L.lab,
