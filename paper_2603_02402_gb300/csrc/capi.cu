@@ -256,7 +256,10 @@ struct BatchedPlan {
     int64_t n = 0;
     int d = 0, S = 0, kw = 0, kx = 0, metric = 0, DP = 0;
     int parts = 4;      // threads (column parts) per query row
-    int64_t T = 0;
+    int64_t T = 0;      // query tiles (128 rows inside one sample)
+    int64_t DT = 0;     // database tiles (256 rows inside one sample)
+    bool order = false; // rows in cluster order inside each sample
+    bool prune = false; // window pass + tile bounds + list pass
 };
 
 struct BatchedLayout {
@@ -265,6 +268,11 @@ struct BatchedLayout {
     void *Qb, *Db;
     void *tables;
     int32_t *cand_w, *cand_x;
+    int32_t *perm;             // ordering
+    void *order_scratch;
+    float *Rp;                 // re-rank rows in sorted order
+    float *st_w, *st_x;        // saved keys of the pruned search
+    void *prune_scratch;
 };
 
 rsc_status plan_batched(int64_t n, int32_t d, const int64_t *off, int32_t S, int32_t kw, int32_t kx,
@@ -299,7 +307,15 @@ rsc_status plan_batched(int64_t n, int32_t d, const int64_t *off, int32_t S, int
     p->metric = metric;
     p->DP = ((d + (metric == RSC_COSINE ? 1 : 0) + 7) / 8) * 8;
     p->T = batched_query_tiles(off, S);
+    p->DT = batched_db_tiles(off, S);
     if (p->T * S >= (int64_t(1) << 31)) return fail(RSC_ERR_UNSUPPORTED, "too many (tile, sample) work items");
+    if (o->locality < 0 || o->locality > 2) return fail(RSC_ERR_INVALID_ARG, "locality=%d (0, 1 or 2)", o->locality);
+    if (o->prune < 0 || o->prune > 2) return fail(RSC_ERR_INVALID_ARG, "prune=%d (0, 1 or 2)", o->prune);
+    const bool order_ok = S <= kOrderMaxLeaves;
+    if (o->locality == 2 && !order_ok) return fail(RSC_ERR_UNSUPPORTED, "locality ordering supports %d samples", kOrderMaxLeaves);
+    p->order = order_ok && (o->locality == 2 || (o->locality == 0 && n >= kOrderMinRows));
+    if (o->prune == 2 && !p->order) return fail(RSC_ERR_UNSUPPORTED, "prune needs the locality ordering");
+    p->prune = p->order && o->prune != 1;
     return RSC_OK;
 }
 
@@ -312,10 +328,25 @@ BatchedLayout carve_batched(void *ws, const BatchedPlan &p, size_t *bytes) {
     L.prep_scratch = cv.take<float>(prep_scratch_floats());
     L.Qb = cv.take<uint16_t>((size_t)p.n * 64);
     L.Db = cv.take<uint16_t>((size_t)p.n * 64);
-    L.tables = cv.take<uint8_t>(batched_tables_bytes((int)p.T, p.S));
+    L.tables = cv.take<uint8_t>(batched_tables_bytes(p.T, p.S, p.DT));
     // sized for the widest part count, so a tuned choice always fits
     L.cand_w = cv.take<int32_t>((size_t)kBatchedParts * p.n * kBatchedList);
     L.cand_x = cv.take<int32_t>((size_t)p.n * p.S * kBatchedParts * kBatchedShort);
+    L.perm = nullptr;
+    L.order_scratch = nullptr;
+    L.Rp = nullptr;
+    L.st_w = L.st_x = nullptr;
+    L.prune_scratch = nullptr;
+    if (p.order) {
+        L.perm = cv.take<int32_t>((size_t)p.n);
+        L.order_scratch = cv.take<uint8_t>(order_scratch_bytes(p.n, p.DP, p.S));
+        L.Rp = cv.take<float>((size_t)p.n * (p.metric == RSC_EUCLIDEAN ? ceil_div(p.d, 4) * 4 : p.DP));
+    }
+    if (p.prune) {
+        L.st_w = cv.take<float>((size_t)kBatchedParts * p.n * kBatchedList);
+        L.st_x = cv.take<float>((size_t)p.n * p.S * kBatchedParts * kBatchedShort);
+        L.prune_scratch = cv.take<uint8_t>(batched_prune_scratch_bytes(p.n, p.T, p.S, p.DT));
+    }
     if (bytes) *bytes = cv.used;
     return L;
 }
@@ -325,17 +356,40 @@ rsc_status enqueue_batched(const float *X, const BatchedPlan &p, const BatchedLa
     const int64_t n = p.n;
     const int d = p.d, metric = p.metric;
     RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(unsigned int), st));
-    RSC_CUDA_TRY(cudaMemcpyAsync(L.tables, tables_host, batched_tables_bytes((int)p.T, p.S), cudaMemcpyHostToDevice, st));
+    RSC_CUDA_TRY(cudaMemcpyAsync(L.tables, tables_host, batched_tables_bytes(p.T, p.S, p.DT), cudaMemcpyHostToDevice,
+                                 st));
     RSC_CUDA_TRY(launch_prep_fp32(X, n, d, p.DP, metric, L.Y, L.ny, L.prep_scratch, st));
-    RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, nullptr, L.Qb, L.Db, st));
-    RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.parts, L.tables, L.cand_w,
-                                       L.cand_x, L.status, st));
+    const BatchedTables tb = batched_tables(L.tables, p.T, p.S, p.DT);
+    if (p.order)   // cluster order inside each sample (the samples keep their row ranges)
+        RSC_CUDA_TRY(launch_locality_order(L.Y, n, p.DP, kOrderIters, L.perm, L.order_scratch, st, tb.samp_off, p.S));
+    RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.perm, L.Qb, L.Db, st));
+    if (p.prune) {
+        const BatchedPruneOut po = batched_prune_outputs(L.prune_scratch, n, p.T, p.S, p.DT);
+        RSC_CUDA_TRY(launch_batched_prune_window(L.Qb, n, d, metric, L.tables, p.T, p.S, p.DT, L.prune_scratch, st));
+        RSC_CUDA_TRY(launch_knn_tc_batched_window(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, L.tables,
+                                                  po.win, kOrderWindow, L.st_w, L.cand_w, L.st_x, L.cand_x, L.status,
+                                                  st));
+        RSC_CUDA_TRY(launch_batched_prune_bounds(n, d, metric, L.tables, p.T, p.S, p.DT, kOrderWindow, p.parts, L.st_w,
+                                                 L.st_x, L.prune_scratch, st));
+        RSC_CUDA_TRY(launch_knn_tc_batched_list(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, L.tables,
+                                                po.win, kOrderWindow, L.st_w, L.cand_w, L.st_x, L.cand_x, po.tiles,
+                                                po.tile_off, po.overflow, L.status, st));
+    } else {
+        RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, L.tables,
+                                           L.cand_w, L.cand_x, L.status, st));
+    }
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
-    const int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
-    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, p.parts, p.kw, nullptr, false, iw, dw,
+    int64_t rs = (metric == RSC_EUCLIDEAN) ? d : p.DP;
+    if (p.order) {   // rows in search order, 16-byte aligned
+        const int64_t rsr = (metric == RSC_EUCLIDEAN) ? ceil_div(d, 4) * 4 : p.DP;
+        RSC_CUDA_TRY(launch_gather_rows(R, rs, n, (int)rs, L.perm, L.Rp, rsr, st));
+        R = L.Rp;
+        rs = rsr;
+    }
+    RSC_CUDA_TRY(launch_rerank(R, rs, n, d, metric, L.cand_w, kBatchedList, p.parts, p.kw, L.perm, p.order, iw, dw,
                                st));
-    RSC_CUDA_TRY(launch_rerank_cross(R, rs, n, d, metric, L.tables, p.S, (int)p.T, p.parts, L.cand_x, iw, dw, p.kw,
-                                     p.kx, ix, dx, st));
+    RSC_CUDA_TRY(launch_rerank_cross(R, rs, n, d, metric, L.tables, p.S, (int)p.T, p.DT, p.parts, L.cand_x, L.perm,
+                                     p.order, iw, dw, p.kw, p.kx, ix, dx, st));
     return RSC_OK;
 }
 
@@ -494,7 +548,7 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
     if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
     BatchedLayout L = carve_batched(workspace, p, nullptr);
     cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
-    const size_t tb = batched_tables_bytes((int)p.T, p.S);
+    const size_t tb = batched_tables_bytes(p.T, p.S, p.DT);
     if (st == nullptr) {   // legacy default stream cannot be captured: launch directly
         std::vector<uint8_t> host(tb);
         batched_fill_tables(sample_offsets, n_samples, host.data());
@@ -505,7 +559,7 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
     std::vector<uint64_t> key = {(uint64_t)X, (uint64_t)n, (uint64_t)d, (uint64_t)n_samples, (uint64_t)k_within,
                                  (uint64_t)k_cross, (uint64_t)metric, (uint64_t)idx_within, (uint64_t)dist_within,
                                  (uint64_t)idx_cross, (uint64_t)dist_cross, (uint64_t)workspace,
-                                 (uint64_t)p.parts};
+                                 (uint64_t)p.parts, (uint64_t)p.order, (uint64_t)p.prune};
     for (int i = 0; i <= n_samples; ++i) key.push_back((uint64_t)sample_offsets[i]);
     int dev = 0;
     RSC_CUDA_TRY(cudaGetDevice(&dev));

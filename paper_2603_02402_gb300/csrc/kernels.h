@@ -64,10 +64,12 @@ struct OrderShape {
     int nchunk;
 };
 OrderShape order_shape(int64_t n);
-size_t order_scratch_bytes(int64_t n, int DP);
+size_t order_scratch_bytes(int64_t n, int DP, int groups = 0);
 // perm[sorted position] = original row, for the FP32 prep rows Y [n, DP].
+// goff (device, [G + 1], nullable): row groups (samples) whose position
+// ranges must be kept; each group's rows come out in cluster order.
 cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, int32_t *perm, void *scratch,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const int64_t *goff = nullptr, int G = 0);
 
 // ---- knn_tc_prune.cu / prune.cu ---------------------------------------------------
 // Pruned search on rows in locality order (one database split, KB = 1):
@@ -108,16 +110,54 @@ int knn_tc_bn();   // database rows per tensor-core tile
 constexpr int kBatchedList = 16;      // within-sample ids per (row, part); k_within <= 16
 constexpr int kBatchedShort = 4;      // cross-sample ids per (row, sample, part); k_cross <= 4
 constexpr int kBatchedParts = 4;
-size_t batched_tables_bytes(int T, int S);
+// Host-built work tables (see knn_tc_batched.cu for the byte layout).
+struct BatchedTables {
+    int64_t *tile_row, *tile_end, *samp_off, *dtile_start, *dtile_end;
+    int32_t *tile_samp, *samp_order, *counter, *dtile_off;
+};
+BatchedTables batched_tables(void *base, int64_t T, int S, int64_t DT);
+size_t batched_tables_bytes(int64_t T, int S, int64_t DT);
 int64_t batched_query_tiles(const int64_t *offsets_host, int S);
+int64_t batched_db_tiles(const int64_t *offsets_host, int S);
 void batched_fill_tables(const int64_t *offsets_host, int S, void *host_buf);
 cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                  int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
+                                  int64_t DT, int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
                                   unsigned int *status, cudaStream_t st);
+// Pruned batched search on rows in sample-preserving locality order: a window
+// pass around win[t * T + qt] saving keys (st_w [parts, N, kBatchedList],
+// st_x [N, S, parts, kBatchedShort]) and ids (cand_w, cand_x), then a list
+// pass over the kept tiles (tile_off over items t * T + qt).
+cudaError_t launch_knn_tc_batched_window(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
+                                         int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                         float *st_w, int32_t *cand_w, float *st_x, int32_t *cand_x,
+                                         unsigned int *status, cudaStream_t st);
+cudaError_t launch_knn_tc_batched_list(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
+                                       int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                       const float *st_w, int32_t *cand_w, const float *st_x, int32_t *cand_x,
+                                       const int32_t *tiles, const int64_t *tile_off, const int32_t *overflow,
+                                       unsigned int *status, cudaStream_t st);
+// perm (nullable): query and candidate positions map to original rows; R by
+// position when r_by_pos.  Output rows by original row.
 cudaError_t launch_rerank_cross(const float *R, int64_t rs, int64_t N, int d, int metric, const void *tables_dev,
-                                int S, int T, int parts, const int32_t *cand_x, const int32_t *idx_w,
-                                const float *dist_w, int k_within, int k_cross, int32_t *idx_x, float *dist_x,
-                                cudaStream_t st);
+                                int S, int T, int64_t DT, int parts, const int32_t *cand_x, const int32_t *perm,
+                                bool r_by_pos, const int32_t *idx_w, const float *dist_w, int k_within, int k_cross,
+                                int32_t *idx_x, float *dist_x, cudaStream_t st);
+// Bounds of the pruned batched search (prune.cu): tile spheres, the nearest
+// database tile of every sample for every query tile (win), tau per item from
+// the window pass's saved keys, kept-tile lists per item.
+struct BatchedPruneOut {
+    int32_t *win;        // [S * T]
+    int64_t *tile_off;   // [S * T + 1]
+    int32_t *tiles;      // [cap]
+    int32_t *overflow;   // [1]
+};
+size_t batched_prune_scratch_bytes(int64_t N, int64_t T, int S, int64_t DT);
+BatchedPruneOut batched_prune_outputs(void *scratch, int64_t N, int64_t T, int S, int64_t DT);
+cudaError_t launch_batched_prune_window(const void *Qb, int64_t N, int d, int metric, const void *tables_dev, int64_t T,
+                                        int S, int64_t DT, void *scratch, cudaStream_t st);
+cudaError_t launch_batched_prune_bounds(int64_t N, int d, int metric, const void *tables_dev, int64_t T, int S,
+                                        int64_t DT, int window, int parts, const float *st_w, const float *st_x,
+                                        void *scratch, cudaStream_t st);
 
 // ---- autotune.cu --------------------------------------------------------------
 // Tuned-choice table consulted when options are automatic (all zero).

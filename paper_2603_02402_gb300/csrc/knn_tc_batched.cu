@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "knn_tc.cuh"
+#include "warp_sort.cuh"
 
 namespace rsc {
 
@@ -72,38 +73,193 @@ struct BatchedWork {
     }
 };
 
+// Pruned batched search (rows in locality order inside each sample).
+// Pass 1: item (query tile qt, sample t) scans only the tiles of sample t
+// around win[t * T + qt], the tile of t whose bounding-sphere centre is
+// nearest the query tile's, and saves its lists (keys in st_w / st_x, ids in
+// cand_w / cand_x).
+struct BatchedWindowWork {
+    static constexpr int kShort = kBatchedShort;
+    static constexpr bool kResume = false;
+    static constexpr bool kDynamic = true;
+    int T, S;
+    const int64_t *tile_row, *tile_end;
+    const int32_t *tile_samp;
+    const int64_t *samp_off;
+    const int32_t *samp_order;
+    int *counter;
+    int64_t N;
+    const int32_t *win;
+    int window;
+    float *st_w;
+    int32_t *cand_w;
+    float *st_x;
+    int32_t *cand_x;
+
+    int64_t count_host() const { return (int64_t)T * S; }
+    __device__ __forceinline__ int count() const { return T * S; }
+    __device__ __forceinline__ WorkItem get(int it) const {
+        const int r = it / T, qt = it - r * T;
+        const int t = samp_order[r];
+        const int64_t b = samp_off[t], e = samp_off[t + 1];
+        const int Tt = (int)((e - b + BN - 1) / BN);
+        const int w = win[(int64_t)t * T + qt];
+        const int lo = max(0, w - window), hi = min(Tt, w + window + 1);
+        WorkItem wi;
+        wi.q0 = tile_row[qt];
+        wi.q_end = tile_end[qt];
+        wi.j_begin = b + (int64_t)lo * BN;
+        wi.j_end = min(e, b + (int64_t)hi * BN);
+        wi.tag = t;
+        wi.short_list = tile_samp[qt] != t;
+        wi.win_lo = wi.win_hi = 0;
+        wi.tiles = nullptr;
+        wi.n_tiles = 0;
+        wi.skip_window = false;
+        return wi;
+    }
+    template <int EG, int KCP>
+    __device__ __forceinline__ void emit(const WorkItem &w, int part, int64_t q, const RowTopK<KCP> &list) const {
+        if (!w.short_list) {
+            const int64_t base = ((int64_t)part * N + q) * KCP;
+#pragma unroll
+            for (int c = 0; c < KCP; ++c) {
+                st_w[base + c] = list.key[c];
+                cand_w[base + c] = list.id[c];
+            }
+        } else {
+            const int64_t base = (((int64_t)q * S + w.tag) * EG + part) * kShort;
+#pragma unroll
+            for (int c = 0; c < kShort; ++c) {
+                st_x[base + c] = list.key[c];
+                cand_x[base + c] = list.id[c];
+            }
+        }
+    }
+};
+
+// Pass 2: resume the saved lists and scan the kept tiles of sample t
+// (local tile indices, ascending, window excluded); if the kept-tile lists
+// overflowed their buffer, every tile of t outside the window instead.
+struct BatchedListWork {
+    static constexpr int kShort = kBatchedShort;
+    static constexpr bool kResume = true;
+    static constexpr bool kDynamic = true;
+    int T, S;
+    const int64_t *tile_row, *tile_end;
+    const int32_t *tile_samp;
+    const int64_t *samp_off;
+    const int32_t *samp_order;
+    int *counter;
+    int64_t N;
+    const int32_t *win;
+    int window;
+    const float *st_w;
+    int32_t *cand_w;
+    const float *st_x;
+    int32_t *cand_x;
+    const int32_t *tiles;
+    const int64_t *tile_off;    // [T * S + 1], item t * T + qt
+    const int32_t *overflow;
+
+    int64_t count_host() const { return (int64_t)T * S; }
+    __device__ __forceinline__ int count() const { return T * S; }
+    __device__ __forceinline__ WorkItem get(int it) const {
+        const int r = it / T, qt = it - r * T;
+        const int t = samp_order[r];
+        const int64_t item = (int64_t)t * T + qt;
+        WorkItem wi;
+        wi.q0 = tile_row[qt];
+        wi.q_end = tile_end[qt];
+        wi.j_begin = samp_off[t];
+        wi.j_end = samp_off[t + 1];
+        wi.tag = t;
+        wi.short_list = tile_samp[qt] != t;
+        wi.win_lo = wi.win_hi = 0;
+        wi.skip_window = false;
+        if (*overflow == 0) {
+            wi.tiles = tiles + tile_off[item];
+            wi.n_tiles = (int)(tile_off[item + 1] - tile_off[item]);
+        } else {
+            const int Tt = (int)((wi.j_end - wi.j_begin + BN - 1) / BN);
+            const int w = win[item];
+            wi.tiles = nullptr;
+            wi.n_tiles = 0;
+            wi.win_lo = max(0, w - window);
+            wi.win_hi = min(Tt, w + window + 1);
+            wi.skip_window = true;
+        }
+        return wi;
+    }
+    template <int EG, int KCP>
+    __device__ __forceinline__ void resume(const WorkItem &w, int part, int64_t q, RowTopK<KCP> &list) const {
+        if (!w.short_list) {
+            const int64_t base = ((int64_t)part * N + q) * KCP;
+#pragma unroll
+            for (int c = 0; c < KCP; ++c) {
+                list.key[c] = st_w[base + c];
+                list.id[c] = cand_w[base + c];
+            }
+        } else {
+            const int64_t base = (((int64_t)q * S + w.tag) * EG + part) * kShort;
+#pragma unroll
+            for (int c = 0; c < kShort; ++c) {
+                list.key[c] = st_x[base + c];
+                list.id[c] = cand_x[base + c];
+            }
+        }
+    }
+    template <int EG, int KCP>
+    __device__ __forceinline__ void emit(const WorkItem &w, int part, int64_t q, const RowTopK<KCP> &list) const {
+        if (!w.short_list) {
+            int32_t *out = cand_w + ((int64_t)part * N + q) * KCP;
+#pragma unroll
+            for (int c = 0; c < KCP; ++c) out[c] = list.id[c];
+        } else {
+            int32_t *out = cand_x + (((int64_t)q * S + w.tag) * EG + part) * kShort;
+#pragma unroll
+            for (int c = 0; c < kShort; ++c) out[c] = list.id[c];
+        }
+    }
+};
+
 }  // namespace tck
 
 namespace {
 
 constexpr int kXWarps = 4;
 
-__device__ __forceinline__ bool pair_gt(float ka, int ia, float kb, int ib) {
-    return ka > kb || (ka == kb && ia > ib);
-}
-
-// One warp per query: for every sample, re-score its 16 cross candidates
-// exactly (direct difference in FP32), keep the k_cross best by (distance,
-// id), take the own sample's from the exact within lists, then order the
-// row's S * k_cross entries by (distance, id).
+// One warp per query position q (original row qo = perm[q], or q without a
+// permutation): for every sample, re-score its cross candidates exactly
+// (direct difference in FP32), keep the k_cross best by (distance, id), take
+// the own sample's from the exact within lists, then order the row's
+// S * k_cross entries by (distance, id) with a register bitonic network
+// (E = L2 / 32 entries per lane).  Candidate ids are positions, mapped to
+// original rows through perm; R holds the rows by position when r_by_pos.
+template <int E>
 __global__ void __launch_bounds__(kXWarps * 32)
-rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, int metric,
+rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, int metric, int w4,
                     const int64_t *__restrict__ samp_off, int S, const int32_t *__restrict__ cand_x,
-                    const int32_t *__restrict__ idx_w, const float *__restrict__ dist_w, int k_within,
-                    int k_cross, int L2, int parts, int32_t *__restrict__ idx_x, float *__restrict__ dist_x) {
+                    const int32_t *__restrict__ perm, bool r_by_pos, const int32_t *__restrict__ idx_w,
+                    const float *__restrict__ dist_w, int k_within, int k_cross, int parts,
+                    int32_t *__restrict__ idx_x, float *__restrict__ dist_x) {
+    constexpr int L2 = 32 * E;
     const int n_cand = parts * tck::BatchedWork::kShort;   // candidates per (query, sample)
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int XQ = 65;
+    __shared__ __align__(16) float xq_s[kXWarps][68];
+    __shared__ float rkey_s[kXWarps][L2];
+    __shared__ int rid_s[kXWarps][L2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *xq = reinterpret_cast<float *>(smem) + warp * XQ;
-    float *rkey = reinterpret_cast<float *>(smem) + kXWarps * XQ + warp * L2;
-    int *rid = reinterpret_cast<int *>(reinterpret_cast<float *>(smem) + kXWarps * XQ + kXWarps * L2) + warp * L2;
+    float *xq = xq_s[warp];
+    float *rkey = rkey_s[warp];
+    int *rid = rid_s[warp];
     const int64_t q = (int64_t)blockIdx.x * kXWarps + warp;
     if (q >= N) return;
+    const int64_t qo = perm ? (int64_t)perm[q] : q;
+    const int64_t qr = r_by_pos ? q : qo;
     const bool cosine = metric == RSC_COSINE;
     const int width = cosine ? d + 1 : d;
-    for (int t = lane; t < width; t += 32) xq[t] = R[q * rs + t];
-    // own sample (binary search in the offsets)
+    for (int t = lane; t < width; t += 32) xq[t] = R[qr * rs + t];
+    // own sample (binary search in the offsets; positions keep the sample ranges)
     int lo = 0, hi = S;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -125,14 +281,11 @@ rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, i
         float key = INFINITY;
         int id = INT_MAX;
         if (t < S && t != own && hl < n_cand) {
-            const int32_t j = cand_x[((int64_t)q * S + t) * n_cand + hl];
-            if (j >= 0) {
-                const float *yr = R + (int64_t)j * rs;
-                float acc = 0.f;
-                for (int u = 0; u < d; ++u) {
-                    const float diff = xq[u] - __ldg(yr + u);
-                    acc = fmaf(diff, diff, acc);
-                }
+            const int32_t jp = cand_x[((int64_t)q * S + t) * n_cand + hl];
+            if (jp >= 0) {
+                const int32_t j = perm ? perm[jp] : jp;
+                const float *yr = R + (int64_t)(r_by_pos ? jp : j) * rs;
+                float acc = row_dist2(xq, yr, d, w4);
                 if (cosine) {
                     const bool fy = __ldg(yr + d) != 0.f;
                     if (fq || fy) acc = (fq && fy) ? 0.f : 2.f;
@@ -165,43 +318,57 @@ rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, i
     }
     // own sample: the first k_cross of the exact within list
     for (int c = lane; c < k_cross; c += 32) {
-        rkey[own * k_cross + c] = dist_w[q * k_within + c];
-        rid[own * k_cross + c] = idx_w[q * k_within + c];
+        rkey[own * k_cross + c] = dist_w[qo * k_within + c];
+        rid[own * k_cross + c] = idx_w[qo * k_within + c];
     }
     __syncwarp();
     // order the whole row by (distance, id)
-    for (int size = 2; size <= L2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < L2 / 2; i += 32) {
-                const int a = (i / stride) * 2 * stride + (i % stride), b = a + stride;
-                const bool asc = (a & size) == 0;
-                const float ka = rkey[a], kb = rkey[b];
-                const int ia = rid[a], ib = rid[b];
-                if (asc ? pair_gt(ka, ia, kb, ib) : pair_gt(kb, ib, ka, ia)) {
-                    rkey[a] = kb;
-                    rkey[b] = ka;
-                    rid[a] = ib;
-                    rid[b] = ia;
-                }
-            }
-            __syncwarp();
-        }
+    float key[E];
+    int id[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        key[e] = rkey[e * 32 + lane];
+        id[e] = rid[e * 32 + lane];
     }
+    warp_sort_pairs<E>(key, id);
     const int W = S * k_cross;
-    for (int c = lane; c < W; c += 32) {
-        const bool valid = rid[c] != INT_MAX;
-        idx_x[q * W + c] = valid ? rid[c] : -1;
-        dist_x[q * W + c] = valid ? rkey[c] : INFINITY;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = e * 32 + lane;
+        if (c < W) {
+            const bool valid = id[e] != INT_MAX;
+            idx_x[qo * W + c] = valid ? id[e] : -1;
+            dist_x[qo * W + c] = valid ? key[e] : INFINITY;
+        }
     }
 }
 
 }  // namespace
 
-// Host-built tables, uploaded once per call: tile_row[T], tile_end[T],
-// samp_off[S + 1] (int64), tile_samp[T], samp_order[S], item counter (int32,
-// uploaded as 0).
-size_t batched_tables_bytes(int T, int S) {
-    return sizeof(int64_t) * (2 * (size_t)T + S + 1) + sizeof(int32_t) * ((size_t)T + S + 1);
+// Host-built tables, uploaded once per call (BatchedTables in kernels.h):
+// int64 tile_row[T], tile_end[T], samp_off[S + 1], dtile_start[DT],
+// dtile_end[DT]; int32 tile_samp[T], samp_order[S], item counter (uploaded
+// as 0), dtile_off[S + 1].  Query tiles are 128 rows inside one sample;
+// database tiles are 256 rows inside one sample (sample t's tiles are
+// dtile_off[t] .. dtile_off[t + 1]).
+BatchedTables batched_tables(void *base, int64_t T, int S, int64_t DT) {
+    BatchedTables b;
+    int64_t *p64 = static_cast<int64_t *>(base);
+    b.tile_row = p64;
+    b.tile_end = b.tile_row + T;
+    b.samp_off = b.tile_end + T;
+    b.dtile_start = b.samp_off + S + 1;
+    b.dtile_end = b.dtile_start + DT;
+    int32_t *p32 = reinterpret_cast<int32_t *>(b.dtile_end + DT);
+    b.tile_samp = p32;
+    b.samp_order = b.tile_samp + T;
+    b.counter = b.samp_order + S;
+    b.dtile_off = b.counter + 1;
+    return b;
+}
+
+size_t batched_tables_bytes(int64_t T, int S, int64_t DT) {
+    return sizeof(int64_t) * (2 * (size_t)T + S + 1 + 2 * (size_t)DT) + sizeof(int32_t) * ((size_t)T + S + 1 + S + 1);
 }
 
 int64_t batched_query_tiles(const int64_t *offsets_host, int S) {
@@ -210,65 +377,118 @@ int64_t batched_query_tiles(const int64_t *offsets_host, int S) {
     return T;
 }
 
-// Host tables: tile_row [T], tile_end [T], samp_off [S+1], tile_samp [T] (in this order).
+int64_t batched_db_tiles(const int64_t *offsets_host, int S) {
+    int64_t DT = 0;
+    for (int s = 0; s < S; ++s) DT += ceil_div(offsets_host[s + 1] - offsets_host[s], tck::BN);
+    return DT;
+}
+
 void batched_fill_tables(const int64_t *offsets_host, int S, void *host_buf) {
-    const int64_t T = batched_query_tiles(offsets_host, S);
-    int64_t *tile_row = static_cast<int64_t *>(host_buf);
-    int64_t *tile_end = tile_row + T;
-    int64_t *samp_off = tile_end + T;
-    int32_t *tile_samp = reinterpret_cast<int32_t *>(samp_off + S + 1);
-    int64_t t = 0;
+    const int64_t T = batched_query_tiles(offsets_host, S), DT = batched_db_tiles(offsets_host, S);
+    BatchedTables b = batched_tables(host_buf, T, S, DT);
+    int64_t t = 0, g = 0;
     for (int s = 0; s < S; ++s) {
         for (int64_t r = offsets_host[s]; r < offsets_host[s + 1]; r += tck::BM) {
-            tile_row[t] = r;
-            tile_end[t] = std::min<int64_t>(offsets_host[s + 1], r + tck::BM);
-            tile_samp[t] = s;
+            b.tile_row[t] = r;
+            b.tile_end[t] = std::min<int64_t>(offsets_host[s + 1], r + tck::BM);
+            b.tile_samp[t] = s;
             ++t;
         }
+        b.dtile_off[s] = (int32_t)g;
+        for (int64_t r = offsets_host[s]; r < offsets_host[s + 1]; r += tck::BN) {
+            b.dtile_start[g] = r;
+            b.dtile_end[g] = std::min<int64_t>(offsets_host[s + 1], r + tck::BN);
+            ++g;
+        }
     }
-    for (int s = 0; s <= S; ++s) samp_off[s] = offsets_host[s];
-    int32_t *samp_order = tile_samp + T;
-    for (int s = 0; s < S; ++s) samp_order[s] = s;
-    std::stable_sort(samp_order, samp_order + S, [&](int32_t a, int32_t b) {
-        return offsets_host[a + 1] - offsets_host[a] > offsets_host[b + 1] - offsets_host[b];
+    b.dtile_off[S] = (int32_t)g;
+    for (int s = 0; s <= S; ++s) b.samp_off[s] = offsets_host[s];
+    for (int s = 0; s < S; ++s) b.samp_order[s] = s;
+    std::stable_sort(b.samp_order, b.samp_order + S, [&](int32_t a, int32_t c) {
+        return offsets_host[a + 1] - offsets_host[a] > offsets_host[c + 1] - offsets_host[c];
     });
-    samp_order[S] = 0;   // the item counter
+    *b.counter = 0;
 }
 
 cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                  int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
+                                  int64_t DT, int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
                                   unsigned int *status, cudaStream_t st) {
     if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
     CUtensorMap mq, md;
     cudaError_t e = tck::make_map(&mq, Qb, N, 1, tck::BM);
     if (e != cudaSuccess) return e;
     if ((e = tck::make_map(&md, Db, N, 1, tck::BN)) != cudaSuccess) return e;
-    const int64_t *tile_row = static_cast<const int64_t *>(tables_dev);
-    const int64_t *tile_end = tile_row + T;
-    const int64_t *samp_off = tile_end + T;
-    const int32_t *tile_samp = reinterpret_cast<const int32_t *>(samp_off + S + 1);
-    const int32_t *samp_order = tile_samp + T;
-    int *counter = const_cast<int *>(samp_order + S);
-    tck::BatchedWork work{T, S, tile_row, tile_end, tile_samp, samp_off, N, cand_w, cand_x, samp_order, counter};
+    const BatchedTables b = batched_tables(const_cast<void *>(tables_dev), T, S, DT);
+    tck::BatchedWork work{T,     S, b.tile_row, b.tile_end, b.tile_samp, b.samp_off, N, cand_w, cand_x,
+                          b.samp_order, b.counter};
     if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
     if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_rerank_cross(const float *R, int64_t rs, int64_t N, int d, int metric, const void *tables_dev,
-                                int S, int T, int parts, const int32_t *cand_x, const int32_t *idx_w,
-                                const float *dist_w, int k_within, int k_cross, int32_t *idx_x, float *dist_x,
-                                cudaStream_t st) {
+                                int S, int T, int64_t DT, int parts, const int32_t *cand_x, const int32_t *perm,
+                                bool r_by_pos, const int32_t *idx_w, const float *dist_w, int k_within, int k_cross,
+                                int32_t *idx_x, float *dist_x, cudaStream_t st) {
     if (parts != 2 && parts != 4) return cudaErrorInvalidValue;
-    const int64_t *samp_off = static_cast<const int64_t *>(tables_dev) + 2 * (int64_t)T;
+    const BatchedTables b = batched_tables(const_cast<void *>(tables_dev), T, S, DT);
     int L2 = 32;
     while (L2 < S * k_cross) L2 <<= 1;
-    if (L2 > 1024) return cudaErrorInvalidValue;
-    constexpr int XQ = 65;
-    const size_t smem = sizeof(float) * kXWarps * XQ + (sizeof(float) + sizeof(int)) * kXWarps * L2;
-    rerank_cross_kernel<<<(unsigned)ceil_div(N, kXWarps), kXWarps * 32, smem, st>>>(
-        R, rs, N, d, metric, samp_off, S, cand_x, idx_w, dist_w, k_within, k_cross, L2, parts, idx_x, dist_x);
+    const int width = metric == RSC_COSINE ? d + 1 : d;
+    const bool vec = rs % 4 == 0 && reinterpret_cast<uintptr_t>(R) % 16 == 0 && width <= 64;
+    const int w4 = vec ? (width + 3) / 4 : 0;
+    const unsigned blocks = (unsigned)ceil_div(N, kXWarps);
+#define RSC_RX(e)                                                                                                 \
+    case 32 * e:                                                                                                  \
+        rerank_cross_kernel<e><<<blocks, kXWarps * 32, 0, st>>>(R, rs, N, d, metric, w4, b.samp_off, S, cand_x, \
+                                                                perm, r_by_pos, idx_w, dist_w, k_within, k_cross, \
+                                                                parts, idx_x, dist_x);                            \
+        break
+    switch (L2) {
+        RSC_RX(1); RSC_RX(2); RSC_RX(4); RSC_RX(8); RSC_RX(16); RSC_RX(32);
+        default: return cudaErrorInvalidValue;
+    }
+#undef RSC_RX
     return cudaGetLastError();
+}
+
+
+cudaError_t launch_knn_tc_batched_window(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
+                                         int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                         float *st_w, int32_t *cand_w, float *st_x, int32_t *cand_x,
+                                         unsigned int *status, cudaStream_t st) {
+    if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
+    CUtensorMap mq, md;
+    cudaError_t e = tck::make_map(&mq, Qb, N, 1, tck::BM);
+    if (e != cudaSuccess) return e;
+    if ((e = tck::make_map(&md, Db, N, 1, tck::BN)) != cudaSuccess) return e;
+    const BatchedTables b = batched_tables(const_cast<void *>(tables_dev), T, S, DT);
+    if ((e = cudaMemsetAsync(b.counter, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+    tck::BatchedWindowWork work{T, S, b.tile_row, b.tile_end, b.tile_samp, b.samp_off, b.samp_order, b.counter, N,
+                                win, window, st_w, cand_w, st_x, cand_x};
+    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
+    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_knn_tc_batched_list(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
+                                       int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                       const float *st_w, int32_t *cand_w, const float *st_x, int32_t *cand_x,
+                                       const int32_t *tiles, const int64_t *tile_off, const int32_t *overflow,
+                                       unsigned int *status, cudaStream_t st) {
+    if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
+    CUtensorMap mq, md;
+    cudaError_t e = tck::make_map(&mq, Qb, N, 1, tck::BM);
+    if (e != cudaSuccess) return e;
+    if ((e = tck::make_map(&md, Db, N, 1, tck::BN)) != cudaSuccess) return e;
+    const BatchedTables b = batched_tables(const_cast<void *>(tables_dev), T, S, DT);
+    if ((e = cudaMemsetAsync(b.counter, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+    tck::BatchedListWork work{T,      S,     b.tile_row, b.tile_end, b.tile_samp, b.samp_off, b.samp_order,
+                              b.counter, N,  win,        window,     st_w,        cand_w,     st_x,
+                              cand_x, tiles, tile_off,   overflow};
+    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
+    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace rsc

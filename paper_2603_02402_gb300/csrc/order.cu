@@ -448,14 +448,14 @@ struct OrderLayout {
     int32_t *lab1, *lab, *perm1, *cnt, *off, *srows, *rank1, *rank2;
 };
 
-OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, size_t *bytes) {
+OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, int groups, size_t *bytes) {
     Carve cv(scratch);
     OrderLayout L;
-    const int C = s.C1 * s.C2;
+    const int C = std::max(s.C1 * s.C2, groups);   // widest counting sort
     L.cent1 = cv.take<float>((size_t)s.C1 * DP);
     L.cnorm1 = cv.take<float>((size_t)s.C1);
-    L.cent2 = cv.take<float>((size_t)C * DP);
-    L.cnorm2 = cv.take<float>((size_t)C);
+    L.cent2 = cv.take<float>((size_t)s.C1 * s.C2 * DP);
+    L.cnorm2 = cv.take<float>((size_t)s.C1 * s.C2);
     L.lab1 = cv.take<int32_t>((size_t)n);
     L.lab = cv.take<int32_t>((size_t)n);
     L.perm1 = cv.take<int32_t>((size_t)n);
@@ -464,24 +464,44 @@ OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, 
     L.off = cv.take<int32_t>(ncnt + 1);
     L.srows = cv.take<int32_t>((size_t)std::max(s.m1, s.m2));
     L.rank1 = cv.take<int32_t>((size_t)s.C1);
-    L.rank2 = cv.take<int32_t>((size_t)C);
+    L.rank2 = cv.take<int32_t>((size_t)s.C1 * s.C2);
     if (bytes) *bytes = cv.used;
     return L;
 }
 
 }  // namespace
 
-size_t order_scratch_bytes(int64_t n, int DP) {
+size_t order_scratch_bytes(int64_t n, int DP, int groups) {
     size_t bytes = 0;
-    order_layout(nullptr, n, DP, order_shape(n), &bytes);
+    order_layout(nullptr, n, DP, order_shape(n), groups, &bytes);
     return bytes;
 }
 
+namespace {
+
+// key[pos] = the group (sample) of row rows[pos]: goff[g] <= row < goff[g + 1].
+__global__ void group_key_kernel(const int32_t *__restrict__ rows, int64_t n, const int64_t *__restrict__ goff,
+                                 int G, int32_t *__restrict__ key) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t r = rows[i];
+    int lo = 0, hi = G;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (goff[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    key[i] = lo;
+}
+
+}  // namespace
+
 cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, int32_t *perm, void *scratch,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const int64_t *goff, int G) {
     const OrderShape s = order_shape(n);
     if (DP % 8 != 0 || DP > 64) return cudaErrorInvalidValue;
-    const OrderLayout L = order_layout(scratch, n, DP, s, nullptr);
+    if (goff && (G < 1 || G > kOrderMaxLeaves)) return cudaErrorInvalidValue;
+    const OrderLayout L = order_layout(scratch, n, DP, s, goff ? G : 0, nullptr);
     const int C = s.C1 * s.C2;
     const int mean_warps = 4;
     cudaError_t e;
@@ -521,7 +541,13 @@ cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, 
     if ((e = launch_assign_sub(Y, DP, n, 1, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, true, L.rank1, L.rank2, L.lab,
                                st)) != cudaSuccess)
         return e;
-    return counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, perm, st);
+    if (!goff) return counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, perm, st);
+    // groups (samples) keep their row ranges: the cluster order, then a stable
+    // partition by group (perm1 and lab1 are free again)
+    if ((e = counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, L.perm1, st)) != cudaSuccess) return e;
+    group_key_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(L.perm1, n, goff, G, L.lab1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return counting_sort(L.lab1, n, 1, L.perm1, G, L.cnt, L.off, perm, st);
 }
 
 }  // namespace rsc

@@ -37,16 +37,19 @@ __device__ __forceinline__ float bf(const uint16_t *p) {
     return __uint_as_float((uint32_t)(*p) << 16);
 }
 
-// Warp per group of R consecutive rows of the BF16 query operand (row stride
-// W elements, v = the first dv of them): centre (mean of v), radius
-// (max |v - c|, inflated), max |v|^2; row_norm[i] = |v_i|^2 when requested.
+// Warp per group of rows of the BF16 query operand (row stride W elements,
+// v = the first dv of them): rows [g * R, (g + 1) * R) clipped to n, or
+// [g_start[g], g_end[g]) when given.  Centre (mean of v), radius (max |v - c|,
+// inflated), max |v|^2; row_norm[i] = |v_i|^2 when requested.
 __global__ void tile_sphere_kernel(const uint16_t *__restrict__ Qb, int64_t n, int W, int dv, int R, int groups,
+                                   const int64_t *__restrict__ g_start, const int64_t *__restrict__ g_end,
                                    float *__restrict__ cen, float *__restrict__ rad, float *__restrict__ nmax,
                                    float *__restrict__ row_norm) {
     const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= groups) return;
-    const int64_t r0 = (int64_t)g * R, r1 = min(n, r0 + R);
+    const int64_t r0 = g_start ? g_start[g] : (int64_t)g * R;
+    const int64_t r1 = g_end ? g_end[g] : min(n, r0 + R);
     const bool a0 = lane < dv, a1 = lane + 32 < dv;
     float s0 = 0.f, s1 = 0.f;
     for (int64_t r = r0; r < r1; ++r) {
@@ -218,6 +221,144 @@ __global__ void tile_offsets_kernel(int qtiles, int nchunk, const int64_t *__res
     if (Q <= qtiles) tile_off[Q] = off[(int64_t)Q * nchunk];
 }
 
+// ---- batched search: items (query tile qt, sample t), item index t * T + qt
+
+// Sample t's database tiles dtile_off[t] .. dtile_off[t + 1], staged kStage at
+// a time; thread per query tile.  FN(local tile index, centre distance^2,
+// radius, max norm) is called for every tile of t.
+template <class FN>
+__device__ __forceinline__ void for_sample_tiles(int t, const int32_t *__restrict__ dtile_off,
+                                                 const float *__restrict__ dcen, const float *__restrict__ drad,
+                                                 const float *__restrict__ dn, bool active, const float (&c)[kCen],
+                                                 float (*sc)[kCen], float *sr, float *sn, FN fn) {
+    const int g0 = dtile_off[t], g1 = dtile_off[t + 1];
+    for (int s0 = g0; s0 < g1; s0 += kStage) {
+        const int ns = min(kStage, g1 - s0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < ns * kCen; e += blockDim.x) sc[e / kCen][e % kCen] = dcen[(int64_t)s0 * kCen + e];
+        for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+            sr[e] = drad[s0 + e];
+            sn[e] = dn[s0 + e];
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int e = 0; e < ns; ++e) {
+            const float4 *dc = reinterpret_cast<const float4 *>(sc[e]);
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int u = 0; u < kCen / 4; u += 2) {
+                const float4 x = dc[u], y = dc[u + 1];
+                float f;
+                f = c[4 * u] - x.x; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 1] - x.y; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 2] - x.z; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 3] - x.w; a0 = fmaf(f, f, a0);
+                f = c[4 * u + 4] - y.x; a1 = fmaf(f, f, a1);
+                f = c[4 * u + 5] - y.y; a1 = fmaf(f, f, a1);
+                f = c[4 * u + 6] - y.z; a1 = fmaf(f, f, a1);
+                f = c[4 * u + 7] - y.w; a1 = fmaf(f, f, a1);
+            }
+            fn(s0 + e - g0, a0 + a1, sr[e], sn[e]);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_centre(const float *__restrict__ cen, int g, bool active, float (&c)[kCen]) {
+    const float4 *qc = reinterpret_cast<const float4 *>(cen + (int64_t)(active ? g : 0) * kCen);
+#pragma unroll
+    for (int u = 0; u < kCen / 4; ++u) {
+        const float4 v = qc[u];
+        c[4 * u] = v.x;
+        c[4 * u + 1] = v.y;
+        c[4 * u + 2] = v.z;
+        c[4 * u + 3] = v.w;
+    }
+}
+
+// win[t * T + qt] = the tile of sample t whose centre is nearest query tile
+// qt's (ties to the lower index).  Grid (query-tile blocks, samples).
+__global__ void __launch_bounds__(kBoundThreads)
+batched_nearest_kernel(int T, const int32_t *__restrict__ dtile_off, const float *__restrict__ qcen,
+                       const float *__restrict__ dcen, const float *__restrict__ drad, const float *__restrict__ dn,
+                       int32_t *__restrict__ win) {
+    __shared__ __align__(16) float sc[kStage][kCen];
+    __shared__ float sr[kStage], sn[kStage];
+    const int qt = blockIdx.x * kBoundThreads + threadIdx.x, t = blockIdx.y;
+    const bool active = qt < T;
+    float c[kCen];
+    load_centre(qcen, qt, active, c);
+    float best = INFINITY;
+    int bi = 0;
+    for_sample_tiles(t, dtile_off, dcen, drad, dn, active, c, sc, sr, sn, [&](int m, float d2, float, float) {
+        if (d2 < best) {
+            best = d2;
+            bi = m;
+        }
+    });
+    if (active) win[(int64_t)t * T + qt] = bi;
+}
+
+// tau of item (qt, t) = max over the query tile's rows and parts of (saved
+// threshold + |v_i|^2): the 16th key of a within list, the kShort-th of a
+// cross list.  Warp per item.
+__global__ void batched_tau_kernel(int64_t N, int T, int S, int parts, const int64_t *__restrict__ tile_row,
+                                   const int64_t *__restrict__ tile_end, const int32_t *__restrict__ tile_samp,
+                                   const float *__restrict__ st_w, const float *__restrict__ st_x,
+                                   const float *__restrict__ row_norm, float *__restrict__ tau) {
+    const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (item >= (int64_t)T * S) return;
+    const int t = (int)(item / T), qt = (int)(item - (int64_t)t * T);
+    const bool within = tile_samp[qt] == t;
+    float m = -INFINITY;
+    for (int64_t q = tile_row[qt] + lane; q < tile_end[qt]; q += 32) {
+        for (int p = 0; p < parts; ++p) {
+            const float key = within ? st_w[((int64_t)p * N + q) * kBatchedList + kBatchedList - 1]
+                                     : st_x[((q * S + t) * parts + p) * kBatchedShort + kBatchedShort - 1];
+            m = fmaxf(m, key + row_norm[q]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) tau[item] = m;
+}
+
+// Kept tiles of item (qt, t): every tile of sample t outside the window
+// [win - window, win + window] that the sphere bound cannot drop.  FILL =
+// false: count into cnt[item]; FILL = true: write them, ascending, from
+// off[item].  Grid (query-tile blocks, samples).
+template <bool FILL>
+__global__ void __launch_bounds__(kBoundThreads)
+batched_prune_kernel(int T, int window, float beta, const int32_t *__restrict__ dtile_off,
+                     const float *__restrict__ qcen, const float *__restrict__ qrad, const float *__restrict__ qn,
+                     const float *__restrict__ tau, const int32_t *__restrict__ win, const float *__restrict__ dcen,
+                     const float *__restrict__ drad, const float *__restrict__ dn, int32_t *__restrict__ cnt,
+                     const int64_t *__restrict__ off, int32_t *__restrict__ tiles, int64_t cap) {
+    __shared__ __align__(16) float sc[kStage][kCen];
+    __shared__ float sr[kStage], sn[kStage];
+    const int qt = blockIdx.x * kBoundThreads + threadIdx.x, t = blockIdx.y;
+    const bool active = qt < T;
+    const int64_t item = (int64_t)t * T + (active ? qt : 0);
+    float c[kCen];
+    load_centre(qcen, qt, active, c);
+    const float rq = active ? qrad[qt] : 0.f, nq = active ? qn[qt] : 0.f, tq = active ? tau[item] : INFINITY;
+    const int w = active ? win[item] : 0;
+    int kept = 0;
+    int64_t pos = (FILL && active) ? off[item] : 0;
+    for_sample_tiles(t, dtile_off, dcen, drad, dn, active, c, sc, sr, sn, [&](int m, float d2, float rt, float nt) {
+        if (m >= w - window && m <= w + window) return;
+        const float gap = sqrtf(d2) - rq - rt;
+        const float margin = 0x1p-11f * (nq + nt);
+        const bool drop = gap > 0.f && gap * gap - beta * nt - margin > tq;
+        if (!drop) {
+            if (FILL && pos < cap) tiles[pos] = m;
+            ++pos;
+            ++kept;
+        }
+    });
+    if (!FILL && active) cnt[item] = kept;
+}
+
 }  // namespace
 
 PruneShape prune_shape(int64_t n, int BM, int BN) {
@@ -286,10 +427,10 @@ cudaError_t launch_prune_bounds(const void *Qb, int64_t n, int d, int metric, in
     const int dv = metric == RSC_COSINE ? d + 1 : d;
     const float beta = metric == RSC_COSINE ? 1.f : 0.f;
     const uint16_t *q16 = static_cast<const uint16_t *>(Qb);
-    tile_sphere_kernel<<<(unsigned)ceil_div((int64_t)s.qtiles * 32, 256), 256, 0, st>>>(q16, n, W, dv, BM, s.qtiles,
-                                                                                        qcen, qrad, qn, row_norm);
-    tile_sphere_kernel<<<(unsigned)ceil_div((int64_t)s.dtiles * 32, 256), 256, 0, st>>>(q16, n, W, dv, BN, s.dtiles,
-                                                                                        dcen, drad, dn, nullptr);
+    tile_sphere_kernel<<<(unsigned)ceil_div((int64_t)s.qtiles * 32, 256), 256, 0, st>>>(
+        q16, n, W, dv, BM, s.qtiles, nullptr, nullptr, qcen, qrad, qn, row_norm);
+    tile_sphere_kernel<<<(unsigned)ceil_div((int64_t)s.dtiles * 32, 256), 256, 0, st>>>(
+        q16, n, W, dv, BN, s.dtiles, nullptr, nullptr, dcen, drad, dn, nullptr);
     tile_tau_kernel<<<(unsigned)ceil_div((int64_t)s.qtiles * 32, 256), 256, 0, st>>>(st_key, n, EG, KCP, row_norm,
                                                                                      s.qtiles, BM, tau);
     const dim3 grid((unsigned)ceil_div(s.qtiles, kBoundThreads), (unsigned)s.nchunk);
@@ -303,6 +444,94 @@ cudaError_t launch_prune_bounds(const void *Qb, int64_t n, int d, int metric, in
                                                              s.cap);
     tile_offsets_kernel<<<(unsigned)ceil_div(s.qtiles + 1, 256), 256, 0, st>>>(s.qtiles, s.nchunk, off,
                                                                                out->tile_off);
+    return cudaGetLastError();
+}
+
+
+// ---- batched bounds: scratch layout and launchers
+
+namespace {
+
+struct BatchedPruneLayout {
+    float *row_norm, *qcen, *qrad, *qn, *dcen, *drad, *dn, *tau;
+    int32_t *cnt;
+    BatchedPruneOut out;
+};
+
+BatchedPruneLayout batched_prune_layout(void *scratch, int64_t N, int64_t T, int S, int64_t DT, size_t *bytes) {
+    Carve cv(scratch);
+    BatchedPruneLayout L;
+    const size_t items = (size_t)T * S;
+    L.row_norm = cv.take<float>((size_t)N);
+    L.qcen = cv.take<float>((size_t)T * kCen);
+    L.qrad = cv.take<float>((size_t)T);
+    L.qn = cv.take<float>((size_t)T);
+    L.dcen = cv.take<float>((size_t)DT * kCen);
+    L.drad = cv.take<float>((size_t)DT);
+    L.dn = cv.take<float>((size_t)DT);
+    L.tau = cv.take<float>(items);
+    L.cnt = cv.take<int32_t>(items);
+    L.out.win = cv.take<int32_t>(items);
+    L.out.tile_off = cv.take<int64_t>(items + 1);
+    L.out.tiles = cv.take<int32_t>((size_t)std::min<int64_t>((int64_t)items * std::max<int64_t>(DT / S, 1),
+                                                             kPruneListCap));
+    L.out.overflow = cv.take<int32_t>(1);
+    if (bytes) *bytes = cv.used;
+    return L;
+}
+
+int64_t batched_prune_cap(int64_t T, int S, int64_t DT) {
+    return std::min<int64_t>(T * S * std::max<int64_t>(DT / S, 1), kPruneListCap);
+}
+
+}  // namespace
+
+size_t batched_prune_scratch_bytes(int64_t N, int64_t T, int S, int64_t DT) {
+    size_t bytes = 0;
+    batched_prune_layout(nullptr, N, T, S, DT, &bytes);
+    return bytes;
+}
+
+BatchedPruneOut batched_prune_outputs(void *scratch, int64_t N, int64_t T, int S, int64_t DT) {
+    return batched_prune_layout(scratch, N, T, S, DT, nullptr).out;
+}
+
+cudaError_t launch_batched_prune_window(const void *Qb, int64_t N, int d, int metric, const void *tables_dev, int64_t T,
+                                        int S, int64_t DT, void *scratch, cudaStream_t st) {
+    const BatchedPruneLayout L = batched_prune_layout(scratch, N, T, S, DT, nullptr);
+    const BatchedTables b = batched_tables(const_cast<void *>(tables_dev), T, S, DT);
+    const int W = 64 * tc_kb(d, metric);
+    const int dv = metric == RSC_COSINE ? d + 1 : d;
+    const uint16_t *q16 = static_cast<const uint16_t *>(Qb);
+    tile_sphere_kernel<<<(unsigned)ceil_div(T * 32, 256), 256, 0, st>>>(q16, N, W, dv, 0, (int)T, b.tile_row, b.tile_end,
+                                                                       L.qcen, L.qrad, L.qn, L.row_norm);
+    tile_sphere_kernel<<<(unsigned)ceil_div(DT * 32, 256), 256, 0, st>>>(q16, N, W, dv, 0, (int)DT, b.dtile_start,
+                                                                        b.dtile_end, L.dcen, L.drad, L.dn, nullptr);
+    const dim3 grid((unsigned)ceil_div(T, kBoundThreads), (unsigned)S);
+    batched_nearest_kernel<<<grid, kBoundThreads, 0, st>>>((int)T, b.dtile_off, L.qcen, L.dcen, L.drad, L.dn,
+                                                           L.out.win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_prune_bounds(int64_t N, int d, int metric, const void *tables_dev, int64_t T, int S,
+                                        int64_t DT, int window, int parts, const float *st_w, const float *st_x,
+                                        void *scratch, cudaStream_t st) {
+    (void)d;
+    const BatchedPruneLayout L = batched_prune_layout(scratch, N, T, S, DT, nullptr);
+    const BatchedTables b = batched_tables(const_cast<void *>(tables_dev), T, S, DT);
+    const int64_t items = T * S;
+    const float beta = metric == RSC_COSINE ? 1.f : 0.f;
+    const int64_t cap = batched_prune_cap(T, S, DT);
+    batched_tau_kernel<<<(unsigned)ceil_div(items * 32, 256), 256, 0, st>>>(N, (int)T, S, parts, b.tile_row, b.tile_end,
+                                                                           b.tile_samp, st_w, st_x, L.row_norm, L.tau);
+    const dim3 grid((unsigned)ceil_div(T, kBoundThreads), (unsigned)S);
+    batched_prune_kernel<false><<<grid, kBoundThreads, 0, st>>>((int)T, window, beta, b.dtile_off, L.qcen, L.qrad,
+                                                                L.qn, L.tau, L.out.win, L.dcen, L.drad, L.dn, L.cnt,
+                                                                nullptr, nullptr, cap);
+    scan64_kernel<<<1, 1024, 0, st>>>(L.cnt, items, L.out.tile_off, cap, L.out.overflow);
+    batched_prune_kernel<true><<<grid, kBoundThreads, 0, st>>>((int)T, window, beta, b.dtile_off, L.qcen, L.qrad,
+                                                               L.qn, L.tau, L.out.win, L.dcen, L.drad, L.dn, nullptr,
+                                                               L.out.tile_off, L.out.tiles, cap);
     return cudaGetLastError();
 }
 

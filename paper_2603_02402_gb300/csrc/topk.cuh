@@ -31,9 +31,15 @@ struct RowTopK {
 
     // Sorted insertion; strict '<' keeps the earlier of equal keys first.
     // Caller guarantees v < thr().
-    __device__ __forceinline__ void insert(float v, int j) {
+    __device__ __forceinline__ void insert(float v, int j) { insert_prefix<KC>(v, j); }
+
+    // Sorted insertion into the first P entries only (the rest untouched):
+    // for lists of which only the best P are wanted.  Caller guarantees
+    // v < key[P - 1].
+    template <int P>
+    __device__ __forceinline__ void insert_prefix(float v, int j) {
 #pragma unroll
-        for (int c = KC - 1; c > 0; --c) {
+        for (int c = P - 1; c > 0; --c) {
             const bool lt_prev = v < key[c - 1];
             const bool lt_cur = v < key[c];
             const float nk = lt_prev ? key[c - 1] : (lt_cur ? v : key[c]);
@@ -62,7 +68,8 @@ struct RowTopK {
 // one of the KC best, because thresholds only decrease.
 //
 // SHORT > 0: when `shortl` is set only the best SHORT entries are wanted, so
-// the filtering threshold is the SHORT-th key (the list still keeps KC).
+// the filtering threshold is the SHORT-th key and insertions shift only the
+// first SHORT entries.
 template <int KC, int CAP, int STRIDE, int SHORT = 0>
 struct BufferedTopK {
     static constexpr uint32_t kEntry = 4u * STRIDE;          // bytes between entries
@@ -112,7 +119,14 @@ struct BufferedTopK {
         for (int e = 0; e < rounds; ++e) {
             if (e < cnt) {
                 const float v = key_at(e);
-                if (v < bound()) list.insert(v, id_at(e));
+                if (v < bound()) {
+                    if constexpr (SHORT > 0 && SHORT < KC) {
+                        if (shortl) list.template insert_prefix<SHORT>(v, id_at(e));   // warp-uniform per item
+                        else list.insert(v, id_at(e));
+                    } else {
+                        list.insert(v, id_at(e));
+                    }
+                }
             }
         }
         cnt = 0;

@@ -205,9 +205,9 @@ def _offsets_host(sample_offsets):
 
 
 def rsc_knn_batched_workspace_size(n, d, sample_offsets, k_within, k_cross, metric="euclidean",
-                                   precision="bf16") -> int:
+                                   precision="bf16", locality="auto", prune="auto") -> int:
     off, optr = _offsets_host(sample_offsets)
-    o = rsc_knn_opts(_PRECISIONS[precision], 0, 0, 0, None, None)
+    o = rsc_knn_opts(_PRECISIONS[precision], 0, 0, 0, None, None, _LOCALITY[locality], _LOCALITY[prune])
     out = _sz(0)
     _check(lib().rsc_knn_batched_workspace_size(n, d, optr, len(off) - 1, k_within, k_cross,
                                                 _METRICS.get(metric, metric), ctypes.byref(o), ctypes.byref(out)))
@@ -215,7 +215,7 @@ def rsc_knn_batched_workspace_size(n, d, sample_offsets, k_within, k_cross, metr
 
 
 def rsc_knn_batched(X: torch.Tensor, sample_offsets, k_within: int, k_cross: int, metric="euclidean",
-                    precision="bf16", stream=None, workspace=None, out=None):
+                    precision="bf16", stream=None, workspace=None, out=None, locality="auto", prune="auto"):
     """Per-sample kNN and k_cross nearest from every sample (host offsets).
 
     Returns (idx_within [n, k_within], dist_within, idx_cross [n, S * k_cross], dist_cross).
@@ -226,7 +226,7 @@ def rsc_knn_batched(X: torch.Tensor, sample_offsets, k_within: int, k_cross: int
     off, optr = _offsets_host(sample_offsets)
     S = len(off) - 1
     m = _METRICS[metric] if isinstance(metric, str) else int(metric)
-    o = knn_opts(precision, 0, 0, stream)
+    o = knn_opts(precision, 0, 0, stream, locality=locality, prune=prune)
     need = _sz(0)
     _check(lib().rsc_knn_batched_workspace_size(n, d, optr, S, k_within, k_cross, m, ctypes.byref(o),
                                                 ctypes.byref(need)))

@@ -10,8 +10,9 @@ components) of the 1.3M-cell mouse-brain, 2.4M brain and 11M embryo datasets
 
 * ``mixture``     -- Gaussian mixture, cluster means ~ N(0, 4 I), noise on PC t
                      ~ N(0, 1/t) (decaying PC variance, like a PCA embedding).
-* ``batched``     -- many samples of log-uniform size, each its own mixture plus
-                     a per-sample offset ~ N(0, 0.5 I) (a batch effect).
+* ``batched``     -- many samples of log-uniform size sharing one mixture (the
+                     same cell types), each shifted by its own offset
+                     ~ N(0, 0.5 I) (a batch effect).
 * ``anisotropic`` -- mixture whose components have random rotated covariances
                      Q diag(lambda) Q^T, lambda log-uniform in [0.05, 2].
 """
@@ -27,14 +28,18 @@ def _rng(seed: int) -> np.random.Generator:
 
 
 def mixture(n: int, d: int = 50, n_comp: int = 20, seed: int = 0,
-            mean_std: float = 2.0, offset: np.ndarray | None = None) -> np.ndarray:
+            mean_std: float = 2.0, offset: np.ndarray | None = None,
+            means: np.ndarray | None = None) -> np.ndarray:
     """n x d float32 rows of a Gaussian mixture with uniform component weights.
 
-    mean_c ~ N(0, mean_std^2 I); row = mean_c + eps, eps_t ~ N(0, 1/t) for
-    t = 1..d.  Drawn chunk by chunk so 11M-row inputs stay within memory.
+    mean_c ~ N(0, mean_std^2 I) (or the given `means`); row = mean_c + eps,
+    eps_t ~ N(0, 1/t) for t = 1..d.  Drawn chunk by chunk so 11M-row inputs
+    stay within memory.
     """
     rng = _rng(seed)
-    means = rng.standard_normal((n_comp, d)) * mean_std
+    if means is None:
+        means = rng.standard_normal((n_comp, d)) * mean_std
+    n_comp = len(means)
     if offset is not None:
         means = means + offset[None, :]
     scale = 1.0 / np.sqrt(np.arange(1, d + 1, dtype=np.float64))
@@ -59,10 +64,13 @@ def batched_sizes(n_samples: int = 64, lo: float = 2e3, hi: float = 2e5,
 def batched(sizes, d: int = 50, n_comp: int = 30, seed: int = 0):
     """Concatenated samples and their offsets (category offsets, CSR-like).
 
-    Sample s is a ``n_comp``-component mixture shifted by o_s ~ N(0, 0.5 I).
+    The samples share one ``n_comp``-component mixture (the same cell types,
+    means ~ N(0, 4 I)); sample s is shifted by its own o_s ~ N(0, 0.5 I) (a
+    batch effect) and draws its own rows.
     Returns (X float32 [sum(sizes), d], offsets int64 [len(sizes) + 1]).
     """
     rng = _rng(seed)
+    means = rng.standard_normal((n_comp, d)) * 2.0
     sizes = np.asarray(sizes, dtype=np.int64)
     offsets = np.zeros(len(sizes) + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(sizes)
@@ -70,7 +78,7 @@ def batched(sizes, d: int = 50, n_comp: int = 30, seed: int = 0):
     for s, ns in enumerate(sizes):
         off = rng.standard_normal(d) * np.sqrt(0.5)
         sub_seed = int(rng.integers(0, 2**62))
-        X[offsets[s]:offsets[s + 1]] = mixture(int(ns), d, n_comp, sub_seed, offset=off)
+        X[offsets[s]:offsets[s + 1]] = mixture(int(ns), d, seed=sub_seed, offset=off, means=means)
     return X, offsets
 
 

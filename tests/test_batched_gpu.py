@@ -27,15 +27,15 @@ def _recall(gi, gd, oi, od):
     return float(ok.mean())
 
 
-def run(rsc, X, off, kw, kx, metric="euclidean", use_stream=True):
+def run(rsc, X, off, kw, kx, metric="euclidean", use_stream=True, **opts):
     Xd = torch.from_numpy(X).cuda()
     stream = torch.cuda.Stream() if use_stream else None
     ctx = torch.cuda.stream(stream) if use_stream else torch.cuda.stream(torch.cuda.default_stream())
     with ctx:
-        ws = torch.empty(rsc.rsc_knn_batched_workspace_size(len(X), X.shape[1], off, kw, kx, metric),
+        ws = torch.empty(rsc.rsc_knn_batched_workspace_size(len(X), X.shape[1], off, kw, kx, metric, **opts),
                          dtype=torch.uint8, device="cuda")
-        out = rsc.rsc_knn_batched(Xd, off, kw, kx, metric, stream=stream, workspace=ws)
-        out2 = rsc.rsc_knn_batched(Xd, off, kw, kx, metric, stream=stream, workspace=ws)   # graph replay
+        out = rsc.rsc_knn_batched(Xd, off, kw, kx, metric, stream=stream, workspace=ws, **opts)
+        out2 = rsc.rsc_knn_batched(Xd, off, kw, kx, metric, stream=stream, workspace=ws, **opts)   # graph replay
         assert rsc.rsc_workspace_status(ws, stream) == rsc.RSC_OK
     torch.cuda.synchronize()
     res = [t.cpu().numpy() for t in out]
@@ -120,3 +120,21 @@ def test_batched_full_size_sampled(rsc):
     np.testing.assert_allclose(gxd[q], dex, rtol=1e-5, atol=1e-6)
     row_ok = np.all(np.abs(gxd[q] - exp_d) <= 1e-5 * exp_d + 1e-6, axis=1)
     assert row_ok.mean() >= 0.95
+
+
+@pytest.mark.parametrize("metric", ["euclidean", "cosine"])
+@pytest.mark.parametrize("prune", ["on", "off"])
+def test_batched_ordered_and_pruned(rsc, metric, prune):
+    # above the ordering threshold: rows in cluster order inside each sample,
+    # window pass + sphere bounds + list pass (or the ordered full scan); both
+    # against the FP64 oracle on every row
+    sizes = [9000, 14000, 2500, 8000, 700]
+    X, off = synth.batched(sizes, d=50, n_comp=12, seed=21)
+    kw, kx = 15, 3
+    m = oracle.COSINE if metric == "cosine" else oracle.EUCLIDEAN
+    wi, wd, xi, xd = oracle.batched_knn(X, off, kw, kx, m)
+    gi, gd, gxi, gxd = run(rsc, X, off, kw, kx, metric, locality="on", prune=prune)
+    assert _recall(gi, gd, wi, wd) >= 0.999
+    assert _recall(gxi, gxd, xi, xd) >= 0.999
+    np.testing.assert_allclose(np.sort(gd, axis=1)[:, 0], wd[:, 0], rtol=1e-5, atol=1e-6)
+    assert (np.diff(gxd, axis=1) >= 0).all()
