@@ -494,7 +494,10 @@ def run_batched(args):
             "roofline": {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops / (ms / 1e3) / 1e12 / peak, "traffic": None, "kernel": "knn_tc_kernel (batched)",
                          "note": "whole call (prep + search + both re-ranks) timed; 2*d flops per (query, row) pair"},
-            "gpu_launches": 7 * args.steps, "clocks": sampler.summary()}
+            # prep 3, ordering 32 + 4 (sample-preserving partition), BF16 operands 1, pruned search 9
+            # (2 sphere passes, nearest tiles, window pass, tau, count, scan, fill, list pass), gather +
+            # within re-rank + cross re-rank 3; 7 without the ordering (fewer than ORDER_MIN_ROWS rows)
+            "gpu_launches": (52 if n >= ORDER_MIN_ROWS else 7) * args.steps, "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
