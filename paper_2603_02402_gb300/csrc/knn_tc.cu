@@ -182,11 +182,22 @@ TcShape knn_tc_shape(int d, int metric, int k, int want, int parts_req) {
     // fall in one part), and parts x list >= the requested candidate count
     const bool four_ok = tc_kb(d, metric) == 1 && k <= 16 && want <= 64;
     if (parts_req == 4) return four_ok ? TcShape{4, 16} : TcShape{0, 0};
-    if (parts_req == 0 && four_ok) return TcShape{4, 16};
     if (parts_req != 0 && parts_req != 2) return TcShape{0, 0};
-    for (int list : {16, 32, 64})
-        if (list >= k && 2 * list >= want) return TcShape{2, list};
-    return TcShape{0, 0};
+    TcShape two{0, 0};
+    for (int list : {16, 32, 64}) {
+        if (list >= k && 2 * list >= want) {
+            two = TcShape{2, list};
+            break;
+        }
+    }
+    if (parts_req == 2) return two;
+    // automatic: two parts of 16 when they cover the request (half the
+    // per-tile epilogue overhead per value and half the re-rank of four
+    // parts; 1.14x faster at 1M cells, k = 15), else four parts of 16 (short
+    // lists insert faster than two of 32), else two longer lists
+    if (two.parts != 0 && two.list == 16) return two;
+    if (four_ok) return TcShape{4, 16};
+    return two;
 }
 
 bool knn_tc_supported(int d, int metric) { return d >= 1 && d + (metric == RSC_EUCLIDEAN ? 3 : 1) <= 128; }
