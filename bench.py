@@ -47,13 +47,14 @@ def launches_per_step(metric, precision, n):
     alone for cosine), the BF16 operand prep (tensor-core path), the locality
     ordering (two k-means levels of 1 init + 2 Lloyd rounds x 5 + 4 for the
     full assignment and sort, 2 chain passes, + 1 gather of the re-rank rows), the candidate
-    search (one launch, or 9 when pruned: window pass, 2 sphere passes, tau,
-    count, scan, fill, offsets, list pass) and the re-rank;
+    search (one launch, or 12 when pruned: window pass, 2 sphere passes, group
+    spheres, tau, count, scan, fill, offsets, item order, nearest-first order,
+    list pass) and the re-rank;
     rsc_connectivities: 11.
     """
     knn = (3 if metric == "euclidean" else 1) + 2
     if precision == "bf16":
-        knn += 1 + (33 + 8 if n >= ORDER_MIN_ROWS else 0)
+        knn += 1 + (33 + 11 if n >= ORDER_MIN_ROWS else 0)
     return knn + 11
 
 

@@ -464,7 +464,7 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
             RSC_CUDA_TRY(launch_prune_bounds(L.Qb, n, d, metric, knn_tc_bm(), knn_tc_bn(), kOrderWindow, L.st_key,
                                              p.parts, p.KC, L.prune_scratch, &po, st));
             RSC_CUDA_TRY(launch_knn_tc_list(L.Qb, L.Db, n, d, metric, sh, kOrderWindow, L.st_key, L.st_id, po.tiles,
-                                            po.tile_off, po.overflow, L.cand, po.counter, L.status, st));
+                                            po.tile_off, po.order, po.overflow, L.cand, po.counter, L.status, st));
         } else {
             RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, sh, p.splits, p.split_len,
                                        p.order ? kOrderWindow : 0, L.cand, L.status, st));

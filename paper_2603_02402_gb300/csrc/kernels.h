@@ -84,6 +84,7 @@ struct PruneShape {
 struct PruneOut {
     int64_t *tile_off;   // [qtiles + 1]
     int32_t *tiles;      // [cap]
+    int32_t *order;      // [qtiles]: query tiles by decreasing kept-tile count (list pass item order)
     int32_t *overflow;   // [1]: more kept pairs than cap (the list pass then scans every tile)
     int32_t *counter;    // [1]: the list pass's dynamic item counter
 };
@@ -97,7 +98,8 @@ cudaError_t launch_knn_tc_window(const void *Qb, const void *Db, int64_t n, int 
                                  int window, float *st_key, int32_t *st_id, unsigned int *status, cudaStream_t st);
 cudaError_t launch_knn_tc_list(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int window,
                                const float *st_key, const int32_t *st_id, const int32_t *tiles,
-                               const int64_t *tile_off, const int32_t *overflow, int32_t *cand, int *counter,
+                               const int64_t *tile_off, const int32_t *order, const int32_t *overflow,
+                               int32_t *cand, int *counter,
                                unsigned int *status, cudaStream_t st);
 int knn_tc_bm();   // query rows per tensor-core work item
 int knn_tc_bn();   // database rows per tensor-core tile
@@ -149,6 +151,7 @@ struct BatchedPruneOut {
     int32_t *win;        // [S * T]
     int64_t *tile_off;   // [S * T + 1]
     int32_t *tiles;      // [cap]
+    int32_t *order;      // [qtiles]: query tiles by decreasing kept-tile count (list pass item order)
     int32_t *overflow;   // [1]
 };
 size_t batched_prune_scratch_bytes(int64_t N, int64_t T, int S, int64_t DT);

@@ -123,7 +123,7 @@ struct PlainWork {
         w.j_end = min(n, w.j_begin + split_len);
         w.tag = sp;
         w.short_list = false;
-        w.win_lo = w.win_hi = 0;
+        w.win_lo = w.win_hi = w.win_c = 0;
         w.tiles = nullptr;
         w.n_tiles = 0;
         w.skip_window = false;
@@ -132,6 +132,7 @@ struct PlainWork {
             const int tq = (int)((w.q0 - w.j_begin) / BN);
             w.win_lo = max(0, tq - window);
             w.win_hi = min(T, tq + window + 1);
+            w.win_c = tq;
         }
         return w;
     }

@@ -55,15 +55,18 @@ struct WorkItem {
     int64_t q0, q_end, j_begin, j_end;
     int tag;
     bool short_list;
-    int win_lo, win_hi;     // database tiles [win_lo, win_hi) (counted from j_begin) are scanned first
-    const int32_t *tiles;   // non-null: scan exactly these tiles (ascending), nothing else
+    int win_lo, win_hi;     // database tiles [win_lo, win_hi) (counted from j_begin) are scanned first,
+    int win_c;              // starting at tile win_c
+    const int32_t *tiles;   // non-null: scan exactly these tiles, in this order, nothing else
     int n_tiles;
     bool skip_window;       // scan [0, win_lo) and [win_hi, T) only (the window is already done)
 };
 
 // Visiting order of an item's T database tiles: the window [wlo, whi) first,
+// from tile c (the query tile's own neighbourhood, so its lists fill with
+// near-final values and later tiles insert little): [c, whi), then [wlo, c),
 // then [0, wlo), then [whi, T); every tile exactly once.  A tile costs one
-// increment and one compare; the range switch runs three times per item.
+// increment and one compare; the range switch runs four times per item.
 // Requires 0 <= wlo <= whi <= T.  With an explicit list the tiles are
 // lst[0 .. nl) instead, read kAhead entries ahead of use so the list's
 // global-memory latency overlaps the tiles in flight (the producer and MMA
@@ -71,13 +74,13 @@ struct WorkItem {
 // ahead and keeps its registers).
 template <int kAhead>
 struct TileSeq {
-    int m, end, T, wlo, whi, phase;
+    int m, end, T, wlo, whi, c, phase;
     const int32_t *lst;
     int pos, nl;
     int q[kAhead];   // lst[pos + 1 .. pos + kAhead]
 
-    __device__ __forceinline__ void init(int T_, int wlo_, int whi_, const int32_t *lst_ = nullptr, int nl_ = 0,
-                                         bool skip_window = false) {
+    __device__ __forceinline__ void init(int T_, int wlo_, int whi_, int c_, const int32_t *lst_ = nullptr,
+                                         int nl_ = 0, bool skip_window = false) {
         lst = lst_;
         if (lst) {
             pos = 0;
@@ -90,21 +93,31 @@ struct TileSeq {
         T = T_;
         wlo = wlo_;
         whi = whi_;
-        m = wlo;
-        end = skip_window ? wlo : whi;   // an empty first range moves straight on
-        phase = 0;
+        c = 0;
+        if (skip_window || wlo >= whi) {   // straight to [0, wlo)
+            phase = 1;
+            m = end = 0;
+        } else {
+            c = min(max(c_, wlo), whi - 1);
+            phase = 0;
+            m = c;
+            end = whi;
+        }
         settle();
     }
     __device__ __forceinline__ void settle() {
-        while (m == end && phase < 2) {
-            if (phase == 0) {
+        while (m == end && phase < 3) {
+            ++phase;
+            if (phase == 1) {
+                m = wlo;
+                end = c;
+            } else if (phase == 2) {
                 m = 0;
                 end = wlo;
             } else {
                 m = whi;
                 end = T;
             }
-            ++phase;
         }
     }
     __device__ __forceinline__ bool done() const { return lst ? pos >= nl : m >= end; }
@@ -266,7 +279,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 q_parity = item_no & 1;
                 const int jb = (int)j_begin, T = (int)((j_end - j_begin + BN - 1) / BN);
                 TileSeq<4> sq;
-                for (sq.init(T, wi.win_lo, wi.win_hi, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
+                for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
                     if (!(ok = wait(&empty[s], (u & 1) ^ 1))) break;
@@ -299,7 +312,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 tc::tc_fence_after();
                 const int T = (int)((j_end - j_begin + BN - 1) / BN);
                 TileSeq<4> sq;
-                for (sq.init(T, wi.win_lo, wi.win_hi, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
+                for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
                     const int s = gt % S;
                     const uint32_t u = gt / S;
                     const uint32_t b = gt & 1u, v = gt >> 1;
@@ -356,7 +369,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 if (q < wi.q_end) work.template resume<EG>(wi, part, q, tk.list);
             }
             TileSeq<1> sq;
-            for (sq.init(T, wi.win_lo, wi.win_hi, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
+            for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
                 const uint32_t b = gt & 1u;
                 ok = wait(&acc_full[b], (gt >> 1) & 1u);
                 ok = __all_sync(0xffffffffu, ok);

@@ -53,7 +53,7 @@ struct BatchedWork {
         w.j_end = samp_off[t + 1];
         w.tag = t;
         w.short_list = tile_samp[qt] != t;
-        w.win_lo = w.win_hi = 0;
+        w.win_lo = w.win_hi = w.win_c = 0;
         w.tiles = nullptr;
         w.n_tiles = 0;
         w.skip_window = false;
@@ -112,7 +112,9 @@ struct BatchedWindowWork {
         wi.j_end = min(e, b + (int64_t)hi * BN);
         wi.tag = t;
         wi.short_list = tile_samp[qt] != t;
-        wi.win_lo = wi.win_hi = 0;
+        wi.win_lo = 0;             // the whole range is the window, from the centre
+        wi.win_hi = hi - lo;
+        wi.win_c = w - lo;
         wi.tiles = nullptr;
         wi.n_tiles = 0;
         wi.skip_window = false;
@@ -175,7 +177,7 @@ struct BatchedListWork {
         wi.j_end = samp_off[t + 1];
         wi.tag = t;
         wi.short_list = tile_samp[qt] != t;
-        wi.win_lo = wi.win_hi = 0;
+        wi.win_lo = wi.win_hi = wi.win_c = 0;
         wi.skip_window = false;
         if (*overflow == 0) {
             wi.tiles = tiles + tile_off[item];
@@ -187,6 +189,7 @@ struct BatchedListWork {
             wi.n_tiles = 0;
             wi.win_lo = max(0, w - window);
             wi.win_hi = min(Tt, w + window + 1);
+            wi.win_c = w;
             wi.skip_window = true;
         }
         return wi;

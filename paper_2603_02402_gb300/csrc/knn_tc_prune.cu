@@ -7,13 +7,14 @@
 // database tile) pair keeps only the tiles that can still hold a value below
 // some list's saved threshold.
 // Pass 2 (ListWork): every query tile resumes its saved lists and scans its
-// kept tiles in ascending order.
+// kept tiles nearest first (largest lists first across the launch).
 //
-// The unpruned scan visits the window first and then the other tiles in
-// ascending order; a dropped tile's values all lie at or above every
-// threshold its query tile reached after the window, and thresholds only
-// decrease, so the unpruned scan rejects each of them.  The lists, and the
-// candidates, are therefore exactly those of the unpruned scan.
+// The unpruned scan visits the window first and then the other tiles; a
+// dropped tile's values all lie at or above every threshold its query tile
+// reached after the window, and thresholds only decrease, so the unpruned
+// scan rejects each of them.  The lists therefore hold exactly the keys of
+// the unpruned scan's lists; only which of several equal keys at a list's
+// end is kept (the first offered) can depend on the visiting order.
 #include "knn_tc.cuh"
 
 namespace rsc {
@@ -43,7 +44,9 @@ struct WindowWork {
         w.j_end = min(n, (int64_t)hi * BN);
         w.tag = 0;
         w.short_list = false;
-        w.win_lo = w.win_hi = 0;
+        w.win_lo = 0;              // the whole range is the window, from the centre
+        w.win_hi = hi - lo;
+        w.win_c = tq - lo;
         w.tiles = nullptr;
         w.n_tiles = 0;
         w.skip_window = false;
@@ -71,8 +74,9 @@ struct ListWork {
     int window;
     const float *st_key;
     const int32_t *st_id;
-    const int32_t *tiles;       // kept tiles, query tile after query tile
+    const int32_t *tiles;       // kept tiles, query tile after query tile (nearest first)
     const int64_t *tile_off;    // [n_items + 1]
+    const int32_t *order;       // [n_items]: query tiles, largest kept-tile count first
     const int32_t *overflow;    // [1]
     int32_t *cand;              // [EG, n, KCP]
     int n_items;
@@ -80,7 +84,8 @@ struct ListWork {
 
     int64_t count_host() const { return n_items; }
     __device__ __forceinline__ int count() const { return n_items; }
-    __device__ __forceinline__ WorkItem get(int it) const {
+    __device__ __forceinline__ WorkItem get(int pos) const {
+        const int it = order[pos];
         WorkItem w;
         w.q0 = (int64_t)it * BM;
         w.q_end = min(n, w.q0 + BM);
@@ -88,7 +93,7 @@ struct ListWork {
         w.j_end = n;
         w.tag = 0;
         w.short_list = false;
-        w.win_lo = w.win_hi = 0;
+        w.win_lo = w.win_hi = w.win_c = 0;
         w.skip_window = false;
         if (*overflow == 0) {
             w.tiles = tiles + tile_off[it];
@@ -100,6 +105,7 @@ struct ListWork {
             const int tq = (int)(w.q0 / BN);
             w.win_lo = max(0, tq - window);
             w.win_hi = min(T, tq + window + 1);
+            w.win_c = tq;
             w.skip_window = true;
         }
         return w;
@@ -142,14 +148,14 @@ cudaError_t launch_knn_tc_window(const void *Qb, const void *Db, int64_t n, int 
 
 cudaError_t launch_knn_tc_list(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int window,
                                const float *st_key, const int32_t *st_id, const int32_t *tiles,
-                               const int64_t *tile_off, const int32_t *overflow, int32_t *cand, int *counter,
-                               unsigned int *status, cudaStream_t st) {
+                               const int64_t *tile_off, const int32_t *order, const int32_t *overflow,
+                               int32_t *cand, int *counter, unsigned int *status, cudaStream_t st) {
     if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
     CUtensorMap mq, md;
     cudaError_t e = tck::make_map(&mq, Qb, n, 1, tck::BM);
     if (e != cudaSuccess) return e;
     if ((e = tck::make_map(&md, Db, n, 1, tck::BN)) != cudaSuccess) return e;
-    tck::ListWork work{n, window, st_key, st_id, tiles, tile_off, overflow, cand, (int)ceil_div(n, tck::BM), counter};
+    tck::ListWork work{n, window, st_key, st_id, tiles, tile_off, order, overflow, cand, (int)ceil_div(n, tck::BM), counter};
     if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
 #define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg>(mq, md, work, status, st)
     if (sh.parts == 4 && sh.list == 16) RSC_TC_CASE(16, 4);

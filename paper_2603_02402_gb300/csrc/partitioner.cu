@@ -514,7 +514,7 @@ struct ProbeWork {
         w.j_end = doff[lo + 1];
         w.tag = lo;
         w.short_list = false;
-        w.win_lo = w.win_hi = 0;
+        w.win_lo = w.win_hi = w.win_c = 0;
         w.tiles = nullptr;
         w.n_tiles = 0;
         w.skip_window = false;

@@ -17,12 +17,14 @@
 // bounds: 2^-11 (N_Q + N_t), sixteen times the worst-case error of a K = 64
 // FP32 accumulation of terms summing to at most 2 (N_Q + N_t) in magnitude.
 // Radii are inflated by 2^-10 relative plus 1e-6 for their own rounding.
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "warp_sort.cuh"
 
 namespace rsc {
 
@@ -32,15 +34,20 @@ constexpr int kCen = 64;           // centre stride (floats); v has at most 64 c
 constexpr int kChunkTiles = 256;   // database tiles per block in the bound passes
 constexpr int kBoundThreads = 128; // query tiles per block in the bound passes
 constexpr int kStage = 32;         // database tiles staged in shared memory at once
+constexpr int kGroupTiles = 16;    // database tiles per group sphere (tested before its tiles)
 
 __device__ __forceinline__ float bf(const uint16_t *p) {
     return __uint_as_float((uint32_t)(*p) << 16);
 }
 
 // Warp per group of rows of the BF16 query operand (row stride W elements,
-// v = the first dv of them): rows [g * R, (g + 1) * R) clipped to n, or
+// v = the first dv <= 64 of them): rows [g * R, (g + 1) * R) clipped to n, or
 // [g_start[g], g_end[g]) when given.  Centre (mean of v), radius (max |v - c|,
 // inflated), max |v|^2; row_norm[i] = |v_i|^2 when requested.
+// Lane l reads 16 bytes (components 8 (l & 7) .. + 7) of row l >> 3 of every
+// 4-row step, so a warp moves four 128-byte rows per load and keeps several
+// steps in flight; the 8 lanes of a row combine by shuffles.  The centre is
+// any point (its rounding does not matter); the radius is measured from it.
 __global__ void tile_sphere_kernel(const uint16_t *__restrict__ Qb, int64_t n, int W, int dv, int R, int groups,
                                    const int64_t *__restrict__ g_start, const int64_t *__restrict__ g_end,
                                    float *__restrict__ cen, float *__restrict__ rad, float *__restrict__ nmax,
@@ -50,32 +57,70 @@ __global__ void tile_sphere_kernel(const uint16_t *__restrict__ Qb, int64_t n, i
     if (g >= groups) return;
     const int64_t r0 = g_start ? g_start[g] : (int64_t)g * R;
     const int64_t r1 = g_end ? g_end[g] : min(n, r0 + R);
-    const bool a0 = lane < dv, a1 = lane + 32 < dv;
-    float s0 = 0.f, s1 = 0.f;
-    for (int64_t r = r0; r < r1; ++r) {
-        const uint16_t *row = Qb + r * W;
-        if (a0) s0 += bf(row + lane);
-        if (a1) s1 += bf(row + lane + 32);
+    const int ch = lane & 7, rs = lane >> 3;
+    int nv = dv - 8 * ch;   // valid components of this lane's 8
+    nv = nv < 0 ? 0 : (nv > 8 ? 8 : nv);
+    auto load = [&](int64_t r, float (&v)[8]) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(Qb + r * W + 8 * ch);
+        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[2 * i] = 2 * i < nv ? __uint_as_float(w4[i] << 16) : 0.f;
+            v[2 * i + 1] = 2 * i + 1 < nv ? __uint_as_float(w4[i] & 0xffff0000u) : 0.f;
+        }
+    };
+    float c[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c[i] = 0.f;
+#pragma unroll 4
+    for (int64_t r = r0 + rs; r < r1; r += 4) {
+        float v[8];
+        load(r, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] += v[i];
     }
     const float inv = 1.f / (float)(r1 - r0);
-    const float c0 = s0 * inv, c1 = s1 * inv;
-    float md = 0.f, mn = 0.f;
-    for (int64_t r = r0; r < r1; ++r) {
-        const uint16_t *row = Qb + r * W;
-        const float v0 = a0 ? bf(row + lane) : 0.f, v1 = a1 ? bf(row + lane + 32) : 0.f;
-        float dd = (v0 - c0) * (v0 - c0) + (v1 - c1) * (v1 - c1);
-        float nn = v0 * v0 + v1 * v1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+    for (int i = 0; i < 8; ++i) {
+        c[i] += __shfl_xor_sync(0xffffffffu, c[i], 8);
+        c[i] += __shfl_xor_sync(0xffffffffu, c[i], 16);
+        c[i] *= inv;
+    }
+    float md = 0.f, mn = 0.f;
+    // rows of the last, partial step: lanes past r1 contribute nothing but
+    // still take part in the shuffles
+    for (int64_t base = r0; base < r1; base += 4) {
+        const int64_t r = base + rs;
+        const bool ok = r < r1;
+        float v[8];
+        if (ok) load(r, v);
+        float dd = 0.f, nn = 0.f;
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float e = v[i] - c[i];
+                dd = fmaf(e, e, dd);
+                nn = fmaf(v[i], v[i], nn);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
             dd += __shfl_xor_sync(0xffffffffu, dd, o);
             nn += __shfl_xor_sync(0xffffffffu, nn, o);
         }
         md = fmaxf(md, dd);
         mn = fmaxf(mn, nn);
-        if (row_norm && lane == 0) row_norm[r] = nn;
+        if (row_norm && ok && ch == 0) row_norm[r] = nn;
     }
-    cen[(int64_t)g * kCen + lane] = a0 ? c0 : 0.f;
-    cen[(int64_t)g * kCen + lane + 32] = a1 ? c1 : 0.f;
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, 8));
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, 16));
+    mn = fmaxf(mn, __shfl_xor_sync(0xffffffffu, mn, 8));
+    mn = fmaxf(mn, __shfl_xor_sync(0xffffffffu, mn, 16));
+    if (rs == 0) {
+        float4 *out = reinterpret_cast<float4 *>(cen + (int64_t)g * kCen + 8 * ch);
+        out[0] = make_float4(c[0], c[1], c[2], c[3]);
+        out[1] = make_float4(c[4], c[5], c[6], c[7]);
+    }
     if (lane == 0) {
         rad[g] = sqrtf(md) * (1.f + 0x1p-10f) + 1e-6f;
         nmax[g] = mn;
@@ -98,18 +143,85 @@ __global__ void tile_tau_kernel(const float *__restrict__ st_key, int64_t n, int
     if (lane == 0) tau[qt] = m;
 }
 
+// Spheres around groups of kGroupTiles consecutive database tiles, from the
+// tiles' own spheres: centre = mean of the tile centres, radius = max over
+// the tiles of |c_G - c_t| + r_t (inflated), max norm = max over the tiles.
+// Every row of the group lies inside it, so a group that fails the drop test
+// for a query tile drops each of its tiles.  Warp per group.
+__global__ void group_sphere_kernel(const float *__restrict__ dcen, const float *__restrict__ drad,
+                                    const float *__restrict__ dn, int dtiles, int groups, float *__restrict__ gcen,
+                                    float *__restrict__ grad, float *__restrict__ gn) {
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= groups) return;
+    const int t0 = g * kGroupTiles, t1 = min(dtiles, t0 + kGroupTiles);
+    float c0 = 0.f, c1 = 0.f;
+    for (int t = t0; t < t1; ++t) {
+        c0 += dcen[(int64_t)t * kCen + lane];
+        c1 += dcen[(int64_t)t * kCen + lane + 32];
+    }
+    const float inv = 1.f / (float)(t1 - t0);
+    c0 *= inv;
+    c1 *= inv;
+    float r = 0.f, m = 0.f;
+    for (int t = t0; t < t1; ++t) {
+        const float e0 = dcen[(int64_t)t * kCen + lane] - c0, e1 = dcen[(int64_t)t * kCen + lane + 32] - c1;
+        float dd = e0 * e0 + e1 * e1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        r = fmaxf(r, sqrtf(dd) * (1.f + 0x1p-10f) + drad[t]);
+        m = fmaxf(m, dn[t]);
+    }
+    gcen[(int64_t)g * kCen + lane] = c0;
+    gcen[(int64_t)g * kCen + lane + 32] = c1;
+    if (lane == 0) {
+        grad[g] = r * (1.f + 0x1p-10f) + 1e-6f;
+        gn[g] = m;
+    }
+}
+
+// Drop test of a database sphere (centre sc, radius r, max norm nt) for the
+// query tile with centre c, radius rq, max norm nq and threshold tq.
+__device__ __forceinline__ bool sphere_drop(const float (&c)[kCen], const float *sc, float r, float nt, float rq,
+                                            float nq, float tq, float beta) {
+    const float4 *dc = reinterpret_cast<const float4 *>(sc);
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < kCen / 4; u += 2) {
+        const float4 x = dc[u], y = dc[u + 1];
+        float f;
+        f = c[4 * u] - x.x; a0 = fmaf(f, f, a0);
+        f = c[4 * u + 1] - x.y; a0 = fmaf(f, f, a0);
+        f = c[4 * u + 2] - x.z; a0 = fmaf(f, f, a0);
+        f = c[4 * u + 3] - x.w; a0 = fmaf(f, f, a0);
+        f = c[4 * u + 4] - y.x; a1 = fmaf(f, f, a1);
+        f = c[4 * u + 5] - y.y; a1 = fmaf(f, f, a1);
+        f = c[4 * u + 6] - y.z; a1 = fmaf(f, f, a1);
+        f = c[4 * u + 7] - y.w; a1 = fmaf(f, f, a1);
+    }
+    const float gap = sqrtf(a0 + a1) - rq - r;
+    const float margin = 0x1p-11f * (nq + nt);
+    return gap > 0.f && gap * gap - beta * nt - margin > tq;
+}
+
 // Thread per query tile Q, block column = a chunk of kChunkTiles database
 // tiles.  FILL = false: count the kept tiles of (Q, chunk); FILL = true:
-// write them, ascending, from off[Q * nchunk + chunk].
+// write them, ascending, from off[Q * nchunk + chunk].  Each group of
+// kGroupTiles tiles is tested first: a query tile that drops the group skips
+// its tiles (each of them would be dropped too).
 template <bool FILL>
 __global__ void __launch_bounds__(kBoundThreads)
 prune_tiles_kernel(int qtiles, int dtiles, int nchunk, int qpt, int window, float beta,
                    const float *__restrict__ qcen, const float *__restrict__ qrad, const float *__restrict__ qn,
                    const float *__restrict__ tau, const float *__restrict__ dcen, const float *__restrict__ drad,
-                   const float *__restrict__ dn, int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
+                   const float *__restrict__ dn, const float *__restrict__ gcen, const float *__restrict__ grad,
+                   const float *__restrict__ gn, int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
                    int32_t *__restrict__ tiles, int64_t cap) {
+    static_assert(kStage % kGroupTiles == 0 && kChunkTiles % kStage == 0, "stages hold whole groups");
+    constexpr int kStageGroups = kStage / kGroupTiles;
     __shared__ __align__(16) float sc[kStage][kCen];
-    __shared__ float sr[kStage], sn[kStage];
+    __shared__ __align__(16) float sgc[kStageGroups][kCen];
+    __shared__ float sr[kStage], sn[kStage], sgr[kStageGroups], sgn[kStageGroups];
     const int Q = blockIdx.x * kBoundThreads + threadIdx.x;
     const int chunk = blockIdx.y;
     const bool active = Q < qtiles;
@@ -132,39 +244,32 @@ prune_tiles_kernel(int qtiles, int dtiles, int nchunk, int qpt, int window, floa
     int64_t pos = (FILL && active) ? off[(int64_t)Q * nchunk + chunk] : 0;
     for (int s0 = t0; s0 < t1; s0 += kStage) {
         const int ns = min(kStage, t1 - s0);
+        const int ng = (ns + kGroupTiles - 1) / kGroupTiles;
+        const int g0 = s0 / kGroupTiles;
         __syncthreads();
         for (int e = threadIdx.x; e < ns * kCen; e += blockDim.x) sc[e / kCen][e % kCen] = dcen[(int64_t)s0 * kCen + e];
+        for (int e = threadIdx.x; e < ng * kCen; e += blockDim.x)
+            sgc[e / kCen][e % kCen] = gcen[(int64_t)g0 * kCen + e];
         for (int e = threadIdx.x; e < ns; e += blockDim.x) {
             sr[e] = drad[s0 + e];
             sn[e] = dn[s0 + e];
         }
+        for (int e = threadIdx.x; e < ng; e += blockDim.x) {
+            sgr[e] = grad[g0 + e];
+            sgn[e] = gn[g0 + e];
+        }
         __syncthreads();
-        if (!active) continue;
-        for (int e = 0; e < ns; ++e) {
-            const int t = s0 + e;
-            if (t >= wlo && t < whi) continue;
-            const float4 *dc = reinterpret_cast<const float4 *>(sc[e]);
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-            for (int u = 0; u < kCen / 4; u += 2) {
-                const float4 x = dc[u], y = dc[u + 1];
-                float f;
-                f = c[4 * u] - x.x; a0 = fmaf(f, f, a0);
-                f = c[4 * u + 1] - x.y; a0 = fmaf(f, f, a0);
-                f = c[4 * u + 2] - x.z; a0 = fmaf(f, f, a0);
-                f = c[4 * u + 3] - x.w; a0 = fmaf(f, f, a0);
-                f = c[4 * u + 4] - y.x; a1 = fmaf(f, f, a1);
-                f = c[4 * u + 5] - y.y; a1 = fmaf(f, f, a1);
-                f = c[4 * u + 6] - y.z; a1 = fmaf(f, f, a1);
-                f = c[4 * u + 7] - y.w; a1 = fmaf(f, f, a1);
-            }
-            const float gap = sqrtf(a0 + a1) - rq - sr[e];
-            const float margin = 0x1p-11f * (nq + sn[e]);
-            const bool drop = gap > 0.f && gap * gap - beta * sn[e] - margin > tq;
-            if (!drop) {
-                if (FILL && pos < cap) tiles[pos] = t;
-                ++pos;
-                ++kept;
+        for (int h = 0; h < ng; ++h) {
+            if (!active || sphere_drop(c, sgc[h], sgr[h], sgn[h], rq, nq, tq, beta)) continue;
+            const int e1 = min(ns, (h + 1) * kGroupTiles);
+            for (int e = h * kGroupTiles; e < e1; ++e) {
+                const int t = s0 + e;
+                if (t >= wlo && t < whi) continue;
+                if (!sphere_drop(c, sc[e], sr[e], sn[e], rq, nq, tq, beta)) {
+                    if (FILL && pos < cap) tiles[pos] = t;
+                    ++pos;
+                    ++kept;
+                }
             }
         }
     }
@@ -219,6 +324,119 @@ __global__ void tile_offsets_kernel(int qtiles, int nchunk, const int64_t *__res
                                     int64_t *__restrict__ tile_off) {
     const int Q = blockIdx.x * blockDim.x + threadIdx.x;
     if (Q <= qtiles) tile_off[Q] = off[(int64_t)Q * nchunk];
+}
+
+// Visiting order of one query tile's kept tiles: by the lower bound
+// |c_Q - c_t| - r_t of their rows' distance from the query tile's centre,
+// nearest first (ties by tile index).  The lists then meet their final
+// values early and most later tiles take the epilogue's fast path.  The kept
+// set, and so the keys that reach the lists, do not depend on the order.
+constexpr int kNearestWarps = 8;
+constexpr int kNearestMaxE = 16;   // lists of up to 32 * 16 tiles are sorted; longer ones stay ascending
+
+template <int E>
+__device__ __forceinline__ void sort_kept(const float *cq, const float *__restrict__ dcen,
+                                          const float *__restrict__ drad, int32_t *lst, int nl) {
+    const int lane = threadIdx.x & 31;
+    float key[E];
+    int id[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int v = e * 32 + lane;
+        key[e] = INFINITY;
+        id[e] = INT_MAX;
+        if (v < nl) {
+            const int t = lst[v];
+            const float4 *c4 = reinterpret_cast<const float4 *>(dcen + (int64_t)t * kCen);
+            const float4 *q4 = reinterpret_cast<const float4 *>(cq);
+            float a = 0.f;
+#pragma unroll
+            for (int u = 0; u < kCen / 4; ++u) {
+                const float4 x = c4[u], y = q4[u];
+                a = fmaf(x.x - y.x, x.x - y.x, a);
+                a = fmaf(x.y - y.y, x.y - y.y, a);
+                a = fmaf(x.z - y.z, x.z - y.z, a);
+                a = fmaf(x.w - y.w, x.w - y.w, a);
+            }
+            key[e] = sqrtf(a) - drad[t];
+            id[e] = t;
+        }
+    }
+    warp_sort_pairs<E>(key, id);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int v = e * 32 + lane;
+        if (v < nl) lst[v] = id[e];
+    }
+}
+
+// Warp per query tile; nothing to do when the kept-tile lists overflowed.
+__global__ void __launch_bounds__(kNearestWarps * 32)
+nearest_first_kernel(int qtiles, const float *__restrict__ qcen, const float *__restrict__ dcen,
+                     const float *__restrict__ drad, const int64_t *__restrict__ tile_off,
+                     const int32_t *__restrict__ overflow, int32_t *__restrict__ tiles) {
+    __shared__ __align__(16) float cq_s[kNearestWarps][kCen];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Q = blockIdx.x * kNearestWarps + warp;
+    if (Q >= qtiles || *overflow) return;   // warp-uniform
+    float *cq = cq_s[warp];
+    cq[lane] = qcen[(int64_t)Q * kCen + lane];
+    cq[lane + 32] = qcen[(int64_t)Q * kCen + lane + 32];
+    __syncwarp();
+    const int64_t b = tile_off[Q];
+    const int nl = (int)(tile_off[Q + 1] - b);
+    int32_t *lst = tiles + b;
+    if (nl <= 1) return;
+    if (nl <= 32) sort_kept<1>(cq, dcen, drad, lst, nl);
+    else if (nl <= 64) sort_kept<2>(cq, dcen, drad, lst, nl);
+    else if (nl <= 128) sort_kept<4>(cq, dcen, drad, lst, nl);
+    else if (nl <= 256) sort_kept<8>(cq, dcen, drad, lst, nl);
+    else if (nl <= 32 * kNearestMaxE) sort_kept<kNearestMaxE>(cq, dcen, drad, lst, nl);
+}
+
+// Largest-first order of the list pass's items: query tiles by decreasing
+// kept-tile count (counts bucketed by count >> shift into kOrderBins bins;
+// order inside a bin is arbitrary).  A persistent launch that hands items out
+// in this order ends on its smallest items, so its CTAs finish together.
+// Item order does not change any result: every item owns its query rows.
+constexpr int kOrderBins = 2048;
+
+__global__ void __launch_bounds__(1024) item_order_kernel(const int64_t *__restrict__ tile_off, int items,
+                                                          int shift, int32_t *__restrict__ order) {
+    __shared__ int hist[kOrderBins];
+    __shared__ int ws[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b < kOrderBins; b += 1024) hist[b] = 0;
+    __syncthreads();
+    auto bin = [&](int i) {
+        const int64_t c = (tile_off[i + 1] - tile_off[i]) >> shift;
+        return kOrderBins - 1 - (int)(c < kOrderBins - 1 ? c : kOrderBins - 1);
+    };
+    for (int i = tid; i < items; i += 1024) atomicAdd(&hist[bin(i)], 1);
+    __syncthreads();
+    // exclusive scan, two bins per thread
+    const int a0 = hist[2 * tid], a1 = hist[2 * tid + 1];
+    int x = a0 + a1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    const int ex = x - a0 - a1 + (warp > 0 ? ws[warp - 1] : 0);
+    hist[2 * tid] = ex;
+    hist[2 * tid + 1] = ex + a0;
+    __syncthreads();
+    for (int i = tid; i < items; i += 1024) order[atomicAdd(&hist[bin(i)], 1)] = i;
 }
 
 // ---- batched search: items (query tile qt, sample t), item index t * T + qt
@@ -373,7 +591,7 @@ PruneShape prune_shape(int64_t n, int BM, int BN) {
 
 // Layout of the pruning scratch (shared by the launcher and prune_outputs).
 struct PruneLayout {
-    float *row_norm, *qcen, *qrad, *qn, *dcen, *drad, *dn, *tau;
+    float *row_norm, *qcen, *qrad, *qn, *dcen, *drad, *dn, *gcen, *grad, *gn, *tau;
     int32_t *cnt;
     int64_t *off;
     PruneOut out;
@@ -389,12 +607,17 @@ PruneLayout prune_layout(void *scratch, int64_t n, const PruneShape &s, size_t *
     L.dcen = cv.take<float>((size_t)s.dtiles * kCen);
     L.drad = cv.take<float>((size_t)s.dtiles);
     L.dn = cv.take<float>((size_t)s.dtiles);
+    const size_t ngroups = (size_t)ceil_div(s.dtiles, kGroupTiles);
+    L.gcen = cv.take<float>(ngroups * kCen);
+    L.grad = cv.take<float>(ngroups);
+    L.gn = cv.take<float>(ngroups);
     L.tau = cv.take<float>((size_t)s.qtiles);
     const size_t ncnt = (size_t)s.qtiles * s.nchunk;
     L.cnt = cv.take<int32_t>(ncnt);
     L.off = cv.take<int64_t>(ncnt + 1);
     L.out.tile_off = cv.take<int64_t>((size_t)s.qtiles + 1);
     L.out.tiles = cv.take<int32_t>((size_t)s.cap);
+    L.out.order = cv.take<int32_t>((size_t)s.qtiles);
     L.out.overflow = cv.take<int32_t>(1);
     L.out.counter = cv.take<int32_t>(1);
     if (bytes) *bytes = cv.used;
@@ -433,17 +656,27 @@ cudaError_t launch_prune_bounds(const void *Qb, int64_t n, int d, int metric, in
         q16, n, W, dv, BN, s.dtiles, nullptr, nullptr, dcen, drad, dn, nullptr);
     tile_tau_kernel<<<(unsigned)ceil_div((int64_t)s.qtiles * 32, 256), 256, 0, st>>>(st_key, n, EG, KCP, row_norm,
                                                                                      s.qtiles, BM, tau);
+    const int ngroups = (int)ceil_div(s.dtiles, kGroupTiles);
+    group_sphere_kernel<<<(unsigned)ceil_div((int64_t)ngroups * 32, 256), 256, 0, st>>>(
+        dcen, drad, dn, s.dtiles, ngroups, PL.gcen, PL.grad, PL.gn);
     const dim3 grid((unsigned)ceil_div(s.qtiles, kBoundThreads), (unsigned)s.nchunk);
     const int qpt = BN / BM;
     prune_tiles_kernel<false><<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen,
-                                                              qrad, qn, tau, dcen, drad, dn, cnt, nullptr, nullptr,
+                                                              qrad, qn, tau, dcen, drad, dn, PL.gcen, PL.grad, PL.gn,
+                                                              cnt, nullptr, nullptr,
                                                               s.cap);
     scan64_kernel<<<1, 1024, 0, st>>>(cnt, (int64_t)ncnt, off, s.cap, out->overflow);
     prune_tiles_kernel<true><<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen,
-                                                             qrad, qn, tau, dcen, drad, dn, nullptr, off, out->tiles,
+                                                             qrad, qn, tau, dcen, drad, dn, PL.gcen, PL.grad, PL.gn,
+                                                             nullptr, off, out->tiles,
                                                              s.cap);
     tile_offsets_kernel<<<(unsigned)ceil_div(s.qtiles + 1, 256), 256, 0, st>>>(s.qtiles, s.nchunk, off,
                                                                                out->tile_off);
+    int shift = 0;
+    while ((s.dtiles >> shift) >= kOrderBins) ++shift;
+    item_order_kernel<<<1, 1024, 0, st>>>(out->tile_off, s.qtiles, shift, out->order);
+    nearest_first_kernel<<<(unsigned)ceil_div(s.qtiles, kNearestWarps), kNearestWarps * 32, 0, st>>>(
+        s.qtiles, qcen, dcen, drad, out->tile_off, out->overflow, out->tiles);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ namespace rsc {
 
 namespace {
 
-constexpr int kWarps = 4;
+constexpr int kWarps = 16;   // queries per block: neighbouring queries share candidate rows in L1
 
 // Warp per query; E = (candidate slots rounded up to a power of two) / 32
 // (key, id) pairs per lane, element v = e * 32 + lane.  The candidates are
