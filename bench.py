@@ -45,16 +45,17 @@ def launches_per_step(metric, precision, n):
 
     rsc_knn: FP32 prep (column sums + column means + prep for Euclidean, prep
     alone for cosine), the BF16 operand prep (tensor-core path), the locality
-    ordering (two k-means levels of 1 init + 2 Lloyd rounds x 5 + 4 for the
-    full assignment and sort, 2 chain passes, + 1 gather of the re-rank rows), the candidate
-    search (one launch, or 12 when pruned: window pass, 2 sphere passes, group
-    spheres, tau, count, scan, fill, offsets, item order, nearest-first order,
-    list pass) and the re-rank;
+    ordering (two k-means levels of 1 init + 2 Lloyd rounds x 6 + 5 for the
+    full assignment and sort, a sort being 4 launches, 2 chain passes, + 1
+    gather of the re-rank rows), the candidate
+    search (one launch, or 13 when pruned: window pass, 2 sphere passes, group
+    spheres, tau, count, scan (2), fill, offsets, item order, nearest-first
+    order, list pass) and the re-rank;
     rsc_connectivities: 11.
     """
     knn = (3 if metric == "euclidean" else 1) + 2
     if precision == "bf16":
-        knn += 1 + (33 + 11 if n >= ORDER_MIN_ROWS else 0)
+        knn += 1 + (39 + 13 if n >= ORDER_MIN_ROWS else 0)
     return knn + 11
 
 
@@ -498,7 +499,7 @@ def run_batched(args):
             # prep 3, ordering 32 + 4 (sample-preserving partition), BF16 operands 1, pruned search 9
             # (2 sphere passes, nearest tiles, window pass, tau, count, scan, fill, list pass), gather +
             # within re-rank + cross re-rank 3; 7 without the ordering (fewer than ORDER_MIN_ROWS rows)
-            "gpu_launches": (52 if n >= ORDER_MIN_ROWS else 7) * args.steps, "clocks": sampler.summary()}
+            "gpu_launches": (60 if n >= ORDER_MIN_ROWS else 7) * args.steps, "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -32,6 +32,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "scan.cuh"
 
 namespace rsc {
 
@@ -126,44 +127,6 @@ chunk_hist_kernel(const int32_t *__restrict__ lab, int64_t m, int C, int nchunk,
     for (int c = threadIdx.x; c < C; c += blockDim.x) cnt[(int64_t)c * nchunk + ch] = hs[c];
 }
 
-// Exclusive scan of cnt[0 .. N) into off (one block; coalesced 1024-wide
-// tiles with a running carry).  off[N] = total.
-__global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int32_t *__restrict__ cnt, int64_t N,
-                                                              int32_t *__restrict__ off) {
-    __shared__ int32_t ws[32];
-    __shared__ int32_t carry_s;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < N; base += 1024) {
-        const int64_t i = base + tid;
-        const int32_t v = i < N ? cnt[i] : 0;
-        int32_t x = v;   // inclusive warp scan
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) ws[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int32_t w = ws[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            ws[lane] = w;   // inclusive over warps
-        }
-        __syncthreads();
-        const int32_t carry = carry_s;
-        const int32_t incl = x + (warp > 0 ? ws[warp - 1] : 0);
-        if (i < N) off[i] = carry + incl - v;
-        __syncthreads();
-        if (tid == 1023) carry_s = carry + incl;
-        __syncthreads();
-    }
-    if (tid == 0) off[N] = carry_s;
-}
-
 // Stable scatter, block per chunk: warp w walks its kSub-key slice of the
 // chunk in key order, 32 keys a step; keys with equal labels within a step
 // are ranked by lane (match_any) and a per-(warp, label) cursor carries the
@@ -220,10 +183,26 @@ __global__ void centroid_mean_kernel(const float *__restrict__ Y, int DP, const 
     const int32_t b = off[(int64_t)c * nchunk], e = off[(int64_t)(c + 1) * nchunk];
     if (e == b) return;
     float s0 = 0.f, s1 = 0.f;
-    for (int32_t p = b; p < e; ++p) {
-        const float *y = Y + (int64_t)sorted_rows[p] * DP;
-        if (lane < DP) s0 += y[lane];
-        if (lane + 32 < DP) s1 += y[lane + 32];
+    // rows fetched kMeanAhead at a time (independent loads), added in order
+    constexpr int kMeanAhead = 8;
+    for (int32_t p0 = b; p0 < e; p0 += kMeanAhead) {
+        float v0[kMeanAhead], v1[kMeanAhead];
+#pragma unroll
+        for (int u = 0; u < kMeanAhead; ++u) {
+            v0[u] = v1[u] = 0.f;
+            if (p0 + u < e) {
+                const float *y = Y + (int64_t)sorted_rows[p0 + u] * DP;
+                if (lane < DP) v0[u] = y[lane];
+                if (lane + 32 < DP) v1[u] = y[lane + 32];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kMeanAhead; ++u) {
+            if (p0 + u < e) {
+                s0 += v0[u];
+                s1 += v1[u];
+            }
+        }
     }
     const float inv = 1.f / (float)(e - b);
     s0 *= inv;
@@ -312,20 +291,35 @@ __global__ void init_sub_centroids_kernel(const float *__restrict__ Y, int DP, c
 // centroids (cent [groups * gsize, DP]), starting at the group's first:
 // rank[c] = position of centroid c along its group's chain (ties to the lower
 // index).  Consecutive clusters in the final order are then near each other,
-// so tiles that straddle a cluster boundary stay compact.  Warp per group,
-// gsize <= kChainMax.
+// so tiles that straddle a cluster boundary stay compact.  Block per group,
+// gsize <= kChainMax: the block first fills the group's squared-distance
+// matrix (every entry summed over t in order), then one warp walks it.
 constexpr int kChainMax = 128;
+constexpr int kChainThreads = 256;
 static_assert(kOrderMaxCoarse <= kChainMax && kOrderSub <= kChainMax, "chain groups fit the seen flags");
-__global__ void __launch_bounds__(32) chain_kernel(const float *__restrict__ cent, int DP, int gsize,
-                                                   int32_t *__restrict__ rank) {
-    extern __shared__ float cs[];   // [gsize][DP + 1] (padded against bank conflicts)
+__global__ void __launch_bounds__(kChainThreads) chain_kernel(const float *__restrict__ cent, int DP, int gsize,
+                                                              int32_t *__restrict__ rank) {
+    extern __shared__ float cs[];   // [gsize][DP + 1] (padded against bank conflicts), then [gsize][gsize]
     __shared__ bool seen[kChainMax];
-    const int g = blockIdx.x, lane = threadIdx.x;
+    const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     const int W = DP + 1;
+    float *D = cs + gsize * W;
     const float *C = cent + (int64_t)g * gsize * DP;
-    for (int e = lane; e < gsize * DP; e += 32) cs[(e / DP) * W + e % DP] = C[e];
-    for (int c = lane; c < gsize; c += 32) seen[c] = false;
-    __syncwarp();
+    for (int e = tid; e < gsize * DP; e += kChainThreads) cs[(e / DP) * W + e % DP] = C[e];
+    for (int c = tid; c < gsize; c += kChainThreads) seen[c] = false;
+    __syncthreads();
+    for (int e = tid; e < gsize * gsize; e += kChainThreads) {
+        const int a = e / gsize, c = e - a * gsize;   // D[a][c] = |cent_c - cent_a|^2
+        const float *ca = cs + a * W, *cc = cs + c * W;
+        float s = 0.f;
+        for (int t = 0; t < DP; ++t) {
+            const float df = cc[t] - ca[t];
+            s = fmaf(df, df, s);
+        }
+        D[e] = s;
+    }
+    __syncthreads();
+    if (tid >= 32) return;
     int last = 0;
     if (lane == 0) {
         seen[0] = true;
@@ -335,15 +329,10 @@ __global__ void __launch_bounds__(32) chain_kernel(const float *__restrict__ cen
     for (int pos = 1; pos < gsize; ++pos) {
         float best = INFINITY;
         int bi = INT_MAX;
-        const float *cl = cs + last * W;
+        const float *dl = D + last * gsize;
         for (int c = lane; c < gsize; c += 32) {
             if (seen[c]) continue;
-            const float *cc = cs + c * W;
-            float s = 0.f;
-            for (int t = 0; t < DP; ++t) {
-                const float df = cc[t] - cl[t];
-                s = fmaf(df, df, s);
-            }
+            const float s = dl[c];
             if (s < best) {
                 best = s;
                 bi = c;
@@ -413,14 +402,14 @@ cudaError_t launch_assign(const float *Y, int DP, int64_t m, int64_t step, const
 // Stable counting sort of labels lab[0 .. m) -> out (positions hold the row
 // of each key: rows[r * step] when rows is given, else r * step).
 cudaError_t counting_sort(const int32_t *lab, int64_t m, int64_t step, const int32_t *rows, int C, int32_t *cnt,
-                          int32_t *off, int32_t *out, cudaStream_t st) {
+                          int32_t *off, int64_t *ssum, int32_t *out, cudaStream_t st) {
     const int nchunk = (int)ceil_div(m, kChunk);
     const size_t sm = sizeof(int32_t) * kSortWarps * C;
     cudaError_t e = cudaFuncSetAttribute(chunk_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(int32_t) * kSortWarps * kOrderMaxLeaves));
     if (e != cudaSuccess) return e;
     chunk_hist_kernel<<<nchunk, kSortWarps * 32, sizeof(int32_t) * C, st>>>(lab, m, C, nchunk, cnt);
-    exclusive_scan_kernel<<<1, 1024, 0, st>>>(cnt, (int64_t)C * nchunk, off);
+    if ((e = seg_scan::launch(cnt, (int64_t)C * nchunk, off, ssum, st)) != cudaSuccess) return e;
     chunk_scatter_kernel<<<nchunk, kSortWarps * 32, sm, st>>>(lab, m, step, rows, C, nchunk, off, out);
     return cudaGetLastError();
 }
@@ -446,6 +435,7 @@ namespace {
 struct OrderLayout {
     float *cent1, *cnorm1, *cent2, *cnorm2;
     int32_t *lab1, *lab, *perm1, *cnt, *off, *srows, *rank1, *rank2;
+    int64_t *ssum;
 };
 
 OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, int groups, size_t *bytes) {
@@ -462,6 +452,7 @@ OrderLayout order_layout(void *scratch, int64_t n, int DP, const OrderShape &s, 
     const size_t ncnt = (size_t)C * s.nchunk;
     L.cnt = cv.take<int32_t>(ncnt);
     L.off = cv.take<int32_t>(ncnt + 1);
+    L.ssum = cv.take<int64_t>(seg_scan::kMaxSegs);
     L.srows = cv.take<int32_t>((size_t)std::max(s.m1, s.m2));
     L.rank1 = cv.take<int32_t>((size_t)s.C1);
     L.rank2 = cv.take<int32_t>((size_t)s.C1 * s.C2);
@@ -511,14 +502,14 @@ cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, 
     const int nch1 = (int)ceil_div(s.m1, kChunk);
     for (int it = 0; it < iters; ++it) {
         if ((e = launch_assign(Y, DP, s.m1, s.step1, L.cent1, L.cnorm1, s.C1, L.lab1, st)) != cudaSuccess) return e;
-        if ((e = counting_sort(L.lab1, s.m1, s.step1, nullptr, s.C1, L.cnt, L.off, L.srows, st)) != cudaSuccess)
+        if ((e = counting_sort(L.lab1, s.m1, s.step1, nullptr, s.C1, L.cnt, L.off, L.ssum, L.srows, st)) != cudaSuccess)
             return e;
         centroid_mean_kernel<<<(unsigned)ceil_div(s.C1, mean_warps), mean_warps * 32, 0, st>>>(
             Y, DP, L.srows, L.off, nch1, s.C1, L.cent1, L.cnorm1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = launch_assign(Y, DP, n, 1, L.cent1, L.cnorm1, s.C1, L.lab1, st)) != cudaSuccess) return e;
-    if ((e = counting_sort(L.lab1, n, 1, nullptr, s.C1, L.cnt, L.off, L.perm1, st)) != cudaSuccess) return e;
+    if ((e = counting_sort(L.lab1, n, 1, nullptr, s.C1, L.cnt, L.off, L.ssum, L.perm1, st)) != cudaSuccess) return e;
     // level 2: C2 sub-clusters inside each coarse cluster (sample in coarse order)
     init_sub_centroids_kernel<<<C, 32, 0, st>>>(Y, DP, L.perm1, L.off, s.nchunk, s.C2, L.cent1, L.cent2, L.cnorm2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -527,27 +518,31 @@ cudaError_t launch_locality_order(const float *Y, int64_t n, int DP, int iters, 
         if ((e = launch_assign_sub(Y, DP, s.m2, s.step2, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, false, nullptr,
                                    nullptr, L.lab, st)) != cudaSuccess)
             return e;
-        if ((e = counting_sort(L.lab, s.m2, s.step2, L.perm1, C, L.cnt, L.off, L.srows, st)) != cudaSuccess) return e;
+        if ((e = counting_sort(L.lab, s.m2, s.step2, L.perm1, C, L.cnt, L.off, L.ssum, L.srows, st)) != cudaSuccess) return e;
         centroid_mean_kernel<<<(unsigned)ceil_div(C, mean_warps), mean_warps * 32, 0, st>>>(Y, DP, L.srows, L.off,
                                                                                             nch2, C, L.cent2,
                                                                                             L.cnorm2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // chains through the coarse centroids and through each cluster's sub-centroids
-    chain_kernel<<<1, 32, sizeof(float) * s.C1 * (DP + 1), st>>>(L.cent1, DP, s.C1, L.rank1);
-    chain_kernel<<<s.C1, 32, sizeof(float) * s.C2 * (DP + 1), st>>>(L.cent2, DP, s.C2, L.rank2);
+    const size_t sm1 = sizeof(float) * s.C1 * (DP + 1 + s.C1), sm2 = sizeof(float) * s.C2 * (DP + 1 + s.C2);
+    if ((e = cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)std::max(sm1, sm2))) != cudaSuccess)
+        return e;
+    chain_kernel<<<1, kChainThreads, sm1, st>>>(L.cent1, DP, s.C1, L.rank1);
+    chain_kernel<<<s.C1, kChainThreads, sm2, st>>>(L.cent2, DP, s.C2, L.rank2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // every row (walked in coarse order, so a block shares its sub-centroids), keyed by its ranks; the final sort
     if ((e = launch_assign_sub(Y, DP, n, 1, L.perm1, L.lab1, L.cent2, L.cnorm2, s.C2, true, L.rank1, L.rank2, L.lab,
                                st)) != cudaSuccess)
         return e;
-    if (!goff) return counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, perm, st);
+    if (!goff) return counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, L.ssum, perm, st);
     // groups (samples) keep their row ranges: the cluster order, then a stable
     // partition by group (perm1 and lab1 are free again)
-    if ((e = counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, L.perm1, st)) != cudaSuccess) return e;
+    if ((e = counting_sort(L.lab, n, 1, nullptr, C, L.cnt, L.off, L.ssum, L.perm1, st)) != cudaSuccess) return e;
     group_key_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(L.perm1, n, goff, G, L.lab1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return counting_sort(L.lab1, n, 1, L.perm1, G, L.cnt, L.off, perm, st);
+    return counting_sort(L.lab1, n, 1, L.perm1, G, L.cnt, L.off, L.ssum, perm, st);
 }
 
 }  // namespace rsc

@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "scan.cuh"
 #include "warp_sort.cuh"
 
 namespace rsc {
@@ -274,49 +275,6 @@ prune_tiles_kernel(int qtiles, int dtiles, int nchunk, int qpt, int window, floa
         }
     }
     if (!FILL && active) cnt[(int64_t)Q * nchunk + chunk] = kept;
-}
-
-// Exclusive scan of int32 counts into int64 offsets (one block, coalesced
-// 1024-wide tiles with a running carry); off[N] = total; *overflow = total >
-// cap.
-__global__ void __launch_bounds__(1024) scan64_kernel(const int32_t *__restrict__ cnt, int64_t N,
-                                                      int64_t *__restrict__ off, int64_t cap,
-                                                      int32_t *__restrict__ overflow) {
-    __shared__ int64_t ws[32];
-    __shared__ int64_t carry_s;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < N; base += 1024) {
-        const int64_t i = base + tid;
-        const int64_t v = i < N ? cnt[i] : 0;
-        int64_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) ws[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int64_t w = ws[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            ws[lane] = w;
-        }
-        __syncthreads();
-        const int64_t carry = carry_s;
-        const int64_t incl = x + (warp > 0 ? ws[warp - 1] : 0);
-        if (i < N) off[i] = carry + incl - v;
-        __syncthreads();
-        if (tid == 1023) carry_s = carry + incl;
-        __syncthreads();
-    }
-    if (tid == 0) {
-        off[N] = carry_s;
-        *overflow = carry_s > cap ? 1 : 0;
-    }
 }
 
 // tile_off[Q] = off[Q * nchunk] (the query tile's first chunk), tile_off[qtiles] = total.
@@ -593,7 +551,7 @@ PruneShape prune_shape(int64_t n, int BM, int BN) {
 struct PruneLayout {
     float *row_norm, *qcen, *qrad, *qn, *dcen, *drad, *dn, *gcen, *grad, *gn, *tau;
     int32_t *cnt;
-    int64_t *off;
+    int64_t *off, *ssum;
     PruneOut out;
 };
 
@@ -615,6 +573,7 @@ PruneLayout prune_layout(void *scratch, int64_t n, const PruneShape &s, size_t *
     const size_t ncnt = (size_t)s.qtiles * s.nchunk;
     L.cnt = cv.take<int32_t>(ncnt);
     L.off = cv.take<int64_t>(ncnt + 1);
+    L.ssum = cv.take<int64_t>(seg_scan::kMaxSegs);
     L.out.tile_off = cv.take<int64_t>((size_t)s.qtiles + 1);
     L.out.tiles = cv.take<int32_t>((size_t)s.cap);
     L.out.order = cv.take<int32_t>((size_t)s.qtiles);
@@ -665,7 +624,8 @@ cudaError_t launch_prune_bounds(const void *Qb, int64_t n, int d, int metric, in
                                                               qrad, qn, tau, dcen, drad, dn, PL.gcen, PL.grad, PL.gn,
                                                               cnt, nullptr, nullptr,
                                                               s.cap);
-    scan64_kernel<<<1, 1024, 0, st>>>(cnt, (int64_t)ncnt, off, s.cap, out->overflow);
+    cudaError_t e = seg_scan::launch(cnt, (int64_t)ncnt, off, PL.ssum, st, s.cap, out->overflow);
+    if (e != cudaSuccess) return e;
     prune_tiles_kernel<true><<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen,
                                                              qrad, qn, tau, dcen, drad, dn, PL.gcen, PL.grad, PL.gn,
                                                              nullptr, off, out->tiles,
@@ -688,6 +648,7 @@ namespace {
 struct BatchedPruneLayout {
     float *row_norm, *qcen, *qrad, *qn, *dcen, *drad, *dn, *tau;
     int32_t *cnt;
+    int64_t *ssum;
     BatchedPruneOut out;
 };
 
@@ -704,6 +665,7 @@ BatchedPruneLayout batched_prune_layout(void *scratch, int64_t N, int64_t T, int
     L.dn = cv.take<float>((size_t)DT);
     L.tau = cv.take<float>(items);
     L.cnt = cv.take<int32_t>(items);
+    L.ssum = cv.take<int64_t>(seg_scan::kMaxSegs);
     L.out.win = cv.take<int32_t>(items);
     L.out.tile_off = cv.take<int64_t>(items + 1);
     L.out.tiles = cv.take<int32_t>((size_t)std::min<int64_t>((int64_t)items * std::max<int64_t>(DT / S, 1),
@@ -761,7 +723,8 @@ cudaError_t launch_batched_prune_bounds(int64_t N, int d, int metric, const void
     batched_prune_kernel<false><<<grid, kBoundThreads, 0, st>>>((int)T, window, beta, b.dtile_off, L.qcen, L.qrad,
                                                                 L.qn, L.tau, L.out.win, L.dcen, L.drad, L.dn, L.cnt,
                                                                 nullptr, nullptr, cap);
-    scan64_kernel<<<1, 1024, 0, st>>>(L.cnt, items, L.out.tile_off, cap, L.out.overflow);
+    cudaError_t e = seg_scan::launch(L.cnt, items, L.out.tile_off, L.ssum, st, cap, L.out.overflow);
+    if (e != cudaSuccess) return e;
     batched_prune_kernel<true><<<grid, kBoundThreads, 0, st>>>((int)T, window, beta, b.dtile_off, L.qcen, L.qrad,
                                                                L.qn, L.tau, L.out.win, L.dcen, L.drad, L.dn, nullptr,
                                                                L.out.tile_off, L.out.tiles, cap);
