@@ -48,14 +48,14 @@ def launches_per_step(metric, precision, n):
     ordering (two k-means levels of 1 init + 2 Lloyd rounds x 6 + 5 for the
     full assignment and sort, a sort being 4 launches, 2 chain passes, + 1
     gather of the re-rank rows), the candidate
-    search (one launch, or 13 when pruned: window pass, 2 sphere passes, group
-    spheres, tau, count, scan (2), fill, offsets, item order, nearest-first
-    order, list pass) and the re-rank;
+    search (one launch, or 12 when pruned: window pass, 2 sphere passes, group
+    spheres, tau, count, scan (2), fill, offsets, item order, list pass) and
+    the re-rank;
     rsc_connectivities: 11.
     """
     knn = (3 if metric == "euclidean" else 1) + 2
     if precision == "bf16":
-        knn += 1 + (39 + 13 if n >= ORDER_MIN_ROWS else 0)
+        knn += 1 + (39 + 12 if n >= ORDER_MIN_ROWS else 0)
     return knn + 11
 
 

@@ -46,18 +46,41 @@ namespace rsc {
 
 namespace tck {
 
+// BF16 operand rows (row stride W = 64 KB elements): query row = bf16(y),
+// database row = -2 bf16(y) (exact), then the folded terms (Euclidean: 1, 1, 1
+// against |q|^2 split into three BF16 parts; cosine: the zero-row flag
+// against -2 flag), zeros to W.  Row i is source row perm[i].  L = W / 8
+// lanes per row, 8 components (one 16-byte store per operand) per lane; the
+// row's |q|^2 is summed over its lanes by shuffles.  Y rows are DP floats, DP
+// a multiple of 8, so a lane's 8 source floats are two aligned float4 loads.
 __global__ void __launch_bounds__(256)
 prep_bf16_kernel(const float *__restrict__ Y, int64_t n, int d, int DP, int metric, int KB,
                  const int32_t *__restrict__ perm, __nv_bfloat16 *__restrict__ Qb, __nv_bfloat16 *__restrict__ Db) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float *y = Y + (perm ? (int64_t)perm[i] : i) * DP;
-    const int W = 64 * KB;
-    float nrm = 0.f;
-    for (int t = 0; t < d; ++t) {
-        const float q = __bfloat162float(__float2bfloat16_rn(y[t]));
-        nrm = fmaf(q, q, nrm);
+    const int W = 64 * KB, L = W / 8, rpw = 32 / L;
+    const int lane = threadIdx.x & 31, l = lane % L;
+    const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * rpw + lane / L;
+    const bool active = i < n;
+    const float *y = Y + (active ? (perm ? (int64_t)perm[i] : i) : 0) * DP;
+    const int t0 = 8 * l;
+    float v[8];
+    if (active && t0 < DP) {
+        const float4 a = reinterpret_cast<const float4 *>(y + t0)[0], b = reinterpret_cast<const float4 *>(y + t0)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
     }
+    __nv_bfloat16 qv[8];
+    float part = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        qv[e] = __float2bfloat16_rn(t0 + e < d ? v[e] : 0.f);
+        const float q = __bfloat162float(qv[e]);
+        part = fmaf(q, q, part);
+    }
+    for (int o = L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const float nrm = part;
     __nv_bfloat16 ext_q[3], ext_d[3];
     int n_ext;
     if (metric == RSC_EUCLIDEAN) {
@@ -65,38 +88,36 @@ prep_bf16_kernel(const float *__restrict__ Y, int64_t n, int d, int DP, int metr
         const float r1 = nrm - __bfloat162float(h);
         const __nv_bfloat16 m = __float2bfloat16_rn(r1);
         const float r2 = r1 - __bfloat162float(m);
-        const __nv_bfloat16 l = __float2bfloat16_rn(r2);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
         ext_q[0] = ext_q[1] = ext_q[2] = __float2bfloat16_rn(1.f);
         ext_d[0] = h;
         ext_d[1] = m;
-        ext_d[2] = l;
+        ext_d[2] = lo;
         n_ext = 3;
     } else {
-        const float z = y[d];   // all-zero-row flag written by the FP32 prep
+        const float z = active ? y[d] : 0.f;   // all-zero-row flag written by the FP32 prep
         ext_q[0] = __float2bfloat16_rn(z);
         ext_d[0] = __float2bfloat16_rn(-2.f * z);
         n_ext = 1;
     }
-    uint4 *qo = reinterpret_cast<uint4 *>(Qb + i * W);
-    uint4 *dout = reinterpret_cast<uint4 *>(Db + i * W);
-    for (int t8 = 0; t8 < W / 8; ++t8) {
-        __align__(16) __nv_bfloat16 qa[8], da[8];
+    __align__(16) __nv_bfloat16 qa[8], da[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int t = t8 * 8 + e;
-            __nv_bfloat16 qv = __float2bfloat16_rn(0.f), dv = __float2bfloat16_rn(0.f);
-            if (t < d) {
-                qv = __float2bfloat16_rn(y[t]);
-                dv = __float2bfloat16_rn(-2.f * __bfloat162float(qv));   // exact
-            } else if (t < d + n_ext) {
-                qv = ext_q[t - d];
-                dv = ext_d[t - d];
-            }
-            qa[e] = qv;
-            da[e] = dv;
+    for (int e = 0; e < 8; ++e) {
+        const int t = t0 + e;
+        __nv_bfloat16 q = __float2bfloat16_rn(0.f), dd = __float2bfloat16_rn(0.f);
+        if (t < d) {
+            q = qv[e];
+            dd = __float2bfloat16_rn(-2.f * __bfloat162float(q));   // exact
+        } else if (t < d + n_ext) {
+            q = ext_q[t - d];
+            dd = ext_d[t - d];
         }
-        qo[t8] = *reinterpret_cast<const uint4 *>(qa);
-        dout[t8] = *reinterpret_cast<const uint4 *>(da);
+        qa[e] = q;
+        da[e] = dd;
+    }
+    if (active) {
+        reinterpret_cast<uint4 *>(Qb + i * W)[l] = *reinterpret_cast<const uint4 *>(qa);
+        reinterpret_cast<uint4 *>(Db + i * W)[l] = *reinterpret_cast<const uint4 *>(da);
     }
 }
 
@@ -210,7 +231,8 @@ int knn_tc_bn() { return tck::BN; }
 cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metric, const int32_t *perm, void *Qb,
                              void *Db, cudaStream_t st) {
     const int KB = tc_kb(d, metric);
-    tck::prep_bf16_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
+    const int rows_per_block = 256 / 32 * (32 / (8 * KB));
+    tck::prep_bf16_kernel<<<(unsigned)ceil_div(n, rows_per_block), 256, 0, st>>>(
         Y, n, d, DP, metric, KB, perm, static_cast<__nv_bfloat16 *>(Qb), static_cast<__nv_bfloat16 *>(Db));
     return cudaGetLastError();
 }

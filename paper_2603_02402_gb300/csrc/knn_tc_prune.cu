@@ -7,14 +7,13 @@
 // database tile) pair keeps only the tiles that can still hold a value below
 // some list's saved threshold.
 // Pass 2 (ListWork): every query tile resumes its saved lists and scans its
-// kept tiles nearest first (largest lists first across the launch).
+// kept tiles in ascending order (largest lists first across the launch).
 //
-// The unpruned scan visits the window first and then the other tiles; a
-// dropped tile's values all lie at or above every threshold its query tile
-// reached after the window, and thresholds only decrease, so the unpruned
-// scan rejects each of them.  The lists therefore hold exactly the keys of
-// the unpruned scan's lists; only which of several equal keys at a list's
-// end is kept (the first offered) can depend on the visiting order.
+// The unpruned scan visits the window first and then the other tiles in
+// ascending order; a dropped tile's values all lie at or above every
+// threshold its query tile reached after the window, and thresholds only
+// decrease, so the unpruned scan rejects each of them.  The lists, and the
+// candidates, are therefore exactly those of the unpruned scan.
 #include "knn_tc.cuh"
 
 namespace rsc {
@@ -74,7 +73,7 @@ struct ListWork {
     int window;
     const float *st_key;
     const int32_t *st_id;
-    const int32_t *tiles;       // kept tiles, query tile after query tile (nearest first)
+    const int32_t *tiles;       // kept tiles, query tile after query tile (ascending)
     const int64_t *tile_off;    // [n_items + 1]
     const int32_t *order;       // [n_items]: query tiles, largest kept-tile count first
     const int32_t *overflow;    // [1]

@@ -17,7 +17,6 @@
 // bounds: 2^-11 (N_Q + N_t), sixteen times the worst-case error of a K = 64
 // FP32 accumulation of terms summing to at most 2 (N_Q + N_t) in magnitude.
 // Radii are inflated by 2^-10 relative plus 1e-6 for their own rounding.
-#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -25,7 +24,6 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "scan.cuh"
-#include "warp_sort.cuh"
 
 namespace rsc {
 
@@ -206,18 +204,19 @@ __device__ __forceinline__ bool sphere_drop(const float (&c)[kCen], const float 
 }
 
 // Thread per query tile Q, block column = a chunk of kChunkTiles database
-// tiles.  FILL = false: count the kept tiles of (Q, chunk); FILL = true:
-// write them, ascending, from off[Q * nchunk + chunk].  Each group of
-// kGroupTiles tiles is tested first: a query tile that drops the group skips
-// its tiles (each of them would be dropped too).
-template <bool FILL>
+// tiles: count the kept tiles of (Q, chunk) and record them as bits, one
+// 32-bit word per stage of kStage tiles (bits[(Q * nchunk + chunk) * kWords
+// + stage]).  Each group of kGroupTiles tiles is tested first: a query tile
+// that drops the group skips its tiles (each of them would be dropped too).
+constexpr int kWords = kChunkTiles / kStage;
+static_assert(kStage == 32, "one bit word per stage");
+
 __global__ void __launch_bounds__(kBoundThreads)
 prune_tiles_kernel(int qtiles, int dtiles, int nchunk, int qpt, int window, float beta,
                    const float *__restrict__ qcen, const float *__restrict__ qrad, const float *__restrict__ qn,
                    const float *__restrict__ tau, const float *__restrict__ dcen, const float *__restrict__ drad,
                    const float *__restrict__ dn, const float *__restrict__ gcen, const float *__restrict__ grad,
-                   const float *__restrict__ gn, int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
-                   int32_t *__restrict__ tiles, int64_t cap) {
+                   const float *__restrict__ gn, int32_t *__restrict__ cnt, uint32_t *__restrict__ bits) {
     static_assert(kStage % kGroupTiles == 0 && kChunkTiles % kStage == 0, "stages hold whole groups");
     constexpr int kStageGroups = kStage / kGroupTiles;
     __shared__ __align__(16) float sc[kStage][kCen];
@@ -241,9 +240,9 @@ prune_tiles_kernel(int qtiles, int dtiles, int nchunk, int qpt, int window, floa
     const int tw = active ? Q / qpt : 0;
     const int wlo = max(0, tw - window), whi = min(dtiles, tw + window + 1);
     const int t0 = chunk * kChunkTiles, t1 = min(dtiles, t0 + kChunkTiles);
+    uint32_t *wout = bits + ((int64_t)(active ? Q : 0) * nchunk + chunk) * kWords;
     int kept = 0;
-    int64_t pos = (FILL && active) ? off[(int64_t)Q * nchunk + chunk] : 0;
-    for (int s0 = t0; s0 < t1; s0 += kStage) {
+    for (int s0 = t0, w = 0; s0 < t1; s0 += kStage, ++w) {
         const int ns = min(kStage, t1 - s0);
         const int ng = (ns + kGroupTiles - 1) / kGroupTiles;
         const int g0 = s0 / kGroupTiles;
@@ -260,21 +259,46 @@ prune_tiles_kernel(int qtiles, int dtiles, int nchunk, int qpt, int window, floa
             sgn[e] = gn[g0 + e];
         }
         __syncthreads();
+        uint32_t word = 0;
         for (int h = 0; h < ng; ++h) {
             if (!active || sphere_drop(c, sgc[h], sgr[h], sgn[h], rq, nq, tq, beta)) continue;
             const int e1 = min(ns, (h + 1) * kGroupTiles);
             for (int e = h * kGroupTiles; e < e1; ++e) {
                 const int t = s0 + e;
                 if (t >= wlo && t < whi) continue;
-                if (!sphere_drop(c, sc[e], sr[e], sn[e], rq, nq, tq, beta)) {
-                    if (FILL && pos < cap) tiles[pos] = t;
-                    ++pos;
-                    ++kept;
-                }
+                if (!sphere_drop(c, sc[e], sr[e], sn[e], rq, nq, tq, beta)) word |= 1u << e;
             }
         }
+        if (active) {
+            wout[w] = word;
+            kept += __popc(word);
+        }
     }
-    if (!FILL && active) cnt[(int64_t)Q * nchunk + chunk] = kept;
+    if (active) cnt[(int64_t)Q * nchunk + chunk] = kept;
+}
+
+// The kept tiles of (Q, chunk), ascending, from its bit words to
+// tiles[off[Q * nchunk + chunk] ..] (entries past cap are dropped: the list
+// pass then falls back to the full scan outside the window).
+__global__ void __launch_bounds__(256)
+fill_tiles_kernel(int qtiles, int dtiles, int nchunk, const uint32_t *__restrict__ bits,
+                  const int64_t *__restrict__ off, int32_t *__restrict__ tiles, int64_t cap) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // Q * nchunk + chunk
+    if (e >= (int64_t)qtiles * nchunk) return;
+    const int chunk = (int)(e % nchunk);
+    const uint32_t *win = bits + e * kWords;
+    int64_t pos = off[e];
+    const int t0 = chunk * kChunkTiles;
+    const int nw = (int)ceil_div(min(dtiles - t0, kChunkTiles), kStage);
+    for (int w = 0; w < nw; ++w) {
+        uint32_t word = win[w];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            if (pos < cap) tiles[pos] = t0 + w * kStage + b;
+            ++pos;
+        }
+    }
 }
 
 // tile_off[Q] = off[Q * nchunk] (the query tile's first chunk), tile_off[qtiles] = total.
@@ -282,74 +306,6 @@ __global__ void tile_offsets_kernel(int qtiles, int nchunk, const int64_t *__res
                                     int64_t *__restrict__ tile_off) {
     const int Q = blockIdx.x * blockDim.x + threadIdx.x;
     if (Q <= qtiles) tile_off[Q] = off[(int64_t)Q * nchunk];
-}
-
-// Visiting order of one query tile's kept tiles: by the lower bound
-// |c_Q - c_t| - r_t of their rows' distance from the query tile's centre,
-// nearest first (ties by tile index).  The lists then meet their final
-// values early and most later tiles take the epilogue's fast path.  The kept
-// set, and so the keys that reach the lists, do not depend on the order.
-constexpr int kNearestWarps = 8;
-constexpr int kNearestMaxE = 16;   // lists of up to 32 * 16 tiles are sorted; longer ones stay ascending
-
-template <int E>
-__device__ __forceinline__ void sort_kept(const float *cq, const float *__restrict__ dcen,
-                                          const float *__restrict__ drad, int32_t *lst, int nl) {
-    const int lane = threadIdx.x & 31;
-    float key[E];
-    int id[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int v = e * 32 + lane;
-        key[e] = INFINITY;
-        id[e] = INT_MAX;
-        if (v < nl) {
-            const int t = lst[v];
-            const float4 *c4 = reinterpret_cast<const float4 *>(dcen + (int64_t)t * kCen);
-            const float4 *q4 = reinterpret_cast<const float4 *>(cq);
-            float a = 0.f;
-#pragma unroll
-            for (int u = 0; u < kCen / 4; ++u) {
-                const float4 x = c4[u], y = q4[u];
-                a = fmaf(x.x - y.x, x.x - y.x, a);
-                a = fmaf(x.y - y.y, x.y - y.y, a);
-                a = fmaf(x.z - y.z, x.z - y.z, a);
-                a = fmaf(x.w - y.w, x.w - y.w, a);
-            }
-            key[e] = sqrtf(a) - drad[t];
-            id[e] = t;
-        }
-    }
-    warp_sort_pairs<E>(key, id);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int v = e * 32 + lane;
-        if (v < nl) lst[v] = id[e];
-    }
-}
-
-// Warp per query tile; nothing to do when the kept-tile lists overflowed.
-__global__ void __launch_bounds__(kNearestWarps * 32)
-nearest_first_kernel(int qtiles, const float *__restrict__ qcen, const float *__restrict__ dcen,
-                     const float *__restrict__ drad, const int64_t *__restrict__ tile_off,
-                     const int32_t *__restrict__ overflow, int32_t *__restrict__ tiles) {
-    __shared__ __align__(16) float cq_s[kNearestWarps][kCen];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int Q = blockIdx.x * kNearestWarps + warp;
-    if (Q >= qtiles || *overflow) return;   // warp-uniform
-    float *cq = cq_s[warp];
-    cq[lane] = qcen[(int64_t)Q * kCen + lane];
-    cq[lane + 32] = qcen[(int64_t)Q * kCen + lane + 32];
-    __syncwarp();
-    const int64_t b = tile_off[Q];
-    const int nl = (int)(tile_off[Q + 1] - b);
-    int32_t *lst = tiles + b;
-    if (nl <= 1) return;
-    if (nl <= 32) sort_kept<1>(cq, dcen, drad, lst, nl);
-    else if (nl <= 64) sort_kept<2>(cq, dcen, drad, lst, nl);
-    else if (nl <= 128) sort_kept<4>(cq, dcen, drad, lst, nl);
-    else if (nl <= 256) sort_kept<8>(cq, dcen, drad, lst, nl);
-    else if (nl <= 32 * kNearestMaxE) sort_kept<kNearestMaxE>(cq, dcen, drad, lst, nl);
 }
 
 // Largest-first order of the list pass's items: query tiles by decreasing
@@ -551,6 +507,7 @@ PruneShape prune_shape(int64_t n, int BM, int BN) {
 struct PruneLayout {
     float *row_norm, *qcen, *qrad, *qn, *dcen, *drad, *dn, *gcen, *grad, *gn, *tau;
     int32_t *cnt;
+    uint32_t *bits;
     int64_t *off, *ssum;
     PruneOut out;
 };
@@ -572,6 +529,7 @@ PruneLayout prune_layout(void *scratch, int64_t n, const PruneShape &s, size_t *
     L.tau = cv.take<float>((size_t)s.qtiles);
     const size_t ncnt = (size_t)s.qtiles * s.nchunk;
     L.cnt = cv.take<int32_t>(ncnt);
+    L.bits = cv.take<uint32_t>(ncnt * kWords);
     L.off = cv.take<int64_t>(ncnt + 1);
     L.ssum = cv.take<int64_t>(seg_scan::kMaxSegs);
     L.out.tile_off = cv.take<int64_t>((size_t)s.qtiles + 1);
@@ -620,23 +578,17 @@ cudaError_t launch_prune_bounds(const void *Qb, int64_t n, int d, int metric, in
         dcen, drad, dn, s.dtiles, ngroups, PL.gcen, PL.grad, PL.gn);
     const dim3 grid((unsigned)ceil_div(s.qtiles, kBoundThreads), (unsigned)s.nchunk);
     const int qpt = BN / BM;
-    prune_tiles_kernel<false><<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen,
-                                                              qrad, qn, tau, dcen, drad, dn, PL.gcen, PL.grad, PL.gn,
-                                                              cnt, nullptr, nullptr,
-                                                              s.cap);
+    prune_tiles_kernel<<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen, qrad,
+                                                       qn, tau, dcen, drad, dn, PL.gcen, PL.grad, PL.gn, cnt, PL.bits);
     cudaError_t e = seg_scan::launch(cnt, (int64_t)ncnt, off, PL.ssum, st, s.cap, out->overflow);
     if (e != cudaSuccess) return e;
-    prune_tiles_kernel<true><<<grid, kBoundThreads, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, qpt, window, beta, qcen,
-                                                             qrad, qn, tau, dcen, drad, dn, PL.gcen, PL.grad, PL.gn,
-                                                             nullptr, off, out->tiles,
-                                                             s.cap);
+    fill_tiles_kernel<<<(unsigned)ceil_div((int64_t)ncnt, 256), 256, 0, st>>>(s.qtiles, s.dtiles, s.nchunk, PL.bits,
+                                                                             off, out->tiles, s.cap);
     tile_offsets_kernel<<<(unsigned)ceil_div(s.qtiles + 1, 256), 256, 0, st>>>(s.qtiles, s.nchunk, off,
                                                                                out->tile_off);
     int shift = 0;
     while ((s.dtiles >> shift) >= kOrderBins) ++shift;
     item_order_kernel<<<1, 1024, 0, st>>>(out->tile_off, s.qtiles, shift, out->order);
-    nearest_first_kernel<<<(unsigned)ceil_div(s.qtiles, kNearestWarps), kNearestWarps * 32, 0, st>>>(
-        s.qtiles, qcen, dcen, drad, out->tile_off, out->overflow, out->tiles);
     return cudaGetLastError();
 }
 

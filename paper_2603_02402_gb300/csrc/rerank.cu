@@ -82,22 +82,29 @@ rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int met
     }
 }
 
-// dst row i <- src row perm[i] (width floats); warp per row.
+// dst row i <- src row perm[i] (width floats, zero-padded to dst_stride, a
+// multiple of 4 with a 16-byte aligned dst); 16 lanes per row, a float4 store
+// per lane and step.
 __global__ void gather_rows_kernel(const float *__restrict__ src, int64_t src_stride, int64_t n, int width,
                                    const int32_t *__restrict__ perm, float *__restrict__ dst, int64_t dst_stride) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const int l = threadIdx.x & 15;
     if (i >= n) return;
     const float *s = src + (int64_t)perm[i] * src_stride;
-    float *o = dst + i * dst_stride;
-    for (int t = lane; t < dst_stride; t += 32) o[t] = t < width ? s[t] : 0.f;
+    float4 *o = reinterpret_cast<float4 *>(dst + i * dst_stride);
+    for (int f = l; 4 * f < dst_stride; f += 16) {
+        const int t = 4 * f;
+        o[f] = make_float4(t < width ? s[t] : 0.f, t + 1 < width ? s[t + 1] : 0.f, t + 2 < width ? s[t + 2] : 0.f,
+                           t + 3 < width ? s[t + 3] : 0.f);
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_gather_rows(const float *src, int64_t src_stride, int64_t n, int width, const int32_t *perm,
                                float *dst, int64_t dst_stride, cudaStream_t st) {
-    gather_rows_kernel<<<(unsigned)ceil_div(n * 32, 256), 256, 0, st>>>(src, src_stride, n, width, perm, dst,
+    if (dst_stride % 4 != 0 || reinterpret_cast<uintptr_t>(dst) % 16 != 0) return cudaErrorInvalidValue;
+    gather_rows_kernel<<<(unsigned)ceil_div(n * 16, 256), 256, 0, st>>>(src, src_stride, n, width, perm, dst,
                                                                       dst_stride);
     return cudaGetLastError();
 }

@@ -175,9 +175,8 @@ def test_locality_order_is_deterministic(rsc):
     (30000, 50, 15, 25, 64),
 ])
 def test_prune_equals_full_scan(rsc, n, d, k, comp, cands):
-    # the pruned scan's lists hold exactly the unpruned scan's keys (only the
-    # choice among equal keys may differ, which continuous data never shows),
-    # so the re-ranked output is bit-identical; both match the oracle
+    # the pruned scan keeps exactly the unpruned scan's candidates, so the
+    # re-ranked output is bit-identical; both match the oracle
     X = synth.mixture(n, d, n_comp=comp, seed=n + k)
     pi, pd = run_knn(rsc, X, k, precision="bf16", locality="on", prune="on", candidates=cands)
     fi, fd = run_knn(rsc, X, k, precision="bf16", locality="on", prune="off", candidates=cands)
@@ -210,13 +209,14 @@ def test_prune_cosine_zero_rows(rsc):
 
 
 def test_prune_integer_ties(rsc):
-    # many exact distance ties (integer points: BF16 keys are exact): the
-    # pruned and unpruned scans return the same distances, and both are exact
-    # kNN lists up to the choice among tied ids
+    # many exact distance ties (integer points: BF16 keys are exact): pruning
+    # must not change which tied ids survive, and both are exact kNN lists up
+    # to the choice among tied ids
     g = np.stack(np.meshgrid(np.arange(32), np.arange(32), np.arange(24)), -1).reshape(-1, 3)
     X = np.concatenate([g, g[:500]]).astype(np.float32)
     pi, pd = run_knn(rsc, X, 15, precision="bf16", locality="on", prune="on")
     fi, fd = run_knn(rsc, X, 15, precision="bf16", locality="on", prune="off")
+    np.testing.assert_array_equal(pi, fi)
     np.testing.assert_array_equal(pd, fd)
     q = synth.query_sample(len(X), 400, seed=4)
     oi, od, on = oracle.knn(X, 15, queries=q)
