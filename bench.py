@@ -303,14 +303,26 @@ def run_ours(args):
         "data": torch.empty(nnz, dtype=torch.float32).pin_memory(),
     }
 
+    # the kNN lists go back to the host on a second stream while the
+    # connectivities run
+    copy_stream = torch.cuda.Stream(device=dev)
+    knn_done = torch.cuda.Event()
+
     def e2e_step():
         Xd.copy_(X_pin, non_blocking=True)
-        step(precision, ws_knn)
-        out_host["idx"].copy_(idx, non_blocking=True)
-        out_host["dist"].copy_(dst, non_blocking=True)
+        rsc.rsc_knn(Xd, k, metric, precision, workspace=ws_knn, out=(idx, dst), locality=args.locality,
+                    prune=args.prune)
+        knn_done.record(stream)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(knn_done)
+            out_host["idx"].copy_(idx, non_blocking=True)
+            out_host["dist"].copy_(dst, non_blocking=True)
+        rsc.rsc_connectivities(idx, dst, nnz_capacity=cap, workspace=ws_conn,
+                               out=(indptr, indices, data, rho, sigma))
         out_host["indptr"].copy_(indptr, non_blocking=True)
         out_host["indices"].copy_(indices[:nnz], non_blocking=True)
         out_host["data"].copy_(data[:nnz], non_blocking=True)
+        stream.wait_stream(copy_stream)
 
     e2e_step()
     torch.cuda.synchronize(dev)

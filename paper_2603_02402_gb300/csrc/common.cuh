@@ -57,6 +57,11 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
     return r;
 }
 
+// Minimum of v[0 .. 8).
+__device__ __forceinline__ float min8(const float *v) {
+    return fmin3(fmin3(v[0], v[1], v[2]), fmin3(v[3], v[4], v[5]), fminf(v[6], v[7]));
+}
+
 template <int N>
 __device__ __forceinline__ float min_of(const float (&v)[N]) {
     static_assert(N == 16 || N == 32, "chunk of 16 or 32");

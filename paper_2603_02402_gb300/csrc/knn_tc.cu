@@ -125,6 +125,8 @@ prep_bf16_kernel(const float *__restrict__ Y, int64_t n, int d, int DP, int metr
 struct PlainWork {
     static constexpr int kShort = 0;   // never used (short_list is false)
     static constexpr bool kResume = false;
+    static constexpr bool kHitHeavy = false;
+    static constexpr bool kStartBelow = false;
     static constexpr bool kDynamic = false;
     int64_t n;
     int splits;

@@ -37,6 +37,11 @@ struct Cfg {
     static constexpr int kEpiThreads = EG * 128;
     static constexpr int kThreads = 64 + kEpiThreads;
     static constexpr int kCap = (EG == 4) ? 24 : 32;         // buffer entries per thread
+    // epilogue that keeps 64 accumulator columns in registers (no re-read on
+    // a hit): the shapes whose register budget holds them, for works whose
+    // tiles often improve some list (Work::kHitHeavy: the pruned passes; a
+    // full scan mostly rejects whole tiles and keeps one vote per tile)
+    static constexpr bool kResident = EG == 2 && KCP == 16;
     static constexpr int kQBytes = KB * QBLK;
     static constexpr int kStageBytes = KB * DBLK;
     static constexpr int kBufBytes = kCap * kEpiThreads * 8;
@@ -50,7 +55,10 @@ struct Cfg {
 // One work item: query rows [q0, q_end) (at most BM) against database rows
 // [j_begin, j_end).  short_list: only the best Work::kShort of each list are
 // needed (the threshold is the kShort-th key).  A Work with kResume starts
-// each (row, part) list from work.resume() instead of empty.
+// each (row, part) list from work.resume() instead of empty; one with
+// kStartBelow (empty lists, window items whose first tile is the query
+// tile's own neighbourhood) starts them below a bound taken from the first
+// tile.
 struct WorkItem {
     int64_t q0, q_end, j_begin, j_end;
     int tag;
@@ -369,48 +377,104 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 if (q < wi.q_end) work.template resume<EG>(wi, part, q, tk.list);
             }
             TileSeq<1> sq;
-            for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
+            bool first = Work::kStartBelow;   // the item's first tile, lists still empty
+            for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done();
+                 sq.next(), ++gt, first = false) {
                 const uint32_t b = gt & 1u;
                 ok = wait(&acc_full[b], (gt >> 1) & 1u);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc::tc_fence_after();
                 const uint32_t tb = tb0 + b * BN;
-                // fast path: minimum of this thread's kCols values, one vote per tile
-                float mn = INFINITY;
-#pragma unroll 1
-                for (int c0 = 0; c0 < C::kCols; c0 += 32) {
-                    float vv[32];
-                    __syncwarp();
-                    tc::tmem_ld32(tb + c0, vv);
-                    tc::tmem_wait_ld();
-                    mn = fminf(mn, min_of(vv));
-                }
                 const bool rag = sq.m == t_rag;
-                if (__any_sync(0xffffffffu, rag || mn < tk.bound())) {
-                    // some lane may improve its list (or the tile is partial): read
-                    // the accumulator again and offer every value
-                    const int j0 = jb + sq.m * BN + cbeg;
-                    const int valid = rag ? tail - cbeg : C::kCols;
+                const int j0 = jb + sq.m * BN + cbeg;
+                const int valid = rag ? tail - cbeg : C::kCols;
+                if (Work::kStartBelow && first && !rag) {
+                    // first tile of empty lists: the largest of the kCols / 8
+                    // minima of 8 columns bounds the KCP-th smallest value from
+                    // above (kCols / 8 >= KCP distinct values lie at or below
+                    // it), so the lists start from that bound instead of +inf
+                    // and never take the larger values in
+                    float gmax = -INFINITY;
 #pragma unroll 1
                     for (int c0 = 0; c0 < C::kCols; c0 += 32) {
                         float vv[32];
                         __syncwarp();
                         tc::tmem_ld32(tb + c0, vv);
                         tc::tmem_wait_ld();
-                        if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
+                        float g[4];
 #pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                if (c0 + i >= valid) vv[i] = INFINITY;
-                        }
-                        float lo[16], hi[16];
+                        for (int h = 0; h < 4; ++h) g[h] = min8(vv + 8 * h);
+                        gmax = fmaxf(gmax, fmaxf(fmaxf(g[0], g[1]), fmaxf(g[2], g[3])));
+                    }
+                    if constexpr (C::kCols / 8 >= KCP) tk.start_below(gmax);
+                }
+                if constexpr (C::kResident && Work::kHitHeavy) {
+                    // 64 columns at a time held in registers: minima of 8, one
+                    // vote on their minimum, offers straight from the registers
+#pragma unroll 1
+                    for (int c0 = 0; c0 < C::kCols; c0 += 64) {
+                        float va[32], vb[32];
+                        __syncwarp();
+                        tc::tmem_ld32(tb + c0, va);
+                        tc::tmem_ld32(tb + c0 + 32, vb);
+                        tc::tmem_wait_ld();
+                        if (valid < c0 + 64) {   // ragged end of the range (warp-uniform)
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            lo[i] = vv[i];
-                            hi[i] = vv[16 + i];
+                            for (int i = 0; i < 32; ++i) {
+                                if (c0 + i >= valid) va[i] = INFINITY;
+                                if (c0 + 32 + i >= valid) vb[i] = INFINITY;
+                            }
                         }
-                        tk.offer16(lo, j0 + c0);
-                        tk.offer16(hi, j0 + c0 + 16);
+                        float m8[8];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            m8[h] = min8(va + 8 * h);
+                            m8[4 + h] = min8(vb + 8 * h);
+                        }
+                        const float m64 = fminf(fmin3(fmin3(m8[0], m8[1], m8[2]), fmin3(m8[3], m8[4], m8[5]), m8[6]),
+                                                m8[7]);
+                        if (__any_sync(0xffffffffu, m64 < tk.bound())) {
+                            tk.offer16m(va, m8[0], m8[1], j0 + c0);
+                            tk.offer16m(va + 16, m8[2], m8[3], j0 + c0 + 16);
+                            tk.offer16m(vb, m8[4], m8[5], j0 + c0 + 32);
+                            tk.offer16m(vb + 16, m8[6], m8[7], j0 + c0 + 48);
+                        }
+                    }
+                } else {
+                    // fast path: minimum of this thread's kCols values, one vote per tile
+                    float mn = INFINITY;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < C::kCols; c0 += 32) {
+                        float vv[32];
+                        __syncwarp();
+                        tc::tmem_ld32(tb + c0, vv);
+                        tc::tmem_wait_ld();
+                        mn = fminf(mn, min_of(vv));
+                    }
+                    if (__any_sync(0xffffffffu, rag || mn < tk.bound())) {
+                        // some lane may improve its list (or the tile is partial):
+                        // read the accumulator again and offer every value
+#pragma unroll 1
+                        for (int c0 = 0; c0 < C::kCols; c0 += 32) {
+                            float vv[32];
+                            __syncwarp();
+                            tc::tmem_ld32(tb + c0, vv);
+                            tc::tmem_wait_ld();
+                            if (valid < c0 + 32) {   // ragged end of the range (warp-uniform)
+#pragma unroll
+                                for (int i = 0; i < 32; ++i)
+                                    if (c0 + i >= valid) vv[i] = INFINITY;
+                            }
+                            float lo[16], hi[16];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                lo[i] = vv[i];
+                                hi[i] = vv[16 + i];
+                            }
+                            tk.offer16(lo, j0 + c0);
+                            tk.offer16(hi, j0 + c0 + 16);
+                        }
                     }
                 }
                 // hand the accumulator part back to the MMA warp

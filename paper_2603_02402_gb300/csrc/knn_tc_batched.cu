@@ -28,6 +28,8 @@ namespace tck {
 struct BatchedWork {
     static constexpr int kShort = 4;   // ids kept per (query, sample, part) for cross lists
     static constexpr bool kResume = false;
+    static constexpr bool kHitHeavy = false;
+    static constexpr bool kStartBelow = false;
     static constexpr bool kDynamic = true;   // item cost follows its database sample's size
     int T;                             // query tiles
     int S;                             // samples
@@ -81,6 +83,8 @@ struct BatchedWork {
 struct BatchedWindowWork {
     static constexpr int kShort = kBatchedShort;
     static constexpr bool kResume = false;
+    static constexpr bool kHitHeavy = true;   // nearby tiles: most of them improve some list
+    static constexpr bool kStartBelow = true;     // first tile = the nearest of the sample
     static constexpr bool kDynamic = true;
     int T, S;
     const int64_t *tile_row, *tile_end;
@@ -146,6 +150,8 @@ struct BatchedWindowWork {
 struct BatchedListWork {
     static constexpr int kShort = kBatchedShort;
     static constexpr bool kResume = true;
+    static constexpr bool kHitHeavy = true;   // nearby tiles: most of them improve some list
+    static constexpr bool kStartBelow = false;
     static constexpr bool kDynamic = true;
     int T, S;
     const int64_t *tile_row, *tile_end;

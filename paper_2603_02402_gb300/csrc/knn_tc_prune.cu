@@ -23,6 +23,8 @@ namespace tck {
 struct WindowWork {
     static constexpr int kShort = 0;
     static constexpr bool kResume = false;
+    static constexpr bool kHitHeavy = true;   // nearby tiles: most of them improve some list
+    static constexpr bool kStartBelow = true;     // first tile = the query tile's own
     static constexpr bool kDynamic = false;   // every item scans the same few tiles
     int64_t n;
     int window;
@@ -68,6 +70,8 @@ struct WindowWork {
 struct ListWork {
     static constexpr int kShort = 0;
     static constexpr bool kResume = true;
+    static constexpr bool kHitHeavy = true;   // nearby tiles: most of them improve some list
+    static constexpr bool kStartBelow = false;
     static constexpr bool kDynamic = true;    // kept-tile counts differ widely between query tiles
     int64_t n;
     int window;

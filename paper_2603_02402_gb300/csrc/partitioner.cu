@@ -490,6 +490,8 @@ namespace tck {
 struct ProbeWork {
     static constexpr int kShort = 0;
     static constexpr bool kResume = false;
+    static constexpr bool kHitHeavy = false;
+    static constexpr bool kStartBelow = false;
     static constexpr bool kDynamic = true;   // segments differ in size
     int P;
     const int64_t *goff;

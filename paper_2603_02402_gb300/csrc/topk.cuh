@@ -92,6 +92,19 @@ struct BufferedTopK {
         cnt = 0;
     }
 
+    // Empty list that accepts only values <= m: every slot holds the next
+    // float above m (id -1).  Correct when at least KC values <= m will be
+    // offered before the list is read: they displace every such slot, and
+    // larger values could never have been among the KC smallest.
+    __device__ __forceinline__ void start_below(float m) {
+        const float s = nextafterf(m, INFINITY);
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+            list.key[c] = s;
+            list.id[c] = -1;
+        }
+    }
+
     __device__ __forceinline__ float bound() const {
         if constexpr (SHORT > 0 && SHORT < KC) return shortl ? list.key[SHORT - 1] : list.key[KC - 1];
         else return list.thr();
@@ -140,6 +153,19 @@ struct BufferedTopK {
                 put(cnt, v[i], j0 + i);
                 ++cnt;
             }
+        }
+    }
+
+    // Offer 16 values of columns j0 .. j0 + 15 whose two minima of 8 are
+    // known (warp-synchronous).
+    __device__ __forceinline__ void offer16m(const float *v, float m_lo, float m_hi, int j0) {
+        static_assert(CAP >= 16, "buffer smaller than a chunk");
+        const bool hit = fminf(m_lo, m_hi) < bound();
+        if (__any_sync(0xffffffffu, hit)) {
+            if (__any_sync(0xffffffffu, hit && cnt > CAP - 16)) flush();
+            const float t = bound();
+            if (m_lo < t) append<8>(v, j0, t);
+            if (m_hi < t) append<8>(v + 8, j0 + 8, t);
         }
     }
 
