@@ -52,20 +52,29 @@ assign_kernel(const float *__restrict__ Y, int64_t m, int64_t step, const float 
               const float *__restrict__ cnorm, int C, int32_t *__restrict__ lab) {
     __shared__ __align__(16) float cs[kCentTile][DP];
     __shared__ float cn[kCentTile];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < m;
-    float x[DP];
-    const float4 *xr = reinterpret_cast<const float4 *>(Y + (active ? i * step : 0) * DP);
+    // two keys per thread (keys i and i + half of the block's span), so every
+    // centroid read from shared memory serves both
+    const int64_t span = (int64_t)2 * kAssignThreads;
+    const int64_t i0 = (int64_t)blockIdx.x * span + threadIdx.x, i1 = i0 + kAssignThreads;
+    const bool a0 = i0 < m, a1 = i1 < m;
+    float x[DP], z[DP];
+    const float4 *xr = reinterpret_cast<const float4 *>(Y + (a0 ? i0 * step : 0) * DP);
+    const float4 *zr = reinterpret_cast<const float4 *>(Y + (a1 ? i1 * step : 0) * DP);
 #pragma unroll
     for (int t4 = 0; t4 < DP / 4; ++t4) {
-        const float4 v = active ? xr[t4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 v = a0 ? xr[t4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 w = a1 ? zr[t4] : make_float4(0.f, 0.f, 0.f, 0.f);
         x[4 * t4] = v.x;
         x[4 * t4 + 1] = v.y;
         x[4 * t4 + 2] = v.z;
         x[4 * t4 + 3] = v.w;
+        z[4 * t4] = w.x;
+        z[4 * t4 + 1] = w.y;
+        z[4 * t4 + 2] = w.z;
+        z[4 * t4 + 3] = w.w;
     }
-    float best = INFINITY;
-    int bi = 0;
+    float best0 = INFINITY, best1 = INFINITY;
+    int bi0 = 0, bi1 = 0;
     for (int c0 = 0; c0 < C; c0 += kCentTile) {
         const int nc = min(kCentTile, C - c0);
         __syncthreads();
@@ -74,30 +83,42 @@ assign_kernel(const float *__restrict__ Y, int64_t m, int64_t step, const float 
         __syncthreads();
         for (int c = 0; c < nc; ++c) {
             const float4 *cr = reinterpret_cast<const float4 *>(cs[c]);
-            float a0 = 0.f, a1 = 0.f;
+            float p0 = 0.f, p1 = 0.f, q0 = 0.f, q1 = 0.f;
 #pragma unroll
             for (int t4 = 0; t4 < DP / 4; t4 += 2) {
                 const float4 u = cr[t4];
-                a0 = fmaf(x[4 * t4], u.x, a0);
-                a0 = fmaf(x[4 * t4 + 1], u.y, a0);
-                a0 = fmaf(x[4 * t4 + 2], u.z, a0);
-                a0 = fmaf(x[4 * t4 + 3], u.w, a0);
                 const float4 w = cr[t4 + 1];   // DP is a multiple of 8
-                a1 = fmaf(x[4 * t4 + 4], w.x, a1);
-                a1 = fmaf(x[4 * t4 + 5], w.y, a1);
-                a1 = fmaf(x[4 * t4 + 6], w.z, a1);
-                a1 = fmaf(x[4 * t4 + 7], w.w, a1);
+                p0 = fmaf(x[4 * t4], u.x, p0);
+                p0 = fmaf(x[4 * t4 + 1], u.y, p0);
+                p0 = fmaf(x[4 * t4 + 2], u.z, p0);
+                p0 = fmaf(x[4 * t4 + 3], u.w, p0);
+                p1 = fmaf(x[4 * t4 + 4], w.x, p1);
+                p1 = fmaf(x[4 * t4 + 5], w.y, p1);
+                p1 = fmaf(x[4 * t4 + 6], w.z, p1);
+                p1 = fmaf(x[4 * t4 + 7], w.w, p1);
+                q0 = fmaf(z[4 * t4], u.x, q0);
+                q0 = fmaf(z[4 * t4 + 1], u.y, q0);
+                q0 = fmaf(z[4 * t4 + 2], u.z, q0);
+                q0 = fmaf(z[4 * t4 + 3], u.w, q0);
+                q1 = fmaf(z[4 * t4 + 4], w.x, q1);
+                q1 = fmaf(z[4 * t4 + 5], w.y, q1);
+                q1 = fmaf(z[4 * t4 + 6], w.z, q1);
+                q1 = fmaf(z[4 * t4 + 7], w.w, q1);
             }
-            const float s = fmaf(-2.f, a0 + a1, cn[c]);
-            if (s < best) {   // strict: the lower index wins ties
-                best = s;
-                bi = c0 + c;
+            const float s0 = fmaf(-2.f, p0 + p1, cn[c]), s1 = fmaf(-2.f, q0 + q1, cn[c]);
+            if (s0 < best0) {   // strict: the lower index wins ties
+                best0 = s0;
+                bi0 = c0 + c;
+            }
+            if (s1 < best1) {
+                best1 = s1;
+                bi1 = c0 + c;
             }
         }
     }
-    if (active) lab[i] = bi;
+    if (a0) lab[i0] = bi0;
+    if (a1) lab[i1] = bi1;
 }
-
 // Centroid c <- row (c * n) / C; its squared norm alongside.
 __global__ void init_centroids_kernel(const float *__restrict__ Y, int64_t n, int DP, int C, float *__restrict__ cent,
                                       float *__restrict__ cnorm) {
@@ -381,7 +402,7 @@ cudaError_t launch_assign_sub(const float *Y, int DP, int64_t m, int64_t step, c
 
 cudaError_t launch_assign(const float *Y, int DP, int64_t m, int64_t step, const float *cent, const float *cnorm,
                           int C, int32_t *lab, cudaStream_t st) {
-    const unsigned blocks = (unsigned)ceil_div(m, kAssignThreads);
+    const unsigned blocks = (unsigned)ceil_div(m, 2 * kAssignThreads);   // two keys per thread
 #define RSC_ASSIGN(dp) \
     case dp: assign_kernel<dp><<<blocks, kAssignThreads, 0, st>>>(Y, m, step, cent, cnorm, C, lab); break
     switch (DP) {

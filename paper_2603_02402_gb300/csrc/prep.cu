@@ -17,10 +17,12 @@ namespace {
 
 constexpr int kRowsPerWarp = 32;
 constexpr int kWarps = 4;
-constexpr int kColBlocks = 256;
+constexpr int kColBlocks = 1024;
+constexpr int kColAhead = 4;   // rows a thread loads before adding them, in order
 
 // Column sums, deterministic: block b owns a fixed row range; thread (g, c)
-// adds column c of rows g, g + 4, ... with Kahan compensation.
+// adds column c of rows g, g + 4, ... with Kahan compensation (kColAhead
+// rows loaded at a time, added in row order).
 __global__ void __launch_bounds__(256)
 colsum_partials_kernel(const float *__restrict__ X, int64_t n, int d, float *__restrict__ part) {
     __shared__ float red[4][64];
@@ -29,11 +31,19 @@ colsum_partials_kernel(const float *__restrict__ X, int64_t n, int d, float *__r
     const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
     float s = 0.f, comp = 0.f;
     if (c < d) {
-        for (int64_t r = r0 + g; r < r1; r += 4) {
-            const float y = X[r * d + c] - comp;
-            const float t = s + y;
-            comp = (t - s) - y;
-            s = t;
+        for (int64_t r = r0 + g; r < r1; r += 4 * kColAhead) {
+            float v[kColAhead];
+#pragma unroll
+            for (int u = 0; u < kColAhead; ++u) v[u] = r + 4 * u < r1 ? X[(r + 4 * u) * d + c] : 0.f;
+#pragma unroll
+            for (int u = 0; u < kColAhead; ++u) {
+                if (r + 4 * u < r1) {
+                    const float y = v[u] - comp;
+                    const float t = s + y;
+                    comp = (t - s) - y;
+                    s = t;
+                }
+            }
         }
     }
     red[g][c] = s - comp;
@@ -70,7 +80,19 @@ prep_fp32_kernel(const float *__restrict__ X, int64_t n, int d, int DP, int metr
     const int rows = (n - row0 < kRowsPerWarp) ? (int)(n - row0) : kRowsPerWarp;
 
     const float *src = X + row0 * d;
-    for (int e = lane; e < rows * d; e += 32) s[(e / d) * ld + (e % d)] = src[e];
+    if ((rows * d) % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) {   // 16-byte loads
+        const float4 *src4 = reinterpret_cast<const float4 *>(src);
+        for (int f = lane; f < rows * d / 4; f += 32) {
+            const float4 v = src4[f];
+            const int e = 4 * f;
+            s[(e / d) * ld + (e % d)] = v.x;
+            s[((e + 1) / d) * ld + ((e + 1) % d)] = v.y;
+            s[((e + 2) / d) * ld + ((e + 2) % d)] = v.z;
+            s[((e + 3) / d) * ld + ((e + 3) % d)] = v.w;
+        }
+    } else {
+        for (int e = lane; e < rows * d; e += 32) s[(e / d) * ld + (e % d)] = src[e];
+    }
     __syncwarp();
 
     if (lane < rows) {
@@ -97,8 +119,12 @@ prep_fp32_kernel(const float *__restrict__ X, int64_t n, int d, int DP, int metr
     }
     __syncwarp();
 
-    float *dst = Y + row0 * DP;
-    for (int e = lane; e < rows * DP; e += 32) dst[e] = s[(e / DP) * ld + (e % DP)];
+    float *dst = Y + row0 * DP;   // DP is a multiple of 8: 16-byte stores
+    float4 *dst4 = reinterpret_cast<float4 *>(dst);
+    for (int f = lane; f < rows * DP / 4; f += 32) {
+        const int e = 4 * f, r = e / DP, t = e % DP;
+        dst4[f] = make_float4(s[r * ld + t], s[r * ld + t + 1], s[r * ld + t + 2], s[r * ld + t + 3]);
+    }
 }
 
 }  // namespace
