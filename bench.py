@@ -33,9 +33,15 @@ METRIC = "neighbors graph cells/s (50 PCs, k=15): BF16+rerank vs FP32 at recall@
 WORKLOAD = ("1,000,000 cells x 50 PCs fp32, 100-cluster Gaussian mixture (means ~N(0,4I), "
             "PC variance 1/t), euclidean, k=15")
 
-# DRAM traffic per launch of the candidate-search kernel from an ncu capture
-# (profiles/), valid only while the kernel source is unchanged.
-TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one search
+# phase, from an ncu capture summarised under profiles/; valid only while the
+# sources it was measured on are unchanged (their hash is checked).
+SEARCH_SOURCES = ("knn_tc.cuh", "knn_tc_prune.cu", "prune.cu", "topk.cuh", "tc_ptx.cuh")
+TRAFFIC = {
+    # window pass + list pass of the 1,000,000-cell graph (profiles/knn_tc_pruned_passes_bf16_1m.md):
+    # 256.2 + 207.3 MB and 1511.5 + 117.7 MB, cold-cache under ncu; the bound kernels are not included
+    ("knn_tc.cuh", "pruned"): {"bytes_per_launch": 2_092_700_000, "kernel_sha": "ec7747c4e1a29e56"},
+}
 
 ORDER_MIN_ROWS = 16384   # automatic locality ordering from this many rows (BF16 path)
 
@@ -84,9 +90,14 @@ def parse():
     return p.parse_args()
 
 
-def _kernel_sha(name):
-    src = os.path.join(ROOT, "paper_2603_02402_gb300", "csrc", name)
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+def _kernel_sha(names):
+    h = hashlib.sha256()
+    for name in names:
+        src = os.path.join(ROOT, "paper_2603_02402_gb300", "csrc", name)
+        if not os.path.exists(src):
+            return None
+        h.update(open(src, "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -366,14 +377,14 @@ def run_ours(args):
     if precision == "bf16":
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         bound, src = "tensor", "bf16_tflops_sustained of measured" if peaks else "fallback 1.7 PFLOP/s"
-        kname = "knn_tc.cu"
+        kname = "knn_tc.cuh"
     else:
         smc = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
         peak = 152 * 128 * 2 * smc * 1e6 / 1e12       # FP32 FFMA lanes x 2 flops x max SM clock
         bound, src = "alu", f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {smc:.0f} MHz"
         kname = "knn_simt.cuh"
-    tr = TRAFFIC.get(kname)
-    traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_sha") == _kernel_sha(kname) else None
+    tr = TRAFFIC.get((kname, "pruned" if scanned < pairs_total else "full"))
+    traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_sha") == _kernel_sha(SEARCH_SOURCES) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname, "peak_source": src,
                 "algorithmic": "2*d flops per (query, row) pair computed: n^2 for the full scan, "

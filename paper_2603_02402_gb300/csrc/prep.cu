@@ -17,7 +17,7 @@ namespace {
 
 constexpr int kRowsPerWarp = 32;
 constexpr int kWarps = 4;
-constexpr int kColBlocks = 1024;
+constexpr int kColBlocks = 256;
 constexpr int kColAhead = 4;   // rows a thread loads before adding them, in order
 
 // Column sums, deterministic: block b owns a fixed row range; thread (g, c)
