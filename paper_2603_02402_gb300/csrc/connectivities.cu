@@ -141,6 +141,7 @@ smooth_warp_kernel(const int32_t *__restrict__ idx, const float *__restrict__ di
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         const float psum = s;   // identical on every lane (commutative butterfly)
         if (fabsf(psum - target) < kTol) break;
+        const float prev = mid;
         if (psum > target) {
             hi = mid;
             mid = (lo + hi) * 0.5f;
@@ -148,6 +149,9 @@ smooth_warp_kernel(const int32_t *__restrict__ idx, const float *__restrict__ di
             lo = mid;
             mid = isinf(hi) ? mid * 2.f : (lo + hi) * 0.5f;
         }
+        // a repeated midpoint is a fixed point (same sum, same branch, same
+        // bounds): the remaining steps would not move it
+        if (mid == prev) break;
     }
     float rs = 0.f;
 #pragma unroll
@@ -352,6 +356,7 @@ smooth_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dis
         }
         const float psum = s + comp;
         if (fabsf(psum - target) < kTol) break;
+        const float prev = mid;
         if (psum > target) {
             hi = mid;
             mid = (lo + hi) * 0.5f;
@@ -359,6 +364,9 @@ smooth_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dis
             lo = mid;
             mid = isinf(hi) ? mid * 2.f : (lo + hi) * 0.5f;
         }
+        // a repeated midpoint is a fixed point (same sum, same branch, same
+        // bounds): the remaining steps would not move it
+        if (mid == prev) break;
     }
     float row_sum = 0.f;
 #pragma unroll
