@@ -18,31 +18,36 @@ namespace {
 constexpr int kRowsPerWarp = 32;
 constexpr int kWarps = 4;
 constexpr int kColBlocks = 256;
-constexpr int kColAhead = 4;   // rows a thread loads before adding them, in order
+constexpr int kColTile = 64;   // rows staged in shared memory at a time
 
-// Column sums, deterministic: block b owns a fixed row range; thread (g, c)
-// adds column c of rows g, g + 4, ... with Kahan compensation (kColAhead
-// rows loaded at a time, added in row order).
+// Column sums, deterministic: block b owns a fixed row range (a multiple of 4
+// rows long, so every tile of a 16-byte aligned X starts on a 16-byte
+// boundary); tiles of kColTile rows are staged in shared memory (16-byte
+// loads when X is aligned), and thread (g, c) adds column c of rows g, g + 4,
+// ... in order with Kahan compensation.
 __global__ void __launch_bounds__(256)
 colsum_partials_kernel(const float *__restrict__ X, int64_t n, int d, float *__restrict__ part) {
     __shared__ float red[4][64];
+    __shared__ __align__(16) float tile[kColTile * 64];
     const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
-    const int64_t chunk = ceil_div(n, gridDim.x);
-    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+    const int64_t chunk = ceil_div(ceil_div(n, gridDim.x), 4) * 4;
+    const int64_t r0 = min(n, (int64_t)blockIdx.x * chunk), r1 = min(n, r0 + chunk);
     float s = 0.f, comp = 0.f;
-    if (c < d) {
-        for (int64_t r = r0 + g; r < r1; r += 4 * kColAhead) {
-            float v[kColAhead];
-#pragma unroll
-            for (int u = 0; u < kColAhead; ++u) v[u] = r + 4 * u < r1 ? X[(r + 4 * u) * d + c] : 0.f;
-#pragma unroll
-            for (int u = 0; u < kColAhead; ++u) {
-                if (r + 4 * u < r1) {
-                    const float y = v[u] - comp;
-                    const float t = s + y;
-                    comp = (t - s) - y;
-                    s = t;
-                }
+    for (int64_t t0 = r0; t0 < r1; t0 += kColTile) {
+        const int rows = (int)min((int64_t)kColTile, r1 - t0);
+        const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0;   // caller's rows on 16 bytes
+        const int total = rows * d, total4 = vec ? total / 4 : 0;
+        const float4 *src4 = reinterpret_cast<const float4 *>(X + t0 * d);
+        __syncthreads();
+        for (int f = threadIdx.x; f < total4; f += blockDim.x) reinterpret_cast<float4 *>(tile)[f] = src4[f];
+        for (int e = 4 * total4 + threadIdx.x; e < total; e += blockDim.x) tile[e] = X[t0 * d + e];
+        __syncthreads();
+        if (c < d) {
+            for (int r = g; r < rows; r += 4) {
+                const float y = tile[r * d + c] - comp;
+                const float t = s + y;
+                comp = (t - s) - y;
+                s = t;
             }
         }
     }

@@ -246,3 +246,20 @@ def test_scan_stats(rsc):
             assert scanned == total
         else:
             assert 0 < scanned < total   # 40 separated clusters: most tile pairs are provably useless
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_input_rows_off_16_byte_boundary(rsc, precision):
+    # X as a view one row into a larger buffer (d = 50: rows start 8 bytes off
+    # a 16-byte boundary): the prep's vector loads must fall back, results equal
+    # those of an aligned copy
+    n, d, k = 20000, 50, 15
+    X = synth.mixture(n + 1, d, n_comp=20, seed=31)
+    base = torch.from_numpy(X).cuda()
+    Xv = base[1:]
+    assert Xv.data_ptr() % 16 != 0
+    ws = torch.empty(rsc.rsc_knn_workspace_size(n, d, k, "euclidean", precision), dtype=torch.uint8, device="cuda")
+    gi, gd = [t.cpu().numpy() for t in rsc.rsc_knn(Xv, k, "euclidean", precision, workspace=ws)]
+    ai, ad = run_knn(rsc, X[1:], k, precision=precision)
+    np.testing.assert_array_equal(gi, ai)
+    np.testing.assert_array_equal(gd, ad)
