@@ -35,10 +35,6 @@ constexpr int kBoundThreads = 128; // query tiles per block in the bound passes
 constexpr int kStage = 32;         // database tiles staged in shared memory at once
 constexpr int kGroupTiles = 16;    // database tiles per group sphere (tested before its tiles)
 
-__device__ __forceinline__ float bf(const uint16_t *p) {
-    return __uint_as_float((uint32_t)(*p) << 16);
-}
-
 // Warp per group of rows of the BF16 query operand (row stride W elements,
 // v = the first dv <= 64 of them): rows [g * R, (g + 1) * R) clipped to n, or
 // [g_start[g], g_end[g]) when given.  Centre (mean of v), radius (max |v - c|,
