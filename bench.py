@@ -516,12 +516,16 @@ def run_batched(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic", "config": {"workload": BATCHED_WORKLOAD, "n": n, "samples": 64,
                                             "sizes_min_max": [int(sizes.min()), int(sizes.max())]},
+            # the search is pruned, so 2*d flops per (query, row) pair of the whole problem over the
+            # call is a brute-force-equivalent rate, not a utilisation of the tensor pipe: no frac
             "roofline": {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops / (ms / 1e3) / 1e12 / peak, "traffic": None, "kernel": "knn_tc_kernel (batched)",
-                         "note": "whole call (prep + search + both re-ranks) timed; 2*d flops per (query, row) pair"},
-            # prep 3, ordering 32 + 4 (sample-preserving partition), BF16 operands 1, pruned search 9
-            # (2 sphere passes, nearest tiles, window pass, tau, count, scan, fill, list pass), gather +
-            # within re-rank + cross re-rank 3; 7 without the ordering (fewer than ORDER_MIN_ROWS rows)
+                         "frac": None, "traffic": None, "kernel": "knn_tc_kernel (batched)",
+                         "note": "whole call (prep + pruned search + both re-ranks) timed; achieved = 2*d flops per "
+                                 "(query, row) pair of the unpruned problem / call time (brute-force-equivalent)"},
+            # prep 3, ordering 36 + 2 chains + 5 (sample-preserving partition), BF16 operands 1,
+            # pruned search 10 (2 sphere passes, nearest tiles, window pass, tau, count, scan (2),
+            # fill, list pass), gather + within re-rank + cross re-rank 3; 7 without the ordering
+            # (fewer than ORDER_MIN_ROWS rows)
             "gpu_launches": (60 if n >= ORDER_MIN_ROWS else 7) * args.steps, "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
