@@ -441,6 +441,32 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                             tk.offer16m(vb + 16, m8[6], m8[7], j0 + c0 + 48);
                         }
                     }
+                } else if constexpr (KCP >= 64) {
+                    // long lists leave little register room: 16 columns per load
+                    float mn = INFINITY;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < C::kCols; c0 += 16) {
+                        float vv[16];
+                        __syncwarp();
+                        tc::tmem_ld16(tb + c0, vv);
+                        tc::tmem_wait_ld();
+                        mn = fminf(mn, min_of(vv));
+                    }
+                    if (__any_sync(0xffffffffu, rag || mn < tk.bound())) {
+#pragma unroll 1
+                        for (int c0 = 0; c0 < C::kCols; c0 += 16) {
+                            float vv[16];
+                            __syncwarp();
+                            tc::tmem_ld16(tb + c0, vv);
+                            tc::tmem_wait_ld();
+                            if (valid < c0 + 16) {   // ragged end of the range (warp-uniform)
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    if (c0 + i >= valid) vv[i] = INFINITY;
+                            }
+                            tk.offer16(vv, j0 + c0);
+                        }
+                    }
                 } else {
                     // fast path: minimum of this thread's kCols values, one vote per tile
                     float mn = INFINITY;
