@@ -27,9 +27,11 @@
 //               pipe, limit smaller shapes) into one of two 256-column TMEM
 //               accumulators (2 x 256 = 512 columns)
 //   epilogue    EG warpgroups, each owning 256 / EG columns of every tile; a
-//               thread owns one query row's part: tcgen05.ld 32 columns at a
-//               time, 3-input min tree per 16 values, threshold test against
-//               its register top-k, rare appends to a shared-memory buffer.
+//               thread owns one query row's part: tcgen05.ld of 32 columns at
+//               a time (64 held in registers in the pruned passes of the
+//               two-part shape, 16 for 64-entry lists), 3-input min trees,
+//               one warp vote, threshold tests against its register top-k,
+//               appends to a shared-memory buffer merged into the lists.
 //               The row's EG per-part lists together form its candidates.
 // Every wait is bounded; on timeout the CTA records RSC_ERR_TIMEOUT, drains
 // its in-flight copies and MMAs, frees TMEM and exits.
