@@ -538,7 +538,7 @@ PARTITION_WORKLOAD = ("Learned partitioner: 5,000,000 cells x 50 PCs fp32, 200-c
 
 def run_partitioner(args):
     """Partitioned kNN graph of every cell (probe 8 of 1024 parts) + connectivities,
-    against the exact BF16 path on the same GPU as the judge of recall."""
+    against the exact BF16 path on the same GPU as the reference for recall."""
     import numpy as np
     import torch
     from paper_2603_02402_gb300 import rsc, synth
@@ -559,7 +559,7 @@ def run_partitioner(args):
     ev[1].record()
     torch.cuda.synchronize()
     train_ms = ev[0].elapsed_time(ev[1])
-    # exact BF16 path (the judge)
+    # exact BF16 path (the reference for recall)
     ws_exact = torch.empty(rsc.rsc_knn_workspace_size(n, 50, k, "euclidean", "bf16"), dtype=torch.uint8, device=dev)
     ev[2].record()
     ei, ed = rsc.rsc_knn(Xd, k, precision="bf16", workspace=ws_exact)

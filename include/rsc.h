@@ -47,7 +47,7 @@ typedef enum {
     RSC_ERR_CUDA = 2,          /* a CUDA runtime/driver call failed             */
     RSC_ERR_WORKSPACE = 3,     /* workspace missing or smaller than required    */
     RSC_ERR_TIMEOUT = 4,       /* an in-kernel wait exceeded its budget         */
-    RSC_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement   */
+    RSC_ERR_UNSUPPORTED = 5,   /* valid request this library does not implement */
     RSC_ERR_CAPACITY = 6       /* CSR output capacity smaller than nnz          */
 } rsc_status;
 
