@@ -151,7 +151,6 @@ struct BatchedPruneOut {
     int32_t *win;        // [S * T]
     int64_t *tile_off;   // [S * T + 1]
     int32_t *tiles;      // [cap]
-    int32_t *order;      // [qtiles]: query tiles by decreasing kept-tile count (list pass item order)
     int32_t *overflow;   // [1]
 };
 size_t batched_prune_scratch_bytes(int64_t N, int64_t T, int S, int64_t DT);
