@@ -230,6 +230,21 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
                            size_t workspace_bytes);
 
 /*
+ * Work done by the last rsc_knn_batched on `workspace` with these same
+ * arguments (a diagnostic; the paper has no counterpart).  Counts pairs of a
+ * 128-row query tile and a 256-row database tile of one sample:
+ * *pairs_total (host) = query tiles x all samples' database tiles,
+ * *pairs_scanned (host) = the pairs whose distances were computed (= total
+ * without pruning).  Reads the workspace after synchronising opts->stream.
+ * Errors: RSC_ERR_INVALID_ARG for NULL outputs or arguments rsc_knn_batched
+ * would reject; RSC_ERR_WORKSPACE when the workspace is missing or too small.
+ */
+rsc_status rsc_knn_batched_scan_stats(int64_t n, int32_t d, const int64_t *sample_offsets, int32_t n_samples,
+                                      int32_t k_within, int32_t k_cross, int32_t metric,
+                                      const rsc_knn_opts *opts, void *workspace, size_t workspace_bytes,
+                                      int64_t *pairs_scanned, int64_t *pairs_total);
+
+/*
  * Learned partitioner (candidate pruning for the exact search).
  *
  * A handle owns a small network d -> hidden -> hidden -> n_parts (ReLU; FP32

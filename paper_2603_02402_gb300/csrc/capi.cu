@@ -609,6 +609,46 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
     return RSC_OK;
 }
 
+rsc_status rsc_knn_batched_scan_stats(int64_t n, int32_t d, const int64_t *sample_offsets, int32_t n_samples,
+                                      int32_t k_within, int32_t k_cross, int32_t metric,
+                                      const rsc_knn_opts *opts, void *workspace, size_t workspace_bytes,
+                                      int64_t *pairs_scanned, int64_t *pairs_total) {
+    if (!pairs_scanned || !pairs_total) return fail(RSC_ERR_INVALID_ARG, "NULL output");
+    BatchedPlan p;
+    rsc_status s = plan_batched(n, d, sample_offsets, n_samples, k_within, k_cross, metric, opts, &p);
+    if (s != RSC_OK) return s;
+    size_t need = 0;
+    carve_batched(nullptr, p, &need);
+    if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
+    *pairs_total = p.T * p.DT;   // every query tile against every sample's database tiles
+    *pairs_scanned = *pairs_total;
+    if (!p.prune) return RSC_OK;
+    BatchedLayout L = carve_batched(workspace, p, nullptr);
+    const BatchedPruneOut po = batched_prune_outputs(L.prune_scratch, n, p.T, p.S, p.DT);
+    cudaStream_t st = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+    const int64_t items = p.T * p.S;
+    int64_t kept = 0;
+    int32_t overflow = 0;
+    std::vector<int32_t> win((size_t)items);
+    RSC_CUDA_TRY(cudaMemcpyAsync(&kept, po.tile_off + items, sizeof(kept), cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaMemcpyAsync(&overflow, po.overflow, sizeof(overflow), cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaMemcpyAsync(win.data(), po.win, sizeof(int32_t) * (size_t)items, cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (overflow) return RSC_OK;   // the list pass scanned every tile
+    // window tiles of item t * T + qt: sample t's tiles around win[item], +- kOrderWindow
+    const int BN = knn_tc_bn();
+    int64_t window = 0;
+    for (int t = 0; t < n_samples; ++t) {
+        const int64_t Tt = ceil_div(sample_offsets[t + 1] - sample_offsets[t], BN);
+        for (int64_t qt = 0; qt < p.T; ++qt) {
+            const int64_t w = win[(size_t)(t * p.T + qt)];
+            window += std::min<int64_t>(Tt, w + kOrderWindow + 1) - std::max<int64_t>(0, w - kOrderWindow);
+        }
+    }
+    *pairs_scanned = window + kept;
+    return RSC_OK;
+}
+
 int64_t rsc_connectivities_max_nnz(int64_t n, int32_t k) {
     if (n < 1 || k < 1) return 0;
     return 2 * n * (int64_t)(k - 1);

@@ -57,6 +57,8 @@ SIGNATURES = {
                                                ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(_sz)]),
     "rsc_knn_batched": (_i32, [_vp, _i64, _i32, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(rsc_knn_opts), _vp, _sz]),
+    "rsc_knn_batched_scan_stats": (_i32, [_i64, _i32, _vp, _i32, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts),
+                                           _vp, _sz, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "rsc_connectivities_workspace_size": (_i32, [_i64, _i32, ctypes.POINTER(_sz)]),
     "rsc_connectivities_max_nnz": (_i64, [_i64, _i32]),
     "rsc_connectivities": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
@@ -241,6 +243,18 @@ def rsc_knn_batched(X: torch.Tensor, sample_offsets, k_within: int, k_cross: int
     _check(lib().rsc_knn_batched(_ptr(X), n, d, optr, S, k_within, k_cross, m, _ptr(iw), _ptr(dw), _ptr(ix),
                                  _ptr(dx), ctypes.byref(o), _ptr(ws), ws.numel()))
     return iw, dw, ix, dx
+
+
+def rsc_knn_batched_scan_stats(n, d, sample_offsets, k_within, k_cross, workspace, metric="euclidean",
+                               precision="bf16", stream=None, locality="auto", prune="auto"):
+    """(pairs scanned, pairs total) of the last rsc_knn_batched on `workspace` with these arguments."""
+    off, optr = _offsets_host(sample_offsets)
+    o = knn_opts(precision, 0, 0, stream, locality=locality, prune=prune)
+    a, b = _i64(0), _i64(0)
+    _check(lib().rsc_knn_batched_scan_stats(n, d, optr, len(off) - 1, k_within, k_cross,
+                                            _METRICS.get(metric, metric), ctypes.byref(o), _ptr(workspace),
+                                            workspace.numel(), ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
 
 
 def rsc_connectivities_workspace_size(n: int, k: int) -> int:

@@ -138,3 +138,24 @@ def test_batched_ordered_and_pruned(rsc, metric, prune):
     assert _recall(gxi, gxd, xi, xd) >= 0.999
     np.testing.assert_allclose(np.sort(gd, axis=1)[:, 0], wd[:, 0], rtol=1e-5, atol=1e-6)
     assert (np.diff(gxd, axis=1) >= 0).all()
+
+
+def test_batched_scan_stats(rsc):
+    # (128-row query tile, 256-row database tile) pairs of one sample the last
+    # call computed: all of them without pruning, fewer with it
+    sizes = [9000, 14000, 2500, 8000, 700]
+    X, off = synth.batched(sizes, d=50, n_comp=12, seed=21)
+    n = len(X)
+    Xd = torch.from_numpy(X).cuda()
+    T = sum(-(-s // 128) for s in sizes)
+    DT = sum(-(-s // 256) for s in sizes)
+    for prune in ("off", "on"):
+        ws = torch.empty(rsc.rsc_knn_batched_workspace_size(n, 50, off, 15, 3, locality="on", prune=prune),
+                         dtype=torch.uint8, device="cuda")
+        rsc.rsc_knn_batched(Xd, off, 15, 3, workspace=ws, locality="on", prune=prune)
+        scanned, total = rsc.rsc_knn_batched_scan_stats(n, 50, off, 15, 3, ws, locality="on", prune=prune)
+        assert total == T * DT
+        if prune == "off":
+            assert scanned == total
+        else:
+            assert 0 < scanned < total
