@@ -36,7 +36,7 @@ struct Cfg {
     static constexpr int kCols = BN / EG;
     static constexpr int kEpiThreads = EG * 128;
     static constexpr int kThreads = 64 + kEpiThreads;
-    static constexpr int kCap = (EG == 4) ? 24 : 32;         // buffer entries per thread
+    static constexpr int kCap = 24;                                  // buffer entries per thread
     // epilogue that keeps 64 accumulator columns in registers (no re-read on
     // a hit): the shapes whose register budget holds them, for works whose
     // tiles often improve some list (Work::kHitHeavy: the pruned passes; a
