@@ -39,8 +39,8 @@ WORKLOAD = ("1,000,000 cells x 50 PCs fp32, 100-cluster Gaussian mixture (means 
 SEARCH_SOURCES = ("knn_tc.cuh", "knn_tc_prune.cu", "prune.cu", "topk.cuh", "tc_ptx.cuh")
 TRAFFIC = {
     # window pass + list pass of the 1,000,000-cell graph (profiles/knn_tc_pruned_passes_bf16_1m.md):
-    # 256.2 + 207.3 MB and 1511.5 + 117.7 MB, cold-cache under ncu; the bound kernels are not included
-    ("knn_tc.cuh", "pruned"): {"bytes_per_launch": 2_092_700_000, "kernel_sha": "0c66d6916fb88c79"},
+    # 256.1 + 207.1 MB and 1350.3 + 114.3 MB, cold-cache under ncu; the bound kernels are not included
+    ("knn_tc.cuh", "pruned"): {"bytes_per_launch": 1_927_800_000, "kernel_sha": "92e9011f458d5739"},
 }
 
 ORDER_MIN_ROWS = 16384   # automatic locality ordering from this many rows (BF16 path)
