@@ -202,31 +202,34 @@ rsc_status check_ws(void *ws, size_t have, size_t need) {
 struct ConnLayout {
     ConnWork w;
     int64_t *indptr_tmp;
-    int32_t *zeroed;       // in_cnt, cursor, long_count, mid_count (2n + 2 int32)
+    int32_t *zeroed;       // in_cnt, cursor, extra, rho0_count, mid_count, long_count (3n + 3 int32)
 };
 
 ConnLayout carve_conn(void *ws, int64_t n, int k, size_t *bytes) {
+    const ConnShape s = conn_shape(k);
     Carve cv(ws);
     ConnLayout L;
     L.w.status = cv.take<unsigned int>(kStatusBytes / sizeof(unsigned int));
-    L.w.partials = cv.take<float>(kMeanBlocks);
-    L.w.mean_all = cv.take<float>(1);
-    L.w.rho = cv.take<float>((size_t)n);
-    L.w.sigma = cv.take<float>((size_t)n);
-    const size_t KP = (size_t)conn_stride(k);
-    L.w.scol = cv.take<int32_t>((size_t)n * KP);
-    L.w.sw = cv.take<float>((size_t)n * KP);
-    L.w.gv = cv.take<float>((size_t)n * KP);
-    L.w.tslot = cv.take<int32_t>(k <= 32 ? (size_t)n * KP : 1);
+    L.w.rs = cv.take<float2>((size_t)n);
+    L.w.part_sum = cv.take<float>(conn_sum_blocks(n, k));
+    L.w.rho0_rows = cv.take<int32_t>((size_t)n);
+    L.w.ocol = cv.take<int32_t>((size_t)n * s.KP);
+    L.w.og = cv.take<float>((size_t)n * s.KP);
     L.w.own_cnt = cv.take<int32_t>((size_t)n);
-    L.zeroed = cv.take<int32_t>((size_t)2 * n + 2);
+    L.w.bucket = cv.take<int2>((size_t)n * s.B);
+    L.w.ovf = cv.take<uint32_t>((size_t)n * s.MW);
+    L.w.in_kept = cv.take<int32_t>((size_t)n);
+    L.w.local = cv.take<int64_t>((size_t)n);
+    L.w.scan_part = cv.take<int64_t>(conn_scan_blocks(n));
+    L.zeroed = cv.take<int32_t>((size_t)3 * n + 3);
     L.w.in_cnt = L.zeroed;
     L.w.cursor = L.zeroed ? L.zeroed + n : nullptr;
-    L.w.long_count = L.zeroed ? L.zeroed + 2 * n : nullptr;
-    L.w.mid_count = L.zeroed ? L.zeroed + 2 * n + 1 : nullptr;
-    L.w.long_rows = cv.take<int32_t>((size_t)n);
+    L.w.extra = L.zeroed ? L.zeroed + 2 * n : nullptr;
+    L.w.rho0_count = L.zeroed ? L.zeroed + 3 * n : nullptr;
+    L.w.mid_count = L.zeroed ? L.zeroed + 3 * n + 1 : nullptr;
+    L.w.long_count = L.zeroed ? L.zeroed + 3 * n + 2 : nullptr;
     L.w.mid_rows = cv.take<int32_t>((size_t)n);
-    L.w.scan_part = cv.take<int64_t>(conn_scan_blocks(n));
+    L.w.long_rows = cv.take<int32_t>((size_t)n);
     L.indptr_tmp = cv.take<int64_t>((size_t)n + 1);
     if (bytes) *bytes = cv.used;
     return L;
@@ -242,11 +245,9 @@ rsc_status check_conn_args(const int32_t *idx, const float *dist, int64_t n, int
 rsc_status conn_count_phase(const int32_t *idx, const float *dist, int64_t n, int32_t k,
                             int64_t *indptr, float *rho, float *sigma, ConnLayout &L,
                             cudaStream_t st) {
-    if (rho) L.w.rho = rho;
-    if (sigma) L.w.sigma = sigma;
     RSC_CUDA_TRY(cudaMemsetAsync(L.w.status, 0, sizeof(unsigned int), st));
-    RSC_CUDA_TRY(cudaMemsetAsync(L.zeroed, 0, sizeof(int32_t) * (2 * n + 2), st));
-    RSC_CUDA_TRY(launch_conn_count(idx, dist, n, k, indptr, L.w, st));
+    RSC_CUDA_TRY(cudaMemsetAsync(L.zeroed, 0, sizeof(int32_t) * (3 * n + 3), st));
+    RSC_CUDA_TRY(launch_conn_count(idx, dist, n, k, indptr, rho, sigma, L.w, st));
     return RSC_OK;
 }
 
@@ -680,10 +681,12 @@ rsc_status rsc_connectivities(const int32_t *idx, const float *dist, int64_t n, 
         int64_t nnz = 0;
         RSC_CUDA_TRY(cudaMemcpyAsync(&nnz, indptr + n, sizeof(nnz), cudaMemcpyDeviceToHost, st));
         RSC_CUDA_TRY(cudaStreamSynchronize(st));
-        if (nnz > nnz_capacity)
+        if (nnz > nnz_capacity) {
+            RSC_CUDA_TRY(launch_conn_indptr(n, indptr, L.w, st));
             return fail(RSC_ERR_CAPACITY, "nnz=%lld exceeds capacity %lld", (long long)nnz, (long long)nnz_capacity);
+        }
     }
-    RSC_CUDA_TRY(launch_conn_fill(n, k, indptr, indices, data, nnz_capacity, L.w, st));
+    RSC_CUDA_TRY(launch_conn_fill(idx, dist, n, k, indptr, indices, data, nnz_capacity, L.w, st));
     return RSC_OK;
 }
 

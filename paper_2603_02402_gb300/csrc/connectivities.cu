@@ -9,24 +9,29 @@
 //   w_ic    = 0 (self), 1 (d <= rho or sigma == 0), else exp(-(d - rho)/sigma),
 //   G       = A + A^T - A o A^T, no diagonal, no zeros, CSR, sorted columns.
 //
-// Phases (k <= 32: a group of 16 or 32 lanes per row, one lane per kNN
-// entry, so every row-wise loop is a lane-parallel step; k > 32: a warp or a
-// thread per row):
-//   mean      deterministic two-level sum of all distances (for rho == 0 rows)
-//   smooth    rho, sigma, weights (thread per row: the bisection is
-//             arithmetic); the row's (column, weight) pairs sorted by column
-//             into 16-byte rows of KP slots
-//   count     per edge i->j: is i in row j's list (the partner row read whole
-//             with vector loads); own entry value a + b - ab; edges whose
-//             reverse is absent also go to row j (in-degree atomics)
-//   scan      row pointers (int64)
-//   fill      own entries in column order (ballot prefix), transposed entries
-//             via per-row atomic cursors (the scatter-add-with-atomics idea of
-//             the paper's categorical aggregation kernels, Methods, "Custom
-//             GPU kernels")
-//   sort      rows that received transposed entries are sorted by column
-//             (a thread in registers up to 32 entries, a warp in shared
-//             memory up to 512, a block per row beyond)
+// Every directed edge i -> j (weight a) is delivered to row j, so no pass
+// reads another row's kNN list:
+//   smooth  thread per row (k <= 32) or warp per row: rho, sigma (the
+//           bisection is arithmetic; the bucket slots' atomics are issued
+//           before it, so their latency hides behind it), the directed
+//           weights, every edge pushed to its target's bucket of B slots (the
+//           scatter-add with atomics of the paper's aggregation kernels,
+//           Methods, "Custom GPU kernels"; pushes past B are flagged in a
+//           per-row bit mask), the row's non-zero own entries sorted by column
+//   match   G lanes per row: a bucket entry whose source is in the row's own
+//           list is the reverse of a mutual edge: its weight b turns the own
+//           value a into a + b - ab, and the entry leaves the bucket; the
+//           other entries are compacted; flagged pushes are matched against
+//           their target's own list by the source row (rare: in-degree > B)
+//   scan    row pointers from own + bucket + flagged counts; the mean of all
+//           distances and the floor of the rows without a non-zero distance
+//   emit    per row: bucket entries ranked by counting, own and bucket
+//           entries placed by rank (own entry x at x + #bucket entries below
+//           it, bucket entry q at its rank + #own entries below it), so the
+//           row is written in order; flagged entries go after their target's
+//           bucket entries, and such rows are queued
+//   sort    queued rows sorted whole (a warp in shared memory up to 512
+//           entries, a block beyond)
 #include <limits.h>
 #include <math.h>
 
@@ -39,15 +44,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr unsigned kStatusCapacity = RSC_ERR_CAPACITY;
-
-// ------------------------------------------------------------------ mean
-
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
+constexpr float kTol = 1e-5f;
+constexpr int kIters = 64;
+constexpr float kFloor = 1e-3f;
 
 __device__ float block_sum(float v, float *red) {
     const int tid = threadIdx.x;
@@ -62,229 +61,24 @@ __device__ float block_sum(float v, float *red) {
     return r;
 }
 
-__global__ void __launch_bounds__(kThreads)
-mean_partials_kernel(const float *__restrict__ dist, int64_t total, float *__restrict__ partials) {
-    __shared__ float red[kThreads];
-    const int64_t chunk = ceil_div(total, gridDim.x);
-    const int64_t begin = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(total, begin + chunk);
-    float s = 0.f, c = 0.f;
-    for (int64_t e = begin + threadIdx.x; e < end; e += blockDim.x) kahan_add(s, c, dist[e]);
-    const float r = block_sum(s - c, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+// Directed weight of an entry at distance d of a row with (rho, sigma); the
+// self entry and empty slots are handled by the callers.  Every pass that
+// needs a directed weight calls this, so all copies of a weight are the same
+// bits.
+__device__ __forceinline__ float directed_weight(float d, float rho, float sig) {
+    const float g = d - rho;
+    if (g <= 0.f || sig == 0.f) return 1.f;
+    return expf(-(g / sig));
 }
-
-__global__ void __launch_bounds__(kMeanBlocks)
-mean_final_kernel(const float *__restrict__ partials, int64_t total, float *__restrict__ mean_all) {
-    __shared__ float red[kMeanBlocks];
-    const float r = block_sum(partials[threadIdx.x], red);
-    if (threadIdx.x == 0) mean_all[0] = (float)((double)r / (double)total);
-}
-
-// ---------------------------------------------------------------- smooth
-
-constexpr float kTol = 1e-5f;
-constexpr int kIters = 64;
-constexpr float kFloor = 1e-3f;
-
-// One warp per row, 32 < k <= 256 (up to 8 entries per lane).
-constexpr int kWarpRows = 4;
-constexpr int kWarpMaxK = 256;
-
-__global__ void __launch_bounds__(kWarpRows * 32)
-smooth_warp_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n,
-                   int k, const float *__restrict__ mean_all, float *__restrict__ rho_out,
-                   float *__restrict__ sigma_out, int32_t *__restrict__ scol,
-                   float *__restrict__ sw) {
-    __shared__ int s_col[kWarpRows][kWarpMaxK];
-    __shared__ float s_w[kWarpRows][kWarpMaxK];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * kWarpRows + warp;
-    if (i >= n) return;
-    constexpr int E = kWarpMaxK / 32;
-    float dd[E];
-    int col[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int c = lane + 32 * e;
-        dd[e] = (c < k) ? dist[i * k + c] : 0.f;
-        col[e] = (c < k) ? idx[i * k + c] : INT_MAX;
-    }
-    // rho: the non-zero distance with the smallest column position
-    int first = INT_MAX;
-#pragma unroll
-    for (int e = E - 1; e >= 0; --e) {
-        const int c = lane + 32 * e;
-        if (c < k && dd[e] > 0.f) first = c;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, off));
-    float mine = 0.f;
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-        if (lane + 32 * e == first) mine = dd[e];
-    const float r = (first != INT_MAX) ? __shfl_sync(0xffffffffu, mine, first % 32) : 0.f;
-
-    const float target = log2f((float)k);
-    float lo = 0.f, hi = INFINITY, mid = 1.f;
-    for (int it = 0; it < kIters; ++it) {
-        float s = 0.f;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int c = lane + 32 * e;
-            if (c >= 1 && c < k) {
-                const float g = dd[e] - r;
-                s += (g > 0.f) ? expf(-(g / mid)) : 1.f;
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        const float psum = s;   // identical on every lane (commutative butterfly)
-        if (fabsf(psum - target) < kTol) break;
-        const float prev = mid;
-        if (psum > target) {
-            hi = mid;
-            mid = (lo + hi) * 0.5f;
-        } else {
-            lo = mid;
-            mid = isinf(hi) ? mid * 2.f : (lo + hi) * 0.5f;
-        }
-        // a repeated midpoint is a fixed point (same sum, same branch, same
-        // bounds): the remaining steps would not move it
-        if (mid == prev) break;
-    }
-    float rs = 0.f;
-#pragma unroll
-    for (int e = 0; e < E; ++e) rs += (lane + 32 * e < k) ? dd[e] : 0.f;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
-    const float floor_v = (r > 0.f) ? kFloor * (rs / (float)k) : kFloor * mean_all[0];
-    const float sig = (mid < floor_v) ? floor_v : mid;
-    if (lane == 0) {
-        rho_out[i] = r;
-        sigma_out[i] = sig;
-    }
-    int P = 32;
-    while (P < k) P <<= 1;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int c = lane + 32 * e;
-        if (c >= P) continue;
-        float v;
-        if ((int64_t)col[e] == i) v = 0.f;
-        else if (dd[e] - r <= 0.f || sig == 0.f) v = 1.f;
-        else v = expf(-((dd[e] - r) / sig));
-        int cc = col[e];
-        if (cc < 0 || (int64_t)cc >= n || c >= k) {   // empty or malformed slot
-            cc = INT_MAX;
-            v = 0.f;
-        }
-        s_col[warp][c] = cc;
-        s_w[warp][c] = v;
-    }
-    __syncwarp();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < P / 2; t += 32) {
-                const int a = (t / stride) * 2 * stride + (t % stride), b = a + stride;
-                const bool asc = (a & size) == 0;
-                const int ca = s_col[warp][a], cb = s_col[warp][b];
-                if ((ca > cb) == asc) {
-                    s_col[warp][a] = cb;
-                    s_col[warp][b] = ca;
-                    const float tw = s_w[warp][a];
-                    s_w[warp][a] = s_w[warp][b];
-                    s_w[warp][b] = tw;
-                }
-            }
-            __syncwarp();
-        }
-    }
-    for (int c = lane; c < k; c += 32) {
-        scol[i * k + c] = s_col[warp][c];
-        sw[i * k + c] = s_w[warp][c];
-    }
-}
-
-// ----------------------------------------------------------------- count
 
 __device__ __forceinline__ float fuzzy_union(float a, float b) {
     // a + b - a*b, rounded the same way whichever endpoint computes it
     return __fsub_rn(__fadd_rn(a, b), __fmul_rn(a, b));
 }
 
-__global__ void __launch_bounds__(kThreads)
-count_kernel(int64_t n, int k, const int32_t *__restrict__ scol, const float *__restrict__ sw,
-             float *__restrict__ gv, int32_t *__restrict__ own_cnt, int32_t *__restrict__ in_cnt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int own = 0;
-    for (int c = 0; c < k; ++c) {
-        const int32_t j = scol[i * k + c];
-        float out = 0.f;
-        if (j != INT_MAX && (int64_t)j != i) {
-            const float a = sw[i * k + c];
-            const int32_t *rj = scol + (int64_t)j * k;
-            int lo = 0, hi = k;
-            while (lo < hi) {
-                const int m = (lo + hi) >> 1;
-                if ((int64_t)rj[m] < i) lo = m + 1;
-                else hi = m;
-            }
-            const bool mutual = lo < k && (int64_t)rj[lo] == i;
-            const float b = mutual ? sw[(int64_t)j * k + lo] : 0.f;
-            const float g = fuzzy_union(a, b);
-            if (!mutual && a != 0.f) {
-                atomicAdd(in_cnt + j, 1);
-                out = -g;   // negative marks "also emit the transposed entry"
-            } else {
-                out = g;
-            }
-            own += (g != 0.f);
-        }
-        gv[i * k + c] = out;
-    }
-    own_cnt[i] = own;
-}
-
-// ------------------------------------------ lane-per-entry kernels (k <= 32)
-//
-// A row is handled by a group of G lanes (G = 16 for k <= 16, 32 for
-// k <= 32), lane c holding entry c; 32 / G rows per warp.  Row reductions
-// are xor butterflies inside the group (every lane gets the same sum) and
-// the row's (column, weight) pairs are sorted by a shuffle bitonic network.
-
-template <int G>
-__device__ __forceinline__ float group_sum(float v) {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Ascending bitonic sort of one (col, w) pair per lane across each G-lane
-// group (lane c of the group ends with the c-th smallest column).
-template <int G>
-__device__ __forceinline__ void group_sort_by_col(int &col, float &w, int c) {
-#pragma unroll
-    for (int size = 2; size <= G; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const int pc = __shfl_xor_sync(0xffffffffu, col, stride);
-            const float pw = __shfl_xor_sync(0xffffffffu, w, stride);
-            const bool asc = (c & size) == 0;
-            const bool lower = (c & stride) == 0;
-            const bool take = (lower == asc) ? (pc < col) : (pc > col);
-            if (take) {
-                col = pc;
-                w = pw;
-            }
-        }
-    }
-}
-
-// Bitonic sort of KM (column, weight) pairs held in registers, by column.
+// Bitonic sort of KM (key, value) pairs held in registers of one thread.
 template <int KM>
-__device__ __forceinline__ void sort_pairs_by_col(int (&col)[KM], float (&w)[KM]) {
+__device__ __forceinline__ void sort_pairs(int (&key)[KM], float (&val)[KM]) {
 #pragma unroll
     for (int size = 2; size <= KM; size <<= 1) {
 #pragma unroll
@@ -294,13 +88,13 @@ __device__ __forceinline__ void sort_pairs_by_col(int (&col)[KM], float (&w)[KM]
                 const int p = i ^ stride;
                 if (p > i) {
                     const bool asc = (i & size) == 0;
-                    if ((col[i] > col[p]) == asc) {
-                        const int tc = col[i];
-                        col[i] = col[p];
-                        col[p] = tc;
-                        const float tw = w[i];
-                        w[i] = w[p];
-                        w[p] = tw;
+                    if ((key[i] > key[p]) == asc) {
+                        const int tk = key[i];
+                        key[i] = key[p];
+                        key[p] = tk;
+                        const float tv = val[i];
+                        val[i] = val[p];
+                        val[p] = tv;
                     }
                 }
             }
@@ -308,51 +102,82 @@ __device__ __forceinline__ void sort_pairs_by_col(int (&col)[KM], float (&w)[KM]
     }
 }
 
-// Thread per row, k <= KM (16 or 32): the bisection is arithmetic-bound, so
-// each thread runs its own row's loop (no cross-lane reductions per step).
-// exp(-g / sigma) is evaluated as exp2(g * (-log2(e) / sigma)) with one
-// reciprocal per step.  Output rows of KP slots are 16-byte aligned and
-// written with vector stores.
-template <int KM>
-__global__ void __launch_bounds__(kThreads)
-smooth_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP,
-                  const float *__restrict__ mean_all, float *__restrict__ rho_out, float *__restrict__ sigma_out,
-                  int32_t *__restrict__ scol, float *__restrict__ sw) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float dd[KM];
-    int col[KM];
+// Ascending bitonic sort of (key, val) pairs held E per lane across a group
+// of G lanes; element x = e * G + l (l = lane in the group).  Strides of G
+// and above compare registers of one lane, smaller strides exchange with the
+// lane l ^ stride.  Keys are unique except the INT_MAX pads.
+template <int G, int E>
+__device__ __forceinline__ void group_bitonic(int (&key)[E], float (&val)[E], int l) {
+    constexpr int N = G * E;
 #pragma unroll
-    for (int c = 0; c < KM; ++c) {
-        dd[c] = (c < k) ? dist[i * k + c] : 0.f;
-        col[c] = (c < k) ? idx[i * k + c] : INT_MAX;
-    }
-    float r = 0.f;
-    bool found = false;
+    for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
-    for (int c = 0; c < KM; ++c) {
-        if (c < k && !found && dd[c] > 0.f) {
-            r = dd[c];
-            found = true;
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= G) {
+                const int es = stride / G;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int p = e ^ es;
+                    if (p > e) {
+                        const bool asc = ((e * G + l) & size) == 0;
+                        if ((key[e] > key[p]) == asc) {
+                            const int tk = key[e];
+                            key[e] = key[p];
+                            key[p] = tk;
+                            const float tv = val[e];
+                            val[e] = val[p];
+                            val[p] = tv;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int pk = __shfl_xor_sync(0xffffffffu, key[e], stride);
+                    const float pv = __shfl_xor_sync(0xffffffffu, val[e], stride);
+                    const bool asc = ((e * G + l) & size) == 0;
+                    const bool lower = (l & stride) == 0;
+                    const bool take = (lower == asc) ? (pk < key[e]) : (pk > key[e]);
+                    if (take) {
+                        key[e] = pk;
+                        val[e] = pv;
+                    }
+                }
+            }
         }
     }
-    float g[KM];
+}
+
+// Number of entries below x in the ascending array s[0 .. N) (N a power of
+// two, INT_MAX pads at the end).
+template <int N>
+__device__ __forceinline__ int count_below(const int *s, int x) {
+    int p = 0;
 #pragma unroll
-    for (int c = 0; c < KM; ++c) g[c] = dd[c] - r;
-    const float target = log2f((float)k);
+    for (int step = N / 2; step >= 1; step >>= 1)
+        if (s[p + step - 1] < x) p += step;
+    return p + (s[p] < x ? 1 : 0);
+}
+
+// ---------------------------------------------------------------- smooth
+
+// Bisection of one row on g[c] = d_c - rho (entries at or past k are +inf
+// and contribute exp2(-inf) = 0).  exp(-g / sigma) is evaluated as
+// exp2(g * (-log2(e) / sigma)) with one reciprocal per step, summed with
+// Neumaier compensation.
+template <int KM>
+__device__ __forceinline__ float bisect_sigma(const float (&g)[KM], float target) {
     constexpr float kNegLog2e = -1.4426950408889634f;
     float lo = 0.f, hi = INFINITY, mid = 1.f;
     for (int it = 0; it < kIters; ++it) {
         const float sc = kNegLog2e / mid;
-        float s = 0.f, comp = 0.f;   // Neumaier-compensated sum
+        float s = 0.f, comp = 0.f;
 #pragma unroll
         for (int c = 1; c < KM; ++c) {
-            if (c < k) {
-                const float t = (g[c] > 0.f) ? exp2f(g[c] * sc) : 1.f;
-                const float u = s + t;
-                comp += (fabsf(s) >= fabsf(t)) ? ((s - u) + t) : ((t - u) + s);
-                s = u;
-            }
+            const float t = (g[c] > 0.f) ? exp2f(g[c] * sc) : 1.f;
+            const float u = s + t;
+            comp += (fabsf(s) >= fabsf(t)) ? ((s - u) + t) : ((t - u) + s);
+            s = u;
         }
         const float psum = s + comp;
         if (fabsf(psum - target) < kTol) break;
@@ -368,111 +193,333 @@ smooth_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dis
         // bounds): the remaining steps would not move it
         if (mid == prev) break;
     }
-    float row_sum = 0.f;
-#pragma unroll
-    for (int c = 0; c < KM; ++c) row_sum += (c < k) ? dd[c] : 0.f;
-    const float floor_v = (r > 0.f) ? kFloor * (row_sum / (float)k) : kFloor * mean_all[0];
-    const float sig = (mid < floor_v) ? floor_v : mid;
-    rho_out[i] = r;
-    sigma_out[i] = sig;
-
-    float w[KM];
-#pragma unroll
-    for (int c = 0; c < KM; ++c) {
-        float v;
-        if ((int64_t)col[c] == i) v = 0.f;
-        else if (g[c] <= 0.f || sig == 0.f) v = 1.f;
-        else v = expf(-(g[c] / sig));
-        if (col[c] < 0 || (int64_t)col[c] >= n || c >= k) {   // empty or malformed slot
-            col[c] = INT_MAX;
-            v = 0.f;
-        }
-        w[c] = v;
-    }
-    sort_pairs_by_col<KM>(col, w);
-    int4 *oc = reinterpret_cast<int4 *>(scol + i * KP);
-    float4 *ow = reinterpret_cast<float4 *>(sw + i * KP);
-#pragma unroll
-    for (int u = 0; u < KM / 4; ++u) {
-        if (4 * u < KP) {
-            oc[u] = make_int4(col[4 * u], col[4 * u + 1], col[4 * u + 2], col[4 * u + 3]);
-            ow[u] = make_float4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
-        }
-    }
+    return mid;
 }
 
-// Lane per own entry i -> j: is i in row j's list?  The partner row (KP
-// columns, 16-byte aligned) is read with int4 loads and compared whole.
-template <int G>
+// Thread per row, k <= KM (16 or 32).  Rows without a non-zero distance get
+// the unfloored bisection result here and the global-mean floor in the scan
+// pass; their weights are all 1 and do not depend on sigma.  Every valid
+// edge takes a bucket slot of its target (entries with weight 0 fill their
+// slot and are dropped later); pushes past B with a non-zero weight set bit
+// c of ovf[i].
+template <int KM>
 __global__ void __launch_bounds__(kThreads)
-count_group_kernel(int64_t n, int KP, const int32_t *__restrict__ scol, const float *__restrict__ sw,
-                   float *__restrict__ gv, int32_t *__restrict__ tslot, int32_t *__restrict__ own_cnt,
-                   int32_t *__restrict__ in_cnt) {
-    const int lane = threadIdx.x & 31, c = lane & (G - 1), base = lane & ~(G - 1);
-    const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / G) + lane / G;
-    const bool row_ok = i < n;
-    const bool has = row_ok && c < KP;
-    const int32_t j = has ? scol[i * KP + c] : INT_MAX;
-    float out = 0.f;
-    if (j != INT_MAX && (int64_t)j != i) {
-        const float a = sw[i * KP + c];
-        const int4 *rj = reinterpret_cast<const int4 *>(scol + (int64_t)j * KP);
-        int pos = -1;
+smooth_push_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP,
+                       int B, float2 *__restrict__ rs, float *__restrict__ rho_out, float *__restrict__ sigma_out,
+                       float *__restrict__ part_sum, int32_t *__restrict__ rho0_rows,
+                       int32_t *__restrict__ rho0_count, int32_t *__restrict__ in_cnt, int2 *__restrict__ bucket,
+                       uint32_t *__restrict__ ovf, int32_t *__restrict__ ocol, float *__restrict__ og,
+                       int32_t *__restrict__ own_cnt) {
+    __shared__ float red[kThreads];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float row_sum = 0.f;
+    if (i < n) {
+        const int32_t *ir = idx + i * k;
+        const float *dr = dist + i * k;
+        const int me = (int)i;
+        int col[KM];
+        float dd[KM];
 #pragma unroll
-        for (int u = 0; u < G / 4; ++u) {
-            if (4 * u < KP) {
-                const int4 q = __ldg(rj + u);
-                if ((int64_t)q.x == i) pos = 4 * u;
-                if ((int64_t)q.y == i) pos = 4 * u + 1;
-                if ((int64_t)q.z == i) pos = 4 * u + 2;
-                if ((int64_t)q.w == i) pos = 4 * u + 3;
+        for (int c = 0; c < KM; ++c) {
+            col[c] = -1;
+            dd[c] = 0.f;
+            if (c < k) {
+                const int32_t j = ir[c];
+                dd[c] = dr[c];
+                if (j >= 0 && (int64_t)j < n && j != me) col[c] = j;
             }
         }
-        const bool mutual = pos >= 0;
-        const float b = mutual ? sw[(int64_t)j * KP + pos] : 0.f;
-        const float g = fuzzy_union(a, b);
-        if (!mutual && a != 0.f) {
-            tslot[i * KP + c] = atomicAdd(in_cnt + j, 1);   // its place among row j's transposed entries
-            out = -g;   // negative marks "also emit the transposed entry"
-        } else {
-            out = g;
+        int slot[KM];
+#pragma unroll
+        for (int c = 0; c < KM; ++c) slot[c] = (col[c] >= 0) ? atomicAdd(in_cnt + col[c], 1) : 0;
+        float r = 0.f;
+        bool found = false;
+#pragma unroll
+        for (int c = 0; c < KM; ++c) {
+            if (c < k && !found && dd[c] > 0.f) {
+                r = dd[c];
+                found = true;
+            }
         }
+#pragma unroll
+        for (int c = 0; c < KM; ++c) row_sum += dd[c];
+        float g[KM];
+#pragma unroll
+        for (int c = 0; c < KM; ++c) g[c] = (c < k) ? dd[c] - r : INFINITY;
+        const float mid = bisect_sigma<KM>(g, log2f((float)k));
+        float sig = mid;
+        if (r > 0.f) {
+            const float floor_v = kFloor * (row_sum / (float)k);
+            if (sig < floor_v) sig = floor_v;
+        } else {
+            rho0_rows[atomicAdd(rho0_count, 1)] = me;
+        }
+        rs[i] = make_float2(r, sig);
+        if (rho_out) rho_out[i] = r;
+        if (sigma_out) sigma_out[i] = sig;
+        float a[KM];
+        int key[KM];
+        uint32_t spill = 0;
+        int cnt = 0;
+#pragma unroll
+        for (int c = 0; c < KM; ++c) {
+            a[c] = 0.f;
+            if (col[c] >= 0) {
+                a[c] = directed_weight(dd[c], r, sig);
+                if (slot[c] < B) bucket[(int64_t)col[c] * B + slot[c]] = make_int2(me, __float_as_int(a[c]));
+                else if (a[c] != 0.f) spill |= 1u << c;
+            }
+            key[c] = (col[c] >= 0 && a[c] != 0.f) ? col[c] : INT_MAX;
+            cnt += key[c] != INT_MAX;
+        }
+        ovf[i] = spill;
+        sort_pairs<KM>(key, a);
+        int4 *oc = reinterpret_cast<int4 *>(ocol + i * KP);
+        float4 *ow = reinterpret_cast<float4 *>(og + i * KP);
+#pragma unroll
+        for (int u = 0; u < KM / 4; ++u) {
+            if (4 * u < KP) {
+                oc[u] = make_int4(key[4 * u], key[4 * u + 1], key[4 * u + 2], key[4 * u + 3]);
+                ow[u] = make_float4(a[4 * u], a[4 * u + 1], a[4 * u + 2], a[4 * u + 3]);
+            }
+        }
+        own_cnt[i] = cnt;
     }
-    if (has) gv[i * KP + c] = out;
-    const unsigned own = (__ballot_sync(0xffffffffu, out != 0.f) >> base) & (G == 32 ? 0xffffffffu : ((1u << G) - 1));
-    if (row_ok && c == 0) own_cnt[i] = __popc(own);
+    const float b = block_sum(row_sum, red);
+    if (threadIdx.x == 0) part_sum[blockIdx.x] = b;
 }
 
-// Lane per own entry: own entries at indptr[i] + (rank among the row's
-// non-zero entries), in column order; a transposed entry at its slot (taken
-// by the count pass) after the receiving row's own entries.
-template <int G>
-__global__ void __launch_bounds__(kThreads)
-fill_group_kernel(int64_t n, int KP, const int64_t *__restrict__ indptr, const int32_t *__restrict__ scol,
-                  const float *__restrict__ gv, const int32_t *__restrict__ own_cnt, const int32_t *__restrict__ tslot,
-                  int32_t *__restrict__ indices, float *__restrict__ data, int64_t cap, unsigned int *status) {
-    const int lane = threadIdx.x & 31, c = lane & (G - 1), base = lane & ~(G - 1);
-    const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / G) + lane / G;
-    const bool has = i < n && c < KP;
-    const float v = has ? gv[i * KP + c] : 0.f;
-    const unsigned nzm = (__ballot_sync(0xffffffffu, v != 0.f) >> base);
-    if (v == 0.f) return;
-    const int32_t j = scol[i * KP + c];
-    const int64_t p = indptr[i] + __popc(nzm & ((1u << c) - 1));
-    if (p < cap) {
-        indices[p] = j;
-        data[p] = fabsf(v);
-    } else {
-        record_status(status, kStatusCapacity);
-    }
-    if (v < 0.f) {
-        const int64_t q = indptr[j] + own_cnt[j] + tslot[i * KP + c];
-        if (q < cap) {
-            indices[q] = (int32_t)i;
-            data[q] = -v;
-        } else {
-            record_status(status, kStatusCapacity);
+// Warp per row, 32 < k <= 32 E (entry c = lane + 32 e).  Flag bit of entry
+// c: bit lane of ovf[i * E + e]; own entries sorted across the warp into
+// ocol / og rows of KP = 32 E.
+constexpr int kWarpRows = 4;
+
+template <int E>
+__global__ void __launch_bounds__(kWarpRows * 32)
+smooth_push_warp_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP,
+                        int B, float2 *__restrict__ rs, float *__restrict__ rho_out, float *__restrict__ sigma_out,
+                        float *__restrict__ part_sum, int32_t *__restrict__ rho0_rows,
+                        int32_t *__restrict__ rho0_count, int32_t *__restrict__ in_cnt, int2 *__restrict__ bucket,
+                        uint32_t *__restrict__ ovf, int32_t *__restrict__ ocol, float *__restrict__ og,
+                        int32_t *__restrict__ own_cnt) {
+    __shared__ float red[kWarpRows * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kWarpRows + warp;
+    float rs_sum = 0.f;
+    if (i < n) {   // uniform within the warp
+        const int me = (int)i;
+        float dd[E];
+        int col[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = lane + 32 * e;
+            dd[e] = 0.f;
+            col[e] = -1;
+            if (c < k) {
+                const int32_t j = idx[i * k + c];
+                dd[e] = dist[i * k + c];
+                if (j >= 0 && (int64_t)j < n && j != me) col[e] = j;
+            }
         }
+        int slot[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) slot[e] = (col[e] >= 0) ? atomicAdd(in_cnt + col[e], 1) : 0;
+        // rho: the non-zero distance with the smallest column position
+        int first = INT_MAX;
+#pragma unroll
+        for (int e = E - 1; e >= 0; --e) {
+            const int c = lane + 32 * e;
+            if (c < k && dd[e] > 0.f) first = c;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, off));
+        float mine = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (lane + 32 * e == first) mine = dd[e];
+        const float r = (first != INT_MAX) ? __shfl_sync(0xffffffffu, mine, first % 32) : 0.f;
+        const float target = log2f((float)k);
+        float lo = 0.f, hi = INFINITY, mid = 1.f;
+        for (int it = 0; it < kIters; ++it) {
+            float s = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int c = lane + 32 * e;
+                if (c >= 1 && c < k) {
+                    const float g = dd[e] - r;
+                    s += (g > 0.f) ? expf(-(g / mid)) : 1.f;
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            const float psum = s;   // identical on every lane (commutative butterfly)
+            if (fabsf(psum - target) < kTol) break;
+            const float prev = mid;
+            if (psum > target) {
+                hi = mid;
+                mid = (lo + hi) * 0.5f;
+            } else {
+                lo = mid;
+                mid = isinf(hi) ? mid * 2.f : (lo + hi) * 0.5f;
+            }
+            if (mid == prev) break;
+        }
+        float sum = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) sum += dd[e];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        float sig = mid;
+        if (r > 0.f) {
+            const float floor_v = kFloor * (sum / (float)k);
+            if (sig < floor_v) sig = floor_v;
+        } else if (lane == 0) {
+            rho0_rows[atomicAdd(rho0_count, 1)] = me;
+        }
+        if (lane == 0) {
+            rs[i] = make_float2(r, sig);
+            if (rho_out) rho_out[i] = r;
+            if (sigma_out) sigma_out[i] = sig;
+            rs_sum = sum;
+        }
+        int key[E];
+        float a[E];
+        int cnt = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            a[e] = 0.f;
+            bool spill = false;
+            if (col[e] >= 0) {
+                a[e] = directed_weight(dd[e], r, sig);
+                if (slot[e] < B) bucket[(int64_t)col[e] * B + slot[e]] = make_int2(me, __float_as_int(a[e]));
+                else spill = a[e] != 0.f;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, spill);
+            if (lane == 0) ovf[i * E + e] = m;
+            key[e] = (col[e] >= 0 && a[e] != 0.f) ? col[e] : INT_MAX;
+            cnt += __popc(__ballot_sync(0xffffffffu, key[e] != INT_MAX));
+        }
+        group_bitonic<32, E>(key, a, lane);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            ocol[i * KP + e * 32 + lane] = key[e];
+            og[i * KP + e * 32 + lane] = a[e];
+        }
+        if (lane == 0) own_cnt[i] = cnt;
+    }
+    const float b = block_sum(rs_sum, red);
+    if (threadIdx.x == 0) part_sum[blockIdx.x] = b;
+}
+
+// ----------------------------------------------------------------- match
+
+// G lanes per row, own entries E per lane (x = e * G + l), bucket entries
+// two per lane (q = e * G + l, B = 2G).  A bucket entry whose source is an
+// own entry is the reverse of a mutual edge: the own value becomes
+// a + b - ab and the entry is dropped; entries with weight 0 are dropped;
+// the rest are compacted to the front of the bucket (in_kept of them).  The
+// row's flagged pushes (its edges that found the target's bucket full) are
+// looked up in the target's own list: a mutual one updates the target's own
+// value, the others count toward the target's row (extra) and keep their
+// flag for the emit pass.
+template <int G, int E>
+__global__ void __launch_bounds__(kThreads)
+match_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP, int B,
+             int MW, const float2 *__restrict__ rs, const int32_t *__restrict__ ocol, float *__restrict__ og,
+             const int32_t *__restrict__ own_cnt, const int32_t *__restrict__ in_cnt, int2 *__restrict__ bucket,
+             uint32_t *__restrict__ ovf, int32_t *__restrict__ in_kept, int32_t *__restrict__ extra) {
+    constexpr int GPW = 32 / G;
+    __shared__ int s_own[kThreads / 32][GPW][G * E];
+    __shared__ float s_hit[kThreads / 32][GPW][G * E];
+    const int lane = threadIdx.x & 31, l = lane & (G - 1), grp = lane / G, warp = threadIdx.x >> 5;
+    const int base = grp * G;
+    const unsigned gbits = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
+    const unsigned gmask = gbits << base;
+    const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW + grp;
+    const bool row_ok = i < n;
+    int oc = 0, ic = 0;
+    if (row_ok) {
+        oc = own_cnt[i];
+        ic = min(in_cnt[i], B);
+    }
+    const int32_t *orow = ocol + (size_t)(row_ok ? i : 0) * KP;
+    float *grow = og + (size_t)(row_ok ? i : 0) * KP;
+    int2 *brow = bucket + (size_t)(row_ok ? i : 0) * B;
+    int *so = s_own[warp][grp];
+    float *sh = s_hit[warp][grp];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int x = e * G + l;
+        so[x] = (x < oc) ? orow[x] : INT_MAX;
+        sh[x] = 0.f;
+    }
+    int src[2];
+    float wa[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int q = e * G + l;
+        src[e] = INT_MAX;
+        wa[e] = 0.f;
+        if (q < ic) {
+            const int2 t = brow[q];
+            src[e] = t.x;
+            wa[e] = __int_as_float(t.y);
+        }
+    }
+    __syncwarp();
+    bool kept[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        kept[e] = false;
+        if (src[e] != INT_MAX) {
+            const int p = count_below<G * E>(so, src[e]);
+            if (p < oc && so[p] == src[e]) {
+                if (wa[e] != 0.f) sh[p] = wa[e];
+            } else {
+                kept[e] = wa[e] != 0.f;
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int x = e * G + l;
+        if (x < oc && sh[x] != 0.f) grow[x] = fuzzy_union(grow[x], sh[x]);
+    }
+    const unsigned m0 = (__ballot_sync(0xffffffffu, kept[0]) >> base) & gbits;
+    const unsigned m1 = (__ballot_sync(0xffffffffu, kept[1]) >> base) & gbits;
+    const unsigned lt = (1u << l) - 1u;
+    if (kept[0]) brow[__popc(m0 & lt)] = make_int2(src[0], __float_as_int(wa[0]));
+    if (kept[1]) brow[__popc(m0) + __popc(m1 & lt)] = make_int2(src[1], __float_as_int(wa[1]));
+    if (row_ok && l == 0) in_kept[i] = __popc(m0) + __popc(m1);
+    if (!row_ok) return;   // uniform within the group; no warp-wide step follows
+    const int me = (int)i;
+    for (int w = 0; w < MW; ++w) {
+        const uint32_t m = ovf[i * MW + w];
+        if (m == 0) continue;   // uniform within the group
+        const int c = w * 32 + l;
+        bool keep = false;
+        if ((m >> l) & 1u) {
+            const int32_t t = idx[i * k + c];
+            const float2 ri = rs[i];
+            const float a = directed_weight(dist[i * k + c], ri.x, ri.y);
+            const int32_t *tr = ocol + (size_t)t * KP;
+            int lo = 0, hi = own_cnt[t];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (tr[mid] < me) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < own_cnt[t] && tr[lo] == me) {
+                float *gp = og + (size_t)t * KP + lo;
+                *gp = fuzzy_union(*gp, a);
+            } else {
+                atomicAdd(extra + t, 1);
+                keep = true;
+            }
+        }
+        const unsigned km = (__ballot_sync(gmask, keep) >> base) & gbits;
+        if (l == 0) ovf[i * MW + w] = km;
     }
 }
 
@@ -509,9 +556,11 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *warp_sums, int64_t &
     return warp_off + x - v;
 }
 
+// Row lengths own + bucket + flagged -> offsets inside each tile of
+// kScanTile rows (local) and the tiles' totals (part).
 __global__ void __launch_bounds__(kScanThreads)
-scan_local_kernel(int64_t n, const int32_t *__restrict__ own_cnt, const int32_t *__restrict__ in_cnt,
-                  int64_t *__restrict__ indptr, int64_t *__restrict__ part) {
+scan_local_kernel(int64_t n, const int32_t *__restrict__ own_cnt, const int32_t *__restrict__ in_kept,
+                  const int32_t *__restrict__ extra, int64_t *__restrict__ local, int64_t *__restrict__ part) {
     __shared__ int64_t warp_sums[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
@@ -519,7 +568,7 @@ scan_local_kernel(int64_t n, const int32_t *__restrict__ own_cnt, const int32_t 
 #pragma unroll
     for (int e = 0; e < kScanItems; ++e) {
         const int64_t i = base + e;
-        v[e] = (i < n) ? (int64_t)own_cnt[i] + (int64_t)in_cnt[i] : 0;
+        v[e] = (i < n) ? (int64_t)own_cnt[i] + (int64_t)in_kept[i] + (int64_t)extra[i] : 0;
         sum += v[e];
     }
     int64_t total;
@@ -527,15 +576,22 @@ scan_local_kernel(int64_t n, const int32_t *__restrict__ own_cnt, const int32_t 
 #pragma unroll
     for (int e = 0; e < kScanItems; ++e) {
         const int64_t i = base + e;
-        if (i < n) indptr[i] = run;
+        if (i < n) local[i] = run;
         run += v[e];
     }
     if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
 
+// One block: exclusive scan of the tile totals (indptr[n] = nnz), then the
+// mean of all distances from the smooth pass's partial sums and the floor
+// 1e-3 * mean of the rows without a non-zero distance.
 __global__ void __launch_bounds__(1024)
-scan_part_kernel(int64_t nb, int64_t *__restrict__ part, int64_t n, int64_t *__restrict__ indptr) {
+scan_part_kernel(int64_t nb, int64_t *__restrict__ part, int64_t n, int64_t *__restrict__ indptr,
+                 const float *__restrict__ part_sum, int64_t n_sum, int64_t total_entries,
+                 const int32_t *__restrict__ rho0_rows, const int32_t *__restrict__ rho0_count,
+                 float2 *__restrict__ rs, float *__restrict__ sigma_out) {
     __shared__ int64_t warp_sums[32];
+    __shared__ float red[1024];
     int64_t carry = 0;
     for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
         const int64_t b = b0 + threadIdx.x;
@@ -546,43 +602,159 @@ scan_part_kernel(int64_t nb, int64_t *__restrict__ part, int64_t n, int64_t *__r
         carry += total;
     }
     if (threadIdx.x == 0) indptr[n] = carry;
+    const int c0 = *rho0_count;
+    if (c0 == 0) return;   // uniform
+    float s = 0.f;
+    for (int64_t b = threadIdx.x; b < n_sum; b += blockDim.x) s += part_sum[b];
+    const float mean_all = block_sum(s, red) / (float)total_entries;
+    const float floor_v = kFloor * mean_all;
+    for (int r = threadIdx.x; r < c0; r += blockDim.x) {
+        const int32_t i = rho0_rows[r];
+        float2 v = rs[i];
+        if (v.y < floor_v) v.y = floor_v;
+        rs[i] = v;
+        if (sigma_out) sigma_out[i] = v.y;
+    }
 }
 
+// indptr[i] = local[i] + part[tile of i] (used when the CSR is not filled).
 __global__ void __launch_bounds__(kScanThreads)
-scan_add_kernel(int64_t n, const int64_t *__restrict__ part, int64_t *__restrict__ indptr) {
+scan_add_kernel(int64_t n, const int64_t *__restrict__ local, const int64_t *__restrict__ part,
+                int64_t *__restrict__ indptr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) indptr[i] += part[i / kScanTile];
+    if (i < n) indptr[i] = local[i] + part[i / kScanTile];
 }
 
-// ------------------------------------------------------------------ fill
+// ------------------------------------------------------------------ emit
 
+constexpr int kWarpSortMax = 512;
+constexpr int kBlockSortMax = 4096;
+
+__device__ __forceinline__ void put(int32_t *indices, float *data, int64_t p, int64_t cap, int c, float v,
+                                    unsigned int *status) {
+    if (p < cap) {
+        indices[p] = c;
+        data[p] = v;
+    } else {
+        record_status(status, kStatusCapacity);
+    }
+}
+
+// G lanes per row.  A row without flagged entries: its kept bucket entries
+// (at most B = 2G, two per lane) are ranked by counting (rank = entries with
+// a smaller source), written to shared memory in order, and each own and
+// bucket entry is placed at its rank in the union.  A row with flagged
+// entries gets its own and bucket entries written unsorted and is queued for
+// a whole-row sort; its flagged entries are placed by their source rows,
+// after its bucket entries.
+template <int G, int E>
 __global__ void __launch_bounds__(kThreads)
-fill_kernel(int64_t n, int k, const int64_t *__restrict__ indptr, const int32_t *__restrict__ scol,
-            const float *__restrict__ gv, const int32_t *__restrict__ own_cnt,
-            int32_t *__restrict__ cursor, int32_t *__restrict__ indices, float *__restrict__ data,
-            int64_t cap, unsigned int *status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t p = indptr[i];
-    for (int c = 0; c < k; ++c) {
-        const float v = gv[i * k + c];
-        if (v == 0.f) continue;
-        const int32_t j = scol[i * k + c];
-        if (p < cap) {
-            indices[p] = j;
-            data[p] = fabsf(v);
-        } else {
-            record_status(status, kStatusCapacity);
+emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__ idx,
+            const float *__restrict__ dist, const float2 *__restrict__ rs, const int32_t *__restrict__ ocol,
+            const float *__restrict__ og, const int32_t *__restrict__ own_cnt, const int32_t *__restrict__ in_kept,
+            const int32_t *__restrict__ extra, const int2 *__restrict__ bucket, const uint32_t *__restrict__ ovf,
+            const int64_t *__restrict__ local, const int64_t *__restrict__ part, int64_t *__restrict__ indptr,
+            int32_t *__restrict__ cursor, int32_t *__restrict__ indices, float *__restrict__ data, int64_t cap,
+            int32_t *__restrict__ mid_rows, int32_t *__restrict__ mid_count, int32_t *__restrict__ long_rows,
+            int32_t *__restrict__ long_count, unsigned int *status) {
+    constexpr int GPW = 32 / G;   // rows per warp
+    __shared__ int s_own[kThreads / 32][GPW][G * E];
+    __shared__ int s_in[kThreads / 32][GPW][2 * G];
+    const int lane = threadIdx.x & 31, l = lane & (G - 1), grp = lane / G, warp = threadIdx.x >> 5;
+    const int base = grp * G;
+    const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW + grp;
+    const bool row_ok = i < n;
+    int64_t start = 0;
+    int oc = 0, ic = 0, ex = 0;
+    if (row_ok) {
+        start = local[i] + part[i / kScanTile];
+        oc = own_cnt[i];
+        ic = in_kept[i];
+        ex = extra[i];
+        if (l == 0) indptr[i] = start;
+    }
+    const int32_t *orow = ocol + (size_t)(row_ok ? i : 0) * KP;
+    const float *grow = og + (size_t)(row_ok ? i : 0) * KP;
+    const int2 *brow = bucket + (size_t)(row_ok ? i : 0) * B;
+    int col[E];
+    float gv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int x = e * G + l;
+        col[e] = (x < oc) ? orow[x] : INT_MAX;
+        gv[e] = (x < oc) ? grow[x] : 0.f;
+    }
+    int src[2];
+    float wa[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int q = e * G + l;
+        src[e] = INT_MAX;
+        wa[e] = 0.f;
+        if (q < ic) {
+            const int2 t = brow[q];
+            src[e] = t.x;
+            wa[e] = __int_as_float(t.y);
         }
-        ++p;
-        if (v < 0.f) {
-            const int slot = atomicAdd(cursor + j, 1);
-            const int64_t q = indptr[j] + own_cnt[j] + slot;
-            if (q < cap) {
-                indices[q] = (int32_t)i;
-                data[q] = -v;
-            } else {
-                record_status(status, kStatusCapacity);
+    }
+    const bool hub = ex > 0;
+    if (hub) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int x = e * G + l;
+            if (x < oc) put(indices, data, start + x, cap, col[e], gv[e], status);
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int q = e * G + l;
+            if (q < ic) put(indices, data, start + oc + q, cap, src[e], wa[e], status);
+        }
+        if (l == 0) {
+            const int L = oc + ic + ex;
+            if (L <= kWarpSortMax) mid_rows[atomicAdd(mid_count, 1)] = (int32_t)i;
+            else long_rows[atomicAdd(long_count, 1)] = (int32_t)i;
+        }
+    }
+    // ranks of the bucket entries (pads are INT_MAX and never below a key)
+    const int icmax = __reduce_max_sync(0xffffffffu, hub ? 0 : ic);
+    int r0 = 0, r1 = 0;
+    for (int t = 0; t < icmax; ++t) {
+        const int v = (t < G) ? __shfl_sync(0xffffffffu, src[0], base + t)
+                              : __shfl_sync(0xffffffffu, src[1], base + t - G);
+        r0 += v < src[0];
+        r1 += v < src[1];
+    }
+    int *so = s_own[warp][grp];
+    int *si = s_in[warp][grp];
+#pragma unroll
+    for (int e = 0; e < E; ++e) so[e * G + l] = col[e];
+    // position p < ic holds the entry of rank p, p >= ic a pad (ranks are a
+    // permutation of [0, ic): sources are distinct)
+    si[(!hub && l < ic) ? r0 : l] = src[0];
+    si[(!hub && G + l < ic) ? r1 : G + l] = src[1];
+    __syncwarp();
+    if (row_ok && !hub) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int x = e * G + l;
+            if (x < oc) put(indices, data, start + x + count_below<2 * G>(si, col[e]), cap, col[e], gv[e], status);
+        }
+        if (l < ic) put(indices, data, start + r0 + count_below<G * E>(so, src[0]), cap, src[0], wa[0], status);
+        if (G + l < ic) put(indices, data, start + r1 + count_below<G * E>(so, src[1]), cap, src[1], wa[1], status);
+    }
+    // this row's flagged edges go after the bucket entries of their targets
+    if (row_ok) {
+        for (int w = 0; w < MW; ++w) {
+            const uint32_t m = ovf[i * MW + w];
+            if (m == 0) continue;   // uniform within the group
+            const int c = w * 32 + l;
+            if ((m >> l) & 1u) {
+                const int32_t t = idx[i * k + c];
+                const float2 ri = rs[i];
+                const float a = directed_weight(dist[i * k + c], ri.x, ri.y);
+                const int slot = atomicAdd(cursor + t, 1);
+                const int64_t p = local[t] + part[t / kScanTile] + own_cnt[t] + in_kept[t] + slot;
+                put(indices, data, p, cap, (int32_t)i, a, status);
             }
         }
     }
@@ -591,8 +763,6 @@ fill_kernel(int64_t n, int k, const int64_t *__restrict__ indptr, const int32_t 
 // ------------------------------------------------------------------ sort
 
 constexpr int kSortWarps = 8;
-constexpr int kWarpSortMax = 512;
-constexpr int kBlockSortMax = 4096;
 
 // Ascending-only bitonic network ("mirrored" first step of each merge), on a
 // virtual power-of-two length P = 2^lp >= L; slots at or past L act as +inf
@@ -636,63 +806,10 @@ __device__ __forceinline__ int ceil_log2(int L) {
     return lp;
 }
 
-// Rows that received transposed entries are re-sorted by column.  Thread
-// per row for the common short rows (up to 32 entries: loaded and sorted in
-// registers, so a warp keeps 32 rows' loads in flight); longer rows are
-// queued: up to kWarpSortMax entries for a warp in shared memory, beyond
-// that for a block.
-__global__ void __launch_bounds__(kThreads)
-sort_short_rows_kernel(int64_t n, const int64_t *__restrict__ indptr, const int32_t *__restrict__ in_cnt,
-                       int32_t *__restrict__ indices, float *__restrict__ data, int64_t cap,
-                       int32_t *__restrict__ mid_rows, int32_t *__restrict__ mid_count,
-                       int32_t *__restrict__ long_rows, int32_t *__restrict__ long_count) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || in_cnt[i] == 0) return;
-    const int64_t b = indptr[i], e = indptr[i + 1];
-    if (e > cap) return;   // capacity error already recorded by the fill
-    const int L = (int)(e - b);
-    if (L > 32) {
-        if (L <= kWarpSortMax) mid_rows[atomicAdd(mid_count, 1)] = (int32_t)i;
-        else long_rows[atomicAdd(long_count, 1)] = (int32_t)i;
-        return;
-    }
-    int col[32];
-    float w[32];
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-        col[t] = (t < L) ? indices[b + t] : INT_MAX;
-        w[t] = (t < L) ? data[b + t] : 0.f;
-    }
-    if (L <= 16) {
-        int c16[16];
-        float w16[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            c16[t] = col[t];
-            w16[t] = w[t];
-        }
-        sort_pairs_by_col<16>(c16, w16);
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            col[t] = c16[t];
-            w[t] = w16[t];
-        }
-    } else {
-        sort_pairs_by_col<32>(col, w);
-    }
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-        if (t < L) {
-            indices[b + t] = col[t];
-            data[b + t] = w[t];
-        }
-    }
-}
-
-// Warp per queued row of 33 .. kWarpSortMax entries, in shared memory.
+// Warp per queued row of up to kWarpSortMax entries, in shared memory.
 __global__ void __launch_bounds__(kSortWarps * 32)
 sort_mid_rows_kernel(const int64_t *__restrict__ indptr, int32_t *__restrict__ indices, float *__restrict__ data,
-                     const int32_t *__restrict__ mid_rows, const int32_t *__restrict__ mid_count) {
+                     int64_t cap, const int32_t *__restrict__ mid_rows, const int32_t *__restrict__ mid_count) {
     __shared__ int s_col[kSortWarps][kWarpSortMax];
     __shared__ float s_w[kSortWarps][kWarpSortMax];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -703,6 +820,7 @@ sort_mid_rows_kernel(const int64_t *__restrict__ indptr, int32_t *__restrict__ i
         const int64_t i = mid_rows[r];
         const int64_t b = indptr[i];
         const int L = (int)(indptr[i + 1] - b);
+        if (b + L > cap) continue;   // capacity error already recorded
         for (int t = lane; t < L; t += 32) {
             sc[t] = indices[b + t];
             sv[t] = data[b + t];
@@ -723,7 +841,7 @@ sort_mid_rows_kernel(const int64_t *__restrict__ indptr, int32_t *__restrict__ i
 
 __global__ void __launch_bounds__(1024)
 sort_long_rows_kernel(const int64_t *__restrict__ indptr, int32_t *__restrict__ indices,
-                      float *__restrict__ data, const int32_t *__restrict__ long_rows,
+                      float *__restrict__ data, int64_t cap, const int32_t *__restrict__ long_rows,
                       const int32_t *__restrict__ long_count) {
     __shared__ int s_col[kBlockSortMax];
     __shared__ float s_w[kBlockSortMax];
@@ -732,6 +850,7 @@ sort_long_rows_kernel(const int64_t *__restrict__ indptr, int32_t *__restrict__ 
         const int64_t i = long_rows[r];
         const int64_t b = indptr[i];
         const int L = (int)(indptr[i + 1] - b);
+        if (b + L > cap) continue;   // uniform: capacity error already recorded
         const int lp = ceil_log2(L);
         if (L <= kBlockSortMax) {
             for (int t = threadIdx.x; t < L; t += blockDim.x) {
@@ -761,60 +880,94 @@ sort_long_rows_kernel(const int64_t *__restrict__ indptr, int32_t *__restrict__ 
     }
 }
 
+template <int G, int E>
+void launch_match(const int32_t *idx, const float *dist, int64_t n, int k, const ConnShape &s, const ConnWork &w,
+                  cudaStream_t st) {
+    const unsigned blocks = (unsigned)ceil_div(n, kThreads / 32 * (32 / G));
+    match_kernel<G, E><<<blocks, kThreads, 0, st>>>(idx, dist, n, k, s.KP, s.B, s.MW, w.rs, w.ocol, w.og, w.own_cnt,
+                                                    w.in_cnt, w.bucket, w.ovf, w.in_kept, w.extra);
+}
+
+template <int G, int E>
+void launch_emit(const int32_t *idx, const float *dist, int64_t n, int k, const ConnShape &s, int64_t *indptr,
+                 int32_t *indices, float *data, int64_t cap, const ConnWork &w, cudaStream_t st) {
+    const unsigned blocks = (unsigned)ceil_div(n, kThreads / 32 * (32 / G));
+    emit_kernel<G, E><<<blocks, kThreads, 0, st>>>(n, k, s.KP, s.B, s.MW, idx, dist, w.rs, w.ocol, w.og, w.own_cnt,
+                                                   w.in_kept, w.extra, w.bucket, w.ovf, w.local, w.scan_part, indptr,
+                                                   w.cursor, indices, data, cap, w.mid_rows, w.mid_count,
+                                                   w.long_rows, w.long_count, w.status);
+}
+
+template <int E>
+void launch_smooth_warp(const int32_t *idx, const float *dist, int64_t n, int k, const ConnShape &s, float *rho_out,
+                        float *sigma_out, const ConnWork &w, unsigned blocks, cudaStream_t st) {
+    smooth_push_warp_kernel<E><<<blocks, kWarpRows * 32, 0, st>>>(idx, dist, n, k, s.KP, s.B, w.rs, rho_out,
+                                                                  sigma_out, w.part_sum, w.rho0_rows, w.rho0_count,
+                                                                  w.in_cnt, w.bucket, w.ovf, w.ocol, w.og,
+                                                                  w.own_cnt);
+}
+
 }  // namespace
+
+ConnShape conn_shape(int k) {
+    ConnShape s;
+    s.G = (k <= 16) ? 16 : 32;
+    s.E = (k <= 32) ? 1 : (k <= 64 ? 2 : (k <= 128 ? 4 : 8));
+    s.KP = (k <= 32) ? (k + 3) / 4 * 4 : 32 * s.E;
+    s.B = 2 * s.G;
+    s.MW = s.E;
+    s.smooth_rows = (k <= 32) ? kThreads : kWarpRows;
+    return s;
+}
 
 size_t conn_scan_blocks(int64_t n) { return (size_t)ceil_div(n, kScanTile); }
 
-cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, int k,
-                              int64_t *indptr, const ConnWork &w, cudaStream_t st) {
-    const int64_t total = n * (int64_t)k;
-    mean_partials_kernel<<<kMeanBlocks, kThreads, 0, st>>>(dist, total, w.partials);
-    mean_final_kernel<<<1, kMeanBlocks, 0, st>>>(w.partials, total, w.mean_all);
-    const unsigned row_blocks = (unsigned)ceil_div(n, kThreads);
-    const int KP = conn_stride(k);
-    const unsigned g16_blocks = (unsigned)ceil_div(n, kThreads / 16), g32_blocks = (unsigned)ceil_div(n, kThreads / 32);
-    if (k <= 16) {
-        smooth_row_kernel<16><<<row_blocks, kThreads, 0, st>>>(idx, dist, n, k, KP, w.mean_all, w.rho, w.sigma,
-                                                               w.scol, w.sw);
-        count_group_kernel<16><<<g16_blocks, kThreads, 0, st>>>(n, KP, w.scol, w.sw, w.gv, w.tslot, w.own_cnt,
-                                                                w.in_cnt);
-    } else if (k <= 32) {
-        smooth_row_kernel<32><<<row_blocks, kThreads, 0, st>>>(idx, dist, n, k, KP, w.mean_all, w.rho, w.sigma,
-                                                               w.scol, w.sw);
-        count_group_kernel<32><<<g32_blocks, kThreads, 0, st>>>(n, KP, w.scol, w.sw, w.gv, w.tslot, w.own_cnt,
-                                                                w.in_cnt);
-    } else {
-        smooth_warp_kernel<<<(unsigned)ceil_div(n, kWarpRows), kWarpRows * 32, 0, st>>>(
-            idx, dist, n, k, w.mean_all, w.rho, w.sigma, w.scol, w.sw);
-        count_kernel<<<row_blocks, kThreads, 0, st>>>(n, k, w.scol, w.sw, w.gv, w.own_cnt, w.in_cnt);
-    }
+size_t conn_sum_blocks(int64_t n, int k) { return (size_t)ceil_div(n, conn_shape(k).smooth_rows); }
+
+cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, int k, int64_t *indptr,
+                              float *rho_out, float *sigma_out, const ConnWork &w, cudaStream_t st) {
+    const ConnShape s = conn_shape(k);
+    const unsigned sum_blocks = (unsigned)conn_sum_blocks(n, k);
+    if (k <= 16)
+        smooth_push_row_kernel<16><<<sum_blocks, kThreads, 0, st>>>(
+            idx, dist, n, k, s.KP, s.B, w.rs, rho_out, sigma_out, w.part_sum, w.rho0_rows, w.rho0_count, w.in_cnt,
+            w.bucket, w.ovf, w.ocol, w.og, w.own_cnt);
+    else if (k <= 32)
+        smooth_push_row_kernel<32><<<sum_blocks, kThreads, 0, st>>>(
+            idx, dist, n, k, s.KP, s.B, w.rs, rho_out, sigma_out, w.part_sum, w.rho0_rows, w.rho0_count, w.in_cnt,
+            w.bucket, w.ovf, w.ocol, w.og, w.own_cnt);
+    else if (k <= 64) launch_smooth_warp<2>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
+    else if (k <= 128) launch_smooth_warp<4>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
+    else launch_smooth_warp<8>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
+    if (k <= 16) launch_match<16, 1>(idx, dist, n, k, s, w, st);
+    else if (k <= 32) launch_match<32, 1>(idx, dist, n, k, s, w, st);
+    else if (k <= 64) launch_match<32, 2>(idx, dist, n, k, s, w, st);
+    else if (k <= 128) launch_match<32, 4>(idx, dist, n, k, s, w, st);
+    else launch_match<32, 8>(idx, dist, n, k, s, w, st);
     const int64_t nb = ceil_div(n, kScanTile);
-    scan_local_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(n, w.own_cnt, w.in_cnt, indptr, w.scan_part);
-    scan_part_kernel<<<1, 1024, 0, st>>>(nb, w.scan_part, n, indptr);
-    scan_add_kernel<<<(unsigned)ceil_div(n, kScanThreads), kScanThreads, 0, st>>>(n, w.scan_part, indptr);
+    scan_local_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(n, w.own_cnt, w.in_kept, w.extra, w.local,
+                                                             w.scan_part);
+    scan_part_kernel<<<1, 1024, 0, st>>>(nb, w.scan_part, n, indptr, w.part_sum, (int64_t)sum_blocks,
+                                         n * (int64_t)k, w.rho0_rows, w.rho0_count, w.rs, sigma_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_conn_fill(int64_t n, int k, const int64_t *indptr, int32_t *indices,
-                             float *data, int64_t cap, const ConnWork &w, cudaStream_t st) {
-    const unsigned row_blocks = (unsigned)ceil_div(n, kThreads);
-    const int KP = conn_stride(k);
-    if (k <= 16) {
-        fill_group_kernel<16><<<(unsigned)ceil_div(n, kThreads / 16), kThreads, 0, st>>>(
-            n, KP, indptr, w.scol, w.gv, w.own_cnt, w.tslot, indices, data, cap, w.status);
-    } else if (k <= 32) {
-        fill_group_kernel<32><<<(unsigned)ceil_div(n, kThreads / 32), kThreads, 0, st>>>(
-            n, KP, indptr, w.scol, w.gv, w.own_cnt, w.tslot, indices, data, cap, w.status);
-    } else {
-        fill_kernel<<<row_blocks, kThreads, 0, st>>>(n, k, indptr, w.scol, w.gv, w.own_cnt, w.cursor,
-                                                     indices, data, cap, w.status);
-    }
-    sort_short_rows_kernel<<<row_blocks, kThreads, 0, st>>>(n, indptr, w.in_cnt, indices, data, cap, w.mid_rows,
-                                                            w.mid_count, w.long_rows, w.long_count);
-    sort_mid_rows_kernel<<<sm_count() * 4, kSortWarps * 32, 0, st>>>(indptr, indices, data, w.mid_rows,
+cudaError_t launch_conn_indptr(int64_t n, int64_t *indptr, const ConnWork &w, cudaStream_t st) {
+    scan_add_kernel<<<(unsigned)ceil_div(n, kScanThreads), kScanThreads, 0, st>>>(n, w.local, w.scan_part, indptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conn_fill(const int32_t *idx, const float *dist, int64_t n, int k, int64_t *indptr,
+                             int32_t *indices, float *data, int64_t cap, const ConnWork &w, cudaStream_t st) {
+    const ConnShape s = conn_shape(k);
+    if (k <= 16) launch_emit<16, 1>(idx, dist, n, k, s, indptr, indices, data, cap, w, st);
+    else if (k <= 32) launch_emit<32, 1>(idx, dist, n, k, s, indptr, indices, data, cap, w, st);
+    else if (k <= 64) launch_emit<32, 2>(idx, dist, n, k, s, indptr, indices, data, cap, w, st);
+    else if (k <= 128) launch_emit<32, 4>(idx, dist, n, k, s, indptr, indices, data, cap, w, st);
+    else launch_emit<32, 8>(idx, dist, n, k, s, indptr, indices, data, cap, w, st);
+    sort_mid_rows_kernel<<<sm_count() * 4, kSortWarps * 32, 0, st>>>(indptr, indices, data, cap, w.mid_rows,
                                                                     w.mid_count);
-    sort_long_rows_kernel<<<sm_count() * 2, 1024, 0, st>>>(indptr, indices, data, w.long_rows,
-                                                          w.long_count);
+    sort_long_rows_kernel<<<sm_count() * 2, 1024, 0, st>>>(indptr, indices, data, cap, w.long_rows, w.long_count);
     return cudaGetLastError();
 }
 

@@ -189,35 +189,46 @@ cudaError_t launch_gather_rows(const float *src, int64_t src_stride, int64_t n, 
                                float *dst, int64_t dst_stride, cudaStream_t st);
 
 // ---- connectivities.cu -------------------------------------------------------
-struct ConnWork {
-    float *partials;     // [kMeanBlocks]
-    float *mean_all;     // [1]
-    float *rho, *sigma;  // [n]
-    int32_t *scol;       // [n, KP] row's columns, ascending (INT32_MAX pads)
-    float *sw;           // [n, KP] directed weights in scol order
-    float *gv;           // [n, KP] union value of each own entry (negative: also
-                         //        emit the transposed entry)
-    int32_t *tslot;      // [n, KP] place of a transposed entry in its row (k <= 32)
-    int32_t *own_cnt;    // [n]
-    int32_t *in_cnt;     // [n]   (zeroed by the launcher)
-    int32_t *cursor;     // [n]   (zeroed by the launcher)
-    int32_t *long_rows;  // [n]
-    int32_t *long_count; // [1]   (zeroed by the launcher)
-    int32_t *mid_rows;   // [n]
-    int32_t *mid_count;  // [1]   (zeroed by the launcher)
-    int64_t *scan_part;  // [scan blocks]
-    unsigned int *status;
+// Shape of the connectivities passes for k: G lanes per row (16 or 32), E own
+// entries per lane, KP = row stride of the sorted own entries, B = bucket
+// slots per row (transposed entries that are merged in registers), MW = words
+// of the per-row overflow bit mask, smooth_rows = rows per smooth-pass block.
+struct ConnShape {
+    int G, E, KP, B, MW, smooth_rows;
 };
-constexpr int kMeanBlocks = 512;
+ConnShape conn_shape(int k);
+struct ConnWork {
+    unsigned int *status;
+    float2 *rs;          // [n] (rho, sigma)
+    float *part_sum;     // [conn_sum_blocks] distance sums of the smooth blocks
+    int32_t *rho0_rows;  // [n] rows without a non-zero distance
+    int32_t *ocol;       // [n, KP] own entries with a non-zero weight, by column (INT32_MAX pads)
+    float *og;           // [n, KP] their values (the union value after the match pass)
+    int32_t *own_cnt;    // [n]
+    int2 *bucket;        // [n, B] pushed entries (source row, weight bits)
+    uint32_t *ovf;       // [n, MW] pushes that found their target's bucket full
+    int32_t *in_kept;    // [n] bucket entries kept by the match pass
+    int64_t *local;      // [n] row offset inside its scan tile
+    int64_t *scan_part;  // [scan blocks]
+    int32_t *in_cnt;     // [n]   zeroed by the launcher: pushes per row
+    int32_t *cursor;     // [n]   zeroed by the launcher
+    int32_t *extra;      // [n]   zeroed by the launcher: flagged entries per row
+    int32_t *rho0_count; // [1]   zeroed by the launcher
+    int32_t *mid_count;  // [1]   zeroed by the launcher
+    int32_t *long_count; // [1]   zeroed by the launcher
+    int32_t *mid_rows;   // [n]
+    int32_t *long_rows;  // [n]
+};
 size_t conn_scan_blocks(int64_t n);
-// Row stride KP of scol / sw / gv: k rounded up to 4 (16-byte rows) when
-// k <= 32 (lane-per-entry kernels), else k.
-inline int conn_stride(int k) { return k <= 32 ? (k + 3) / 4 * 4 : k; }
-// Phases: rho/sigma/weights + in-degree counts + row pointers.
-cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, int k,
-                              int64_t *indptr, const ConnWork &w, cudaStream_t st);
-// Phases: CSR fill and per-row column sort.
-cudaError_t launch_conn_fill(int64_t n, int k, const int64_t *indptr, int32_t *indices,
-                             float *data, int64_t cap, const ConnWork &w, cudaStream_t st);
+size_t conn_sum_blocks(int64_t n, int k);
+// Passes smooth, match and scan: rho/sigma (rho_out/sigma_out nullable),
+// union values, buckets, tile offsets and indptr[n] = nnz.
+cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, int k, int64_t *indptr,
+                              float *rho_out, float *sigma_out, const ConnWork &w, cudaStream_t st);
+// indptr[0 .. n) from the count passes (when the CSR is not filled).
+cudaError_t launch_conn_indptr(int64_t n, int64_t *indptr, const ConnWork &w, cudaStream_t st);
+// Passes emit and sort: indptr[0 .. n), indices and data.
+cudaError_t launch_conn_fill(const int32_t *idx, const float *dist, int64_t n, int k, int64_t *indptr,
+                             int32_t *indices, float *data, int64_t cap, const ConnWork &w, cudaStream_t st);
 
 }  // namespace rsc

@@ -10,8 +10,6 @@
 // allocates nor asks the caller for a workspace.  The array is part of the
 // library's device image: every GPU that loads the library holds it until
 // the process exits.
-#include <mutex>
-
 #include "common.cuh"
 #include "kernels.h"
 
@@ -22,26 +20,18 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB, shared by 
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch, looked up once per device.  In host
-// code the array's name only stands for the symbol; a kernel needs the
-// device address that cudaGetSymbolAddress returns.
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
+// Device address of g_static_scratch in the current context.  In host code
+// the array's name only stands for the symbol; a kernel needs the device
+// address that cudaGetSymbolAddress returns.  The address belongs to the
+// context that loaded the module, so it is looked up on every call (a host
+// query, no GPU work): a cached value would go stale after cudaDeviceReset
+// or when the caller makes another context current on the same device.
 rsc_status static_scratch(void **out) {
-    int dev = 0;
-    RSC_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(RSC_ERR_UNSUPPORTED, "device index %d above %d", dev, kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || p == nullptr)
-            return fail(RSC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr)
+        return fail(RSC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+    *out = p;
     return RSC_OK;
 }
 

@@ -263,3 +263,19 @@ def test_input_rows_off_16_byte_boundary(rsc, precision):
     ai, ad = run_knn(rsc, X[1:], k, precision=precision)
     np.testing.assert_array_equal(gi, ai)
     np.testing.assert_array_equal(gd, ad)
+
+
+def test_headline_1m_on_20k_query_sample(rsc):
+    # the 1,000,000-cell x 50-PC workload (100-component mixture, k = 15) in
+    # the bench's launch configuration (automatic options: BF16 candidates on
+    # ordered rows with tile pruning, exact FP32 re-rank), and the plain FP32
+    # path, against the FP64 oracle on a seeded 20,000-query subsample
+    X = synth.mixture(1_000_000, 50, n_comp=100, seed=0)
+    q = synth.query_sample(len(X), 20_000, seed=5)
+    oi, od, on = oracle.knn(X, 15, queries=q)
+    for precision in PRECISIONS:
+        gi, gd = run_knn(rsc, X, 15, precision=precision)
+        st = check_knn(X, gi[q], gd[q], oi, od, on, rows=q, allow_miss=MISS[precision])
+        print(f"1M {precision} on 20k queries:", st)
+        assert st["recall"] >= 0.999
+        assert st["max_rel_dist_err"] <= 1e-5
