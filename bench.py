@@ -37,6 +37,7 @@ WORKLOAD = ("1,000,000 cells x 50 PCs fp32, 100-cluster Gaussian mixture (means 
 # phase, from an ncu capture summarised under profiles/; valid only while the
 # sources it was measured on are unchanged (their hash is checked).
 SEARCH_SOURCES = ("knn_tc.cuh", "knn_tc_prune.cu", "prune.cu", "topk.cuh", "tc_ptx.cuh")
+CONN_SOURCES = ("connectivities.cu",)
 TRAFFIC = {
     # window pass + list pass of the 1,000,000-cell graph (profiles/knn_tc_pruned_passes_bf16_1m.md):
     # 256.1 + 207.1 MB and 1350.3 + 114.3 MB, cold-cache under ncu; the bound kernels are not included
@@ -57,12 +58,13 @@ def launches_per_step(metric, precision, n):
     search (one launch, or 12 when pruned: window pass, 2 sphere passes, group
     spheres, tau, count, scan (2), fill, offsets, item order, list pass) and
     the re-rank;
-    rsc_connectivities: 11.
+    rsc_connectivities: 8 (smooth, push, match, two scan launches, emit and the
+    two queued-row sorts).
     """
     knn = (3 if metric == "euclidean" else 1) + 2
     if precision == "bf16":
         knn += 1 + (39 + 12 if n >= ORDER_MIN_ROWS else 0)
-    return knn + 11
+    return knn + 8
 
 
 def parse():
@@ -252,11 +254,13 @@ def run_ours(args):
     def step(prec, ws_knn, ev=None, prune=args.prune):
         arr = None
         if ev is not None:
-            arr = (ctypes.c_void_p * 4)(*[e.cuda_event for e in ev])
+            arr = (ctypes.c_void_p * 4)(*[e.cuda_event for e in ev[:4]])
         rsc.rsc_knn(Xd, k, metric, prec, workspace=ws_knn, out=(idx, dst), phase_events=arr, locality=args.locality,
                     prune=prune)
         rsc.rsc_connectivities(idx, dst, nnz_capacity=cap, workspace=ws_conn,
                                out=(indptr, indices, data, rho, sigma))
+        if ev is not None:
+            ev[4].record(stream)
 
     def barrier():
         if world > 1:
@@ -274,7 +278,7 @@ def run_ours(args):
         for _ in range(warmup):
             step(prec, ws_knn, prune=prune)
         torch.cuda.synchronize(dev)
-        phase = [make_events(4) for _ in range(steps)]
+        phase = [make_events(5) for _ in range(steps)]
         start, end = make_events(2)
         sampler = ClockSampler(_smi_id(dev)) if clocks else None
         if sampler:
@@ -295,8 +299,10 @@ def run_ours(args):
         search = [p[1].elapsed_time(p[2]) for p in phase]
         rerank = [p[2].elapsed_time(p[3]) for p in phase]
         prep = [p[0].elapsed_time(p[1]) for p in phase]
+        conn = [p[3].elapsed_time(p[4]) for p in phase]
         return ms, {"search_ms": statistics.mean(search), "rerank_ms": statistics.mean(rerank),
-                    "prep_ms": statistics.mean(prep)}, (sampler.summary() if sampler else None), ws_knn
+                    "prep_ms": statistics.mean(prep), "connectivities_ms": statistics.mean(conn)}, \
+            (sampler.summary() if sampler else None), ws_knn
 
     ms, phases, clocks, ws_knn = timed(precision, args.steps, args.warmup, clocks=True)
     scanned, pairs_total = rsc.rsc_knn_scan_stats(n, d, k, ws_knn, metric, precision, locality=args.locality,
@@ -390,6 +396,20 @@ def run_ours(args):
                 "algorithmic": "2*d flops per (query, row) pair computed: n^2 for the full scan, "
                                "128*256 per kept tile pair when pruned; time = the whole search phase"}
 
+    # the connectivities step is bound by HBM: algorithmic bytes = read idx and
+    # dist (8 n k), write indptr (8 (n + 1)), indices and data (8 nnz), rho and
+    # sigma (8 n), over its CUDA-event time inside the timed steps
+    conn_bytes = 8.0 * n * k + 8.0 * (n + 1) + 8.0 * nnz + 8.0 * n
+    conn_gbs = conn_bytes / (phases["connectivities_ms"] / 1e3) / 1e9
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    ctr = TRAFFIC.get(("connectivities.cu", "graph"))
+    roofline_conn = {"bound": "hbm", "achieved": conn_gbs, "peak": hbm, "unit": "GB/s", "frac": conn_gbs / hbm,
+                     "traffic": ctr["bytes_per_launch"] if ctr and ctr.get("kernel_sha") == _kernel_sha(CONN_SOURCES)
+                     else None,
+                     "kernel": "connectivities.cu (smooth, push, match, scan, emit, row sorts)",
+                     "peak_source": "hbm_gbs of measured" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
+                     "algorithmic": "8nk + 8(n+1) + 8 nnz + 8n bytes per graph over the step's CUDA-event time"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(X, idx_main.cpu().numpy(), dist_main.cpu().numpy(), k, args.cpu_seconds)
@@ -409,6 +429,7 @@ def run_ours(args):
                                    "frac": scanned / pairs_total}},
             "phases_ms": phases,
             "roofline": roofline,
+            "roofline_connectivities": roofline_conn,
             "cpu_baseline": cpu,
             "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

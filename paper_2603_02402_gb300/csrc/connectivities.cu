@@ -43,7 +43,6 @@ namespace rsc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr unsigned kStatusCapacity = RSC_ERR_CAPACITY;
 constexpr float kTol = 1e-5f;
 constexpr int kIters = 64;
 constexpr float kFloor = 1e-3f;
@@ -161,25 +160,35 @@ __device__ __forceinline__ int count_below(const int *s, int x) {
 
 // ---------------------------------------------------------------- smooth
 
+// 2^x by the ex2.approx.ftz.f32 instruction (PTX ISA; relative error about
+// 2^-22, subnormal results flushed to 0, which no sum below can notice).
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Bisection of one row on g[c] = d_c - rho (entries at or past k are +inf
-// and contribute exp2(-inf) = 0).  exp(-g / sigma) is evaluated as
-// exp2(g * (-log2(e) / sigma)) with one reciprocal per step, summed with
-// Neumaier compensation.
+// and contribute 2^-inf = 0).  exp(-g / sigma) is evaluated as
+// 2^(g * (-log2(e) / sigma)) with one reciprocal per step; the terms are
+// summed pairwise (a balanced tree: rounding error grows with the tree depth,
+// 4 levels for 15 terms, not with the number of terms).
 template <int KM>
 __device__ __forceinline__ float bisect_sigma(const float (&g)[KM], float target) {
     constexpr float kNegLog2e = -1.4426950408889634f;
     float lo = 0.f, hi = INFINITY, mid = 1.f;
     for (int it = 0; it < kIters; ++it) {
-        const float sc = kNegLog2e / mid;
-        float s = 0.f, comp = 0.f;
+        const float sc = kNegLog2e * __frcp_rn(mid);
+        float t[KM];
+        t[0] = 0.f;
 #pragma unroll
-        for (int c = 1; c < KM; ++c) {
-            const float t = (g[c] > 0.f) ? exp2f(g[c] * sc) : 1.f;
-            const float u = s + t;
-            comp += (fabsf(s) >= fabsf(t)) ? ((s - u) + t) : ((t - u) + s);
-            s = u;
+        for (int c = 1; c < KM; ++c) t[c] = (g[c] > 0.f) ? fast_exp2(g[c] * sc) : 1.f;
+#pragma unroll
+        for (int w = 1; w < KM; w <<= 1) {
+#pragma unroll
+            for (int c = 0; c + w < KM; c += 2 * w) t[c] += t[c + w];
         }
-        const float psum = s + comp;
+        const float psum = t[0];
         if (fabsf(psum - target) < kTol) break;
         const float prev = mid;
         if (psum > target) {
@@ -198,40 +207,20 @@ __device__ __forceinline__ float bisect_sigma(const float (&g)[KM], float target
 
 // Thread per row, k <= KM (16 or 32).  Rows without a non-zero distance get
 // the unfloored bisection result here and the global-mean floor in the scan
-// pass; their weights are all 1 and do not depend on sigma.  Every valid
-// edge takes a bucket slot of its target (entries with weight 0 fill their
-// slot and are dropped later); pushes past B with a non-zero weight set bit
-// c of ovf[i].
+// pass; their weights are all 1 and do not depend on sigma.
 template <int KM>
 __global__ void __launch_bounds__(kThreads)
-smooth_push_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP,
-                       int B, float2 *__restrict__ rs, float *__restrict__ rho_out, float *__restrict__ sigma_out,
-                       float *__restrict__ part_sum, int32_t *__restrict__ rho0_rows,
-                       int32_t *__restrict__ rho0_count, int32_t *__restrict__ in_cnt, int2 *__restrict__ bucket,
-                       uint32_t *__restrict__ ovf, int32_t *__restrict__ ocol, float *__restrict__ og,
-                       int32_t *__restrict__ own_cnt) {
+smooth_row_kernel(const float *__restrict__ dist, int64_t n, int k, float2 *__restrict__ rs,
+                  float *__restrict__ rho_out, float *__restrict__ sigma_out, float *__restrict__ part_sum,
+                  int32_t *__restrict__ rho0_rows, int32_t *__restrict__ rho0_count) {
     __shared__ float red[kThreads];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float row_sum = 0.f;
     if (i < n) {
-        const int32_t *ir = idx + i * k;
         const float *dr = dist + i * k;
-        const int me = (int)i;
-        int col[KM];
         float dd[KM];
 #pragma unroll
-        for (int c = 0; c < KM; ++c) {
-            col[c] = -1;
-            dd[c] = 0.f;
-            if (c < k) {
-                const int32_t j = ir[c];
-                dd[c] = dr[c];
-                if (j >= 0 && (int64_t)j < n && j != me) col[c] = j;
-            }
-        }
-        int slot[KM];
-#pragma unroll
-        for (int c = 0; c < KM; ++c) slot[c] = (col[c] >= 0) ? atomicAdd(in_cnt + col[c], 1) : 0;
+        for (int c = 0; c < KM; ++c) dd[c] = (c < k) ? dr[c] : 0.f;
         float r = 0.f;
         bool found = false;
 #pragma unroll
@@ -252,41 +241,76 @@ smooth_push_row_kernel(const int32_t *__restrict__ idx, const float *__restrict_
             const float floor_v = kFloor * (row_sum / (float)k);
             if (sig < floor_v) sig = floor_v;
         } else {
-            rho0_rows[atomicAdd(rho0_count, 1)] = me;
+            rho0_rows[atomicAdd(rho0_count, 1)] = (int32_t)i;
         }
         rs[i] = make_float2(r, sig);
         if (rho_out) rho_out[i] = r;
         if (sigma_out) sigma_out[i] = sig;
-        float a[KM];
-        int key[KM];
-        uint32_t spill = 0;
-        int cnt = 0;
-#pragma unroll
-        for (int c = 0; c < KM; ++c) {
-            a[c] = 0.f;
-            if (col[c] >= 0) {
-                a[c] = directed_weight(dd[c], r, sig);
-                if (slot[c] < B) bucket[(int64_t)col[c] * B + slot[c]] = make_int2(me, __float_as_int(a[c]));
-                else if (a[c] != 0.f) spill |= 1u << c;
-            }
-            key[c] = (col[c] >= 0 && a[c] != 0.f) ? col[c] : INT_MAX;
-            cnt += key[c] != INT_MAX;
-        }
-        ovf[i] = spill;
-        sort_pairs<KM>(key, a);
-        int4 *oc = reinterpret_cast<int4 *>(ocol + i * KP);
-        float4 *ow = reinterpret_cast<float4 *>(og + i * KP);
-#pragma unroll
-        for (int u = 0; u < KM / 4; ++u) {
-            if (4 * u < KP) {
-                oc[u] = make_int4(key[4 * u], key[4 * u + 1], key[4 * u + 2], key[4 * u + 3]);
-                ow[u] = make_float4(a[4 * u], a[4 * u + 1], a[4 * u + 2], a[4 * u + 3]);
-            }
-        }
-        own_cnt[i] = cnt;
     }
     const float b = block_sum(row_sum, red);
     if (threadIdx.x == 0) part_sum[blockIdx.x] = b;
+}
+
+// Thread per row, k <= KM: the directed weights; every valid edge takes a
+// bucket slot of its target (all slots' atomics are issued first; entries
+// with weight 0 fill their slot and are dropped by the match pass); pushes
+// past B with a non-zero weight set bit c of ovf[i]; the non-zero own
+// entries sorted by column into ocol / og.
+template <int KM>
+__global__ void __launch_bounds__(kThreads)
+push_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP, int B,
+                const float2 *__restrict__ rs, int32_t *__restrict__ in_cnt, int2 *__restrict__ bucket,
+                uint32_t *__restrict__ ovf, int32_t *__restrict__ ocol, float *__restrict__ og,
+                int32_t *__restrict__ own_cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t *ir = idx + i * k;
+    const float *dr = dist + i * k;
+    const int me = (int)i;
+    int col[KM];
+    float a[KM];
+#pragma unroll
+    for (int c = 0; c < KM; ++c) {
+        col[c] = -1;
+        a[c] = 0.f;
+        if (c < k) {
+            const int32_t j = ir[c];
+            a[c] = dr[c];
+            if (j >= 0 && (int64_t)j < n && j != me) col[c] = j;
+        }
+    }
+    int slot[KM];
+#pragma unroll
+    for (int c = 0; c < KM; ++c) slot[c] = (col[c] >= 0) ? atomicAdd(in_cnt + col[c], 1) : 0;
+    const float2 ri = rs[i];
+    int key[KM];
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < KM; ++c) {
+        a[c] = (col[c] >= 0) ? directed_weight(a[c], ri.x, ri.y) : 0.f;
+        key[c] = (col[c] >= 0 && a[c] != 0.f) ? col[c] : INT_MAX;
+        cnt += key[c] != INT_MAX;
+    }
+    uint32_t spill = 0;
+#pragma unroll
+    for (int c = 0; c < KM; ++c) {
+        if (col[c] >= 0) {
+            if (slot[c] < B) bucket[(int64_t)col[c] * B + slot[c]] = make_int2(me, __float_as_int(a[c]));
+            else if (a[c] != 0.f) spill |= 1u << c;
+        }
+    }
+    ovf[i] = spill;
+    sort_pairs<KM>(key, a);
+    int4 *oc = reinterpret_cast<int4 *>(ocol + i * KP);
+    float4 *ow = reinterpret_cast<float4 *>(og + i * KP);
+#pragma unroll
+    for (int u = 0; u < KM / 4; ++u) {
+        if (4 * u < KP) {
+            oc[u] = make_int4(key[4 * u], key[4 * u + 1], key[4 * u + 2], key[4 * u + 3]);
+            ow[u] = make_float4(a[4 * u], a[4 * u + 1], a[4 * u + 2], a[4 * u + 3]);
+        }
+    }
+    own_cnt[i] = cnt;
 }
 
 // Warp per row, 32 < k <= 32 E (entry c = lane + 32 e).  Flag bit of entry
@@ -630,14 +654,11 @@ scan_add_kernel(int64_t n, const int64_t *__restrict__ local, const int64_t *__r
 constexpr int kWarpSortMax = 512;
 constexpr int kBlockSortMax = 4096;
 
-__device__ __forceinline__ void put(int32_t *indices, float *data, int64_t p, int64_t cap, int c, float v,
-                                    unsigned int *status) {
-    if (p < cap) {
-        indices[p] = c;
-        data[p] = v;
-    } else {
-        record_status(status, kStatusCapacity);
-    }
+// The host launches the fill only when the CSR capacity holds nnz, so every
+// position is in range.
+__device__ __forceinline__ void put(int32_t *indices, float *data, int64_t p, int c, float v) {
+    indices[p] = c;
+    data[p] = v;
 }
 
 // G lanes per row.  A row without flagged entries: its kept bucket entries
@@ -702,12 +723,12 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int x = e * G + l;
-            if (x < oc) put(indices, data, start + x, cap, col[e], gv[e], status);
+            if (x < oc) put(indices, data, start + x, col[e], gv[e]);
         }
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int q = e * G + l;
-            if (q < ic) put(indices, data, start + oc + q, cap, src[e], wa[e], status);
+            if (q < ic) put(indices, data, start + oc + q, src[e], wa[e]);
         }
         if (l == 0) {
             const int L = oc + ic + ex;
@@ -737,10 +758,10 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int x = e * G + l;
-            if (x < oc) put(indices, data, start + x + count_below<2 * G>(si, col[e]), cap, col[e], gv[e], status);
+            if (x < oc) put(indices, data, start + x + count_below<2 * G>(si, col[e]), col[e], gv[e]);
         }
-        if (l < ic) put(indices, data, start + r0 + count_below<G * E>(so, src[0]), cap, src[0], wa[0], status);
-        if (G + l < ic) put(indices, data, start + r1 + count_below<G * E>(so, src[1]), cap, src[1], wa[1], status);
+        if (l < ic) put(indices, data, start + r0 + count_below<G * E>(so, src[0]), src[0], wa[0]);
+        if (G + l < ic) put(indices, data, start + r1 + count_below<G * E>(so, src[1]), src[1], wa[1]);
     }
     // this row's flagged edges go after the bucket entries of their targets
     if (row_ok) {
@@ -754,7 +775,7 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
                 const float a = directed_weight(dist[i * k + c], ri.x, ri.y);
                 const int slot = atomicAdd(cursor + t, 1);
                 const int64_t p = local[t] + part[t / kScanTile] + own_cnt[t] + in_kept[t] + slot;
-                put(indices, data, p, cap, (int32_t)i, a, status);
+                put(indices, data, p, (int32_t)i, a);
             }
         }
     }
@@ -928,14 +949,18 @@ cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, 
                               float *rho_out, float *sigma_out, const ConnWork &w, cudaStream_t st) {
     const ConnShape s = conn_shape(k);
     const unsigned sum_blocks = (unsigned)conn_sum_blocks(n, k);
-    if (k <= 16)
-        smooth_push_row_kernel<16><<<sum_blocks, kThreads, 0, st>>>(
-            idx, dist, n, k, s.KP, s.B, w.rs, rho_out, sigma_out, w.part_sum, w.rho0_rows, w.rho0_count, w.in_cnt,
-            w.bucket, w.ovf, w.ocol, w.og, w.own_cnt);
-    else if (k <= 32)
-        smooth_push_row_kernel<32><<<sum_blocks, kThreads, 0, st>>>(
-            idx, dist, n, k, s.KP, s.B, w.rs, rho_out, sigma_out, w.part_sum, w.rho0_rows, w.rho0_count, w.in_cnt,
-            w.bucket, w.ovf, w.ocol, w.og, w.own_cnt);
+    const unsigned row_blocks = (unsigned)ceil_div(n, kThreads);
+    if (k <= 16) {
+        smooth_row_kernel<16><<<sum_blocks, kThreads, 0, st>>>(dist, n, k, w.rs, rho_out, sigma_out, w.part_sum,
+                                                                w.rho0_rows, w.rho0_count);
+        push_row_kernel<16><<<row_blocks, kThreads, 0, st>>>(idx, dist, n, k, s.KP, s.B, w.rs, w.in_cnt, w.bucket,
+                                                              w.ovf, w.ocol, w.og, w.own_cnt);
+    } else if (k <= 32) {
+        smooth_row_kernel<32><<<sum_blocks, kThreads, 0, st>>>(dist, n, k, w.rs, rho_out, sigma_out, w.part_sum,
+                                                                w.rho0_rows, w.rho0_count);
+        push_row_kernel<32><<<row_blocks, kThreads, 0, st>>>(idx, dist, n, k, s.KP, s.B, w.rs, w.in_cnt, w.bucket,
+                                                              w.ovf, w.ocol, w.og, w.own_cnt);
+    }
     else if (k <= 64) launch_smooth_warp<2>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
     else if (k <= 128) launch_smooth_warp<4>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
     else launch_smooth_warp<8>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
