@@ -43,6 +43,7 @@ namespace rsc {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kBucket = 64;   // bucket slots per row (pushes merged in registers)
 constexpr float kTol = 1e-5f;
 constexpr int kIters = 64;
 constexpr float kFloor = 1e-3f;
@@ -73,32 +74,6 @@ __device__ __forceinline__ float directed_weight(float d, float rho, float sig) 
 __device__ __forceinline__ float fuzzy_union(float a, float b) {
     // a + b - a*b, rounded the same way whichever endpoint computes it
     return __fsub_rn(__fadd_rn(a, b), __fmul_rn(a, b));
-}
-
-// Bitonic sort of KM (key, value) pairs held in registers of one thread.
-template <int KM>
-__device__ __forceinline__ void sort_pairs(int (&key)[KM], float (&val)[KM]) {
-#pragma unroll
-    for (int size = 2; size <= KM; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-#pragma unroll
-            for (int i = 0; i < KM; ++i) {
-                const int p = i ^ stride;
-                if (p > i) {
-                    const bool asc = (i & size) == 0;
-                    if ((key[i] > key[p]) == asc) {
-                        const int tk = key[i];
-                        key[i] = key[p];
-                        key[p] = tk;
-                        const float tv = val[i];
-                        val[i] = val[p];
-                        val[p] = tv;
-                    }
-                }
-            }
-        }
-    }
 }
 
 // Ascending bitonic sort of (key, val) pairs held E per lane across a group
@@ -251,66 +226,56 @@ smooth_row_kernel(const float *__restrict__ dist, int64_t n, int k, float2 *__re
     if (threadIdx.x == 0) part_sum[blockIdx.x] = b;
 }
 
-// Thread per row, k <= KM: the directed weights; every valid edge takes a
-// bucket slot of its target (all slots' atomics are issued first; entries
-// with weight 0 fill their slot and are dropped by the match pass); pushes
-// past B with a non-zero weight set bit c of ovf[i]; the non-zero own
-// entries sorted by column into ocol / og.
-template <int KM>
+// G lanes per row (k <= G), lane c holding entry c: the directed weight;
+// every valid edge takes a bucket slot of its target (entries with weight 0
+// fill their slot and are dropped by the match pass); pushes past B with a
+// non-zero weight set bit c of ovf[i]; the non-zero own entries sorted by
+// column across the group into ocol / og.  Few registers per lane, so many
+// rows' atomics are in flight at once.
+template <int G>
 __global__ void __launch_bounds__(kThreads)
-push_row_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP, int B,
-                const float2 *__restrict__ rs, int32_t *__restrict__ in_cnt, int2 *__restrict__ bucket,
-                uint32_t *__restrict__ ovf, int32_t *__restrict__ ocol, float *__restrict__ og,
-                int32_t *__restrict__ own_cnt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t *ir = idx + i * k;
-    const float *dr = dist + i * k;
+push_group_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP, int B,
+                  const float2 *__restrict__ rs, int32_t *__restrict__ in_cnt, int2 *__restrict__ bucket,
+                  uint32_t *__restrict__ ovf, int32_t *__restrict__ ocol, float *__restrict__ og,
+                  int32_t *__restrict__ own_cnt) {
+    const int lane = threadIdx.x & 31, l = lane & (G - 1), base = lane & ~(G - 1);
+    const unsigned gbits = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
+    const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / G) + lane / G;
+    const bool row_ok = i < n;
     const int me = (int)i;
-    int col[KM];
-    float a[KM];
-#pragma unroll
-    for (int c = 0; c < KM; ++c) {
-        col[c] = -1;
-        a[c] = 0.f;
-        if (c < k) {
-            const int32_t j = ir[c];
-            a[c] = dr[c];
-            if (j >= 0 && (int64_t)j < n && j != me) col[c] = j;
+    int j = -1;
+    float d = 0.f;
+    if (row_ok && l < k) {
+        const int32_t jj = idx[i * k + l];
+        d = dist[i * k + l];
+        if (jj >= 0 && (int64_t)jj < n && jj != me) j = jj;
+    }
+    const int slot = (j >= 0) ? atomicAdd(in_cnt + j, 1) : 0;
+    float a = 0.f;
+    if (j >= 0) {
+        const float2 ri = rs[i];
+        a = directed_weight(d, ri.x, ri.y);
+    }
+    bool spill = false;
+    if (j >= 0) {
+        if (slot < B) bucket[(int64_t)j * B + slot] = make_int2(me, __float_as_int(a));
+        else spill = a != 0.f;
+    }
+    int key[1] = {(j >= 0 && a != 0.f) ? j : INT_MAX};
+    float val[1] = {a};
+    const unsigned own = (__ballot_sync(0xffffffffu, key[0] != INT_MAX) >> base) & gbits;
+    const unsigned sp = (__ballot_sync(0xffffffffu, spill) >> base) & gbits;
+    group_bitonic<G, 1>(key, val, l);
+    if (row_ok) {
+        if (l < KP) {
+            ocol[i * KP + l] = key[0];
+            og[i * KP + l] = val[0];
+        }
+        if (l == 0) {
+            own_cnt[i] = __popc(own);
+            ovf[i] = sp;
         }
     }
-    int slot[KM];
-#pragma unroll
-    for (int c = 0; c < KM; ++c) slot[c] = (col[c] >= 0) ? atomicAdd(in_cnt + col[c], 1) : 0;
-    const float2 ri = rs[i];
-    int key[KM];
-    int cnt = 0;
-#pragma unroll
-    for (int c = 0; c < KM; ++c) {
-        a[c] = (col[c] >= 0) ? directed_weight(a[c], ri.x, ri.y) : 0.f;
-        key[c] = (col[c] >= 0 && a[c] != 0.f) ? col[c] : INT_MAX;
-        cnt += key[c] != INT_MAX;
-    }
-    uint32_t spill = 0;
-#pragma unroll
-    for (int c = 0; c < KM; ++c) {
-        if (col[c] >= 0) {
-            if (slot[c] < B) bucket[(int64_t)col[c] * B + slot[c]] = make_int2(me, __float_as_int(a[c]));
-            else if (a[c] != 0.f) spill |= 1u << c;
-        }
-    }
-    ovf[i] = spill;
-    sort_pairs<KM>(key, a);
-    int4 *oc = reinterpret_cast<int4 *>(ocol + i * KP);
-    float4 *ow = reinterpret_cast<float4 *>(og + i * KP);
-#pragma unroll
-    for (int u = 0; u < KM / 4; ++u) {
-        if (4 * u < KP) {
-            oc[u] = make_int4(key[4 * u], key[4 * u + 1], key[4 * u + 2], key[4 * u + 3]);
-            ow[u] = make_float4(a[4 * u], a[4 * u + 1], a[4 * u + 2], a[4 * u + 3]);
-        }
-    }
-    own_cnt[i] = cnt;
 }
 
 // Warp per row, 32 < k <= 32 E (entry c = lane + 32 e).  Flag bit of entry
@@ -438,7 +403,7 @@ smooth_push_warp_kernel(const int32_t *__restrict__ idx, const float *__restrict
 // ----------------------------------------------------------------- match
 
 // G lanes per row, own entries E per lane (x = e * G + l), bucket entries
-// two per lane (q = e * G + l, B = 2G).  A bucket entry whose source is an
+// NB per lane (q = e * G + l, B = NB G).  A bucket entry whose source is an
 // own entry is the reverse of a mutual edge: the own value becomes
 // a + b - ab and the entry is dropped; entries with weight 0 are dropped;
 // the rest are compacted to the front of the bucket (in_kept of them).  The
@@ -446,7 +411,7 @@ smooth_push_warp_kernel(const int32_t *__restrict__ idx, const float *__restrict
 // looked up in the target's own list: a mutual one updates the target's own
 // value, the others count toward the target's row (extra) and keep their
 // flag for the emit pass.
-template <int G, int E>
+template <int G, int E, int NB>
 __global__ void __launch_bounds__(kThreads)
 match_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, int64_t n, int k, int KP, int B,
              int MW, const float2 *__restrict__ rs, const int32_t *__restrict__ ocol, float *__restrict__ og,
@@ -477,10 +442,10 @@ match_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, in
         so[x] = (x < oc) ? orow[x] : INT_MAX;
         sh[x] = 0.f;
     }
-    int src[2];
-    float wa[2];
+    int src[NB];
+    float wa[NB];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
+    for (int e = 0; e < NB; ++e) {
         const int q = e * G + l;
         src[e] = INT_MAX;
         wa[e] = 0.f;
@@ -491,9 +456,9 @@ match_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, in
         }
     }
     __syncwarp();
-    bool kept[2];
+    bool kept[NB];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
+    for (int e = 0; e < NB; ++e) {
         kept[e] = false;
         if (src[e] != INT_MAX) {
             const int p = count_below<G * E>(so, src[e]);
@@ -510,12 +475,15 @@ match_kernel(const int32_t *__restrict__ idx, const float *__restrict__ dist, in
         const int x = e * G + l;
         if (x < oc && sh[x] != 0.f) grow[x] = fuzzy_union(grow[x], sh[x]);
     }
-    const unsigned m0 = (__ballot_sync(0xffffffffu, kept[0]) >> base) & gbits;
-    const unsigned m1 = (__ballot_sync(0xffffffffu, kept[1]) >> base) & gbits;
     const unsigned lt = (1u << l) - 1u;
-    if (kept[0]) brow[__popc(m0 & lt)] = make_int2(src[0], __float_as_int(wa[0]));
-    if (kept[1]) brow[__popc(m0) + __popc(m1 & lt)] = make_int2(src[1], __float_as_int(wa[1]));
-    if (row_ok && l == 0) in_kept[i] = __popc(m0) + __popc(m1);
+    int run = 0;
+#pragma unroll
+    for (int e = 0; e < NB; ++e) {
+        const unsigned m = (__ballot_sync(0xffffffffu, kept[e]) >> base) & gbits;
+        if (kept[e]) brow[run + __popc(m & lt)] = make_int2(src[e], __float_as_int(wa[e]));
+        run += __popc(m);
+    }
+    if (row_ok && l == 0) in_kept[i] = run;
     if (!row_ok) return;   // uniform within the group; no warp-wide step follows
     const int me = (int)i;
     for (int w = 0; w < MW; ++w) {
@@ -662,13 +630,13 @@ __device__ __forceinline__ void put(int32_t *indices, float *data, int64_t p, in
 }
 
 // G lanes per row.  A row without flagged entries: its kept bucket entries
-// (at most B = 2G, two per lane) are ranked by counting (rank = entries with
+// (at most B = NB G, NB per lane) are ranked by counting (rank = entries with
 // a smaller source), written to shared memory in order, and each own and
 // bucket entry is placed at its rank in the union.  A row with flagged
 // entries gets its own and bucket entries written unsorted and is queued for
 // a whole-row sort; its flagged entries are placed by their source rows,
 // after its bucket entries.
-template <int G, int E>
+template <int G, int E, int NB>
 __global__ void __launch_bounds__(kThreads)
 emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__ idx,
             const float *__restrict__ dist, const float2 *__restrict__ rs, const int32_t *__restrict__ ocol,
@@ -679,6 +647,7 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
             int32_t *__restrict__ mid_rows, int32_t *__restrict__ mid_count, int32_t *__restrict__ long_rows,
             int32_t *__restrict__ long_count, unsigned int *status) {
     constexpr int GPW = 32 / G;   // rows per warp
+    static_assert(NB >= 2, "the bucket holds at least the 2G entries a row merges in registers");
     __shared__ int s_own[kThreads / 32][GPW][G * E];
     __shared__ int s_in[kThreads / 32][GPW][2 * G];
     const int lane = threadIdx.x & 31, l = lane & (G - 1), grp = lane / G, warp = threadIdx.x >> 5;
@@ -705,10 +674,10 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
         col[e] = (x < oc) ? orow[x] : INT_MAX;
         gv[e] = (x < oc) ? grow[x] : 0.f;
     }
-    int src[2];
-    float wa[2];
+    int src[NB];
+    float wa[NB];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
+    for (int e = 0; e < NB; ++e) {
         const int q = e * G + l;
         src[e] = INT_MAX;
         wa[e] = 0.f;
@@ -718,7 +687,9 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
             wa[e] = __int_as_float(t.y);
         }
     }
-    const bool hub = ex > 0;
+    // rows with flagged entries or more bucket entries than the merge's
+    // 2G are written unsorted and queued
+    const bool hub = ex > 0 || ic > 2 * G;
     if (hub) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -726,7 +697,7 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
             if (x < oc) put(indices, data, start + x, col[e], gv[e]);
         }
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
+        for (int e = 0; e < NB; ++e) {
             const int q = e * G + l;
             if (q < ic) put(indices, data, start + oc + q, src[e], wa[e]);
         }
@@ -736,14 +707,16 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
             else long_rows[atomicAdd(long_count, 1)] = (int32_t)i;
         }
     }
-    // ranks of the bucket entries (pads are INT_MAX and never below a key)
+    // ranks of the bucket entries (pads are INT_MAX and never below a key);
+    // merged rows hold at most 2G of them, in src[0 .. 2)
     const int icmax = __reduce_max_sync(0xffffffffu, hub ? 0 : ic);
-    int r0 = 0, r1 = 0;
+    int rk[NB];
+#pragma unroll
+    for (int e = 0; e < NB; ++e) rk[e] = 0;
     for (int t = 0; t < icmax; ++t) {
-        const int v = (t < G) ? __shfl_sync(0xffffffffu, src[0], base + t)
-                              : __shfl_sync(0xffffffffu, src[1], base + t - G);
-        r0 += v < src[0];
-        r1 += v < src[1];
+        const int v = __shfl_sync(0xffffffffu, t < G ? src[0] : src[1], base + (t & (G - 1)));
+        rk[0] += v < src[0];
+        rk[1] += v < src[1];
     }
     int *so = s_own[warp][grp];
     int *si = s_in[warp][grp];
@@ -751,8 +724,11 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
     for (int e = 0; e < E; ++e) so[e * G + l] = col[e];
     // position p < ic holds the entry of rank p, p >= ic a pad (ranks are a
     // permutation of [0, ic): sources are distinct)
-    si[(!hub && l < ic) ? r0 : l] = src[0];
-    si[(!hub && G + l < ic) ? r1 : G + l] = src[1];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int q = e * G + l;
+        si[(!hub && q < ic) ? rk[e] : q] = src[e];
+    }
     __syncwarp();
     if (row_ok && !hub) {
 #pragma unroll
@@ -760,8 +736,11 @@ emit_kernel(int64_t n, int k, int KP, int B, int MW, const int32_t *__restrict__
             const int x = e * G + l;
             if (x < oc) put(indices, data, start + x + count_below<2 * G>(si, col[e]), col[e], gv[e]);
         }
-        if (l < ic) put(indices, data, start + r0 + count_below<G * E>(so, src[0]), src[0], wa[0]);
-        if (G + l < ic) put(indices, data, start + r1 + count_below<G * E>(so, src[1]), src[1], wa[1]);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int q = e * G + l;
+            if (q < ic) put(indices, data, start + rk[e] + count_below<G * E>(so, src[e]), src[e], wa[e]);
+        }
     }
     // this row's flagged edges go after the bucket entries of their targets
     if (row_ok) {
@@ -901,19 +880,19 @@ sort_long_rows_kernel(const int64_t *__restrict__ indptr, int32_t *__restrict__ 
     }
 }
 
-template <int G, int E>
+template <int G, int E, int NB = kBucket / G>
 void launch_match(const int32_t *idx, const float *dist, int64_t n, int k, const ConnShape &s, const ConnWork &w,
                   cudaStream_t st) {
     const unsigned blocks = (unsigned)ceil_div(n, kThreads / 32 * (32 / G));
-    match_kernel<G, E><<<blocks, kThreads, 0, st>>>(idx, dist, n, k, s.KP, s.B, s.MW, w.rs, w.ocol, w.og, w.own_cnt,
+    match_kernel<G, E, NB><<<blocks, kThreads, 0, st>>>(idx, dist, n, k, s.KP, s.B, s.MW, w.rs, w.ocol, w.og, w.own_cnt,
                                                     w.in_cnt, w.bucket, w.ovf, w.in_kept, w.extra);
 }
 
-template <int G, int E>
+template <int G, int E, int NB = kBucket / G>
 void launch_emit(const int32_t *idx, const float *dist, int64_t n, int k, const ConnShape &s, int64_t *indptr,
                  int32_t *indices, float *data, int64_t cap, const ConnWork &w, cudaStream_t st) {
     const unsigned blocks = (unsigned)ceil_div(n, kThreads / 32 * (32 / G));
-    emit_kernel<G, E><<<blocks, kThreads, 0, st>>>(n, k, s.KP, s.B, s.MW, idx, dist, w.rs, w.ocol, w.og, w.own_cnt,
+    emit_kernel<G, E, NB><<<blocks, kThreads, 0, st>>>(n, k, s.KP, s.B, s.MW, idx, dist, w.rs, w.ocol, w.og, w.own_cnt,
                                                    w.in_kept, w.extra, w.bucket, w.ovf, w.local, w.scan_part, indptr,
                                                    w.cursor, indices, data, cap, w.mid_rows, w.mid_count,
                                                    w.long_rows, w.long_count, w.status);
@@ -935,7 +914,7 @@ ConnShape conn_shape(int k) {
     s.G = (k <= 16) ? 16 : 32;
     s.E = (k <= 32) ? 1 : (k <= 64 ? 2 : (k <= 128 ? 4 : 8));
     s.KP = (k <= 32) ? (k + 3) / 4 * 4 : 32 * s.E;
-    s.B = 2 * s.G;
+    s.B = kBucket;
     s.MW = s.E;
     s.smooth_rows = (k <= 32) ? kThreads : kWarpRows;
     return s;
@@ -949,17 +928,16 @@ cudaError_t launch_conn_count(const int32_t *idx, const float *dist, int64_t n, 
                               float *rho_out, float *sigma_out, const ConnWork &w, cudaStream_t st) {
     const ConnShape s = conn_shape(k);
     const unsigned sum_blocks = (unsigned)conn_sum_blocks(n, k);
-    const unsigned row_blocks = (unsigned)ceil_div(n, kThreads);
     if (k <= 16) {
         smooth_row_kernel<16><<<sum_blocks, kThreads, 0, st>>>(dist, n, k, w.rs, rho_out, sigma_out, w.part_sum,
                                                                 w.rho0_rows, w.rho0_count);
-        push_row_kernel<16><<<row_blocks, kThreads, 0, st>>>(idx, dist, n, k, s.KP, s.B, w.rs, w.in_cnt, w.bucket,
-                                                              w.ovf, w.ocol, w.og, w.own_cnt);
+        push_group_kernel<16><<<(unsigned)ceil_div(n, kThreads / 16), kThreads, 0, st>>>(
+            idx, dist, n, k, s.KP, s.B, w.rs, w.in_cnt, w.bucket, w.ovf, w.ocol, w.og, w.own_cnt);
     } else if (k <= 32) {
         smooth_row_kernel<32><<<sum_blocks, kThreads, 0, st>>>(dist, n, k, w.rs, rho_out, sigma_out, w.part_sum,
                                                                 w.rho0_rows, w.rho0_count);
-        push_row_kernel<32><<<row_blocks, kThreads, 0, st>>>(idx, dist, n, k, s.KP, s.B, w.rs, w.in_cnt, w.bucket,
-                                                              w.ovf, w.ocol, w.og, w.own_cnt);
+        push_group_kernel<32><<<(unsigned)ceil_div(n, kThreads / 32), kThreads, 0, st>>>(
+            idx, dist, n, k, s.KP, s.B, w.rs, w.in_cnt, w.bucket, w.ovf, w.ocol, w.og, w.own_cnt);
     }
     else if (k <= 64) launch_smooth_warp<2>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
     else if (k <= 128) launch_smooth_warp<4>(idx, dist, n, k, s, rho_out, sigma_out, w, sum_blocks, st);
