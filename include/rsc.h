@@ -345,7 +345,9 @@ int64_t rsc_connectivities_max_nnz(int64_t n, int32_t k);
 /*
  * Fuzzy connectivities of a kNN graph (UMAP smooth-kNN + fuzzy union).
  *   idx, dist  [n, k] as returned by rsc_knn (each row ascending by
- *              distance; slots with idx < 0 are ignored).  2 <= k <= 256.
+ *              distance, distinct ids per row; slots with idx < 0 or >= n
+ *              are ignored).  1 <= k <= 256 (with k = 1 every row lists only
+ *              itself and the graph is empty).
  *   indptr     [n + 1] int64 out; indptr[n] = nnz.
  *   indices    [nnz_capacity] int32 out, ascending within each row.
  *   data       [nnz_capacity] float32 out.
@@ -376,16 +378,19 @@ rsc_status rsc_connectivities(const int32_t *idx, const float *dist, int64_t n, 
  * rsc_connectivities, except:
  *   - scratch comes from a 32 MiB array declared by the library (held by
  *     every GPU that loads the library until the process exits); problems
- *     whose rsc_connectivities_workspace_size exceeds 32 MiB are rejected
- *     with RSC_ERR_WORKSPACE (k = 15: up to about 150,000 rows);
+ *     whose rsc_connectivities_workspace_size(n, k) exceeds 32 MiB are
+ *     rejected with RSC_ERR_WORKSPACE before any GPU work (about 700 bytes
+ *     per row at k = 15: up to 47,932 rows; up to 40,520 rows at k = 30);
  *   - nnz_capacity must be at least rsc_connectivities_max_nnz(n, k), so the
  *     call never synchronises to check the size;
- *   - the first call on a device looks up the array's device address (a
- *     host-side query, done once per device).
- * All calls share the one array: calls whose work overlaps on the GPU (on
- * different streams, or from different host threads) race and corrupt each
- * other's results.  Issue them on one stream, or order them.  The call itself
- * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - every call looks up the array's device address in the calling thread's
+ *     current context (a host query, no GPU work), so the call stays valid
+ *     after cudaDeviceReset or under a context the caller made current.
+ * All calls share the one array, which keeps the last call's contents (the
+ * call clears what must start at zero): calls whose work overlaps on the GPU
+ * (on different streams, or from different host threads) race and corrupt
+ * each other's results.  Issue them on one stream, or order them.  The call
+ * itself calls no cudaMalloc, cudaFree or other allocating routine.
  */
 rsc_status rsc_connectivities_static(const int32_t *idx, const float *dist, int64_t n, int32_t k,
                                      int64_t *indptr, int32_t *indices, float *data,

@@ -157,3 +157,41 @@ def test_autotune_table_save_load_roundtrip(L, tmp_path):
     with pytest.raises(rsc.RscError):
         rsc.rsc_autotune_load(str(bad))
     rsc.rsc_autotune_clear()
+
+
+def _static_limit(k):
+    """Largest n whose connectivities workspace fits the 32 MiB static scratch."""
+    lo, hi = 1, 10 ** 7
+    while lo < hi:
+        m = (lo + hi + 1) // 2
+        if rsc.rsc_connectivities_workspace_size(m, k) <= 32 << 20:
+            lo = m
+        else:
+            hi = m - 1
+    return lo
+
+
+@pytest.mark.parametrize("k", [15, 30])
+def test_static_connectivities_rejects_before_any_gpu_work(L, k):
+    # argument and size checks return before the scratch address is looked
+    # up; the pointers are never dereferenced
+    fake = ctypes.c_void_p(256)
+    n = _static_limit(k) + 1
+    cap = rsc.rsc_connectivities_max_nnz(n, k)
+    st = L.rsc_connectivities_static(fake, fake, n, k, fake, fake, fake, cap, None, None, None)
+    assert st == rsc.RSC_ERR_WORKSPACE
+    assert b"32 MiB" in L.rsc_last_error()
+    for bad_k in (0, 257):
+        assert L.rsc_connectivities_static(fake, fake, 100, bad_k, fake, fake, fake, 10 ** 6, None, None,
+                                           None) == rsc.RSC_ERR_INVALID_ARG
+    # a capacity below the 2 n (k - 1) bound is refused (the call never synchronises)
+    assert L.rsc_connectivities_static(fake, fake, 100, k, fake, fake, fake, rsc.rsc_connectivities_max_nnz(100, k) - 1,
+                                       None, None, None) == rsc.RSC_ERR_INVALID_ARG
+
+
+def test_connectivities_k_range(L):
+    fake = ctypes.c_void_p(256)
+    for bad_k in (0, 257):
+        assert L.rsc_connectivities(fake, fake, 10, bad_k, fake, fake, fake, 100, None, None, fake, 1 << 30,
+                                    None) == rsc.RSC_ERR_INVALID_ARG
+    assert rsc.rsc_connectivities_max_nnz(10, 1) == 0     # k = 1: every row lists only itself

@@ -72,6 +72,35 @@ def test_static_scratch_matches_workspace_entry_point(rsc):
             _static_via_abi(rsc, torch.from_numpy(other_i).cuda(), torch.from_numpy(other_d).cuda(), 5_000, 30)
 
 
+def _static_limit(rsc, k):
+    lo, hi = 1, 10 ** 7
+    while lo < hi:
+        m = (lo + hi + 1) // 2
+        if rsc.rsc_connectivities_workspace_size(m, k) <= 32 << 20:
+            lo = m
+        else:
+            hi = m - 1
+    return lo
+
+
+def test_static_scratch_size_boundary(rsc):
+    # the largest problem the 32 MiB scratch holds runs and matches the
+    # workspace entry point; one more row is refused
+    k = 15
+    n = _static_limit(rsc, k)
+    idx, dist = synth.knn_lists(n, k, seed=33)
+    it, dt = torch.from_numpy(idx).cuda(), torch.from_numpy(dist).cuda()
+    got = _static_via_abi(rsc, it, dt, n, k)
+    ref = _csr(rsc.rsc_connectivities(it, dt))
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[1], ref[1])
+    np.testing.assert_allclose(got[2], ref[2], rtol=0, atol=W_ABS)
+    idx1, dist1 = synth.knn_lists(n + 1, k, seed=34)
+    with pytest.raises(rsc.RscError) as e:
+        rsc.rsc_connectivities_static(torch.from_numpy(idx1).cuda(), torch.from_numpy(dist1).cuda())
+    assert e.value.status == rsc.RSC_ERR_WORKSPACE
+
+
 def test_static_scratch_rejects_oversized_problems(rsc):
     n, k = 400_000, 15       # needs more than the 32 MiB of static scratch
     it = torch.zeros((n, k), dtype=torch.int32, device="cuda")
