@@ -100,6 +100,21 @@ const char *rsc_version(void);
 const char *rsc_last_error(void);
 
 /*
+ * Budget, in SM clock cycles, of every bounded wait inside the tensor-core
+ * kernels (the barrier waits of the TMA producer, the MMA issuer and the
+ * epilogue); 0 restores the default of about 1 s.  A diagnostic for
+ * exercising the timeout path (the paper has no counterpart): with a budget
+ * of a few hundred cycles the first wait of a search gives up, the kernel
+ * records RSC_ERR_TIMEOUT in the workspace status word, lets its in-flight
+ * copies and MMAs finish (those drains keep the default budget), frees its
+ * tensor memory and returns; the outputs of that call are unspecified and
+ * the next call with the default budget runs normally.  Process-wide;
+ * applies to launches issued after the call.  Errors: RSC_ERR_INVALID_ARG
+ * for a negative budget.
+ */
+rsc_status rsc_set_wait_budget(int64_t clocks);
+
+/*
  * Reads and clears the status word that kernels write into `workspace`
  * (first 4 bytes).  Synchronises `stream`.  Returns RSC_OK when no kernel
  * recorded a failure, else the recorded rsc_status.

@@ -4,6 +4,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -42,6 +43,13 @@ int sm_count() {
         cached[dev] = v;
     }
     return cached[dev];
+}
+
+static std::atomic<long long> g_wait_budget{0};
+
+long long tc_wait_budget() {
+    const long long b = g_wait_budget.load(std::memory_order_relaxed);
+    return b > 0 ? b : 2000000000LL;   // default: about 1 s of SM clocks
 }
 
 // ------------------------------------------------------------------ kNN plan
@@ -416,6 +424,12 @@ extern "C" {
 const char *rsc_version(void) { return "rsc-gb300 0.1 (sm_103a)"; }
 
 const char *rsc_last_error(void) { return g_err; }
+
+rsc_status rsc_set_wait_budget(int64_t clocks) {
+    if (clocks < 0) return fail(RSC_ERR_INVALID_ARG, "negative wait budget");
+    g_wait_budget.store((long long)clocks, std::memory_order_relaxed);
+    return RSC_OK;
+}
 
 rsc_status rsc_workspace_status(void *workspace, void *stream) {
     if (!workspace) return fail(RSC_ERR_INVALID_ARG, "workspace is NULL");

@@ -101,6 +101,10 @@ cudaError_t launch_knn_tc_list(const void *Qb, const void *Db, int64_t n, int d,
                                const int64_t *tile_off, const int32_t *order, const int32_t *overflow,
                                int32_t *cand, int *counter,
                                unsigned int *status, cudaStream_t st);
+// SM clock cycles each bounded wait of the tensor-core kernels may take
+// before the kernel records RSC_ERR_TIMEOUT (process-wide, see
+// rsc_set_wait_budget).
+long long tc_wait_budget();
 int knn_tc_bm();   // query rows per tensor-core work item
 int knn_tc_bn();   // database rows per tensor-core tile
 

@@ -25,7 +25,8 @@ constexpr int NBUF = 2;              // accumulators (NBUF x BN = 512 TMEM colum
 constexpr int QBLK = BM * 128;       // bytes of one 128-row x 64-element bf16 query block
 constexpr int DBLK = BN * 128;       // bytes of one 256-row x 64-element bf16 database block
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks
+constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks: the default budget, and the
+                                                  // budget of the drains after a timeout
 constexpr uint32_t kSleepNs = 100000;             // suspend limit of one try_wait (ns)
 constexpr int kRing = 2;                          // item-index ring slots (dynamic works)
 
@@ -150,7 +151,7 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 template <int KB, int KCP, int EG, class Work>
 __global__ void __launch_bounds__(Cfg<KB, KCP, EG>::kThreads, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmD,
-              const Work work, unsigned int *status) {
+              const Work work, unsigned int *status, long long wait_budget) {
     using C = Cfg<KB, KCP, EG>;
     constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
@@ -204,14 +205,17 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     tc::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    // bounded wait: false on timeout (recorded) or when another role aborted
+    // bounded wait: false on timeout (recorded) or when another role aborted;
+    // a suspend lasts at most a quarter of the budget (in ns, at least 2
+    // clocks per ns), so the budget is checked in time even when it is short
+    const uint32_t sleep_ns = (uint32_t)min((long long)kSleepNs, wait_budget / 4);
     auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
         if (tc::mbar_try_wait(bar, parity)) return true;
         const long long t0 = clock64();
         while (true) {
-            if (tc::mbar_try_wait_sleep(bar, parity, kSleepNs)) return true;
+            if (tc::mbar_try_wait_sleep(bar, parity, sleep_ns)) return true;
             if (*abort_flag) return false;
-            if (clock64() - t0 > kWaitBudget) {
+            if (clock64() - t0 > wait_budget) {
                 *abort_flag = 1;
                 record_status(status, RSC_ERR_TIMEOUT);
                 return false;
@@ -534,7 +538,7 @@ cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, const Wo
     const int64_t items = work.count_host();
     if (items <= 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(items, sm_count());
-    kern<<<grid, C::kThreads, C::kSmem, st>>>(mq, md, work, status);
+    kern<<<grid, C::kThreads, C::kSmem, st>>>(mq, md, work, status, tc_wait_budget());
     return cudaGetLastError();
 }
 

@@ -291,7 +291,7 @@ rerank_cross_kernel(const float *__restrict__ R, int64_t rs, int64_t N, int d, i
         int id = INT_MAX;
         if (t < S && t != own && hl < n_cand) {
             const int32_t jp = cand_x[((int64_t)q * S + t) * n_cand + hl];
-            if (jp >= 0) {
+            if (jp >= 0 && (int64_t)jp < N) {   // ids outside [0, N) (an aborted search) are skipped
                 const int32_t j = perm ? perm[jp] : jp;
                 const float *yr = R + (int64_t)(r_by_pos ? jp : j) * rs;
                 float acc = row_dist2(xq, yr, d, w4);

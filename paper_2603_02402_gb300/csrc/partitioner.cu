@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kRWarps * 32)
 rerank_probe_kernel(const float *__restrict__ X, int d, const int32_t *__restrict__ qrows, int64_t q_base,
                     int64_t nq, int R,
                     const int64_t *__restrict__ gpos, const int32_t *__restrict__ cand, int per_slot,
-                    const int32_t *__restrict__ perm, int C2, int k, int32_t *__restrict__ idx,
+                    const int32_t *__restrict__ perm, int64_t n_db, int C2, int k, int32_t *__restrict__ idx,
                     float *__restrict__ dist) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -439,7 +439,7 @@ rerank_probe_kernel(const float *__restrict__ X, int d, const int32_t *__restric
         if (c < C) {
             const int r = c / per_slot;
             const int32_t j = cand[gpos[q * R + r] * per_slot + (c - r * per_slot)];
-            if (j >= 0) {
+            if (j >= 0 && (int64_t)j < n_db) {   // ids outside [0, n_db) (an aborted search) are skipped
                 const int32_t o = perm ? perm[j] : j;
                 const float *yr = X + (int64_t)o * d;
                 float acc = 0.f;
@@ -839,15 +839,15 @@ rsc_status probe_search(cudaStream_t st, const void *Dop, int64_t n_db, int64_t 
     return RSC_OK;
 }
 
-rsc_status launch_rerank_probe(cudaStream_t st, const float *X, int d, const int32_t *qrows, int64_t q_base,
-                               int64_t nq, int R, const int64_t *gpos, const int32_t *cand, const int32_t *perm,
-                               int k, int32_t *idx, float *dist) {
+rsc_status launch_rerank_probe(cudaStream_t st, const float *X, int64_t n_db, int d, const int32_t *qrows,
+                               int64_t q_base, int64_t nq, int R, const int64_t *gpos, const int32_t *cand,
+                               const int32_t *perm, int k, int32_t *idx, float *dist) {
     int C2 = 32;
     while (C2 < R * kPerSlot) C2 <<= 1;
     if (C2 > 1024) return fail(RSC_ERR_INVALID_ARG, "too many probe candidates");
     const size_t smem = sizeof(float) * part::kRWarps * 64 + (sizeof(float) + sizeof(int)) * part::kRWarps * C2;
     part::rerank_probe_kernel<<<(unsigned)ceil_div(nq, part::kRWarps), part::kRWarps * 32, smem, st>>>(
-        X, d, qrows, q_base, nq, R, gpos, cand, kPerSlot, perm, C2, k, idx, dist);
+        X, d, qrows, q_base, nq, R, gpos, cand, kPerSlot, perm, n_db, C2, k, idx, dist);
     RSC_CUDA_TRY(cudaGetLastError());
     return RSC_OK;
 }
@@ -997,7 +997,7 @@ rsc_status rsc_partitioner_train(rsc_partitioner *p, const float *X, int64_t n, 
     part::set_segment_kernel<<<1, 1, 0, st>>>(L.gcnt, (int32_t)n_train, L.doff, 0, n);
     if ((s = probe_search(st, L.Db, n, n_train, 1, L, L.doff)) != RSC_OK) return s;
     part::iota64_kernel<<<(unsigned)ceil_div(n_train, 256), 256, 0, st>>>(n_train, L.gpos);
-    if ((s = launch_rerank_probe(st, X, d, train_rows, 0, n_train, 1, L.gpos, L.cand, nullptr, k, L.nbr,
+    if ((s = launch_rerank_probe(st, X, n, d, train_rows, 0, n_train, 1, L.gpos, L.cand, nullptr, k, L.nbr,
                                  L.nbr_dist)) != RSC_OK)
         return s;
     part::gather_rows_kernel<<<(unsigned)ceil_div(n_train * d, 256), 256, 0, st>>>(train_rows, n_train, X, d, L.Xt);
@@ -1088,7 +1088,7 @@ rsc_status rsc_knn_partitioned(rsc_partitioner *p, const float *X, int64_t n, in
         // 3. each part's gathered queries against that part's database rows
         if ((s = probe_search(st, p->Db_sorted, n, slots, p->P, L, p->doff)) != RSC_OK) return s;
         // 4. merge the probed parts' candidates with the exact FP32 re-rank
-        if ((s = launch_rerank_probe(st, X, p->d, rows, q0, cq, R, L.gpos, L.cand, p->perm, k, idx + q0 * k,
+        if ((s = launch_rerank_probe(st, X, n, p->d, rows, q0, cq, R, L.gpos, L.cand, p->perm, k, idx + q0 * k,
                                      dist + q0 * k)) != RSC_OK)
             return s;
     }

@@ -55,7 +55,7 @@ rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int met
         if (c < C) {
             const int s = c / KC, slot = c - s * KC;
             const int32_t jp = cand[((int64_t)s * n + q) * KC + slot];
-            if (jp >= 0) {
+            if (jp >= 0 && (int64_t)jp < n) {   // ids outside [0, n) (an aborted search) are skipped
                 const int32_t j = perm ? perm[jp] : jp;                    // original id
                 const float *yr = R + (int64_t)(r_by_pos ? jp : j) * rs;
                 float acc = row_dist2(xq, yr, d, w4);

@@ -49,6 +49,7 @@ SIGNATURES = {
     "rsc_version": (ctypes.c_char_p, []),
     "rsc_last_error": (ctypes.c_char_p, []),
     "rsc_workspace_status": (_i32, [_vp, _vp]),
+    "rsc_set_wait_budget": (_i32, [_i64]),
     "rsc_knn_workspace_size": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts), ctypes.POINTER(_sz)]),
     "rsc_knn_scan_stats": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(rsc_knn_opts), _vp, _sz,
                                   ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -132,6 +133,12 @@ def _workspace(nbytes: int, device, workspace=None):
 
 def rsc_version() -> str:
     return lib().rsc_version().decode()
+
+
+def rsc_set_wait_budget(clocks: int) -> None:
+    """Budget (SM clock cycles) of the tensor-core kernels' bounded waits; 0
+    restores the default (about 1 s).  For exercising the timeout path."""
+    _check(lib().rsc_set_wait_budget(int(clocks)))
 
 
 def rsc_workspace_status(workspace: torch.Tensor, stream=None) -> int:

@@ -279,3 +279,26 @@ def test_headline_1m_on_20k_query_sample(rsc):
         print(f"1M {precision} on 20k queries:", st)
         assert st["recall"] >= 0.999
         assert st["max_rel_dist_err"] <= 1e-5
+
+
+def test_bounded_wait_times_out_and_the_next_call_recovers(rsc):
+    # a wait budget of a few hundred SM clocks makes the tensor-core search's
+    # first barrier wait give up: the kernel records RSC_ERR_TIMEOUT in the
+    # workspace status word (after letting its in-flight copies and MMAs
+    # finish), and the next call with the default budget is correct
+    X = synth.mixture(4097, 50, n_comp=5, seed=3)
+    oi, od, on = oracle.knn(X, 15)
+    Xd = torch.from_numpy(X).cuda()
+    ws = torch.empty(rsc.rsc_knn_workspace_size(len(X), 50, 15, "euclidean", "bf16"), dtype=torch.uint8,
+                     device="cuda")
+    rsc.rsc_set_wait_budget(300)
+    try:
+        rsc.rsc_knn(Xd, 15, precision="bf16", workspace=ws)
+        assert rsc.rsc_workspace_status(ws) == rsc.RSC_ERR_TIMEOUT
+    finally:
+        rsc.rsc_set_wait_budget(0)
+    gi, gd = rsc.rsc_knn(Xd, 15, precision="bf16", workspace=ws)
+    assert rsc.rsc_workspace_status(ws) == rsc.RSC_OK
+    check_knn(X, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, on, allow_miss=MISS["bf16"])
+    with pytest.raises(rsc.RscError):
+        rsc.rsc_set_wait_budget(-1)
