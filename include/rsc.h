@@ -59,8 +59,16 @@ typedef enum {
 
 typedef enum {
     RSC_FP32 = 0,              /* FP32 SIMT distances for candidate selection   */
-    RSC_BF16 = 1               /* BF16 tcgen05 tensor-core distances (FP32
+    RSC_BF16 = 1,              /* BF16 tcgen05 tensor-core distances (FP32
                                   accumulate) for candidate selection            */
+    RSC_FP8 = 3                /* FP8 E4M3 tcgen05 tensor-core distances (FP32
+                                  accumulate; rows scaled by one power of two
+                                  per call): half the operand bytes and MMA
+                                  time of BF16, 3 mantissa bits, so long
+                                  candidate lists (default 8k, at most 128);
+                                  full scan only (no tile pruning); d <= 59
+                                  (Euclidean) or 63 (cosine).  (Value 2 is
+                                  reserved.)                                    */
 } rsc_precision;
 
 /* Options of rsc_knn.  Zero-initialise and set what you need. */
@@ -68,7 +76,8 @@ typedef struct {
     int32_t precision;   /* rsc_precision used to select candidates          */
     int32_t candidates;  /* candidates kept per query before the exact FP32
                             re-rank; 0 = default (k + 8 for FP32, 2k for BF16
-                            Euclidean, 4k for BF16 cosine, at most 64 / 128);
+                            Euclidean, 4k for BF16 cosine, 8k for FP8, at
+                            most 64 / 128);
                             rounded up to a supported width (16, 32, 64)  */
     int32_t db_splits;   /* split the database into this many ranges handled
                             by separate CTAs (small n); 0 = automatic          */

@@ -75,7 +75,8 @@ struct KnnLayout {
     float *Y;
     float *ny;
     float *prep_scratch;
-    void *Qb, *Db;       // BF16 operands (tensor-core path only)
+    void *Qb, *Db;       // BF16 or FP8 operands (tensor-core path only)
+    unsigned int *amax;  // largest |y| (FP8 scale), FP8 only
     int32_t *cand;
     int32_t *perm;       // locality order (sorted position -> row), when planned
     void *order_scratch;
@@ -94,7 +95,7 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     const int dmax = (metric == RSC_COSINE) ? 63 : 64;
     if (d < 1 || d > dmax) return fail(RSC_ERR_INVALID_ARG, "d=%d out of [1, %d]", d, dmax);
     if (k < 1 || k > 64 || k > n) return fail(RSC_ERR_INVALID_ARG, "k=%d out of [1, min(n, 64)]", k);
-    if (o->precision != RSC_FP32 && o->precision != RSC_BF16)
+    if (o->precision != RSC_FP32 && o->precision != RSC_BF16 && o->precision != RSC_FP8)
         return fail(RSC_ERR_INVALID_ARG, "unknown precision %d", o->precision);
     if (o->candidates < 0 || o->db_splits < 0) return fail(RSC_ERR_INVALID_ARG, "negative option");
     if (o->tc_parts != 0 && o->tc_parts != 2 && o->tc_parts != 4)
@@ -115,26 +116,36 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     p->precision = o->precision;
     p->d = d;
     p->metric = metric;
-    p->order = o->precision == RSC_BF16 && (o->locality == 2 || (o->locality == 0 && n >= kOrderMinRows));
+    const bool tc = o->precision == RSC_BF16 || o->precision == RSC_FP8;   // tensor-core candidate search
+    p->order = tc && (o->locality == 2 || (o->locality == 0 && n >= kOrderMinRows));
     p->DP = ((d + (metric == RSC_COSINE ? 1 : 0) + 7) / 8) * 8;
     int want = o->candidates;
     // BF16 candidates: 2k for Euclidean rows; unit-length cosine rows crowd
     // their distances together, so BF16 rounding reorders more of them: 4k
-    if (want == 0) want = (p->precision == RSC_FP32) ? k + 8 : (metric == RSC_COSINE ? 4 * k : 2 * k);
+    // defaults: FP32 lists are exact up to ties (k + 8); BF16 needs 2k
+    // (Euclidean) or 4k (cosine: unit-length rows crowd their distances);
+    // E4M3's 3 mantissa bits need 8k
+    if (want == 0)
+        want = (p->precision == RSC_FP32) ? k + 8
+               : (p->precision == RSC_FP8) ? 8 * k
+                                           : (metric == RSC_COSINE ? 4 * k : 2 * k);
     if (want < k) return fail(RSC_ERR_INVALID_ARG, "candidates=%d smaller than k=%d", want, k);
     if (want > 64) {
         if (o->candidates != 0 && p->precision == RSC_FP32)
             return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 64", want);
         if (o->candidates > 128) return fail(RSC_ERR_INVALID_ARG, "candidates=%d above 128", want);
         if (o->candidates == 0)
-            want = (metric == RSC_COSINE && p->precision == RSC_BF16) ? std::min(want, 128) : 64;
+            want = ((metric == RSC_COSINE && p->precision == RSC_BF16) || p->precision == RSC_FP8) ? std::min(want, 128)
+                                                                                                  : 64;
     }
     // candidates per row: FP32 lists of KC; tensor-core rows as parts x list
-    const bool tc = p->precision == RSC_BF16;
     p->KC = 0;
     p->parts = 1;
     if (tc) {
         if (!knn_tc_supported(d, metric)) return fail(RSC_ERR_UNSUPPORTED, "no tensor-core kernel for d=%d", d);
+        if (p->precision == RSC_FP8 && !knn_tc_fp8_supported(d, metric))
+            return fail(RSC_ERR_UNSUPPORTED, "no FP8 kernel for d=%d (d + %d <= 64)", d,
+                        metric == RSC_EUCLIDEAN ? 5 : 1);
         TcShape sh = knn_tc_shape(d, metric, k, want, o->tc_parts);
         if (sh.parts == 0) return fail(RSC_ERR_UNSUPPORTED, "no tensor-core list shape for k=%d candidates=%d", k, want);
         p->parts = sh.parts;
@@ -157,8 +168,8 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
     if (splits * per_split > 1024) return fail(RSC_ERR_INVALID_ARG, "db_splits * candidates above 1024");
     p->split_len = ceil_div(ceil_div(n, splits), align) * align;
     p->splits = (int)ceil_div(n, p->split_len);
-    // pruning: rows in locality order, one database split, one 64-element K block
-    const bool prune_ok = p->order && p->splits == 1 && tc && tc_kb(d, metric) == 1;
+    // pruning: BF16 rows in locality order, one database split, one 64-element K block
+    const bool prune_ok = p->order && p->splits == 1 && p->precision == RSC_BF16 && tc_kb(d, metric) == 1;
     if (o->prune == 2 && !prune_ok)
         return fail(RSC_ERR_UNSUPPORTED, "prune needs BF16, the locality ordering, one database split and d + 3 <= 64");
     p->prune = prune_ok && o->prune != 1;
@@ -173,9 +184,14 @@ KnnLayout carve_knn(void *ws, int64_t n, const KnnPlan &p, size_t *bytes) {
     L.ny = cv.take<float>((size_t)n);
     L.prep_scratch = cv.take<float>(prep_scratch_floats());
     L.Qb = L.Db = nullptr;
+    L.amax = nullptr;
     if (p.precision == RSC_BF16) {
         L.Qb = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
         L.Db = cv.take<uint16_t>((size_t)n * 64 * tc_kb(p.d, p.metric));
+    } else if (p.precision == RSC_FP8) {
+        L.Qb = cv.take<uint8_t>((size_t)n * 64);
+        L.Db = cv.take<uint8_t>((size_t)n * 64);
+        L.amax = cv.take<unsigned int>(1);
     }
     L.cand = cv.take<int32_t>((size_t)p.splits * p.parts * n * p.KC);
     L.perm = nullptr;
@@ -484,6 +500,12 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
             RSC_CUDA_TRY(launch_knn_tc(L.Qb, L.Db, n, d, metric, sh, p.splits, p.split_len,
                                        p.order ? kOrderWindow : 0, L.cand, L.status, st));
         }
+    } else if (p.precision == RSC_FP8) {
+        if (p.order) RSC_CUDA_TRY(launch_locality_order(L.Y, n, p.DP, kOrderIters, L.perm, L.order_scratch, st));
+        RSC_CUDA_TRY(launch_prep_fp8(L.Y, n, d, p.DP, metric, L.perm, L.Qb, L.Db, L.amax, st));
+        if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
+        RSC_CUDA_TRY(launch_knn_tc_fp8(L.Qb, L.Db, n, d, metric, TcShape{p.parts, p.KC}, p.splits, p.split_len,
+                                       p.order ? kOrderWindow : 0, L.cand, L.status, st));
     } else {
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
         RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
@@ -514,7 +536,7 @@ rsc_status rsc_knn_scan_stats(int64_t n, int32_t d, int32_t k, int32_t metric, c
     size_t need = 0;
     carve_knn(nullptr, n, p, &need);
     if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
-    const int BM = knn_tc_bm(), BN = p.precision == RSC_BF16 ? knn_tc_bn() : BM;
+    const int BM = knn_tc_bm(), BN = p.precision != RSC_FP32 ? knn_tc_bn() : BM;
     const int64_t qt = ceil_div(n, BM), dt = ceil_div(n, BN);
     *pairs_total = qt * dt;
     *pairs_scanned = *pairs_total;

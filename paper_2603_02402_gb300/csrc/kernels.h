@@ -47,6 +47,17 @@ cudaError_t launch_prep_bf16(const float *Y, int64_t n, int d, int DP, int metri
 cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int metric, TcShape sh, int splits,
                           int64_t split_len, int window, int32_t *cand, unsigned int *status, cudaStream_t st);
 
+// ---- knn_tc_fp8.cu --------------------------------------------------------
+// FP8 (E4M3) variant of the tensor-core search: Qf/Df [n, 64] bytes built by
+// launch_prep_fp8 (one power-of-two scale per call from the largest |y|,
+// written to *amax), full scan (window first on ordered rows), candidate
+// lists as launch_knn_tc.
+bool knn_tc_fp8_supported(int d, int metric);
+cudaError_t launch_prep_fp8(const float *Y, int64_t n, int d, int DP, int metric, const int32_t *perm, void *Qf,
+                            void *Df, unsigned int *amax, cudaStream_t st);
+cudaError_t launch_knn_tc_fp8(const void *Qf, const void *Df, int64_t n, int d, int metric, TcShape sh, int splits,
+                              int64_t split_len, int window, int32_t *cand, unsigned int *status, cudaStream_t st);
+
 // ---- order.cu -------------------------------------------------------------------
 // Locality ordering: two-level k-means (C1 coarse clusters, then C2 sub-
 // clusters inside each; Lloyd on strided samples), then a stable counting

@@ -123,52 +123,6 @@ prep_bf16_kernel(const float *__restrict__ Y, int64_t n, int d, int DP, int metr
     }
 }
 
-// Whole-matrix work: query tile qt (BM rows) x database split sp.
-struct PlainWork {
-    static constexpr int kShort = 0;   // never used (short_list is false)
-    static constexpr bool kResume = false;
-    static constexpr bool kHitHeavy = false;
-    static constexpr bool kStartBelow = false;
-    static constexpr bool kDynamic = false;
-    int64_t n;
-    int splits;
-    int64_t split_len;
-    int32_t *cand;    // [splits * EG, n, KCP]
-    int n_items;
-    int window;       // tiles on either side of the query tile scanned first (0: none)
-
-    int64_t count_host() const { return n_items; }
-    __device__ __forceinline__ int count() const { return n_items; }
-    __device__ __forceinline__ WorkItem get(int it) const {
-        const int qt = it / splits, sp = it - qt * splits;
-        WorkItem w;
-        w.q0 = (int64_t)qt * BM;
-        w.q_end = min(n, w.q0 + BM);
-        w.j_begin = (int64_t)sp * split_len;
-        w.j_end = min(n, w.j_begin + split_len);
-        w.tag = sp;
-        w.short_list = false;
-        w.win_lo = w.win_hi = w.win_c = 0;
-        w.tiles = nullptr;
-        w.n_tiles = 0;
-        w.skip_window = false;
-        if (window > 0 && w.q0 >= w.j_begin && w.q0 < w.j_end) {
-            const int T = (int)((w.j_end - w.j_begin + BN - 1) / BN);
-            const int tq = (int)((w.q0 - w.j_begin) / BN);
-            w.win_lo = max(0, tq - window);
-            w.win_hi = min(T, tq + window + 1);
-            w.win_c = tq;
-        }
-        return w;
-    }
-    template <int EG, int KCP>
-    __device__ __forceinline__ void emit(const WorkItem &w, int part, int64_t q, const RowTopK<KCP> &list) const {
-        int32_t *out = cand + ((int64_t)(w.tag * EG + part) * n + q) * KCP;
-#pragma unroll
-        for (int c = 0; c < KCP; ++c) out[c] = list.id[c];
-    }
-};
-
 // --------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -195,6 +149,20 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB, int
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// [rows, 64] FP8 bytes, box_rows x 64-byte boxes, 64-byte swizzle
+cudaError_t make_map_fp8(CUtensorMap *m, const void *base, int64_t rows, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {64};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }

@@ -24,6 +24,9 @@ constexpr int NBUF = 2;              // accumulators (NBUF x BN = 512 TMEM colum
                                      // buffer of tile g is g & 1, its phase (g >> 1) & 1
 constexpr int QBLK = BM * 128;       // bytes of one 128-row x 64-element bf16 query block
 constexpr int DBLK = BN * 128;       // bytes of one 256-row x 64-element bf16 database block
+// Operand element size EB: 2 = BF16 (128-byte rows, kind::f16 MMAs of K = 16,
+// 128-byte swizzle), 1 = FP8 E4M3 (64-byte rows, kind::f8f6f4 MMAs of K = 32,
+// 64-byte swizzle); a 64-element K block is 64 * EB bytes of every row.
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitBudget = 2000000000LL;   // ~1 s of SM clocks: the default budget, and the
                                                   // budget of the drains after a timeout
@@ -32,7 +35,7 @@ constexpr int kRing = 2;                          // item-index ring slots (dyna
 
 // EG epilogue warpgroups, each owning kCols = BN / EG columns of every tile;
 // KCP = top-k list length per (row, part).
-template <int KB, int KCP, int EG>
+template <int KB, int KCP, int EG, int EB = 2>
 struct Cfg {
     static constexpr int kCols = BN / EG;
     static constexpr int kEpiThreads = EG * 128;
@@ -43,8 +46,10 @@ struct Cfg {
     // tiles often improve some list (Work::kHitHeavy: the pruned passes; a
     // full scan mostly rejects whole tiles and keeps one vote per tile)
     static constexpr bool kResident = EG == 2 && KCP == 16;
-    static constexpr int kQBytes = KB * QBLK;
-    static constexpr int kStageBytes = KB * DBLK;
+    static constexpr int kQBlk = BM * 64 * EB;    // bytes of one 64-element query K block
+    static constexpr int kDBlk = BN * 64 * EB;    // bytes of one 64-element database K block
+    static constexpr int kQBytes = KB * kQBlk;
+    static constexpr int kStageBytes = KB * kDBlk;
     static constexpr int kBufBytes = kCap * kEpiThreads * 8;
     static constexpr int kBudget = 224 * 1024 - kQBytes - kBufBytes;
     static constexpr int kStages = (kBudget / kStageBytes) > 6 ? 6 : (kBudget / kStageBytes);
@@ -148,11 +153,11 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>(a);
 }
 
-template <int KB, int KCP, int EG, class Work>
-__global__ void __launch_bounds__(Cfg<KB, KCP, EG>::kThreads, 1)
+template <int KB, int KCP, int EG, class Work, int EB = 2>
+__global__ void __launch_bounds__(Cfg<KB, KCP, EG, EB>::kThreads, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmD,
               const Work work, unsigned int *status, long long wait_budget) {
-    using C = Cfg<KB, KCP, EG>;
+    using C = Cfg<KB, KCP, EG, EB>;
     constexpr int S = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
@@ -286,7 +291,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 if (!(ok = wait(q_empty, (item_no & 1) ^ 1))) break;
                 tc::mbar_arrive_expect_tx(q_full, C::kQBytes);
                 for (int kb = 0; kb < KB; ++kb)
-                    tc::tma_load_2d(sQ + kb * QBLK, &tmQ, kb * 64, (int)wi.q0, q_full);
+                    tc::tma_load_2d(sQ + kb * C::kQBlk, &tmQ, kb * 64, (int)wi.q0, q_full);
                 q_issued = true;
                 q_parity = item_no & 1;
                 const int jb = (int)j_begin, T = (int)((j_end - j_begin + BN - 1) / BN);
@@ -298,7 +303,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                     tc::mbar_arrive_expect_tx(&full[s], C::kStageBytes);
                     const int j0 = jb + sq.m * BN;
                     for (int kb = 0; kb < KB; ++kb)
-                        tc::tma_load_2d(sD + (s * KB + kb) * DBLK, &tmD, kb * 64, j0, &full[s]);
+                        tc::tma_load_2d(sD + (s * KB + kb) * C::kDBlk, &tmD, kb * 64, j0, &full[s]);
                 }
             }
             if (!ok) {
@@ -311,7 +316,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------ MMA issuer
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            constexpr uint32_t idesc = EB == 2 ? tc::idesc_bf16_f32(BM, BN) : tc::idesc_e4m3_f32(BM, BN);
             uint32_t gt = 0;
             int item_no = 0;
             bool ok = true;
@@ -334,12 +339,20 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                     const uint32_t d_tmem = tmem_base + b * BN;
 #pragma unroll
                     for (int kb = 0; kb < KB; ++kb) {
-                        const uint32_t a_addr = tc::smem_u32(sQ + kb * QBLK);
-                        const uint32_t b_addr = tc::smem_u32(sD + (s * KB + kb) * DBLK);
+                        const uint32_t a_addr = tc::smem_u32(sQ + kb * C::kQBlk);
+                        const uint32_t b_addr = tc::smem_u32(sD + (s * KB + kb) * C::kDBlk);
+                        if constexpr (EB == 2) {   // four K = 16 steps of 32 bytes in a 128-byte row
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            tc::mma_bf16(d_tmem, tc::smem_desc_sw128(a_addr + kk * 32),
-                                         tc::smem_desc_sw128(b_addr + kk * 32), idesc, (kb | kk) != 0);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                tc::mma_bf16(d_tmem, tc::smem_desc_sw128(a_addr + kk * 32),
+                                             tc::smem_desc_sw128(b_addr + kk * 32), idesc, (kb | kk) != 0);
+                            }
+                        } else {                   // two K = 32 steps of 32 bytes in a 64-byte row
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                tc::mma_f8(d_tmem, tc::smem_desc_sw64(a_addr + kk * 32),
+                                           tc::smem_desc_sw64(b_addr + kk * 32), idesc, (kb | kk) != 0);
+                            }
                         }
                     }
                     tc::mma_commit(&acc_full[b]);   // accumulator ready for the epilogue
@@ -528,11 +541,57 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     }
 }
 
-template <int KB, int KCP, int EG, class Work>
+// Whole-matrix work: query tile qt (BM rows) x database split sp.
+struct PlainWork {
+    static constexpr int kShort = 0;   // never used (short_list is false)
+    static constexpr bool kResume = false;
+    static constexpr bool kHitHeavy = false;
+    static constexpr bool kStartBelow = false;
+    static constexpr bool kDynamic = false;
+    int64_t n;
+    int splits;
+    int64_t split_len;
+    int32_t *cand;    // [splits * EG, n, KCP]
+    int n_items;
+    int window;       // tiles on either side of the query tile scanned first (0: none)
+
+    int64_t count_host() const { return n_items; }
+    __device__ __forceinline__ int count() const { return n_items; }
+    __device__ __forceinline__ WorkItem get(int it) const {
+        const int qt = it / splits, sp = it - qt * splits;
+        WorkItem w;
+        w.q0 = (int64_t)qt * BM;
+        w.q_end = min(n, w.q0 + BM);
+        w.j_begin = (int64_t)sp * split_len;
+        w.j_end = min(n, w.j_begin + split_len);
+        w.tag = sp;
+        w.short_list = false;
+        w.win_lo = w.win_hi = w.win_c = 0;
+        w.tiles = nullptr;
+        w.n_tiles = 0;
+        w.skip_window = false;
+        if (window > 0 && w.q0 >= w.j_begin && w.q0 < w.j_end) {
+            const int T = (int)((w.j_end - w.j_begin + BN - 1) / BN);
+            const int tq = (int)((w.q0 - w.j_begin) / BN);
+            w.win_lo = max(0, tq - window);
+            w.win_hi = min(T, tq + window + 1);
+            w.win_c = tq;
+        }
+        return w;
+    }
+    template <int EG, int KCP>
+    __device__ __forceinline__ void emit(const WorkItem &w, int part, int64_t q, const RowTopK<KCP> &list) const {
+        int32_t *out = cand + ((int64_t)(w.tag * EG + part) * n + q) * KCP;
+#pragma unroll
+        for (int c = 0; c < KCP; ++c) out[c] = list.id[c];
+    }
+};
+
+template <int KB, int KCP, int EG, class Work, int EB = 2>
 cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, const Work &work, unsigned int *status,
                           cudaStream_t st) {
-    using C = Cfg<KB, KCP, EG>;
-    auto kern = knn_tc_kernel<KB, KCP, EG, Work>;
+    using C = Cfg<KB, KCP, EG, EB>;
+    auto kern = knn_tc_kernel<KB, KCP, EG, Work, EB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return e;
     const int64_t items = work.count_host();
@@ -543,6 +602,8 @@ cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, const Wo
 }
 
 cudaError_t make_map(CUtensorMap *m, const void *base, int64_t rows, int KB, int box_rows);
+// [rows, 64] FP8 bytes, box_rows x 64-byte boxes, 64-byte swizzle
+cudaError_t make_map_fp8(CUtensorMap *m, const void *base, int64_t rows, int box_rows);
 
 }  // namespace tck
 }  // namespace rsc

@@ -108,6 +108,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f8f6f4 (8-bit A and B of the types
+// named in the instruction descriptor, FP32 accumulate; K = 32 per MMA)
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on `bar` once every tcgen05 op this thread issued so far has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -160,6 +172,28 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     desc |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
     desc |= (uint64_t)2 << 61;                           // swizzle: 128 B
     return desc;
+}
+
+// Shared-memory matrix descriptor: K-major tile whose rows are 64 bytes,
+// 64-byte swizzle, 8-row core-matrix groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+    uint64_t desc = 0;
+    desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);         // start address
+    desc |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+    desc |= (uint64_t)(512u >> 4) << 32;                 // stride byte offset: 8 rows x 64 B
+    desc |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
+    desc |= (uint64_t)4 << 61;                           // swizzle: 64 B
+    return desc;
+}
+
+// Instruction descriptor, kind::f8f6f4: E4M3 A and B (type code 0, K-major),
+// FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(uint32_t M, uint32_t N) {
+    return (1u << 4)            // D format: F32
+           | (0u << 7)          // A format: E4M3
+           | (0u << 10)         // B format: E4M3
+           | ((N >> 3) << 17)   // N / 8
+           | ((M >> 4) << 24);  // M / 16
 }
 
 // Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M x N.

@@ -21,10 +21,10 @@ LIB_PATH = os.path.join(_PKG, "_lib", "librsc.so")
 RSC_OK, RSC_ERR_INVALID_ARG, RSC_ERR_CUDA, RSC_ERR_WORKSPACE, RSC_ERR_TIMEOUT, \
     RSC_ERR_UNSUPPORTED, RSC_ERR_CAPACITY = range(7)
 RSC_EUCLIDEAN, RSC_COSINE = 0, 1
-RSC_FP32, RSC_BF16 = 0, 1
+RSC_FP32, RSC_BF16, RSC_FP8 = 0, 1, 3
 
 _METRICS = {"euclidean": RSC_EUCLIDEAN, "cosine": RSC_COSINE}
-_PRECISIONS = {"fp32": RSC_FP32, "bf16": RSC_BF16}
+_PRECISIONS = {"fp32": RSC_FP32, "bf16": RSC_BF16, "fp8": RSC_FP8}
 
 _lock = threading.Lock()
 _lib = None

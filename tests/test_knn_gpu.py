@@ -31,9 +31,9 @@ def run_knn(rsc, X, k, metric="euclidean", precision="fp32", **kw):
     return idx.cpu().numpy(), dist.cpu().numpy()
 
 
-PRECISIONS = ["fp32", "bf16"]
-# BF16 candidate search + exact re-rank targets recall@k >= 0.999; FP32 is exact
-MISS = {"fp32": 0.0, "bf16": 1e-3}
+PRECISIONS = ["fp32", "bf16", "fp8"]
+# BF16 / FP8 candidate search + exact re-rank targets recall@k >= 0.999; FP32 is exact
+MISS = {"fp32": 0.0, "bf16": 1e-3, "fp8": 1e-3}
 
 
 def _maybe(rsc, fn):
@@ -265,6 +265,17 @@ def test_input_rows_off_16_byte_boundary(rsc, precision):
     np.testing.assert_array_equal(gd, ad)
 
 
+def test_fp8_on_ordered_rows(rsc):
+    # 30,000 rows take the locality ordering (window first, no pruning for
+    # FP8); default candidates (8k, at most 128)
+    X = synth.mixture(30_000, 50, n_comp=20, seed=21)
+    q = synth.query_sample(len(X), 400, seed=21)
+    oi, od, on = oracle.knn(X, 15, queries=q)
+    gi, gd = run_knn(rsc, X, 15, precision="fp8")
+    st = check_knn(X, gi[q], gd[q], oi, od, on, rows=q, allow_miss=MISS["fp8"])
+    assert st["recall"] >= 0.999
+
+
 def test_headline_1m_on_20k_query_sample(rsc):
     # the 1,000,000-cell x 50-PC workload (100-component mixture, k = 15) in
     # the bench's launch configuration (automatic options: BF16 candidates on
@@ -273,7 +284,7 @@ def test_headline_1m_on_20k_query_sample(rsc):
     X = synth.mixture(1_000_000, 50, n_comp=100, seed=0)
     q = synth.query_sample(len(X), 20_000, seed=5)
     oi, od, on = oracle.knn(X, 15, queries=q)
-    for precision in PRECISIONS:
+    for precision in ("bf16", "fp32"):
         gi, gd = run_knn(rsc, X, 15, precision=precision)
         st = check_knn(X, gi[q], gd[q], oi, od, on, rows=q, allow_miss=MISS[precision])
         print(f"1M {precision} on 20k queries:", st)
