@@ -621,14 +621,22 @@ def run_partitioner(args):
     ms = ev[4].elapsed_time(ev[5]) / args.steps
     thr = ed[:, -1:] * (1 + 1e-6)
     recall = float((out[1] <= thr).float().mean())
-    step("centroids")
-    torch.cuda.synchronize()
-    recall_c = float((out[1] <= thr).float().mean())
+    # recall against the exact path for 1, 2, 4 and 8 probed parts, with the
+    # network's routing and with nearest-centroid routing (same parts, same
+    # candidate budget: the method without the network)
+    curves = {"network": {}, "centroids": {}}
+    for routing in ("network", "centroids"):
+        for pr in (1, 2, 4, 8):
+            part.knn(Xd, k=k, n_probe=pr, routing=routing, workspace=ws, out=out)
+            torch.cuda.synchronize()
+            curves[routing][pr] = float((out[1] <= thr).float().mean())
+    recall_c = curves["centroids"][probes]
     line = {"metric": "partitioned neighbors graph cells/s (5M cells, 50 PCs, k=15, 8 of 1024 parts probed)",
             "value": n / (ms / 1e3), "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic", "config": {"workload": PARTITION_WORKLOAD, "n": n, "k": k, "probes": probes},
             "recall_at_k_vs_exact": recall, "recall_at_k_centroid_routing": recall_c,
+            "recall_vs_probes": curves,
             "exact_bf16_knn_ms": exact_ms, "exact_bf16_cells_per_s": n / (exact_ms / 1e3),
             "train_ms": train_ms, "train_final_loss": loss, "clocks": sampler.summary()}
     if rank == 0:

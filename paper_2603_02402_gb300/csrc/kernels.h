@@ -58,6 +58,15 @@ cudaError_t launch_prep_fp8(const float *Y, int64_t n, int d, int DP, int metric
 cudaError_t launch_knn_tc_fp8(const void *Qf, const void *Df, int64_t n, int d, int metric, TcShape sh, int splits,
                               int64_t split_len, int window, int32_t *cand, unsigned int *status, cudaStream_t st);
 
+// ---- mlp_tc.cu ------------------------------------------------------------------
+// C[m, n] = sum_k A(m, k) B(k, n) (+ bias[n]) on the tensor cores (operands
+// rounded to BF16, FP32 accumulation), A(m, k) = A[m*sam + k*sak], B(k, n) =
+// B[k*sbk + n*sbn]; flags 4 / 8: ReLU on A / B as they are read.  Bounded
+// waits record RSC_ERR_TIMEOUT in *status.
+cudaError_t launch_tc_gemm(cudaStream_t st, int M, int N, int K, const float *A, int64_t sam, int64_t sak,
+                           const float *B, int64_t sbk, int64_t sbn, float *C, int64_t ldc, const float *bias,
+                           int flags, unsigned int *status);
+
 // ---- order.cu -------------------------------------------------------------------
 // Locality ordering: two-level k-means (C1 coarse clusters, then C2 sub-
 // clusters inside each; Lloyd on strided samples), then a stable counting

@@ -7,9 +7,10 @@
 //   labels    each training cell's exact k nearest cells (brute force over
 //             the whole data set, tensor-core search + exact re-rank) give a
 //             soft target: the histogram of those neighbours' cells
-//   network   MLP d -> H -> H -> P (ReLU), trained on the GPU with this
-//             file's kernels: SIMT GEMMs with bfloat16-rounded weights and
-//             activations and FP32 accumulation, softmax cross-entropy, Adam
+//   network   MLP d -> H -> H -> P (ReLU), trained on the GPU with the
+//             library's kernels: tcgen05 tensor-core GEMMs (mlp_tc.cu) with
+//             bfloat16 operands and FP32 accumulation (a SIMT GEMM in the
+//             FP32-weight mode), softmax cross-entropy, Adam
 //   index     every database cell goes to the part its network output ranks
 //             first; rows are counting-sorted by part
 //   search    each query probes the n_probe parts its network ranks highest
@@ -550,6 +551,7 @@ struct rsc_partitioner {
     int32_t *perm = nullptr;      // sorted position -> row
     int64_t *doff = nullptr;      // [P + 1]
     void *Db_sorted = nullptr;    // [n_db, 64] bf16 operand rows in part order
+    unsigned int *status = nullptr;   // device word: failures of the training kernels
 };
 
 namespace {
@@ -567,13 +569,29 @@ int64_t b2_off(const rsc_partitioner *p) { return w2_off(p) + (int64_t)p->H * p-
 int64_t w3_off(const rsc_partitioner *p) { return b2_off(p) + p->H; }
 int64_t b3_off(const rsc_partitioner *p) { return w3_off(p) + (int64_t)p->P * p->H; }
 
+// One GEMM of the network: on the tensor cores with BF16 operands (both
+// rounded) when the handle uses BF16 weights, else the FP32 SIMT GEMM
+// (`flags` then says which operands it rounds).
+void mgemm(const rsc_partitioner *p, cudaStream_t st, unsigned int *status, int M, int N, int K, const float *A,
+           int64_t sam, int64_t sak, const float *B, int64_t sbk, int64_t sbn, float *C, int64_t ldc,
+           const float *bias, int flags) {
+    if (p->bf16)
+        launch_tc_gemm(st, M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, flags & (part::kReluA | part::kReluB),
+                       status);
+    else
+        part::gemm(st, M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, flags);
+}
+
 // Forward of B rows (FP32 [B, d] in Xb): Z1, Z2 [B, H], Z3 [B, P] pre-activations.
-void mlp_forward(const rsc_partitioner *p, cudaStream_t st, int B, const float *Xb, float *Z1, float *Z2, float *Z3) {
+void mlp_forward(const rsc_partitioner *p, cudaStream_t st, int B, const float *Xb, float *Z1, float *Z2, float *Z3,
+                 unsigned int *status) {
     const int r = p->bf16 ? (part::kRoundA | part::kRoundB) : 0;
     const float *W = p->params;
-    part::gemm(st, B, p->H, p->d, Xb, p->d, 1, W + w1_off(p), 1, p->d, Z1, p->H, W + b1_off(p), r);
-    part::gemm(st, B, p->H, p->H, Z1, p->H, 1, W + w2_off(p), 1, p->H, Z2, p->H, W + b2_off(p), r | part::kReluA);
-    part::gemm(st, B, p->P, p->H, Z2, p->H, 1, W + w3_off(p), 1, p->H, Z3, p->P, W + b3_off(p), r | part::kReluA);
+    mgemm(p, st, status, B, p->H, p->d, Xb, p->d, 1, W + w1_off(p), 1, p->d, Z1, p->H, W + b1_off(p), r);
+    mgemm(p, st, status, B, p->H, p->H, Z1, p->H, 1, W + w2_off(p), 1, p->H, Z2, p->H, W + b2_off(p),
+          r | part::kReluA);
+    mgemm(p, st, status, B, p->P, p->H, Z2, p->H, 1, W + w3_off(p), 1, p->H, Z3, p->P, W + b3_off(p),
+          r | part::kReluA);
 }
 
 struct TrainBufs {
@@ -586,23 +604,34 @@ void mlp_loss_grad(const rsc_partitioner *p, cudaStream_t st, int B, const Train
     const int ra = p->bf16 ? part::kRoundB : 0;   // activations as the B operand of dW
     const float *W = p->params;
     float *g = b.grad;
-    mlp_forward(p, st, B, b.Xb, b.Z1, b.Z2, b.Z3);
+    mlp_forward(p, st, B, b.Xb, b.Z1, b.Z2, b.Z3, p->status);
     part::softmax_xent_kernel<<<(unsigned)ceil_div((int64_t)B * 32, 256), 256, 0, st>>>(B, p->P, b.Z3, b.T, b.dZ3,
                                                                                           b.loss);
     const int H = p->H, P = p->P, d = p->d;
     // layer 3: dW3 = dZ3^T relu(Z2); db3 = colsum(dZ3); dA2 = dZ3 W3
-    part::gemm(st, P, H, B, b.dZ3, 1, P, b.Z2, H, 1, g + w3_off(p), H, nullptr, ra | part::kReluB);
+    mgemm(p, st, p->status, P, H, B, b.dZ3, 1, P, b.Z2, H, 1, g + w3_off(p), H, nullptr, ra | part::kReluB);
     part::colsum_kernel<<<(unsigned)ceil_div(P, 256), 256, 0, st>>>(B, P, b.dZ3, g + b3_off(p));
-    part::gemm(st, B, H, P, b.dZ3, P, 1, W + w3_off(p), H, 1, b.dA, H, nullptr, rw);
+    mgemm(p, st, p->status, B, H, P, b.dZ3, P, 1, W + w3_off(p), H, 1, b.dA, H, nullptr, rw);
     part::relu_bwd_kernel<<<(unsigned)ceil_div((int64_t)B * H, 256), 256, 0, st>>>((int64_t)B * H, b.dA, b.Z2, b.dZ);
     // layer 2
-    part::gemm(st, H, H, B, b.dZ, 1, H, b.Z1, H, 1, g + w2_off(p), H, nullptr, ra | part::kReluB);
+    mgemm(p, st, p->status, H, H, B, b.dZ, 1, H, b.Z1, H, 1, g + w2_off(p), H, nullptr, ra | part::kReluB);
     part::colsum_kernel<<<(unsigned)ceil_div(H, 256), 256, 0, st>>>(B, H, b.dZ, g + b2_off(p));
-    part::gemm(st, B, H, H, b.dZ, H, 1, W + w2_off(p), H, 1, b.dA, H, nullptr, rw);
+    mgemm(p, st, p->status, B, H, H, b.dZ, H, 1, W + w2_off(p), H, 1, b.dA, H, nullptr, rw);
     part::relu_bwd_kernel<<<(unsigned)ceil_div((int64_t)B * H, 256), 256, 0, st>>>((int64_t)B * H, b.dA, b.Z1, b.dZ);
     // layer 1: dW1 = dZ1^T x
-    part::gemm(st, H, d, B, b.dZ, 1, H, b.Xb, d, 1, g + w1_off(p), d, nullptr, ra);
+    mgemm(p, st, p->status, H, d, B, b.dZ, 1, H, b.Xb, d, 1, g + w1_off(p), d, nullptr, ra);
     part::colsum_kernel<<<(unsigned)ceil_div(H, 256), 256, 0, st>>>(B, H, b.dZ, g + b1_off(p));
+}
+
+// Failure recorded by the handle's training kernels (read and cleared; the
+// stream has been synchronised).
+rsc_status take_status(const rsc_partitioner *p, cudaStream_t st) {
+    unsigned int word = 0;
+    RSC_CUDA_TRY(cudaMemcpyAsync(&word, p->status, sizeof(word), cudaMemcpyDeviceToHost, st));
+    RSC_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(word), st));
+    RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (word != 0) return fail((rsc_status)word, "a training kernel recorded status %u", word);
+    return RSC_OK;
 }
 
 rsc_status check_handle(const rsc_partitioner *p) {
@@ -641,6 +670,8 @@ rsc_status rsc_partitioner_create(int32_t d, int32_t n_parts, int32_t hidden, in
     if (e == cudaSuccess) e = cudaMalloc(&p->adam_m, sizeof(float) * p->np);
     if (e == cudaSuccess) e = cudaMalloc(&p->adam_v, sizeof(float) * p->np);
     if (e == cudaSuccess) e = cudaMalloc(&p->centroids, sizeof(float) * (size_t)n_parts * d);
+    if (e == cudaSuccess) e = cudaMalloc(&p->status, kStatusBytes);
+    if (e == cudaSuccess) e = cudaMemset(p->status, 0, kStatusBytes);
     if (e == cudaSuccess) e = cudaMemcpy(p->params, h.data(), sizeof(float) * p->np, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->adam_m, 0, sizeof(float) * p->np);
     if (e == cudaSuccess) e = cudaMemset(p->adam_v, 0, sizeof(float) * p->np);
@@ -650,6 +681,7 @@ rsc_status rsc_partitioner_create(int32_t d, int32_t n_parts, int32_t hidden, in
         cudaFree(p->adam_m);
         cudaFree(p->adam_v);
         cudaFree(p->centroids);
+        cudaFree(p->status);
         delete p;
         return fail(RSC_ERR_CUDA, "partitioner allocation failed: %s", cudaGetErrorString(e));
     }
@@ -663,6 +695,7 @@ rsc_status rsc_partitioner_destroy(rsc_partitioner *p) {
     cudaFree(p->adam_m);
     cudaFree(p->adam_v);
     cudaFree(p->centroids);
+    cudaFree(p->status);
     cudaFree(p->perm);
     cudaFree(p->doff);
     cudaFree(p->Db_sorted);
@@ -737,6 +770,8 @@ rsc_status rsc_partitioner_loss_grad(rsc_partitioner *p, const float *Xb, const 
     float l = 0.f;
     RSC_CUDA_TRY(cudaMemcpyAsync(&l, b.loss, sizeof(float), cudaMemcpyDeviceToHost, st));
     RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    rsc_status ks = take_status(p, st);
+    if (ks != RSC_OK) return ks;
     *loss_host = l / (float)batch;
     return RSC_OK;
 }
@@ -889,7 +924,7 @@ rsc_status network_route(const rsc_partitioner *p, cudaStream_t st, const float 
                                                                                                L.Xq);
             xb = L.Xq;
         }
-        mlp_forward(p, st, B, xb, L.Z1, L.Z2, L.Z3);
+        mlp_forward(p, st, B, xb, L.Z1, L.Z2, L.Z3, L.status);
         launch_top_logits(st, R, B, p->P, L.Z3, out + c0 * R);
     }
     RSC_CUDA_TRY(cudaGetLastError());
@@ -1035,6 +1070,8 @@ rsc_status rsc_partitioner_train(rsc_partitioner *p, const float *X, int64_t n, 
         epoch_loss = rows_seen ? l / (float)rows_seen : 0.f;
     }
     RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    rsc_status ks = take_status(p, st);
+    if (ks != RSC_OK) return ks;
     if (final_loss) *final_loss = epoch_loss;
     // 4. index the database by the trained network
     return rsc_partitioner_build_index(p, X, n, workspace, workspace_bytes, stream);

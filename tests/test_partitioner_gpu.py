@@ -52,6 +52,12 @@ def _recall(gi, oi, gd, od):
 
 
 def test_partitioned_search_recall_and_gain(rsc):
+    # 60,000 anisotropic cells, 64 parts: recall@15 of the partitioned search
+    # against the exact oracle for 1, 2 and 4 probed parts, with the network's
+    # routing and with the nearest-centroid routing over the same parts (the
+    # method without the network, same candidate budget).  The network must
+    # beat the centroids at one probe by a clear margin (measured on this
+    # workload: 0.850 against 0.818) and never fall behind.
     n, d, k = 60_000, 50, 15
     X = synth.anisotropic(n, d, n_comp=40, seed=7)
     Xd = torch.from_numpy(X).cuda()
@@ -65,19 +71,22 @@ def test_partitioned_search_recall_and_gain(rsc):
     q = torch.from_numpy(queries).cuda()
     oi, od, _ = oracle.knn(X, k, queries=queries)
     res = {}
-    for routing in ("network", "centroids"):
-        gi, gd = part.knn(Xd, k=k, n_probe=4, routing=routing, query_rows=q)
-        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
-        assert (np.diff(gd, axis=1) >= 0).all()
-        # every returned distance is exact for its id
-        ex = np.sqrt(((X[queries][:, None, :].astype(np.float64) - X[gi].astype(np.float64)) ** 2).sum(-1))
-        np.testing.assert_allclose(gd, ex, rtol=1e-5, atol=1e-6)
-        res[routing] = _recall(gi, oi, gd, od)
-    print("recall@15", res)
-    assert res["network"] >= 0.9
-    # probing every part is the exact search
-    gi, gd = part.knn(Xd, k=k, n_probe=8, routing="network", query_rows=q)
-    assert _recall(gi.cpu().numpy(), oi, gd.cpu().numpy(), od) >= res["network"]
+    for probes in (1, 2, 4):
+        for routing in ("network", "centroids"):
+            gi, gd = part.knn(Xd, k=k, n_probe=probes, routing=routing, query_rows=q)
+            gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+            assert (np.diff(gd, axis=1) >= 0).all()
+            # every returned distance is exact for its id
+            ex = np.sqrt(((X[queries][:, None, :].astype(np.float64) - X[gi].astype(np.float64)) ** 2).sum(-1))
+            np.testing.assert_allclose(gd, ex, rtol=1e-5, atol=1e-6)
+            res[(routing, probes)] = _recall(gi, oi, gd, od)
+    print("recall@15 by (routing, probes)", res)
+    assert res[("network", 1)] >= res[("centroids", 1)] + 0.015
+    for probes in (2, 4):
+        assert res[("network", probes)] >= res[("centroids", probes)]
+    assert res[("network", 4)] >= 0.99
+    # more probes never lose a neighbour
+    assert res[("network", 1)] <= res[("network", 2)] <= res[("network", 4)]
 
 
 def test_save_load_roundtrip(rsc, tmp_path):
