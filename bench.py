@@ -520,6 +520,9 @@ def run_batched(args):
     out = (torch.empty((n, kw), dtype=torch.int32, device=dev), torch.empty((n, kw), device=dev),
            torch.empty((n, 64 * kx), dtype=torch.int32, device=dev), torch.empty((n, 64 * kx), device=dev))
     with torch.cuda.stream(stream):
+        # autotuner (column parts x pipeline stages, timed on this data); the
+        # timed calls below use automatic options, which follow its choice
+        tuned, tune_ms, _ = rsc.rsc_autotune_knn_batched(Xd, off, kw, kx, stream=stream, trials=1)
         for _ in range(args.warmup):
             rsc.rsc_knn_batched(Xd, off, kw, kx, stream=stream, workspace=ws, out=out)
         stream.synchronize()
@@ -555,9 +558,49 @@ def run_batched(args):
             # pruned search 10 (2 sphere passes, nearest tiles, window pass, tau, count, scan (2),
             # fill, list pass), gather + within re-rank + cross re-rank 3; 7 without the ordering
             # (fewer than ORDER_MIN_ROWS rows)
-            "gpu_launches": (60 if n >= ORDER_MIN_ROWS else 7) * args.steps, "clocks": sampler.summary()}
+            "gpu_launches": (60 if n >= ORDER_MIN_ROWS else 7) * args.steps, "clocks": sampler.summary(),
+            "autotune": {"choice": tuned, "best_ms": tune_ms}}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batched_baseline(X, off, kw, kx, out)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def batched_baseline(X, off, kw, kx, out):
+    """The FP64 oracle on the five smallest samples (their rows against
+    themselves, within and across those samples), with the recall of the GPU's
+    lists for those rows: within-sample lists as they are, cross lists
+    restricted to the five samples."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    sizes = np.diff(off)
+    pick = np.sort(np.argsort(sizes, kind="stable")[:5])
+    rows = np.concatenate([np.arange(off[s], off[s + 1]) for s in pick])
+    sub_off = np.concatenate([[0], np.cumsum(sizes[pick])])
+    t0 = time.perf_counter()
+    wi, wd, xi, xd = oracle.batched_knn(X[rows], sub_off, kw, kx)
+    dt = time.perf_counter() - t0
+    gw = out[1].cpu().numpy()[rows].astype(np.float64)
+    within = float((gw <= wd[:, -1:] * (1 + 1e-6) + 1e-12).mean())
+    # the GPU's k_cross nearest of each picked sample, for the picked rows
+    gi_all = out[2].cpu().numpy()[rows]
+    gd_all = out[3].cpu().numpy()[rows].astype(np.float64)
+    ok = tot = 0
+    for t, s in enumerate(pick):
+        lo, hi = off[s], off[s + 1]
+        # oracle distances of sample t's k_cross nearest (sorted rows mix samples: select by sample)
+        sel = (xi >= sub_off[t]) & (xi < sub_off[t + 1])
+        ref = np.where(sel, xd, np.inf)
+        kth = np.sort(ref, axis=1)[:, kx - 1]
+        mine = np.where((gi_all >= lo) & (gi_all < hi), gd_all, np.inf)
+        got = np.sort(mine, axis=1)[:, :kx]
+        ok += int((got <= kth[:, None] * (1 + 1e-6) + 1e-12).sum())
+        tot += got.size
+    return {"value": len(rows) / dt, "unit": "cells/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the 5 smallest samples ({len(rows)} rows): per-sample k={kw} and k_cross={kx} from each "
+                      f"of the 5, FP64 brute force",
+            "recall_within": within, "recall_cross": ok / max(tot, 1)}
 
 
 PARTITION_WORKLOAD = ("Learned partitioner: 5,000,000 cells x 50 PCs fp32, 200-cluster mixture with random anisotropic "

@@ -100,6 +100,10 @@ typedef struct {
                             lists (exact: the candidates equal the full scan's).
                             0 = automatic (on with the ordering, one database
                             split, d + 3 <= 64), 1 = off, 2 = on               */
+    int32_t stages;      /* tensor-core path: shared-memory stages of the
+                            database-tile pipeline, 2 .. 6 (clamped to what the
+                            list shape's shared memory holds); 0 = automatic
+                            (as many as fit, or the autotuner's choice)        */
 } rsc_knn_opts;
 
 /* Library version string (static storage). */
@@ -174,10 +178,16 @@ rsc_status rsc_knn_scan_stats(int64_t n, int32_t d, int32_t k, int32_t metric, c
  * "automatic": rsc_knn and rsc_knn_batched then look up a process-wide table
  * of tuned choices keyed by (entry point, precision, metric, d, k, k_cross,
  * floor(log2 n)), and fall back to built-in defaults when it has no entry.
- * The rsc_autotune_* calls fill that table by timing the candidate
- * configurations (database splits, column parts per row, candidate list
- * widths; every candidate keeps the result exact by construction) on the
- * caller's own data with CUDA events on opts->stream, keeping the fastest.
+ * The rsc_autotune_* calls fill that table by timing candidate
+ * configurations on the caller's own data with CUDA events on opts->stream,
+ * by coordinate descent: database splits x column parts per row (list
+ * shapes 2 x 16 and 4 x 16 for k <= 16), then the pipeline stages (3, 4, 5
+ * and as many as fit), then candidate lists twice the default length; every
+ * configuration returns exact FP32 distances of candidate sets at least as
+ * large as the default's, so the choice never lowers recall.  The 128 x 256
+ * tile (one M = 128 accumulator per query tile, N = 256 database rows per
+ * MMA) is fixed: the pruning geometry, the batched work tables and the
+ * TMEM double buffer (2 x 256 of the 512 columns) are built on it.
  * They synchronise the stream and leave the result of the last timed run in
  * the output arrays.
  */

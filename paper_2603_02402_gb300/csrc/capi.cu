@@ -68,6 +68,7 @@ struct KnnPlan {
     int64_t split_len = 0;
     bool order = false; // locality ordering before the tensor-core search
     bool prune = false; // window pass + tile bounds + list pass instead of one full scan
+    int stages = 0;     // tensor-core pipeline stages (0: as many as fit)
 };
 
 struct KnnLayout {
@@ -102,17 +103,21 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
         return fail(RSC_ERR_INVALID_ARG, "tc_parts=%d (0, 2 or 4)", o->tc_parts);
     if (o->locality < 0 || o->locality > 2) return fail(RSC_ERR_INVALID_ARG, "locality=%d (0, 1 or 2)", o->locality);
     if (o->prune < 0 || o->prune > 2) return fail(RSC_ERR_INVALID_ARG, "prune=%d (0, 1 or 2)", o->prune);
+    if (o->stages != 0 && (o->stages < 2 || o->stages > 6))
+        return fail(RSC_ERR_INVALID_ARG, "stages=%d (0 or 2 .. 6)", o->stages);
     rsc_knn_opts tuned;
-    if (o->db_splits == 0 && o->candidates == 0 && o->tc_parts == 0) {   // automatic: tuned table first
+    if (o->db_splits == 0 && o->candidates == 0 && o->tc_parts == 0 && o->stages == 0) {   // automatic: tuned table first
         TunedChoice c;
         if (tuned_lookup(0, o->precision, metric, d, k, 0, n, &c)) {
             tuned = *o;
             tuned.db_splits = c.db_splits;
             tuned.candidates = c.candidates;
             tuned.tc_parts = c.tc_parts;
+            tuned.stages = c.stages;
             o = &tuned;
         }
     }
+    p->stages = o->stages;
     p->precision = o->precision;
     p->d = d;
     p->metric = metric;
@@ -281,6 +286,7 @@ struct BatchedPlan {
     int64_t n = 0;
     int d = 0, S = 0, kw = 0, kx = 0, metric = 0, DP = 0;
     int parts = 4;      // threads (column parts) per query row
+    int stages = 0;     // tensor-core pipeline stages (0: as many as fit)
     int64_t T = 0;      // query tiles (128 rows inside one sample)
     int64_t DT = 0;     // database tiles (256 rows inside one sample)
     bool order = false; // rows in cluster order inside each sample
@@ -316,10 +322,15 @@ rsc_status plan_batched(int64_t n, int32_t d, const int64_t *off, int32_t S, int
     if (o->precision != RSC_BF16) return fail(RSC_ERR_UNSUPPORTED, "batched search runs BF16 candidates only");
     if (o->tc_parts != 0 && o->tc_parts != 2 && o->tc_parts != 4)
         return fail(RSC_ERR_INVALID_ARG, "tc_parts=%d (0, 2 or 4)", o->tc_parts);
+    if (o->stages != 0 && (o->stages < 2 || o->stages > 6))
+        return fail(RSC_ERR_INVALID_ARG, "stages=%d (0 or 2 .. 6)", o->stages);
     p->parts = o->tc_parts;
+    p->stages = o->stages;
     if (p->parts == 0) {
         TunedChoice c;
-        p->parts = tuned_lookup(1, o->precision, metric, d, kw, kx, n, &c) ? c.tc_parts : 4;
+        const bool hit = tuned_lookup(1, o->precision, metric, d, kw, kx, n, &c);
+        p->parts = hit ? c.tc_parts : 4;
+        if (hit && o->stages == 0) p->stages = c.stages;
     }
     if (off[0] != 0 || off[S] != n) return fail(RSC_ERR_INVALID_ARG, "sample_offsets must run from 0 to n");
     for (int s = 0; s < S; ++s)
@@ -391,16 +402,16 @@ rsc_status enqueue_batched(const float *X, const BatchedPlan &p, const BatchedLa
     if (p.prune) {
         const BatchedPruneOut po = batched_prune_outputs(L.prune_scratch, n, p.T, p.S, p.DT);
         RSC_CUDA_TRY(launch_batched_prune_window(L.Qb, n, d, metric, L.tables, p.T, p.S, p.DT, L.prune_scratch, st));
-        RSC_CUDA_TRY(launch_knn_tc_batched_window(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, L.tables,
+        RSC_CUDA_TRY(launch_knn_tc_batched_window(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, p.stages, L.tables,
                                                   po.win, kOrderWindow, L.st_w, L.cand_w, L.st_x, L.cand_x, L.status,
                                                   st));
         RSC_CUDA_TRY(launch_batched_prune_bounds(n, d, metric, L.tables, p.T, p.S, p.DT, kOrderWindow, p.parts, L.st_w,
                                                  L.st_x, L.prune_scratch, st));
-        RSC_CUDA_TRY(launch_knn_tc_batched_list(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, L.tables,
+        RSC_CUDA_TRY(launch_knn_tc_batched_list(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, p.stages, L.tables,
                                                 po.win, kOrderWindow, L.st_w, L.cand_w, L.st_x, L.cand_x, po.tiles,
                                                 po.tile_off, po.overflow, L.status, st));
     } else {
-        RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, L.tables,
+        RSC_CUDA_TRY(launch_knn_tc_batched(L.Qb, L.Db, n, d, metric, p.S, (int)p.T, p.DT, p.parts, p.stages, L.tables,
                                            L.cand_w, L.cand_x, L.status, st));
     }
     const float *R = (metric == RSC_EUCLIDEAN) ? X : L.Y;
@@ -487,7 +498,7 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
         if (p.order) RSC_CUDA_TRY(launch_locality_order(L.Y, n, p.DP, kOrderIters, L.perm, L.order_scratch, st));
         RSC_CUDA_TRY(launch_prep_bf16(L.Y, n, d, p.DP, metric, L.perm, L.Qb, L.Db, st));
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
-        const TcShape sh{p.parts, p.KC};
+        const TcShape sh{p.parts, p.KC, p.stages};
         if (p.prune) {
             RSC_CUDA_TRY(launch_knn_tc_window(L.Qb, L.Db, n, d, metric, sh, kOrderWindow, L.st_key, L.st_id, L.status,
                                               st));
@@ -504,7 +515,7 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
         if (p.order) RSC_CUDA_TRY(launch_locality_order(L.Y, n, p.DP, kOrderIters, L.perm, L.order_scratch, st));
         RSC_CUDA_TRY(launch_prep_fp8(L.Y, n, d, p.DP, metric, L.perm, L.Qb, L.Db, L.amax, st));
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
-        RSC_CUDA_TRY(launch_knn_tc_fp8(L.Qb, L.Db, n, d, metric, TcShape{p.parts, p.KC}, p.splits, p.split_len,
+        RSC_CUDA_TRY(launch_knn_tc_fp8(L.Qb, L.Db, n, d, metric, TcShape{p.parts, p.KC, p.stages}, p.splits, p.split_len,
                                        p.order ? kOrderWindow : 0, L.cand, L.status, st));
     } else {
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
@@ -596,7 +607,7 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
     std::vector<uint64_t> key = {(uint64_t)X, (uint64_t)n, (uint64_t)d, (uint64_t)n_samples, (uint64_t)k_within,
                                  (uint64_t)k_cross, (uint64_t)metric, (uint64_t)idx_within, (uint64_t)dist_within,
                                  (uint64_t)idx_cross, (uint64_t)dist_cross, (uint64_t)workspace,
-                                 (uint64_t)p.parts, (uint64_t)p.order, (uint64_t)p.prune};
+                                 (uint64_t)p.parts, (uint64_t)p.order, (uint64_t)p.prune, (uint64_t)p.stages};
     for (int i = 0; i <= n_samples; ++i) key.push_back((uint64_t)sample_offsets[i]);
     int dev = 0;
     RSC_CUDA_TRY(cudaGetDevice(&dev));

@@ -32,8 +32,9 @@ cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, 
 // Database splits must be multiples of knn_tc_split_align() rows.  Bounded
 // waits record RSC_ERR_TIMEOUT in *status.
 struct TcShape {
-    int parts;   // lists per row and split (0: no kernel for this request)
-    int list;    // ids per list
+    int parts;        // lists per row and split (0: no kernel for this request)
+    int list;         // ids per list
+    int stages = 0;   // database-tile pipeline stages (0: as many as shared memory holds)
 };
 int tc_kb(int d, int metric);
 TcShape knn_tc_shape(int d, int metric, int k, int want, int parts_req);
@@ -147,18 +148,18 @@ int64_t batched_query_tiles(const int64_t *offsets_host, int S);
 int64_t batched_db_tiles(const int64_t *offsets_host, int S);
 void batched_fill_tables(const int64_t *offsets_host, int S, void *host_buf);
 cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                  int64_t DT, int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
+                                  int64_t DT, int parts, int stages, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
                                   unsigned int *status, cudaStream_t st);
 // Pruned batched search on rows in sample-preserving locality order: a window
 // pass around win[t * T + qt] saving keys (st_w [parts, N, kBatchedList],
 // st_x [N, S, parts, kBatchedShort]) and ids (cand_w, cand_x), then a list
 // pass over the kept tiles (tile_off over items t * T + qt).
 cudaError_t launch_knn_tc_batched_window(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                         int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                         int64_t DT, int parts, int stages, const void *tables_dev, const int32_t *win, int window,
                                          float *st_w, int32_t *cand_w, float *st_x, int32_t *cand_x,
                                          unsigned int *status, cudaStream_t st);
 cudaError_t launch_knn_tc_batched_list(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                       int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                       int64_t DT, int parts, int stages, const void *tables_dev, const int32_t *win, int window,
                                        const float *st_w, int32_t *cand_w, const float *st_x, int32_t *cand_x,
                                        const int32_t *tiles, const int64_t *tile_off, const int32_t *overflow,
                                        unsigned int *status, cudaStream_t st);
@@ -189,6 +190,7 @@ cudaError_t launch_batched_prune_bounds(int64_t N, int d, int metric, const void
 // Tuned-choice table consulted when options are automatic (all zero).
 struct TunedChoice {
     int db_splits, candidates, tc_parts;
+    int stages = 0;   // database-tile pipeline stages (0: as many as fit)
 };
 bool tuned_lookup(int kind, int precision, int metric, int d, int k, int kx, int64_t n, TunedChoice *out);
 void tuned_store(int kind, int precision, int metric, int d, int k, int kx, int64_t n, const TunedChoice &c);

@@ -217,7 +217,7 @@ cudaError_t launch_knn_tc(const void *Qb, const void *Db, int64_t n, int d, int 
     if (e != cudaSuccess) return e;
     if ((e = tck::make_map(&md, Db, n, KB, tck::BN)) != cudaSuccess) return e;
     tck::PlainWork work{n, splits, split_len, cand, (int)(ceil_div(n, tck::BM) * splits), window};
-#define RSC_TC_CASE(kb, kcp, eg) return tck::launch_kernel<kb, kcp, eg>(mq, md, work, status, st)
+#define RSC_TC_CASE(kb, kcp, eg) return tck::launch_kernel<kb, kcp, eg>(mq, md, work, status, st, sh.stages)
     if (KB == 1 && sh.parts == 4 && sh.list == 16) RSC_TC_CASE(1, 16, 4);
     if (KB == 1 && sh.parts == 2 && sh.list == 16) RSC_TC_CASE(1, 16, 2);
     if (KB == 1 && sh.parts == 2 && sh.list == 32) RSC_TC_CASE(1, 32, 2);

@@ -56,6 +56,7 @@ struct Cfg {
     static constexpr int kBarOff = kQBytes + kStages * kStageBytes + kBufBytes;
     static constexpr int kSmem = kBarOff + 256 + 1024;       // barriers + alignment slack
     static_assert(kStages >= 2, "shared memory too small for two stages");
+    static_assert(kBarOff % 8 == 0, "barriers 8-byte aligned");
 };
 
 // One work item: query rows [q0, q_end) (at most BM) against database rows
@@ -148,6 +149,19 @@ struct TileSeq {
     }
 };
 
+// Position in the ring of S shared-memory stages: stage index and the parity
+// of its current round, advanced once per tile (no division in the loop).
+struct StageRing {
+    int s = 0, S = 2;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next() {
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023);
     return reinterpret_cast<uint8_t *>(a);
@@ -156,9 +170,10 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 template <int KB, int KCP, int EG, class Work, int EB = 2>
 __global__ void __launch_bounds__(Cfg<KB, KCP, EG, EB>::kThreads, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmD,
-              const Work work, unsigned int *status, long long wait_budget) {
+              const Work work, unsigned int *status, long long wait_budget, int stages) {
     using C = Cfg<KB, KCP, EG, EB>;
-    constexpr int S = C::kStages;
+    // pipeline stages in use (the shared-memory layout is sized for C::kStages)
+    const int S = (stages >= 2 && stages <= C::kStages) ? stages : C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     uint8_t *sQ = smem;
@@ -166,8 +181,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
     float *bkey = reinterpret_cast<float *>(sD + S * C::kStageBytes);   // keys, then ids
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kBarOff);
     uint64_t *full = bars;                     // [S]     database stage loaded
-    uint64_t *empty = bars + S;                // [S]     database stage consumed
-    uint64_t *acc_full = bars + 2 * S;         // [NBUF]  accumulator ready
+    uint64_t *empty = bars + C::kStages;       // [S]     database stage consumed
+    uint64_t *acc_full = bars + 2 * C::kStages;   // [NBUF]  accumulator ready
     uint64_t *acc_empty = acc_full + NBUF;     // [NBUF]  accumulator drained
     uint64_t *q_full = acc_empty + NBUF;
     uint64_t *q_empty = q_full + 1;
@@ -280,6 +295,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
         if (lane == 0) {
             // ------------------------------------------------ TMA producer
             uint32_t gt = 0;
+            StageRing ring;
+            ring.S = S;
             int item_no = 0;
             bool ok = true, q_issued = false;
             uint32_t q_parity = 0;
@@ -296,10 +313,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 q_parity = item_no & 1;
                 const int jb = (int)j_begin, T = (int)((j_end - j_begin + BN - 1) / BN);
                 TileSeq<4> sq;
-                for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
-                    const int s = gt % S;
-                    const uint32_t u = gt / S;
-                    if (!(ok = wait(&empty[s], (u & 1) ^ 1))) break;
+                for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done();
+                     sq.next(), ++gt, ring.next()) {
+                    const int s = ring.s;
+                    if (!(ok = wait(&empty[s], ring.ph ^ 1u))) break;
                     tc::mbar_arrive_expect_tx(&full[s], C::kStageBytes);
                     const int j0 = jb + sq.m * BN;
                     for (int kb = 0; kb < KB; ++kb)
@@ -318,6 +335,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
             // ------------------------------------------------ MMA issuer
             constexpr uint32_t idesc = EB == 2 ? tc::idesc_bf16_f32(BM, BN) : tc::idesc_e4m3_f32(BM, BN);
             uint32_t gt = 0;
+            StageRing ring;
+            ring.S = S;
             int item_no = 0;
             bool ok = true;
             for (;; ++item_no) {
@@ -329,12 +348,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ C
                 tc::tc_fence_after();
                 const int T = (int)((j_end - j_begin + BN - 1) / BN);
                 TileSeq<4> sq;
-                for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done(); sq.next(), ++gt) {
-                    const int s = gt % S;
-                    const uint32_t u = gt / S;
+                for (sq.init(T, wi.win_lo, wi.win_hi, wi.win_c, wi.tiles, wi.n_tiles, wi.skip_window); !sq.done();
+                     sq.next(), ++gt, ring.next()) {
+                    const int s = ring.s;
                     const uint32_t b = gt & 1u, v = gt >> 1;
                     if (!(ok = wait(&acc_empty[b], (v & 1) ^ 1))) break;
-                    if (!(ok = wait(&full[s], u & 1))) break;
+                    if (!(ok = wait(&full[s], ring.ph))) break;
                     tc::tc_fence_after();
                     const uint32_t d_tmem = tmem_base + b * BN;
 #pragma unroll
@@ -589,7 +608,7 @@ struct PlainWork {
 
 template <int KB, int KCP, int EG, class Work, int EB = 2>
 cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, const Work &work, unsigned int *status,
-                          cudaStream_t st) {
+                          cudaStream_t st, int stages = 0) {
     using C = Cfg<KB, KCP, EG, EB>;
     auto kern = knn_tc_kernel<KB, KCP, EG, Work, EB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
@@ -597,7 +616,7 @@ cudaError_t launch_kernel(const CUtensorMap &mq, const CUtensorMap &md, const Wo
     const int64_t items = work.count_host();
     if (items <= 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(items, sm_count());
-    kern<<<grid, C::kThreads, C::kSmem, st>>>(mq, md, work, status, tc_wait_budget());
+    kern<<<grid, C::kThreads, C::kSmem, st>>>(mq, md, work, status, tc_wait_budget(), stages);
     return cudaGetLastError();
 }
 

@@ -420,7 +420,7 @@ void batched_fill_tables(const int64_t *offsets_host, int S, void *host_buf) {
 }
 
 cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                  int64_t DT, int parts, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
+                                  int64_t DT, int parts, int stages, const void *tables_dev, int32_t *cand_w, int32_t *cand_x,
                                   unsigned int *status, cudaStream_t st) {
     if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
     CUtensorMap mq, md;
@@ -430,8 +430,8 @@ cudaError_t launch_knn_tc_batched(const void *Qb, const void *Db, int64_t N, int
     const BatchedTables b = batched_tables(const_cast<void *>(tables_dev), T, S, DT);
     tck::BatchedWork work{T,     S, b.tile_row, b.tile_end, b.tile_samp, b.samp_off, N, cand_w, cand_x,
                           b.samp_order, b.counter};
-    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
-    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
+    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st, stages);
+    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st, stages);
     return cudaErrorInvalidValue;
 }
 
@@ -463,7 +463,7 @@ cudaError_t launch_rerank_cross(const float *R, int64_t rs, int64_t N, int d, in
 
 
 cudaError_t launch_knn_tc_batched_window(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                         int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                         int64_t DT, int parts, int stages, const void *tables_dev, const int32_t *win, int window,
                                          float *st_w, int32_t *cand_w, float *st_x, int32_t *cand_x,
                                          unsigned int *status, cudaStream_t st) {
     if (tc_kb(d, metric) != 1) return cudaErrorInvalidValue;
@@ -475,13 +475,13 @@ cudaError_t launch_knn_tc_batched_window(const void *Qb, const void *Db, int64_t
     if ((e = cudaMemsetAsync(b.counter, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
     tck::BatchedWindowWork work{T, S, b.tile_row, b.tile_end, b.tile_samp, b.samp_off, b.samp_order, b.counter, N,
                                 win, window, st_w, cand_w, st_x, cand_x};
-    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
-    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
+    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st, stages);
+    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st, stages);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_knn_tc_batched_list(const void *Qb, const void *Db, int64_t N, int d, int metric, int S, int T,
-                                       int64_t DT, int parts, const void *tables_dev, const int32_t *win, int window,
+                                       int64_t DT, int parts, int stages, const void *tables_dev, const int32_t *win, int window,
                                        const float *st_w, int32_t *cand_w, const float *st_x, int32_t *cand_x,
                                        const int32_t *tiles, const int64_t *tile_off, const int32_t *overflow,
                                        unsigned int *status, cudaStream_t st) {
@@ -495,8 +495,8 @@ cudaError_t launch_knn_tc_batched_list(const void *Qb, const void *Db, int64_t N
     tck::BatchedListWork work{T,      S,     b.tile_row, b.tile_end, b.tile_samp, b.samp_off, b.samp_order,
                               b.counter, N,  win,        window,     st_w,        cand_w,     st_x,
                               cand_x, tiles, tile_off,   overflow};
-    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st);
-    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st);
+    if (parts == 4) return tck::launch_kernel<1, kBatchedList, 4>(mq, md, work, status, st, stages);
+    if (parts == 2) return tck::launch_kernel<1, kBatchedList, 2>(mq, md, work, status, st, stages);
     return cudaErrorInvalidValue;
 }
 

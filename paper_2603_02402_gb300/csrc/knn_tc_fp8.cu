@@ -136,7 +136,7 @@ cudaError_t launch_knn_tc_fp8(const void *Qf, const void *Df, int64_t n, int d, 
     tck::PlainWork work{n, splits, split_len, cand, (int)(ceil_div(n, tck::BM) * splits), window};
     (void)d;
     (void)metric;
-#define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg, tck::PlainWork, 1>(mq, md, work, status, st)
+#define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg, tck::PlainWork, 1>(mq, md, work, status, st, sh.stages)
     if (sh.parts == 4 && sh.list == 16) RSC_TC_CASE(16, 4);
     if (sh.parts == 2 && sh.list == 16) RSC_TC_CASE(16, 2);
     if (sh.parts == 2 && sh.list == 32) RSC_TC_CASE(32, 2);

@@ -140,7 +140,7 @@ cudaError_t launch_knn_tc_window(const void *Qb, const void *Db, int64_t n, int 
     if (e != cudaSuccess) return e;
     if ((e = tck::make_map(&md, Db, n, 1, tck::BN)) != cudaSuccess) return e;
     tck::WindowWork work{n, window, st_key, st_id, (int)ceil_div(n, tck::BM)};
-#define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg>(mq, md, work, status, st)
+#define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg>(mq, md, work, status, st, sh.stages)
     if (sh.parts == 4 && sh.list == 16) RSC_TC_CASE(16, 4);
     if (sh.parts == 2 && sh.list == 16) RSC_TC_CASE(16, 2);
     if (sh.parts == 2 && sh.list == 32) RSC_TC_CASE(32, 2);
@@ -160,7 +160,7 @@ cudaError_t launch_knn_tc_list(const void *Qb, const void *Db, int64_t n, int d,
     if ((e = tck::make_map(&md, Db, n, 1, tck::BN)) != cudaSuccess) return e;
     tck::ListWork work{n, window, st_key, st_id, tiles, tile_off, order, overflow, cand, (int)ceil_div(n, tck::BM), counter};
     if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
-#define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg>(mq, md, work, status, st)
+#define RSC_TC_CASE(kcp, eg) return tck::launch_kernel<1, kcp, eg>(mq, md, work, status, st, sh.stages)
     if (sh.parts == 4 && sh.list == 16) RSC_TC_CASE(16, 4);
     if (sh.parts == 2 && sh.list == 16) RSC_TC_CASE(16, 2);
     if (sh.parts == 2 && sh.list == 32) RSC_TC_CASE(32, 2);

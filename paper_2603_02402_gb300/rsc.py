@@ -40,7 +40,7 @@ class rsc_knn_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("candidates", ctypes.c_int32),
                 ("db_splits", ctypes.c_int32), ("tc_parts", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("phase_events", ctypes.c_void_p),
-                ("locality", ctypes.c_int32), ("prune", ctypes.c_int32)]
+                ("locality", ctypes.c_int32), ("prune", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); the full exported surface of include/rsc.h
@@ -150,7 +150,7 @@ _LOCALITY = {"auto": 0, "off": 1, "on": 2}
 
 
 def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_events=None,
-             locality="auto", prune="auto") -> rsc_knn_opts:
+             locality="auto", prune="auto", stages=0) -> rsc_knn_opts:
     """Option struct; `phase_events` is a ctypes array of 4 raw cudaEvent_t."""
     o = rsc_knn_opts()
     o.locality = _LOCALITY[locality] if isinstance(locality, str) else int(locality)
@@ -159,6 +159,7 @@ def knn_opts(precision="fp32", candidates=0, db_splits=0, stream=None, phase_eve
     o.precision = _PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.candidates = int(candidates)
     o.db_splits = int(db_splits)
+    o.stages = int(stages)
     o.stream = _stream(stream).value
     return o
 
@@ -184,7 +185,8 @@ def rsc_knn_scan_stats(n, d, k, workspace, metric="euclidean", precision="fp32",
 
 
 def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candidates=0, db_splits=0,
-            stream=None, workspace=None, out=None, phase_events=None, locality="auto", prune="auto"):
+            stream=None, workspace=None, out=None, phase_events=None, locality="auto", prune="auto", stages=0,
+            tc_parts=0):
     """Exact kNN of every row of X (float32 [n, d] on the GPU).
 
     Returns (idx int32 [n, k], dist float32 [n, k]) on X's device.
@@ -193,7 +195,8 @@ def rsc_knn(X: torch.Tensor, k: int, metric="euclidean", precision="fp32", candi
         raise ValueError("X must be a contiguous float32 [n, d] CUDA tensor")
     n, d = X.shape
     m = _METRICS[metric] if isinstance(metric, str) else int(metric)
-    o = knn_opts(precision, candidates, db_splits, stream, phase_events, locality, prune)
+    o = knn_opts(precision, candidates, db_splits, stream, phase_events, locality, prune, stages)
+    o.tc_parts = int(tc_parts)
     need = _sz(0)
     _check(lib().rsc_knn_workspace_size(n, d, k, m, ctypes.byref(o), ctypes.byref(need)))
     ws = _workspace(need.value, X.device, workspace)
@@ -348,13 +351,14 @@ def rsc_autotune_knn(X: torch.Tensor, k: int, metric="euclidean", precision="bf1
     ms = ctypes.c_float(0)
     _check(lib().rsc_autotune_knn(_ptr(X), n, d, k, m, ctypes.byref(o), trials, _ptr(idx), _ptr(dist),
                                   ctypes.byref(best), ctypes.byref(ms), _ptr(ws), ws.numel()))
-    return ({"db_splits": best.db_splits, "candidates": best.candidates, "tc_parts": best.tc_parts},
-            float(ms.value), idx, dist)
+    return ({"db_splits": best.db_splits, "candidates": best.candidates, "tc_parts": best.tc_parts,
+             "stages": best.stages}, float(ms.value), idx, dist)
 
 
 def rsc_autotune_knn_batched(X: torch.Tensor, sample_offsets, k_within: int, k_cross: int, metric="euclidean",
                              trials=2, stream=None):
-    """Tune rsc_knn_batched's column parts; returns (tc_parts, best ms, outputs)."""
+    """Tune rsc_knn_batched's column parts and pipeline stages; returns
+    ({"tc_parts", "stages"}, best ms, outputs)."""
     n, d = X.shape
     off, optr = _offsets_host(sample_offsets)
     S = len(off) - 1
@@ -373,7 +377,7 @@ def rsc_autotune_knn_batched(X: torch.Tensor, sample_offsets, k_within: int, k_c
     _check(lib().rsc_autotune_knn_batched(_ptr(X), n, d, optr, S, k_within, k_cross, m, ctypes.byref(o), trials,
                                           *[_ptr(t) for t in outs], ctypes.byref(best), ctypes.byref(ms), _ptr(ws),
                                           ws.numel()))
-    return int(best.tc_parts), float(ms.value), outs
+    return {"tc_parts": int(best.tc_parts), "stages": int(best.stages)}, float(ms.value), outs
 
 
 def rsc_autotune_save(path: str):

@@ -96,6 +96,12 @@ def test_candidate_option_errors(L):
     assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
     o = rsc.rsc_knn_opts(1, 0, 0, 0, None, None, 1, 2)  # pruning needs the locality ordering
     assert L.rsc_knn_workspace_size(100_000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_UNSUPPORTED
+    for stages in (1, 7):                                 # 0 or 2 .. 6 pipeline stages
+        o = rsc.rsc_knn_opts(1, 0, 0, 0, None, None, 0, 0, stages)
+        assert L.rsc_knn_workspace_size(1000, 50, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.rsc_knn_opts(3, 0, 0, 0, None, None)          # FP8 folds the norm into 5 columns: d <= 59
+    assert L.rsc_knn_workspace_size(1000, 60, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_ERR_UNSUPPORTED
+    assert L.rsc_knn_workspace_size(1000, 59, 15, 0, ctypes.byref(o), ctypes.byref(out)) == rsc.RSC_OK
 
 
 def _ws(L, n, precision, locality, prune=1):
@@ -151,11 +157,20 @@ def test_autotune_table_save_load_roundtrip(L, tmp_path):
     out = tmp_path / "saved.txt"
     rsc.rsc_autotune_save(str(out))
     rows = [l.split() for l in out.read_text().splitlines() if not l.startswith("#")]
-    assert sorted(rows) == sorted([l.split() for l in src.read_text().splitlines() if not l.startswith("#")])
-    bad = tmp_path / "bad.txt"
-    bad.write_text("0 1 0 50 15 0 19 2 0 3\n")    # tc_parts 3 is not a valid choice
-    with pytest.raises(rsc.RscError):
-        rsc.rsc_autotune_load(str(bad))
+    # the saved table carries the pipeline stages as an 11th column (0: automatic)
+    assert sorted(rows) == sorted([l.split() + ["0"] for l in src.read_text().splitlines() if not l.startswith("#")])
+    v2 = tmp_path / "v2.txt"
+    v2.write_text("0 1 0 50 15 0 18 1 0 2 4\n")
+    rsc.rsc_autotune_load(str(v2))
+    rsc.rsc_autotune_save(str(out))
+    assert ["0", "1", "0", "50", "15", "0", "18", "1", "0", "2", "4"] in \
+        [l.split() for l in out.read_text().splitlines() if not l.startswith("#")]
+    for line in ("0 1 0 50 15 0 19 2 0 3\n",       # tc_parts 3 is not a valid choice
+                 "0 1 0 50 15 0 19 2 0 2 7\n"):    # at most 6 stages
+        bad = tmp_path / "bad.txt"
+        bad.write_text(line)
+        with pytest.raises(rsc.RscError):
+            rsc.rsc_autotune_load(str(bad))
     rsc.rsc_autotune_clear()
 
 
