@@ -40,8 +40,11 @@ SEARCH_SOURCES = ("knn_tc.cuh", "knn_tc_prune.cu", "prune.cu", "topk.cuh", "tc_p
 CONN_SOURCES = ("connectivities.cu",)
 TRAFFIC = {
     # window pass + list pass of the 1,000,000-cell graph (profiles/knn_tc_pruned_passes_bf16_1m.md):
-    # 256.1 + 207.1 MB and 1350.3 + 114.3 MB, cold-cache under ncu; the bound kernels are not included
-    ("knn_tc.cuh", "pruned"): {"bytes_per_launch": 1_927_800_000, "kernel_sha": "92e9011f458d5739"},
+    # 256.1 + 206.3 MB and 1403.3 + 116.5 MB, cold-cache under ncu; the bound kernels are not included
+    ("knn_tc.cuh", "pruned"): {"bytes_per_launch": 1_982_258_744, "kernel_sha": "dcf8edee4e3e25bc"},
+    # the eight launches of one rsc_connectivities call on the 1,000,000-cell k = 15 lists
+    # (profiles/connectivities_graph_1m_k15.md), cold-cache under ncu
+    ("connectivities.cu", "graph"): {"bytes_per_launch": 1_800_462_336, "kernel_sha": "d6300e549cd22f3b"},
 }
 
 ORDER_MIN_ROWS = 16384   # automatic locality ordering from this many rows (BF16 path)
