@@ -16,6 +16,9 @@ neighbours step uses the UMAP smooth-kNN / fuzzy-union construction):
 * ``fuzzy_union``  -- G = A + A^T - A o A^T as CSR with sorted columns.
 * ``connectivities`` -- smooth_knn followed by fuzzy_union.
 * ``mlp_loss_grad`` -- the partitioner MLP's soft cross-entropy and gradients.
+* ``umap_epochs``  -- epochs of the UMAP layout SGD on a CSR graph (Methods,
+  "Dimensionality reduction and graph analysis": UMAP on the graph).
+* ``splitmix64`` / ``umap_negative`` -- the counter-based negative sampler.
 
 Parity is pinned by tests/test_oracle_pins.py (brute force on tiny inputs,
 closed forms, a library kNN, invariants).
@@ -69,6 +72,14 @@ def _load():
             lib.oracle_fuzzy_union.restype = i32
             lib.oracle_mlp_loss_grad.argtypes = [vp, vp, i64, i32, i32, i32, i32, vp, i32, vp, vp]
             lib.oracle_mlp_loss_grad.restype = i32
+            u64 = ctypes.c_uint64
+            lib.oracle_splitmix64.argtypes = [u64, u64]
+            lib.oracle_splitmix64.restype = u64
+            lib.oracle_umap_negative.argtypes = [u64, i32, i64, i64, i32, i32, i64]
+            lib.oracle_umap_negative.restype = i64
+            lib.oracle_umap_epochs.argtypes = [vp, vp, vp, i64, i32, vp, dbl, dbl, dbl, dbl, i32, i32,
+                                               i32, i32, u64, vp, vp, vp]
+            lib.oracle_umap_epochs.restype = i32
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i32
             _ = dbl
@@ -208,3 +219,40 @@ def mlp_loss_grad(X, T, params, dims, bf16=False, need_grad=True):
     if rc != 0:
         raise ValueError(f"oracle_mlp_loss_grad failed with status {rc}")
     return loss.value, grad
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """Output number i (i >= 1) of SplitMix64 started from `seed`."""
+    return int(_load().oracle_splitmix64(seed & (2**64 - 1), i & (2**64 - 1)))
+
+
+def umap_negative(seed: int, epoch: int, nnz: int, entry: int, neg_rate: int, q: int, n: int) -> int:
+    """Vertex of negative sample q of graph entry `entry` in epoch `epoch` (1-based)."""
+    return int(_load().oracle_umap_negative(seed & (2**64 - 1), epoch, nnz, entry, neg_rate, q, n))
+
+
+def umap_epochs(indptr, indices, data, Y, a, b, gamma=1.0, lr=1.0, neg_rate=5, n_epochs=200,
+                first=1, last=None, seed=0, mask=None):
+    """Epochs first..last (1-based, inclusive) of the N-epoch UMAP layout.
+
+    Y is the float embedding the epochs start from ([n, dim]); returns
+    (Y double [n, dim], absmove double [n], samples int64 [nnz]): absmove is the
+    sum of |move| over the coordinates of every move applied to a vertex in the
+    last epoch run; samples counts the epochs in which each entry was sampled.
+    With `mask` (bool [n]) a single epoch moves only the masked vertices.
+    """
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.int32)
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    Yd = np.ascontiguousarray(np.asarray(Y, dtype=np.float32), dtype=np.float64).copy()
+    n, dim = Yd.shape
+    last = n_epochs if last is None else last
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    absmove = np.zeros(n)
+    samples = np.zeros(max(1, int(indptr[-1])), dtype=np.int64)
+    rc = _load().oracle_umap_epochs(_ptr(indptr), _ptr(indices), _ptr(data), n, dim, _ptr(Yd), float(a), float(b),
+                                    float(gamma), float(lr), neg_rate, n_epochs, first, last,
+                                    seed & (2**64 - 1), _ptr(m), _ptr(absmove), _ptr(samples))
+    if rc != 0:
+        raise ValueError(f"oracle_umap_epochs failed with status {rc}")
+    return Yd, absmove, samples[:int(indptr[-1])]

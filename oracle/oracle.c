@@ -23,6 +23,9 @@
  * The paper states the graph is stored for UMAP/Leiden (Methods, "Dimensionality
  * reduction and graph analysis"); the rho/sigma/union definitions are those of
  * the UMAP method that scanpy follows.
+ *   - UMAP layout (same passage; the UMAP method's embedding optimisation):
+ *     edge-sampled SGD on the graph, epoch by epoch, with its readings stated
+ *     above oracle_umap_epochs; negative samples from SplitMix64.
  *
  * All arithmetic is double; inputs are the float32 arrays the GPU reads.
  */
@@ -446,5 +449,135 @@ int oracle_mlp_loss_grad(const float *X, const float *T, int64_t B, int D, int H
     }
     *loss = total / (double)B;
     free(z1); free(h1); free(z2); free(h2); free(z3); free(dz3); free(dh2); free(dz2); free(dh1); free(dz1); free(xr);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ UMAP layout
+ *
+ * Edge-sampled stochastic gradient layout of the graph (the UMAP method of
+ * McInnes, Healy & Melville 2018, section "Optimizing the embedding"; the
+ * paper runs UMAP on the neighbourhood graph, Methods, "Dimensionality
+ * reduction and graph analysis").  Low-dimensional similarity
+ * phi(d) = 1 / (1 + a d^(2b)); every sampled graph entry pulls its head and
+ * tail together along the gradient of log phi, and each sample draws
+ * `neg_rate` vertices uniformly that push the head away along the gradient of
+ * gamma log(1 - phi), the squared distance offset by 0.001.  Moves are
+ * clipped to [-4, 4] per coordinate and scaled by the learning rate.
+ *
+ * Readings (the paper gives no layout algorithm of its own):
+ *   - epochs n = 1 .. N with alpha_n = lr (1 - (n - 1) / N);
+ *   - entry e of weight w_e is sampled in epoch n when
+ *     floor(n f_e) > floor((n - 1) f_e), f_e = w_e / max w, so it is sampled
+ *     floor(N f_e) times in N epochs (the epochs-per-sample schedule); f_e
+ *     and the products n f_e are single precision, as the GPU takes them;
+ *   - every sampled entry draws exactly neg_rate negative vertices; the q-th
+ *     of entry e in epoch n is vertex hi32(u) * n_vertices >> 32, with u
+ *     output number ((n - 1) nnz + e) neg_rate + q + 1 of SplitMix64 seeded
+ *     with `seed` (Steele, Lea & Flood 2014);
+ *   - no move when the squared distance is 0 (the head itself, or a vertex
+ *     at the same position);
+ *   - an epoch reads the positions it started with: the moves of all its
+ *     samples are summed and applied together at the end of the epoch.
+ */
+static uint64_t splitmix64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Output number i (i >= 1) of SplitMix64 started from `seed`. */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t i) {
+    return splitmix64_mix(seed + i * 0x9E3779B97F4A7C15ULL);
+}
+
+/* Negative vertex q of entry e in epoch n (1-based), uniform on [0, nv). */
+int64_t oracle_umap_negative(uint64_t seed, int epoch, int64_t nnz, int64_t e, int neg_rate, int q, int64_t nv) {
+    const uint64_t ctr = ((uint64_t)(epoch - 1) * (uint64_t)nnz + (uint64_t)e) * (uint64_t)neg_rate + (uint64_t)q;
+    const uint64_t u = oracle_splitmix64(seed, ctr + 1);
+    return (int64_t)(((u >> 32) * (uint64_t)nv) >> 32);
+}
+
+static double clip4(double v) { return v > 4.0 ? 4.0 : (v < -4.0 ? -4.0 : v); }
+
+/* Entry e sampled in epoch n (single-precision schedule). */
+static int umap_sampled(float w, float wmax, int epoch) {
+    const float f = w / wmax;
+    const float now = (float)epoch * f;
+    const float before = (float)(epoch - 1) * f;
+    return floorf(now) > floorf(before);
+}
+
+/*
+ * Epochs first .. last (1-based, inclusive) of an N-epoch layout.
+ * CSR graph (indptr [n+1], indices, data [nnz], weights > 0 expected);
+ * Y [n, dim] double, updated in place.  absmove [n] (nullable) receives, for
+ * the last epoch run, the sum of |move| over every coordinate of every move
+ * applied to the vertex (for tolerances); samples [nnz] (nullable, int64) is
+ * incremented once per epoch in which the entry was sampled.  mask [n]
+ * (nullable) restricts one epoch to the masked vertices: only they move, and
+ * only moves onto them are computed (first must equal last).
+ */
+int oracle_umap_epochs(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n, int dim,
+                       double *Y, double a, double b, double gamma, double lr, int neg_rate, int n_epochs,
+                       int first, int last, uint64_t seed, const uint8_t *mask, double *absmove,
+                       int64_t *samples) {
+    if (!indptr || !Y || n <= 0 || dim < 1 || dim > 16 || neg_rate < 0 || n_epochs < 1 || first < 1 ||
+        last > n_epochs || (mask && first != last))
+        return ORC_BAD_ARG;
+    const int64_t nnz = indptr[n];
+    if (nnz > 0 && (!indices || !data)) return ORC_BAD_ARG;
+    float wmax = 0.f;
+    for (int64_t e = 0; e < nnz; ++e)
+        if (data[e] > wmax) wmax = data[e];
+    double *delta = (double *)calloc((size_t)n * dim, sizeof(double));
+    double *am = (double *)calloc((size_t)n, sizeof(double));
+    if (!delta || !am) { free(delta); free(am); return ORC_NO_MEM; }
+    for (int epoch = first; epoch <= last; ++epoch) {
+        const double alpha = lr * (1.0 - (double)(epoch - 1) / (double)n_epochs);
+        memset(delta, 0, sizeof(double) * (size_t)n * dim);
+        memset(am, 0, sizeof(double) * (size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            for (int64_t e = indptr[i]; e < indptr[i + 1]; ++e) {
+                if (!(wmax > 0.f) || !umap_sampled(data[e], wmax, epoch)) continue;
+                if (samples) samples[e]++;
+                const int64_t j = indices[e];
+                const int head = !mask || mask[i], tail = !mask || mask[j];
+                const double *yi = Y + (size_t)i * dim;
+                if (head || tail) {   /* attraction: head and tail move */
+                    const double *yj = Y + (size_t)j * dim;
+                    double d2 = 0.0;
+                    for (int t = 0; t < dim; ++t) d2 += (yi[t] - yj[t]) * (yi[t] - yj[t]);
+                    if (d2 > 0.0) {
+                        const double c = -2.0 * a * b * pow(d2, b - 1.0) / (1.0 + a * pow(d2, b));
+                        for (int t = 0; t < dim; ++t) {
+                            const double m = alpha * clip4(c * (yi[t] - yj[t]));
+                            if (head) { delta[(size_t)i * dim + t] += m; am[i] += fabs(m); }
+                            if (tail) { delta[(size_t)j * dim + t] -= m; am[j] += fabs(m); }
+                        }
+                    }
+                }
+                if (!head) continue;
+                for (int q = 0; q < neg_rate; ++q) {   /* repulsion: only the head moves */
+                    const int64_t v = oracle_umap_negative(seed, epoch, nnz, e, neg_rate, q, n);
+                    const double *yv = Y + (size_t)v * dim;
+                    double d2 = 0.0;
+                    for (int t = 0; t < dim; ++t) d2 += (yi[t] - yv[t]) * (yi[t] - yv[t]);
+                    if (!(d2 > 0.0)) continue;
+                    const double c = 2.0 * gamma * b / ((0.001 + d2) * (1.0 + a * pow(d2, b)));
+                    for (int t = 0; t < dim; ++t) {
+                        const double m = alpha * clip4(c * (yi[t] - yv[t]));
+                        delta[(size_t)i * dim + t] += m;
+                        am[i] += fabs(m);
+                    }
+                }
+            }
+        }
+        for (int64_t v = 0; v < n; ++v)
+            if (!mask || mask[v])
+                for (int t = 0; t < dim; ++t) Y[(size_t)v * dim + t] += delta[(size_t)v * dim + t];
+    }
+    if (absmove) memcpy(absmove, am, sizeof(double) * (size_t)n);
+    free(delta);
+    free(am);
     return ORC_OK;
 }
