@@ -438,6 +438,81 @@ rsc_status rsc_connectivities_nnz(const int32_t *idx, const float *dist, int64_t
                                   int64_t *nnz, void *workspace, size_t workspace_bytes,
                                   void *stream);
 
+/* ------------------------------------------------------------ UMAP layout
+ *
+ * The layout step UMAP runs on the neighbourhood graph (paper, Methods,
+ * "Dimensionality reduction and graph analysis": UMAP on the stored graph),
+ * by the UMAP method's edge-sampled stochastic gradient optimisation
+ * (McInnes, Healy & Melville 2018, "Optimizing the embedding").
+ */
+typedef struct {
+    float a, b;                    /* phi(d) = 1 / (1 + a d^(2b)) (rsc_umap_find_ab) */
+    float gamma;                   /* repulsion strength (1)                          */
+    float learning_rate;           /* alpha of the first epoch (1)                    */
+    int32_t negative_sample_rate;  /* negatives drawn per sampled entry (5)           */
+    int32_t n_epochs;              /* N, length of the schedule (200; 500 at <= 10,000
+                                      cells in scanpy)                                */
+    int32_t epoch_first;           /* first epoch run, 1-based (0: 1)                 */
+    int32_t epoch_last;            /* last epoch run, inclusive (0: N)                */
+    uint64_t seed;                 /* negative-sample generator seed                  */
+    void *stream;                  /* cudaStream_t, NULL = legacy default stream      */
+} rsc_umap_opts;
+
+/*
+ * a and b of phi(d) = 1 / (1 + a d^(2b)) fitted by least squares to the
+ * target curve 1 for d < min_dist, exp(-(d - min_dist) / spread) beyond, on
+ * 300 evenly spaced points of [0, 3 spread] (the UMAP method's choice of
+ * a, b from spread and min_dist).  Host only; Levenberg-Marquardt from
+ * a = b = 1.  scanpy's defaults (spread 1, min_dist 0.5) give a = 0.583,
+ * b = 1.334.  Errors: RSC_ERR_INVALID_ARG for NULL outputs, spread <= 0,
+ * min_dist < 0 or a fit that does not converge.
+ */
+rsc_status rsc_umap_find_ab(float spread, float min_dist, float *a, float *b);
+
+/*
+ * Minimum workspace for rsc_umap_layout: two [n, dim] position buffers (rows
+ * padded to 4 floats when dim = 3), the entries' sampling frequencies [nnz]
+ * and the largest weight.
+ */
+rsc_status rsc_umap_workspace_size(int64_t n, int64_t nnz, int32_t dim, size_t *bytes);
+
+/*
+ * Epochs opts->epoch_first .. opts->epoch_last of the N-epoch UMAP layout of a
+ * graph, in place on `embedding`.
+ *   indptr [n + 1] int64, indices [nnz] int32, data [nnz] float32: the graph
+ *              as CSR (rsc_connectivities' output).  It must be symmetric
+ *              with equal values (G_ij == G_ji bit for bit, both entries
+ *              stored), as the fuzzy union is: each vertex gathers the moves
+ *              of its own row, which equal the per-entry moves only then.
+ *   embedding  [n, dim] float32 row-major, 1 <= dim <= 4: the positions the
+ *              epochs start from (an initial layout), replaced by the
+ *              positions after the last epoch run.
+ * Epoch n (alpha_n = learning_rate (1 - (n - 1) / N)) samples entry e of
+ * weight w_e when floor(n f_e) > floor((n - 1) f_e), f_e = w_e / max w, both
+ * in FP32, so entry e is sampled floor(N f_e) times in N epochs.  A sampled
+ * entry i -> j moves i by 2 alpha clip(c (y_i - y_j)) with
+ * c = -2ab d^(2(b-1)) / (1 + a d^(2b)) (its own pull and that of its mirror
+ * j -> i), then draws negative_sample_rate vertices v: negative q is vertex
+ * hi32(u) * n >> 32 with u output number ((n - 1) nnz + e) r + q + 1 of
+ * SplitMix64 seeded with `seed` (r = negative_sample_rate), and moves i by
+ * alpha clip(c' (y_i - y_v)), c' = 2 gamma b / ((0.001 + d^2)(1 + a d^(2b))).
+ * clip() bounds each coordinate to [-4, 4]; a zero distance moves nothing.
+ * Every epoch reads the positions the previous one wrote, and all moves of an
+ * epoch are summed (FP32, a fixed order per vertex): the result is
+ * deterministic, and running epochs 1..m and then m+1..N gives the same
+ * positions as one call.  Asynchronous on opts->stream.
+ * Errors: RSC_ERR_INVALID_ARG for NULL pointers, n < 1, n >= 2^31, nnz < 0,
+ * nnz >= 2^31, dim outside 1..4, n_epochs outside 1..100,000, an epoch range
+ * outside 1..N, negative_sample_rate outside 0..64 or non-finite a, b, gamma
+ * or learning_rate; RSC_ERR_WORKSPACE when the workspace is too small.  An
+ * indptr that is not monotone within [0, nnz], or a sampled column outside
+ * [0, n), is skipped and recorded as RSC_ERR_INVALID_ARG in the workspace
+ * status word (rsc_workspace_status); nothing is read out of bounds.
+ */
+rsc_status rsc_umap_layout(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n,
+                           int64_t nnz, int32_t dim, float *embedding, const rsc_umap_opts *opts,
+                           void *workspace, size_t workspace_bytes);
+
 #ifdef __cplusplus
 }
 #endif

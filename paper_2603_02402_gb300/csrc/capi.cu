@@ -1,5 +1,6 @@
 // C ABI entry points (include/rsc.h): argument checks, workspace layout and
 // launch sequences.  Everything numeric happens in the kernels.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 
@@ -751,6 +752,143 @@ rsc_status rsc_connectivities_nnz(const int32_t *idx, const float *dist, int64_t
     if ((s = conn_count_phase(idx, dist, n, k, L.indptr_tmp, nullptr, nullptr, L, st)) != RSC_OK) return s;
     RSC_CUDA_TRY(cudaMemcpyAsync(nnz, L.indptr_tmp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     RSC_CUDA_TRY(cudaStreamSynchronize(st));
+    return RSC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- UMAP layout
+
+namespace rsc {
+namespace {
+
+struct UmapLayout {
+    unsigned int *status;
+    unsigned int *wmax;
+    float *f;
+    float *buf0, *buf1;
+};
+
+UmapLayout carve_umap(void *ws, int64_t n, int64_t nnz, int dim, size_t *bytes) {
+    Carve cv(ws);
+    UmapLayout L;
+    L.status = cv.take<unsigned int>(kStatusBytes / sizeof(unsigned int));
+    L.wmax = cv.take<unsigned int>(1);
+    L.f = cv.take<float>((size_t)std::max<int64_t>(nnz, 1));
+    L.buf0 = cv.take<float>((size_t)n * umap_row_floats(dim));
+    L.buf1 = cv.take<float>((size_t)n * umap_row_floats(dim));
+    if (bytes) *bytes = cv.used;
+    return L;
+}
+
+// Sum of squared residuals of 1 / (1 + a x^(2b)) against the UMAP target curve.
+double umap_ab_sse(const double *x, const double *y, int m, double a, double b) {
+    double s = 0.0;
+    for (int t = 0; t < m; ++t) {
+        const double r = 1.0 / (1.0 + a * pow(x[t], 2.0 * b)) - y[t];
+        s += r * r;
+    }
+    return s;
+}
+
+}  // namespace
+}  // namespace rsc
+
+using namespace rsc;
+
+extern "C" {
+
+rsc_status rsc_umap_find_ab(float spread, float min_dist, float *a_out, float *b_out) {
+    if (!a_out || !b_out) return fail(RSC_ERR_INVALID_ARG, "NULL output");
+    if (!(spread > 0.f) || !(min_dist >= 0.f) || !std::isfinite(spread) || !std::isfinite(min_dist))
+        return fail(RSC_ERR_INVALID_ARG, "spread=%g, min_dist=%g", spread, min_dist);
+    constexpr int m = 300;
+    double x[m], y[m];
+    for (int t = 0; t < m; ++t) {
+        x[t] = 3.0 * spread * t / (m - 1);
+        y[t] = x[t] < min_dist ? 1.0 : exp(-(x[t] - min_dist) / spread);
+    }
+    // Levenberg-Marquardt on (a, b), damping on the diagonal of J^T J.
+    double a = 1.0, b = 1.0, lam = 1e-3;
+    double sse = umap_ab_sse(x, y, m, a, b);
+    bool done = false;
+    for (int it = 0; it < 1000 && !done; ++it) {
+        double jtj[3] = {0, 0, 0}, jtr[2] = {0, 0};
+        for (int t = 0; t < m; ++t) {
+            if (x[t] <= 0.0) continue;   // model 1, no dependence on a or b
+            const double p = pow(x[t], 2.0 * b), den = 1.0 + a * p;
+            const double r = 1.0 / den - y[t];
+            const double ja = -p / (den * den), jb = -a * p * 2.0 * log(x[t]) / (den * den);
+            jtj[0] += ja * ja;
+            jtj[1] += ja * jb;
+            jtj[2] += jb * jb;
+            jtr[0] += ja * r;
+            jtr[1] += jb * r;
+        }
+        for (int tries = 0; tries < 60; ++tries) {
+            const double m00 = jtj[0] * (1.0 + lam), m11 = jtj[2] * (1.0 + lam), m01 = jtj[1];
+            const double det = m00 * m11 - m01 * m01;
+            if (!(fabs(det) > 0.0)) { lam *= 10.0; continue; }
+            const double da = (-jtr[0] * m11 + jtr[1] * m01) / det;
+            const double db = (-jtr[1] * m00 + jtr[0] * m01) / det;
+            const double na = a + da, nb = b + db;
+            const double ns = (na > 0.0 && nb > 0.0) ? umap_ab_sse(x, y, m, na, nb) : INFINITY;
+            if (ns <= sse) {
+                const double step = fabs(da) / fabs(a) + fabs(db) / fabs(b);
+                a = na;
+                b = nb;
+                const double gain = sse - ns;
+                sse = ns;
+                lam = std::max(lam / 10.0, 1e-12);
+                if (step < 1e-12 || gain <= 1e-16 * std::max(sse, 1e-300)) done = true;
+                break;
+            }
+            lam *= 10.0;
+            if (lam > 1e16) { done = true; break; }
+        }
+    }
+    if (!(a > 0.0) || !(b > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+        return fail(RSC_ERR_INVALID_ARG, "a, b fit did not converge");
+    *a_out = (float)a;
+    *b_out = (float)b;
+    return RSC_OK;
+}
+
+rsc_status rsc_umap_workspace_size(int64_t n, int64_t nnz, int32_t dim, size_t *bytes) {
+    if (!bytes) return fail(RSC_ERR_INVALID_ARG, "bytes is NULL");
+    if (n < 1 || n >= (int64_t(1) << 31) || nnz < 0 || nnz >= (int64_t(1) << 31) || dim < 1 || dim > 4)
+        return fail(RSC_ERR_INVALID_ARG, "n=%lld, nnz=%lld, dim=%d", (long long)n, (long long)nnz, dim);
+    carve_umap(nullptr, n, nnz, dim, bytes);
+    return RSC_OK;
+}
+
+rsc_status rsc_umap_layout(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n,
+                           int64_t nnz, int32_t dim, float *embedding, const rsc_umap_opts *o,
+                           void *workspace, size_t workspace_bytes) {
+    size_t need = 0;
+    rsc_status s = rsc_umap_workspace_size(n, nnz, dim, &need);
+    if (s != RSC_OK) return s;
+    if (!o) return fail(RSC_ERR_INVALID_ARG, "opts is NULL");
+    if (!indptr || !embedding || (nnz > 0 && (!indices || !data)))
+        return fail(RSC_ERR_INVALID_ARG, "NULL graph or embedding pointer");
+    const int N = o->n_epochs;
+    if (N < 1 || N > 100000) return fail(RSC_ERR_INVALID_ARG, "n_epochs=%d out of [1, 100000]", N);
+    const int first = o->epoch_first == 0 ? 1 : o->epoch_first;
+    const int last = o->epoch_last == 0 ? N : o->epoch_last;
+    if (first < 1 || last > N || first > last)
+        return fail(RSC_ERR_INVALID_ARG, "epochs %d..%d outside 1..%d", first, last, N);
+    if (o->negative_sample_rate < 0 || o->negative_sample_rate > 64)
+        return fail(RSC_ERR_INVALID_ARG, "negative_sample_rate=%d out of [0, 64]", o->negative_sample_rate);
+    if (!std::isfinite(o->a) || !std::isfinite(o->b) || !std::isfinite(o->gamma) || !std::isfinite(o->learning_rate))
+        return fail(RSC_ERR_INVALID_ARG, "non-finite a, b, gamma or learning_rate");
+    if ((s = check_ws(workspace, workspace_bytes, need)) != RSC_OK) return s;
+    UmapLayout L = carve_umap(workspace, n, nnz, dim, nullptr);
+    cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+    RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, kStatusBytes, st));
+    RSC_CUDA_TRY(launch_umap_prepare(data, nnz, L.wmax, L.f, st));
+    UmapParams p{o->a, o->b, o->gamma, o->learning_rate, o->negative_sample_rate, N, o->seed};
+    RSC_CUDA_TRY(launch_umap_epochs(indptr, indices, L.f, n, nnz, dim, embedding, L.buf0, L.buf1, first, last, p,
+                                    L.status, st));
     return RSC_OK;
 }
 

@@ -257,4 +257,20 @@ cudaError_t launch_conn_indptr(int64_t n, int64_t *indptr, const ConnWork &w, cu
 cudaError_t launch_conn_fill(const int32_t *idx, const float *dist, int64_t n, int k, int64_t *indptr,
                              int32_t *indices, float *data, int64_t cap, const ConnWork &w, cudaStream_t st);
 
+// ---- umap.cu --------------------------------------------------------------
+// UMAP layout epochs (rsc_umap_layout).  Positions live in rows of
+// umap_row_floats(dim) floats inside the workspace.
+struct UmapParams {
+    float a, b, gamma, lr;
+    int neg_rate, n_epochs;
+    uint64_t seed;
+};
+int umap_row_floats(int dim);
+// *wmax_bits = largest positive weight; f[e] = data[e] / that weight.
+cudaError_t launch_umap_prepare(const float *data, int64_t nnz, unsigned int *wmax_bits, float *f, cudaStream_t st);
+// Epochs first .. last on `embedding` [n, dim] through buffers buf0/buf1.
+cudaError_t launch_umap_epochs(const int64_t *indptr, const int32_t *indices, const float *f, int64_t n, int64_t nnz,
+                               int dim, float *embedding, float *buf0, float *buf1, int first, int last,
+                               UmapParams p, unsigned int *status, cudaStream_t st);
+
 }  // namespace rsc

@@ -43,6 +43,13 @@ class rsc_knn_opts(ctypes.Structure):
                 ("locality", ctypes.c_int32), ("prune", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
+class rsc_umap_opts(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_float), ("b", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("learning_rate", ctypes.c_float), ("negative_sample_rate", ctypes.c_int32),
+                ("n_epochs", ctypes.c_int32), ("epoch_first", ctypes.c_int32), ("epoch_last", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes); the full exported surface of include/rsc.h
 _vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
@@ -88,6 +95,10 @@ SIGNATURES = {
     "rsc_knn_partitioned": (_i32, [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rsc_partitioner_save": (_i32, [_vp, ctypes.c_char_p]),
     "rsc_partitioner_load": (_i32, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
+    "rsc_umap_find_ab": (_i32, [ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(ctypes.c_float)]),
+    "rsc_umap_workspace_size": (_i32, [_i64, _i64, _i32, ctypes.POINTER(_sz)]),
+    "rsc_umap_layout": (_i32, [_vp, _vp, _vp, _i64, _i64, _i32, _vp, ctypes.POINTER(rsc_umap_opts), _vp, _sz]),
 }
 
 
@@ -492,3 +503,43 @@ class Partitioner:
         _check(lib().rsc_partitioner_param_count(h, ctypes.byref(params)))
         obj.d = obj.n_parts = obj.hidden = None
         return obj
+
+
+def rsc_umap_find_ab(spread: float = 1.0, min_dist: float = 0.5):
+    """(a, b) of phi(d) = 1 / (1 + a d^(2b)) fitted to spread / min_dist (host)."""
+    a, b = ctypes.c_float(0), ctypes.c_float(0)
+    _check(lib().rsc_umap_find_ab(spread, min_dist, ctypes.byref(a), ctypes.byref(b)))
+    return float(a.value), float(b.value)
+
+
+def rsc_umap_workspace_size(n: int, nnz: int, dim: int) -> int:
+    out = _sz(0)
+    _check(lib().rsc_umap_workspace_size(n, nnz, dim, ctypes.byref(out)))
+    return int(out.value)
+
+
+def umap_opts(a, b, gamma=1.0, learning_rate=1.0, negative_sample_rate=5, n_epochs=200, epoch_first=0,
+              epoch_last=0, seed=0, stream=None):
+    return rsc_umap_opts(a, b, gamma, learning_rate, negative_sample_rate, n_epochs, epoch_first, epoch_last,
+                         seed & (2**64 - 1), _stream(stream))
+
+
+def rsc_umap_layout(indptr: torch.Tensor, indices: torch.Tensor, data: torch.Tensor, embedding: torch.Tensor,
+                    a: float, b: float, gamma=1.0, learning_rate=1.0, negative_sample_rate=5, n_epochs=200,
+                    epoch_first=0, epoch_last=0, seed=0, nnz=None, stream=None, workspace=None):
+    """Epochs epoch_first..epoch_last (0, 0: all) of the UMAP layout, in place on
+    `embedding` (float32 [n, dim] CUDA tensor, the initial positions).  The
+    graph is the CSR of rsc_connectivities; nnz defaults to indptr[-1] (read
+    from the device, which synchronises: pass it to stay asynchronous)."""
+    if not (embedding.is_cuda and embedding.dtype == torch.float32 and embedding.dim() == 2
+            and embedding.is_contiguous()):
+        raise ValueError("embedding: contiguous float32 [n, dim] CUDA tensor expected")
+    if not (indptr.dtype == torch.int64 and indices.dtype == torch.int32 and data.dtype == torch.float32):
+        raise ValueError("indptr int64, indices int32, data float32 expected")
+    n, dim = embedding.shape
+    nnz = int(indptr[n].item()) if nnz is None else int(nnz)
+    ws = _workspace(rsc_umap_workspace_size(n, nnz, dim), embedding.device, workspace)
+    o = umap_opts(a, b, gamma, learning_rate, negative_sample_rate, n_epochs, epoch_first, epoch_last, seed, stream)
+    _check(lib().rsc_umap_layout(_ptr(indptr), _ptr(indices), _ptr(data), n, nnz, dim, _ptr(embedding),
+                                 ctypes.byref(o), _ptr(ws), ws.numel()))
+    return embedding

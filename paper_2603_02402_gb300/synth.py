@@ -15,6 +15,9 @@ components) of the 1.3M-cell mouse-brain, 2.4M brain and 11M embryo datasets
                      ~ N(0, 0.5 I) (a batch effect).
 * ``anisotropic`` -- mixture whose components have random rotated covariances
                      Q diag(lambda) Q^T, lambda log-uniform in [0.05, 2].
+* ``positions``   -- starting positions for UMAP layout epochs: uniform in
+                     [-10, 10]^dim (a random initial layout) or Gaussian blobs
+                     (a layout part-way through its epochs).
 """
 from __future__ import annotations
 
@@ -138,3 +141,14 @@ def knn_lists(n: int, k: int, seed: int = 0, dup_frac: float = 0.0):
         dist[i, 0] = 0.0
         dist[i, 1:] = dd.astype(np.float32)
     return idx, dist
+
+
+def positions(n: int, dim: int = 2, seed: int = 0, clusters: int = 0, scale: float = 10.0) -> np.ndarray:
+    """n x dim float32 positions: uniform in [-scale, scale]^dim, or with
+    clusters > 0 blobs around centres uniform in that box (spread scale / 10)."""
+    rng = _rng(seed + 104729)
+    if clusters <= 0:
+        return rng.uniform(-scale, scale, size=(n, dim)).astype(np.float32)
+    centres = rng.uniform(-scale, scale, size=(clusters, dim))
+    comp = rng.integers(0, clusters, size=n)
+    return (centres[comp] + rng.standard_normal((n, dim)) * (scale / 10.0)).astype(np.float32)

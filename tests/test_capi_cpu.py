@@ -210,3 +210,40 @@ def test_connectivities_k_range(L):
         assert L.rsc_connectivities(fake, fake, 10, bad_k, fake, fake, fake, 100, None, None, fake, 1 << 30,
                                     None) == rsc.RSC_ERR_INVALID_ARG
     assert rsc.rsc_connectivities_max_nnz(10, 1) == 0     # k = 1: every row lists only itself
+
+
+@pytest.mark.parametrize("spread,min_dist", [(1.0, 0.5), (1.0, 0.1), (2.0, 0.3), (1.0, 0.0), (0.5, 1.0)])
+def test_umap_find_ab_matches_scipy_curve_fit(L, spread, min_dist):
+    optimize = pytest.importorskip("scipy.optimize")
+    import numpy as np
+    x = np.linspace(0, 3 * spread, 300)
+    y = np.where(x < min_dist, 1.0, np.exp(-(x - min_dist) / spread))
+    (sa, sb), _ = optimize.curve_fit(lambda x, a, b: 1.0 / (1.0 + a * x ** (2 * b)), x, y)
+    a, b = rsc.rsc_umap_find_ab(spread, min_dist)
+    assert a == pytest.approx(sa, rel=1e-4) and b == pytest.approx(sb, rel=1e-4)
+    if (spread, min_dist) == (1.0, 0.5):
+        assert a == pytest.approx(0.583, abs=5e-4) and b == pytest.approx(1.334, abs=5e-4)
+
+
+def test_umap_argument_errors(L):
+    import ctypes
+    with pytest.raises(rsc.RscError):
+        rsc.rsc_umap_find_ab(0.0, 0.5)
+    with pytest.raises(rsc.RscError):
+        rsc.rsc_umap_find_ab(1.0, -0.1)
+    assert rsc.rsc_umap_workspace_size(1000, 20000, 2) > 20000 * 4 + 2 * 1000 * 2 * 4
+    assert rsc.rsc_umap_workspace_size(1000, 0, 3) >= 2 * 1000 * 4 * 4
+    for args in ((0, 10, 2), (10, -1, 2), (10, 10, 0), (10, 10, 5), (2**31, 10, 2)):
+        with pytest.raises(rsc.RscError):
+            rsc.rsc_umap_workspace_size(*args)
+    fake = ctypes.c_void_p(4096)
+    def call(n=10, nnz=10, dim=2, ws=1 << 20, **kw):
+        o = rsc.rsc_umap_opts(kw.get("a", 0.58), kw.get("b", 1.33), kw.get("gamma", 1.0), kw.get("lr", 1.0),
+                              kw.get("r", 5), kw.get("N", 200), kw.get("first", 0), kw.get("last", 0), 0, None)
+        return L.rsc_umap_layout(fake, fake, fake, n, nnz, dim, fake, ctypes.byref(o), kw.get("wsp", fake), ws)
+    bad = [dict(n=0), dict(dim=5), dict(nnz=-1), dict(N=0), dict(N=100001), dict(first=5, last=4),
+           dict(last=201), dict(first=-1), dict(r=-1), dict(r=65), dict(a=float("nan")), dict(lr=float("inf"))]
+    for kw in bad:
+        assert call(**kw) == rsc.RSC_ERR_INVALID_ARG, kw
+    assert call(ws=16) == rsc.RSC_ERR_WORKSPACE
+    assert call(wsp=None) == rsc.RSC_ERR_WORKSPACE
