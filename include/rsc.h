@@ -493,8 +493,9 @@ rsc_status rsc_umap_workspace_size(int64_t n, int64_t nnz, int32_t dim, size_t *
  * entry i -> j moves i by 2 alpha clip(c (y_i - y_j)) with
  * c = -2ab d^(2(b-1)) / (1 + a d^(2b)) (its own pull and that of its mirror
  * j -> i), then draws negative_sample_rate vertices v: negative q is vertex
- * hi32(u) * n >> 32 with u output number ((n - 1) nnz + e) r + q + 1 of
- * SplitMix64 seeded with `seed` (r = negative_sample_rate), and moves i by
+ * h * n >> 32, h the high (q even) or low (q odd) 32 bits of output number
+ * ((n - 1) nnz + e) ceil(r / 2) + floor(q / 2) + 1 of SplitMix64 seeded with
+ * `seed` (r = negative_sample_rate), and moves i by
  * alpha clip(c' (y_i - y_v)), c' = 2 gamma b / ((0.001 + d^2)(1 + a d^(2b))).
  * clip() bounds each coordinate to [-4, 4]; a zero distance moves nothing.
  * Every epoch reads the positions the previous one wrote, and all moves of an

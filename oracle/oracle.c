@@ -471,9 +471,10 @@ int oracle_mlp_loss_grad(const float *X, const float *T, int64_t B, int D, int H
  *     floor(N f_e) times in N epochs (the epochs-per-sample schedule); f_e
  *     and the products n f_e are single precision, as the GPU takes them;
  *   - every sampled entry draws exactly neg_rate negative vertices; the q-th
- *     of entry e in epoch n is vertex hi32(u) * n_vertices >> 32, with u
- *     output number ((n - 1) nnz + e) neg_rate + q + 1 of SplitMix64 seeded
- *     with `seed` (Steele, Lea & Flood 2014);
+ *     of entry e in epoch n is vertex h * n_vertices >> 32, h the high (q
+ *     even) or low (q odd) 32 bits of output number
+ *     ((n - 1) nnz + e) ceil(neg_rate / 2) + floor(q / 2) + 1 of SplitMix64
+ *     seeded with `seed` (Steele, Lea & Flood 2014);
  *   - no move when the squared distance is 0 (the head itself, or a vertex
  *     at the same position);
  *   - an epoch reads the positions it started with: the moves of all its
@@ -490,11 +491,14 @@ uint64_t oracle_splitmix64(uint64_t seed, uint64_t i) {
     return splitmix64_mix(seed + i * 0x9E3779B97F4A7C15ULL);
 }
 
-/* Negative vertex q of entry e in epoch n (1-based), uniform on [0, nv). */
+/* Negative vertex q of entry e in epoch n (1-based), uniform on [0, nv):
+ * negatives 2h and 2h + 1 use the high and the low 32 bits of one output. */
 int64_t oracle_umap_negative(uint64_t seed, int epoch, int64_t nnz, int64_t e, int neg_rate, int q, int64_t nv) {
-    const uint64_t ctr = ((uint64_t)(epoch - 1) * (uint64_t)nnz + (uint64_t)e) * (uint64_t)neg_rate + (uint64_t)q;
+    const uint64_t pairs = (uint64_t)(neg_rate + 1) / 2;
+    const uint64_t ctr = ((uint64_t)(epoch - 1) * (uint64_t)nnz + (uint64_t)e) * pairs + (uint64_t)(q / 2);
     const uint64_t u = oracle_splitmix64(seed, ctr + 1);
-    return (int64_t)(((u >> 32) * (uint64_t)nv) >> 32);
+    const uint64_t half = (q % 2 == 0) ? (u >> 32) : (u & 0xFFFFFFFFULL);
+    return (int64_t)((half * (uint64_t)nv) >> 32);
 }
 
 static double clip4(double v) { return v > 4.0 ? 4.0 : (v < -4.0 ? -4.0 : v); }

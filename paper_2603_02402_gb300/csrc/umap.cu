@@ -7,8 +7,9 @@
 // distance offset by 0.001); every coordinate of a move is clipped to [-4, 4]
 // and scaled by alpha_n = lr (1 - (n - 1) / N).  Entry e is sampled in epoch n
 // when floor(n f_e) > floor((n - 1) f_e), f_e = w_e / max w (single
-// precision), and negative q of entry e in epoch n is vertex
-// hi32(u) * n >> 32, u = SplitMix64 output ((n - 1) nnz + e) r + q + 1.
+// precision), and negative q of entry e in epoch n is vertex h * n >> 32,
+// h the high (q even) or low (q odd) 32 bits of SplitMix64 output number
+// ((n - 1) nnz + e) ceil(r / 2) + floor(q / 2) + 1.
 //
 // An epoch reads the positions it started with and writes new ones (two
 // buffers), so its result does not depend on the order threads run in.  On a
@@ -87,7 +88,7 @@ struct Vec {
 };
 
 template <int D, int DS>
-__device__ __forceinline__ Vec<DS> load_row(const float *__restrict__ Y, int64_t i) {
+__device__ __forceinline__ Vec<DS> load_row(const float *__restrict__ Y, int i) {
     Vec<DS> r;
     if constexpr (DS == 4) {
         const float4 q = __ldg(reinterpret_cast<const float4 *>(Y) + i);
@@ -118,19 +119,21 @@ struct UmapWarpSmem {
     int32_t qr[kQueue];              //   its row inside the warp's block
 };
 
-// Moves of a batch: lane L takes queued entry L (L < cnt) and returns its
-// attraction (doubled, for the mirror entry) plus its negatives' repulsion.
+// Moves of a batch: lane L takes queued entry off + L (L < cnt) and returns
+// its attraction (doubled, for the mirror entry) plus its negatives' repulsion.
 template <int D, int DS>
-__device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, int cnt, int64_t r0,
+__device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, int off, int cnt, int64_t r0,
                                             const float *__restrict__ Yin, int64_t n, int64_t nnz, int epoch,
                                             const UmapParams &p, float alpha, float (&acc)[D]) {
 #pragma unroll
     for (int t = 0; t < D; ++t) acc[t] = 0.f;
     if (lane >= cnt) return;
-    const int64_t e = sm.qe[lane];
-    const uint64_t ctr0 = ((uint64_t)(epoch - 1) * (uint64_t)nnz + (uint64_t)e) * (uint64_t)p.neg_rate;
-    const Vec<DS> yi = load_row<D, DS>(Yin, r0 + sm.qr[lane]);
-    const Vec<DS> yj = load_row<D, DS>(Yin, sm.qj[lane]);
+    const int64_t e = sm.qe[off + lane];
+    // negatives 2h and 2h + 1 take the high and low halves of output number
+    // ((n - 1) nnz + e) ceil(r / 2) + h + 1
+    const uint64_t ctr0 = ((uint64_t)(epoch - 1) * (uint64_t)nnz + (uint64_t)e) * (uint64_t)((p.neg_rate + 1) >> 1);
+    const Vec<DS> yi = load_row<D, DS>(Yin, (int)r0 + sm.qr[off + lane]);
+    const Vec<DS> yj = load_row<D, DS>(Yin, sm.qj[off + lane]);
     // attraction: c = -2ab d2^(b-1) / (1 + a d2^b)
     {
         float dy[D], d2 = 0.f;
@@ -140,7 +143,7 @@ __device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, in
             d2 = fmaf(dy[t], dy[t], d2);
         }
         if (d2 > 0.f) {
-            const float lg = log2f(d2);
+            const float lg = __log2f(d2);
             const float pb = exp2f(p.b * lg), pbm1 = exp2f((p.b - 1.f) * lg);
             const float c = __fdividef(-2.f * p.a * p.b * pbm1, fmaf(p.a, pb, 1.f));
             const float s = 2.f * alpha;   // entry i -> j and its mirror j -> i
@@ -154,21 +157,25 @@ __device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, in
     for (int q0 = 0; q0 < p.neg_rate; q0 += kNegGroup) {
         Vec<DS> yv[kNegGroup];
 #pragma unroll
-        for (int g = 0; g < kNegGroup; ++g) {
-            const int q = min(q0 + g, p.neg_rate - 1);   // past the last: reload the last (ignored)
-            const uint64_t r64 = splitmix64_at(p.seed, ctr0 + (uint64_t)q + 1);
-            yv[g] = load_row<D, DS>(Yin, (int64_t)__umulhi((unsigned int)(r64 >> 32), (unsigned int)n));
+        for (int g = 0; g < kNegGroup; g += 2) {
+            if (q0 + g < p.neg_rate) {
+                const uint64_t r64 = splitmix64_at(p.seed, ctr0 + (uint64_t)((q0 + g) >> 1) + 1);
+                yv[g] = load_row<D, DS>(Yin, (int)__umulhi((unsigned int)(r64 >> 32), (unsigned int)n));
+                if (q0 + g + 1 < p.neg_rate)
+                    yv[g + 1] = load_row<D, DS>(Yin, (int)__umulhi((unsigned int)r64, (unsigned int)n));
+            }
         }
 #pragma unroll
         for (int g = 0; g < kNegGroup; ++g) {
+            if (q0 + g >= p.neg_rate) break;
             float dy[D], d2 = 0.f;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
                 dy[t] = yi.v[t] - yv[g].v[t];
                 d2 = fmaf(dy[t], dy[t], d2);
             }
-            if (q0 + g < p.neg_rate && d2 > 0.f) {
-                const float pb = exp2f(p.b * log2f(d2));
+            if (d2 > 0.f) {
+                const float pb = exp2f(p.b * __log2f(d2));
                 const float c = __fdividef(gb2, (0.001f + d2) * fmaf(p.a, pb, 1.f));
 #pragma unroll
                 for (int t = 0; t < D; ++t) acc[t] = fmaf(alpha, clip4(c * dy[t]), acc[t]);
@@ -182,8 +189,8 @@ __device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, in
 // row's segment adds the row's sum.  The order of additions depends only on
 // the queue, so the epoch is deterministic.
 template <int D>
-__device__ __forceinline__ void batch_reduce(UmapWarpSmem &sm, int lane, int cnt, float (&acc)[D]) {
-    const int row = lane < cnt ? sm.qr[lane] : -1;
+__device__ __forceinline__ void batch_reduce(UmapWarpSmem &sm, int lane, int off, int cnt, float (&acc)[D]) {
+    const int row = lane < cnt ? sm.qr[off + lane] : -1;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int ro = __shfl_up_sync(0xffffffffu, row, o);
@@ -287,23 +294,8 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
         int done = 0;
         while (qc - done >= 32 || (!more && qc > done)) {
             const int cnt = min(32, qc - done);
-            if (done > 0) {   // bring the batch to the queue's front
-                int32_t e_ = 0, j_ = 0, r_ = 0;
-                if (lane < cnt) {
-                    e_ = sm.qe[done + lane];
-                    j_ = sm.qj[done + lane];
-                    r_ = sm.qr[done + lane];
-                }
-                __syncwarp();
-                if (lane < cnt) {
-                    sm.qe[lane] = e_;
-                    sm.qj[lane] = j_;
-                    sm.qr[lane] = r_;
-                }
-                __syncwarp();
-            }
-            batch_moves<D, DS>(sm, lane, cnt, r0, Yin, n, nnz, epoch, p, alpha, acc);
-            batch_reduce<D>(sm, lane, cnt, acc);
+            batch_moves<D, DS>(sm, lane, done, cnt, r0, Yin, n, nnz, epoch, p, alpha, acc);
+            batch_reduce<D>(sm, lane, done, cnt, acc);
             done += cnt;
         }
         if (done > 0) {   // move the rest (< 32) to the front
@@ -326,7 +318,7 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
         if (!more) break;
     }
     if (lane < rows) {
-        const Vec<DS> yi = load_row<D, DS>(Yin, r0 + lane);
+        const Vec<DS> yi = load_row<D, DS>(Yin, (int)r0 + lane);
 #pragma unroll
         for (int t = 0; t < DS; ++t) Yout[(r0 + lane) * DS + t] = t < D ? yi.v[t] + sm.acc[lane][t] : 0.f;
     }

@@ -239,3 +239,13 @@ def test_layout_separates_two_cliques():
     inter = d[:h, h:].ravel()
     assert intra.max() < inter.min()
     assert np.median(inter) > 3 * np.median(intra)
+
+
+def test_negative_pairs_share_one_generator_output():
+    # negatives 2h and 2h + 1 of an entry take the high and low halves of one
+    # SplitMix64 output (the generator itself is pinned by published outputs)
+    seed, epoch, nnz, e, r, n = 21, 3, 1000, 17, 5, 123457
+    for q in range(r):
+        u = oracle.splitmix64(seed, ((epoch - 1) * nnz + e) * 3 + q // 2 + 1)
+        h = (u >> 32) if q % 2 == 0 else (u & 0xFFFFFFFF)
+        assert oracle.umap_negative(seed, epoch, nnz, e, r, q, n) == (h * n) >> 32
