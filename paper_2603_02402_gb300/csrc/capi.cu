@@ -766,6 +766,7 @@ struct UmapLayout {
     unsigned int *status;
     unsigned int *wmax;
     float *f;
+    uint8_t *rowoff;
     float *buf0, *buf1;
 };
 
@@ -775,6 +776,7 @@ UmapLayout carve_umap(void *ws, int64_t n, int64_t nnz, int dim, size_t *bytes) 
     L.status = cv.take<unsigned int>(kStatusBytes / sizeof(unsigned int));
     L.wmax = cv.take<unsigned int>(1);
     L.f = cv.take<float>((size_t)std::max<int64_t>(nnz, 1));
+    L.rowoff = cv.take<uint8_t>((size_t)std::max<int64_t>(nnz, 1));
     L.buf0 = cv.take<float>((size_t)n * umap_row_floats(dim));
     L.buf1 = cv.take<float>((size_t)n * umap_row_floats(dim));
     if (bytes) *bytes = cv.used;
@@ -885,10 +887,10 @@ rsc_status rsc_umap_layout(const int64_t *indptr, const int32_t *indices, const 
     UmapLayout L = carve_umap(workspace, n, nnz, dim, nullptr);
     cudaStream_t st = static_cast<cudaStream_t>(o->stream);
     RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, kStatusBytes, st));
-    RSC_CUDA_TRY(launch_umap_prepare(data, nnz, L.wmax, L.f, st));
+    RSC_CUDA_TRY(launch_umap_prepare(indptr, data, n, nnz, L.wmax, L.f, L.rowoff, st));
     UmapParams p{o->a, o->b, o->gamma, o->learning_rate, o->negative_sample_rate, N, o->seed};
-    RSC_CUDA_TRY(launch_umap_epochs(indptr, indices, L.f, n, nnz, dim, embedding, L.buf0, L.buf1, first, last, p,
-                                    L.status, st));
+    RSC_CUDA_TRY(launch_umap_epochs(indptr, indices, L.f, L.rowoff, n, nnz, dim, embedding, L.buf0, L.buf1, first,
+                                    last, p, L.status, st));
     return RSC_OK;
 }
 

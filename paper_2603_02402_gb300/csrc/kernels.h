@@ -266,11 +266,13 @@ struct UmapParams {
     uint64_t seed;
 };
 int umap_row_floats(int dim);
-// *wmax_bits = largest positive weight; f[e] = data[e] / that weight.
-cudaError_t launch_umap_prepare(const float *data, int64_t nnz, unsigned int *wmax_bits, float *f, cudaStream_t st);
+// *wmax_bits = largest positive weight; f[e] = data[e] / that weight;
+// rowoff[e] = (row of e) mod 32.
+cudaError_t launch_umap_prepare(const int64_t *indptr, const float *data, int64_t n, int64_t nnz,
+                                unsigned int *wmax_bits, float *f, uint8_t *rowoff, cudaStream_t st);
 // Epochs first .. last on `embedding` [n, dim] through buffers buf0/buf1.
-cudaError_t launch_umap_epochs(const int64_t *indptr, const int32_t *indices, const float *f, int64_t n, int64_t nnz,
-                               int dim, float *embedding, float *buf0, float *buf1, int first, int last,
-                               UmapParams p, unsigned int *status, cudaStream_t st);
+cudaError_t launch_umap_epochs(const int64_t *indptr, const int32_t *indices, const float *f, const uint8_t *rowoff,
+                               int64_t n, int64_t nnz, int dim, float *embedding, float *buf0, float *buf1, int first,
+                               int last, UmapParams p, unsigned int *status, cudaStream_t st);
 
 }  // namespace rsc

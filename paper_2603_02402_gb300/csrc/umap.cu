@@ -17,9 +17,12 @@
 // the entries i -> j and j -> i are sampled in the same epochs, and the
 // attraction vertex i receives from both is 2 alpha clip(c (y_i - y_j)): each
 // row gathers its own moves, so no vertex is written by two warps and no
-// atomics are needed.  One warp per row: the lanes test the row's entries,
-// the sampled ones are compacted into shared memory, and the (entry, sample)
-// items (one attraction plus r negatives each) are spread over the lanes.
+// atomics are needed.  A warp owns 32 consecutive rows: it streams their
+// entries (sampling frequency, column and a byte holding the entry's row
+// inside the block), queues the sampled ones in shared memory, and works
+// through the queue in batches of 32 entries, one per lane, each lane loading
+// its 1 + r positions together; a segmented scan over the lanes adds each
+// row's share in a fixed order.
 #include <math.h>
 
 #include <algorithm>
@@ -33,11 +36,31 @@ namespace {
 
 constexpr int kUmapWarps = 8;   // rows (warps) per block
 
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
-    uint64_t z = seed + i * 0x9E3779B97F4A7C15ULL;
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;   // SplitMix64 state increment
+
+// SplitMix64 output for state z (= seed + i * kGolden for output number i).
+__device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
+}
+
+// Hardware approximations (PTX lg2 / ex2 / rcp .approx.ftz): log2 with an
+// absolute error near 2^-22, which is what the power 2^(b log2 x) needs.
+__device__ __forceinline__ float lg2_fast(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_fast(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 __device__ __forceinline__ float clip4(float v) { return fminf(fmaxf(v, -4.f), 4.f); }
@@ -61,6 +84,16 @@ __global__ void __launch_bounds__(256) umap_freq_kernel(const float *__restrict_
     const float wmax = __uint_as_float(*wmax_bits);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
         f[e] = wmax > 0.f ? __fdiv_rn(data[e], wmax) : 0.f;
+}
+
+// rowoff[e] = (row of entry e) mod 32, the entry's row inside its warp's block
+// of 32 rows (warp per row; entries outside [0, nnz) are not written).
+__global__ void __launch_bounds__(256) umap_rowoff_kernel(const int64_t *__restrict__ indptr, int64_t n, int64_t nnz,
+                                                          uint8_t *__restrict__ rowoff) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int64_t beg = std::max(indptr[i], (int64_t)0), end = std::min(indptr[i + 1], nnz);
+    for (int64_t e = beg + (threadIdx.x & 31); e < end; e += 32) rowoff[e] = (uint8_t)(i & 31);
 }
 
 // Embedding [n, D] (caller's layout) <-> internal rows of DS floats.
@@ -109,10 +142,9 @@ constexpr int kChunkGroup = 4;
 // Queue of sampled entries: a batch of 32 plus one group's worth.
 constexpr int kQueue = 32 + 32 * kChunkGroup;
 // Negative samples whose positions are loaded together.
-constexpr int kNegGroup = 4;
+constexpr int kNegGroup = 8;
 
 struct UmapWarpSmem {
-    int64_t ptr[kRowsPerWarp];       // row starts of the warp's rows (sanitised; past the last row: INT64_MAX)
     float acc[kRowsPerWarp][4];      // moves gathered per row
     int32_t qe[kQueue];              // queue of sampled entries: entry index
     int32_t qj[kQueue];              //   its column
@@ -130,41 +162,42 @@ __device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, in
     if (lane >= cnt) return;
     const int64_t e = sm.qe[off + lane];
     // negatives 2h and 2h + 1 take the high and low halves of output number
-    // ((n - 1) nnz + e) ceil(r / 2) + h + 1
+    // ((n - 1) nnz + e) ceil(r / 2) + h + 1 (state seed + number * kGolden)
     const uint64_t ctr0 = ((uint64_t)(epoch - 1) * (uint64_t)nnz + (uint64_t)e) * (uint64_t)((p.neg_rate + 1) >> 1);
+    uint64_t state = p.seed + (ctr0 + 1) * kGolden;
     const Vec<DS> yi = load_row<D, DS>(Yin, (int)r0 + sm.qr[off + lane]);
     const Vec<DS> yj = load_row<D, DS>(Yin, sm.qj[off + lane]);
-    // attraction: c = -2ab d2^(b-1) / (1 + a d2^b)
-    {
-        float dy[D], d2 = 0.f;
-#pragma unroll
-        for (int t = 0; t < D; ++t) {
-            dy[t] = yi.v[t] - yj.v[t];
-            d2 = fmaf(dy[t], dy[t], d2);
-        }
-        if (d2 > 0.f) {
-            const float lg = __log2f(d2);
-            const float pb = exp2f(p.b * lg), pbm1 = exp2f((p.b - 1.f) * lg);
-            const float c = __fdividef(-2.f * p.a * p.b * pbm1, fmaf(p.a, pb, 1.f));
-            const float s = 2.f * alpha;   // entry i -> j and its mirror j -> i
-#pragma unroll
-            for (int t = 0; t < D; ++t) acc[t] = fmaf(s, clip4(c * dy[t]), acc[t]);
-        }
-    }
-    // repulsion: c = 2 gamma b / ((0.001 + d2)(1 + a d2^b))
     const float gb2 = 2.f * p.gamma * p.b;
 #pragma unroll 1
-    for (int q0 = 0; q0 < p.neg_rate; q0 += kNegGroup) {
+    for (int q0 = 0; q0 < max(p.neg_rate, 1); q0 += kNegGroup) {   // one pass at least, for the attraction
         Vec<DS> yv[kNegGroup];
 #pragma unroll
         for (int g = 0; g < kNegGroup; g += 2) {
             if (q0 + g < p.neg_rate) {
-                const uint64_t r64 = splitmix64_at(p.seed, ctr0 + (uint64_t)((q0 + g) >> 1) + 1);
+                const uint64_t r64 = splitmix64_mix(state);
+                state += kGolden;
                 yv[g] = load_row<D, DS>(Yin, (int)__umulhi((unsigned int)(r64 >> 32), (unsigned int)n));
                 if (q0 + g + 1 < p.neg_rate)
                     yv[g + 1] = load_row<D, DS>(Yin, (int)__umulhi((unsigned int)r64, (unsigned int)n));
             }
         }
+        if (q0 == 0) {   // attraction: c = -2ab d2^(b-1) / (1 + a d2^b)
+            float dy[D], d2 = 0.f;
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                dy[t] = yi.v[t] - yj.v[t];
+                d2 = fmaf(dy[t], dy[t], d2);
+            }
+            if (d2 > 0.f) {
+                const float lg = lg2_fast(d2);
+                const float pb = ex2_fast(p.b * lg), pbm1 = ex2_fast((p.b - 1.f) * lg);
+                const float c = -2.f * p.a * p.b * pbm1 * rcp_fast(fmaf(p.a, pb, 1.f));
+                const float s = 2.f * alpha;   // entry i -> j and its mirror j -> i
+#pragma unroll
+                for (int t = 0; t < D; ++t) acc[t] = fmaf(s, clip4(c * dy[t]), acc[t]);
+            }
+        }
+        // repulsion: c = 2 gamma b / ((0.001 + d2)(1 + a d2^b))
 #pragma unroll
         for (int g = 0; g < kNegGroup; ++g) {
             if (q0 + g >= p.neg_rate) break;
@@ -175,8 +208,8 @@ __device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, in
                 d2 = fmaf(dy[t], dy[t], d2);
             }
             if (d2 > 0.f) {
-                const float pb = exp2f(p.b * __log2f(d2));
-                const float c = __fdividef(gb2, (0.001f + d2) * fmaf(p.a, pb, 1.f));
+                const float pb = ex2_fast(p.b * lg2_fast(d2));
+                const float c = gb2 * rcp_fast((0.001f + d2) * fmaf(p.a, pb, 1.f));
 #pragma unroll
                 for (int t = 0; t < D; ++t) acc[t] = fmaf(alpha, clip4(c * dy[t]), acc[t]);
             }
@@ -215,8 +248,9 @@ __device__ __forceinline__ void batch_reduce(UmapWarpSmem &sm, int lane, int off
 template <int D, int DS>
 __global__ void __launch_bounds__(32 * kUmapWarps)
 umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
-                  const float *__restrict__ f, int64_t n, int64_t nnz, const float *__restrict__ Yin,
-                  float *__restrict__ Yout, int epoch, UmapParams p, unsigned int *status) {
+                  const float *__restrict__ f, const uint8_t *__restrict__ rowoff, int64_t n, int64_t nnz,
+                  const float *__restrict__ Yin, float *__restrict__ Yout, int epoch, UmapParams p,
+                  unsigned int *status) {
     __shared__ UmapWarpSmem smem[kUmapWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     UmapWarpSmem &sm = smem[warp];
@@ -239,7 +273,6 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
     const int64_t prev = __shfl_sync(0xffffffffu, m, rows - 1);
     const int64_t last = std::max(std::min(std::max(b_last, (int64_t)0), nnz), prev);
     bad |= lane == 0 && (b_last < 0 || b_last > nnz || b_last < prev);
-    sm.ptr[lane] = lane < rows ? m : INT64_MAX;
     if (__any_sync(0xffffffffu, bad) && lane == 0) record_status(status, RSC_ERR_INVALID_ARG);
 #pragma unroll
     for (int t = 0; t < 4; ++t) (&sm.acc[0][0])[t * 32 + lane] = 0.f;
@@ -247,7 +280,7 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
     const int64_t E1 = last;
     const float now = (float)epoch, before = (float)(epoch - 1);
     const float alpha = p.lr * (1.f - (float)(epoch - 1) / (float)p.n_epochs);
-    int64_t base = sm.ptr[0];
+    int64_t base = __shfl_sync(0xffffffffu, m, 0);
     int qc = 0;   // queued entries
     float acc[D];
     while (true) {
@@ -255,11 +288,13 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
         if (more) {
             float fe[kChunkGroup];
             int32_t col[kChunkGroup];
+            int ro[kChunkGroup];
 #pragma unroll
             for (int g = 0; g < kChunkGroup; ++g) {
                 const int64_t e = base + 32 * g + lane;
                 fe[g] = e < E1 ? f[e] : 0.f;
                 col[g] = e < E1 ? indices[e] : 0;
+                ro[g] = e < E1 ? rowoff[e] : 0;
             }
             unsigned int mk[kChunkGroup];
 #pragma unroll
@@ -275,15 +310,10 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
 #pragma unroll
             for (int g = 0; g < kChunkGroup; ++g) {
                 if ((mk[g] >> lane) & 1u) {
-                    const int64_t e = base + 32 * g + lane;
-                    int row = 0;   // last row start <= e (branchless search over 32 starts)
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (sm.ptr[row + step] <= e) row += step;
                     const int slot = qc + __popc(mk[g] & ((1u << lane) - 1u));
-                    sm.qe[slot] = (int32_t)e;
+                    sm.qe[slot] = (int32_t)(base + 32 * g + lane);
                     sm.qj[slot] = col[g];
-                    sm.qr[slot] = row;
+                    sm.qr[slot] = min(ro[g], rows - 1);   // a bad indptr can leave stale bytes: stay in the block
                 }
                 qc += __popc(mk[g]);
             }
@@ -325,16 +355,16 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
 }
 
 template <int D, int DS>
-cudaError_t run_epochs(const int64_t *indptr, const int32_t *indices, const float *f, int64_t n, int64_t nnz,
-                       float *embedding, float *buf0, float *buf1, int first, int last, UmapParams p,
-                       unsigned int *status, cudaStream_t st) {
+cudaError_t run_epochs(const int64_t *indptr, const int32_t *indices, const float *f, const uint8_t *rowoff,
+                       int64_t n, int64_t nnz, float *embedding, float *buf0, float *buf1, int first, int last,
+                       UmapParams p, unsigned int *status, cudaStream_t st) {
     const unsigned pb = (unsigned)ceil_div(n, 256);
     umap_pack_kernel<D, DS><<<pb, 256, 0, st>>>(embedding, n, buf0);
     const unsigned eb = (unsigned)ceil_div(n, (int64_t)kUmapWarps * kRowsPerWarp);
     float *src = buf0, *dst = buf1;
     for (int epoch = first; epoch <= last; ++epoch) {
-        umap_epoch_kernel<D, DS><<<eb, 32 * kUmapWarps, 0, st>>>(indptr, indices, f, n, nnz, src, dst, epoch, p,
-                                                                   status);
+        umap_epoch_kernel<D, DS><<<eb, 32 * kUmapWarps, 0, st>>>(indptr, indices, f, rowoff, n, nnz, src, dst, epoch,
+                                                                   p, status);
         float *t = src;
         src = dst;
         dst = t;
@@ -347,25 +377,30 @@ cudaError_t run_epochs(const int64_t *indptr, const int32_t *indices, const floa
 
 int umap_row_floats(int dim) { return dim == 3 ? 4 : dim; }
 
-cudaError_t launch_umap_prepare(const float *data, int64_t nnz, unsigned int *wmax_bits, float *f, cudaStream_t st) {
+cudaError_t launch_umap_prepare(const int64_t *indptr, const float *data, int64_t n, int64_t nnz,
+                                unsigned int *wmax_bits, float *f, uint8_t *rowoff, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(wmax_bits, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess || nnz == 0) return e;
     const unsigned g = (unsigned)std::min<int64_t>(ceil_div(nnz, 256), (int64_t)sm_count() * 8);
     umap_wmax_kernel<<<g, 256, 0, st>>>(data, nnz, wmax_bits);
     umap_freq_kernel<<<g, 256, 0, st>>>(data, nnz, wmax_bits, f);
+    umap_rowoff_kernel<<<(unsigned)ceil_div(n * 32, 256), 256, 0, st>>>(indptr, n, nnz, rowoff);
     return cudaGetLastError();
 }
 
-cudaError_t launch_umap_epochs(const int64_t *indptr, const int32_t *indices, const float *f, int64_t n, int64_t nnz,
-                               int dim, float *embedding, float *buf0, float *buf1, int first, int last,
-                               UmapParams p, unsigned int *status, cudaStream_t st) {
+cudaError_t launch_umap_epochs(const int64_t *indptr, const int32_t *indices, const float *f, const uint8_t *rowoff,
+                               int64_t n, int64_t nnz, int dim, float *embedding, float *buf0, float *buf1, int first,
+                               int last, UmapParams p, unsigned int *status, cudaStream_t st) {
+#define RSC_UMAP_CASE(D, DS) \
+    return run_epochs<D, DS>(indptr, indices, f, rowoff, n, nnz, embedding, buf0, buf1, first, last, p, status, st)
     switch (dim) {
-        case 1: return run_epochs<1, 1>(indptr, indices, f, n, nnz, embedding, buf0, buf1, first, last, p, status, st);
-        case 2: return run_epochs<2, 2>(indptr, indices, f, n, nnz, embedding, buf0, buf1, first, last, p, status, st);
-        case 3: return run_epochs<3, 4>(indptr, indices, f, n, nnz, embedding, buf0, buf1, first, last, p, status, st);
-        case 4: return run_epochs<4, 4>(indptr, indices, f, n, nnz, embedding, buf0, buf1, first, last, p, status, st);
+        case 1: RSC_UMAP_CASE(1, 1);
+        case 2: RSC_UMAP_CASE(2, 2);
+        case 3: RSC_UMAP_CASE(3, 4);
+        case 4: RSC_UMAP_CASE(4, 4);
         default: return cudaErrorInvalidValue;
     }
+#undef RSC_UMAP_CASE
 }
 
 }  // namespace rsc
