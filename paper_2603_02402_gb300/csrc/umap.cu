@@ -34,7 +34,7 @@ namespace rsc {
 
 namespace {
 
-constexpr int kUmapWarps = 8;   // rows (warps) per block
+constexpr int kUmapWarps = 2;   // warps per block (each owns kRowsPerWarp rows)
 
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;   // SplitMix64 state increment
 
@@ -146,6 +146,7 @@ constexpr int kNegGroup = 8;
 
 struct UmapWarpSmem {
     float acc[kRowsPerWarp][4];      // moves gathered per row
+    float y[kRowsPerWarp][4];        // the rows' own positions
     int32_t qe[kQueue];              // queue of sampled entries: entry index
     int32_t qj[kQueue];              //   its column
     int32_t qr[kQueue];              //   its row inside the warp's block
@@ -165,7 +166,10 @@ __device__ __forceinline__ void batch_moves(const UmapWarpSmem &sm, int lane, in
     // ((n - 1) nnz + e) ceil(r / 2) + h + 1 (state seed + number * kGolden)
     const uint64_t ctr0 = ((uint64_t)(epoch - 1) * (uint64_t)nnz + (uint64_t)e) * (uint64_t)((p.neg_rate + 1) >> 1);
     uint64_t state = p.seed + (ctr0 + 1) * kGolden;
-    const Vec<DS> yi = load_row<D, DS>(Yin, (int)r0 + sm.qr[off + lane]);
+    Vec<DS> yi;
+    const int row = sm.qr[off + lane];
+#pragma unroll
+    for (int t = 0; t < DS; ++t) yi.v[t] = sm.y[row][t];
     const Vec<DS> yj = load_row<D, DS>(Yin, sm.qj[off + lane]);
     const float gb2 = 2.f * p.gamma * p.b;
 #pragma unroll 1
@@ -276,6 +280,11 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
     if (__any_sync(0xffffffffu, bad) && lane == 0) record_status(status, RSC_ERR_INVALID_ARG);
 #pragma unroll
     for (int t = 0; t < 4; ++t) (&sm.acc[0][0])[t * 32 + lane] = 0.f;
+    if (lane < rows) {
+        const Vec<DS> y = load_row<D, DS>(Yin, (int)r0 + lane);
+#pragma unroll
+        for (int t = 0; t < DS; ++t) sm.y[lane][t] = y.v[t];
+    }
     __syncwarp();
     const int64_t E1 = last;
     const float now = (float)epoch, before = (float)(epoch - 1);
@@ -348,9 +357,8 @@ umap_epoch_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict_
         if (!more) break;
     }
     if (lane < rows) {
-        const Vec<DS> yi = load_row<D, DS>(Yin, (int)r0 + lane);
 #pragma unroll
-        for (int t = 0; t < DS; ++t) Yout[(r0 + lane) * DS + t] = t < D ? yi.v[t] + sm.acc[lane][t] : 0.f;
+        for (int t = 0; t < DS; ++t) Yout[(r0 + lane) * DS + t] = t < D ? sm.y[lane][t] + sm.acc[lane][t] : 0.f;
     }
 }
 
