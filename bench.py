@@ -45,6 +45,8 @@ TRAFFIC = {
     # the eight launches of one rsc_connectivities call on the 1,000,000-cell k = 15 lists
     # (profiles/connectivities_graph_1m_k15.md), cold-cache under ncu
     ("connectivities.cu", "graph"): {"bytes_per_launch": 1_800_462_336, "kernel_sha": "d6300e549cd22f3b"},
+    # one UMAP epoch of the 1,000,000-cell k = 15 graph (profiles/umap_epoch_1m.md): 220.9 + 8.1 MB
+    ("umap.cu", "epoch"): {"bytes_per_launch": 228_918_272, "kernel_sha": "3b64a6d38e4b0abd"},
 }
 
 ORDER_MIN_ROWS = 16384   # automatic locality ordering from this many rows (BF16 path)
