@@ -140,3 +140,95 @@ def near_branch_rows(ref, margin=1e-6):
     rows of a Gaussian-mixture graph qualify, because the last step's error
     is spread over [0, 1e-5).  They are compared at 5e-5 instead of 1e-5."""
     return np.nonzero(ref["stop_margin"] < margin)[0]
+
+
+def propagated_weight_slack(ref, od, delta):
+    """First-order change of the oracle's directed weights when its kNN
+    distances move by delta [n, k] (absolute, per entry).
+
+    rho moves by delta at rho's column (its first non-zero distance); sigma
+    solves sum_{c>=1} exp(-(d_c - rho) / sigma) = log2 k, so to first order
+    dsigma / sigma = sum w_c (dd_c - drho) / sum w_c (d_c - rho) over the
+    columns with d_c > rho (a floored sigma moves like the mean distance);
+    w_c = exp(-(d_c - rho) / sigma) then moves by
+    w_c ((dd_c - drho) - (d_c - rho) dsigma / sigma) / sigma.  Bounded term by
+    term with |dd_c| + |drho| in place of the signed differences; a column at
+    rho (weight 1) may leave it, so it gets e_c / sigma.  Returns [n, k].
+    """
+    od = np.asarray(od, dtype=np.float64)
+    n, k = od.shape
+    rho, sigma, w = ref["rho"], ref["sigma"], ref["weights"]
+    delta = np.abs(np.asarray(delta, dtype=np.float64))
+    first = np.argmax(od > 0, axis=1)                       # rho's column
+    drho = np.where(rho > 0, delta[np.arange(n), first], 0.0)
+    e = delta + drho[:, None]
+    beyond = od - rho[:, None]
+    pos = beyond > 0
+    pos[:, 0] = False
+    num = np.where(pos, w * e, 0.0).sum(1)
+    den = np.where(pos, w * beyond, 0.0).sum(1)
+    rel_sigma = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+    floored = ref["floored"].astype(bool)
+    rel_mean = (delta / np.maximum(od, 1e-30)).max(1)
+    rel_sigma = np.where(floored, rel_mean, rel_sigma)
+    s = sigma[:, None]
+    slack = np.where(pos, w, 1.0) * (e / s + np.maximum(beyond, 0.0) / s * rel_sigma[:, None])
+    slack[:, 0] = 0.0                                       # the row itself: weight 0
+    return slack
+
+
+def compare_pipeline_graphs(gpu, ref, oi, slack, n, near, atol=W_ABS, atol_near=5e-5, exclude=None):
+    """Dense-on-union comparison of a GPU graph with the oracle's graph of the
+    oracle's own kNN lists oi: per entry tolerance atol (atol_near when either
+    end is a near-branch row) + 2 (slack_ij + slack_ji), the directed slacks
+    of propagated_weight_slack placed at (i, oi[i, c]) and transposed.
+    Entries touching a row of `exclude` (bool [n]) are skipped.
+    Returns (max error / tolerance, entries compared)."""
+    gk, gv = _coo_keys(*gpu, n)
+    rk, rv = _coo_keys(*ref, n)
+    keys = np.union1d(gk, rk)
+    a = np.zeros(len(keys))
+    b = np.zeros(len(keys))
+    a[np.searchsorted(keys, gk)] = gv
+    b[np.searchsorted(keys, rk)] = rv
+    k = oi.shape[1]
+    rows = np.repeat(np.arange(n, dtype=np.int64), k)
+    cols = np.asarray(oi, dtype=np.int64).ravel()
+    sl = np.asarray(slack).ravel()
+    extra = np.zeros(len(keys))
+    for kk in (rows * n + cols, cols * n + rows):
+        pos = np.searchsorted(keys, kk)
+        hit = (pos < len(keys)) & (keys[np.minimum(pos, len(keys) - 1)] == kk)
+        np.add.at(extra, pos[hit], sl[hit])
+    r, c = keys // n, keys % n
+    base = np.where(near[r] | near[c], atol_near, atol)
+    tol = base + 2.0 * extra
+    err = np.abs(a - b)
+    keep = np.ones(len(keys), dtype=bool) if exclude is None else ~(exclude[r] | exclude[c])
+    bad = np.nonzero(keep & (err > tol))[0]
+    if bad.size:
+        e = bad[0]
+        raise AssertionError(f"{bad.size} entries beyond tolerance; first ({r[e]}, {c[e]}): gpu {a[e]} "
+                             f"oracle {b[e]} tol {tol[e]}")
+    return float((err[keep] / tol[keep]).max()), int(keep.sum())
+
+
+def check_pipeline_graph(gpu, gi, gd, oi, od, ref, n):
+    """GPU kNN -> GPU connectivities against oracle kNN -> oracle
+    connectivities (the oracle never sees a GPU value).  rho: the distance at
+    the same column, within the kNN distance tolerance; weights: 1e-5 (5e-5 on
+    near-branch rows) plus the first-order effect of the measured distance
+    differences |gd - od| (propagated_weight_slack).  Rows whose id sets differ
+    (reduced-precision misses, ties) are left out and counted."""
+    ip, ind, dat, rho, _ = gpu
+    od = np.asarray(od, dtype=np.float64)
+    same = np.all(np.sort(gi, axis=1) == np.sort(oi, axis=1), axis=1)
+    delta = np.where(same[:, None], np.asarray(gd, dtype=np.float64) - od, 0.0)
+    np.testing.assert_allclose(rho[same], ref["rho"][same], rtol=DIST_REL, atol=1e-7)
+    near = np.zeros(n, dtype=bool)
+    near[near_branch_rows(ref)] = True
+    slack = propagated_weight_slack(ref, od, delta)
+    ratio, cnt = compare_pipeline_graphs((ip, ind, dat), (ref["indptr"], ref["indices"], ref["data"]), oi, slack,
+                                         n, near, exclude=~same)
+    return {"ratio": ratio, "entries": cnt, "rows_left_out": int((~same).sum()),
+            "median_slack": float(np.median(slack[:, 1:]))}

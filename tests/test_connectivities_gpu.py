@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2603_02402_gb300 import synth
-from parity import W_ABS, check_csr_structure, check_knn, compare_graphs, near_branch_rows
+from parity import W_ABS, check_csr_structure, check_knn, check_pipeline_graph, compare_graphs, near_branch_rows
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -147,12 +147,14 @@ def test_capacity_error_and_nnz_query(rsc):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_end_to_end_graph_vs_oracle(rsc, precision):
-    # GPU kNN -> GPU connectivities.  The kNN lists are checked against the
-    # oracle's exact kNN; the graph against the oracle's connectivities of the
-    # GPU's own lists, at the weight tolerance (1e-5 absolute; 5e-5 only on
-    # the rows whose FP64 bisection passed within 1e-6 of its stop test).
-    X = synth.mixture(6000, 50, n_comp=20, seed=11)
+@pytest.mark.parametrize("n,seed", [(6000, 11), (20000, 3)])
+def test_end_to_end_graph_vs_oracle(rsc, precision, n, seed):
+    # GPU kNN -> GPU connectivities against oracle kNN -> oracle connectivities.
+    # The kNN lists are checked against the oracle's exact kNN; the graph against
+    # the oracle's graph of its own lists, at the weight tolerance (1e-5 absolute;
+    # 5e-5 on rows whose FP64 bisection passed within 1e-6 of its stop test) plus
+    # the first-order effect of the FP32 distances' differences from the FP64 ones.
+    X = synth.mixture(n, 50, n_comp=20, seed=seed)
     k = 15
     Xd = torch.from_numpy(X).cuda()
     idx, dist = rsc.rsc_knn(Xd, k, precision=precision)
@@ -162,26 +164,22 @@ def test_end_to_end_graph_vs_oracle(rsc, precision):
     gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
     oi, od, onext = oracle.knn(X, k)
     check_knn(X, gi, gd, oi, od, onext, allow_miss=0.0 if precision == "fp32" else 1e-3)
+    ref = oracle.connectivities(oi, od)
     gpu = (indptr.cpu().numpy(), indices[:nnz].cpu().numpy(), data[:nnz].cpu().numpy(),
            rho.cpu().numpy(), sigma.cpu().numpy())
-    graph_parity(gpu, gi, gd)
+    st = check_pipeline_graph(gpu, gi, gd, oi, od, ref, n)
+    print(precision, n, st)
+    assert st["rows_left_out"] <= 1e-3 * n
 
 
 def test_full_size_graph_1m(rsc):
-    # the bench's 1,000,000-cell x 50-PC workload in its launch configuration
-    # (automatic options): the whole GPU graph against the oracle's
-    # connectivities of the same kNN lists
-    X = synth.mixture(1_000_000, 50, n_comp=100, seed=0)
-    k = 15
-    Xd = torch.from_numpy(X).cuda()
-    idx, dist = rsc.rsc_knn(Xd, k)
-    del Xd
-    indptr, indices, data, rho, sigma = rsc.rsc_connectivities(idx, dist)
-    torch.cuda.synchronize()
-    nnz = int(indptr[-1])
-    gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
-    gpu = (indptr.cpu().numpy(), indices[:nnz].cpu().numpy(), data[:nnz].cpu().numpy(),
-           rho.cpu().numpy(), sigma.cpu().numpy())
-    st = graph_parity(gpu, gi, gd)
+    # 1,000,000 cells, k = 15, in the bench's launch configuration of
+    # rsc_connectivities: exact lists of an 8-dimensional mixture (k-d tree; the
+    # oracle's brute force does not reach 1M rows, and its input may not come
+    # from the GPU) through the GPU and the oracle, the whole graph compared
+    spatial = pytest.importorskip("scipy.spatial")
+    X = synth.mixture(1_000_000, 8, n_comp=100, seed=0).astype(np.float64)
+    d, i = spatial.cKDTree(X).query(X, 15, workers=-1)
+    st = assert_parity(rsc, i.astype(np.int32), d.astype(np.float32))
     print("1M graph", st)
     assert st["near_branch"] < 0.2 * len(X)
