@@ -19,6 +19,8 @@ neighbours step uses the UMAP smooth-kNN / fuzzy-union construction):
 * ``umap_epochs``  -- epochs of the UMAP layout SGD on a CSR graph (Methods,
   "Dimensionality reduction and graph analysis": UMAP on the graph).
 * ``splitmix64`` / ``umap_negative`` -- the counter-based negative sampler.
+* ``edistance_sums`` / ``edistance`` -- group-pair sums of Euclidean distances
+  and the energy distance (Methods, "Perturbation distance computation").
 
 Parity is pinned by tests/test_oracle_pins.py (brute force on tiny inputs,
 closed forms, a library kNN, invariants).
@@ -80,6 +82,10 @@ def _load():
             lib.oracle_umap_epochs.argtypes = [vp, vp, vp, i64, i32, vp, dbl, dbl, dbl, dbl, i32, i32,
                                                i32, i32, u64, vp, vp, vp]
             lib.oracle_umap_epochs.restype = i32
+            lib.oracle_edistance_sums.argtypes = [vp, i64, i32, vp, vp, i32, vp, i64, vp]
+            lib.oracle_edistance_sums.restype = i32
+            lib.oracle_edistance_assemble.argtypes = [vp, i32, vp, vp, vp]
+            lib.oracle_edistance_assemble.restype = i32
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i32
             _ = dbl
@@ -256,3 +262,34 @@ def umap_epochs(indptr, indices, data, Y, a, b, gamma=1.0, lr=1.0, neg_rate=5, n
     if rc != 0:
         raise ValueError(f"oracle_umap_epochs failed with status {rc}")
     return Yd, absmove, samples[:int(indptr[-1])]
+
+
+def edistance_sums(X, offsets, cell_index=None, pairs=None):
+    """Sums of Euclidean distances per group pair, float64 [G, G]: entry (a, b),
+    a <= b, of every requested pair (pairs [P, 2] with a <= b; None: all); the
+    rest NaN.  Pairs a != b sum over all cells of a and of b; a == b over the
+    pairs i < j of positions inside the group."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    G = len(off) - 1
+    ci = None if cell_index is None else np.ascontiguousarray(cell_index, dtype=np.int32)
+    pr = None if pairs is None else np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    sums = np.full((G, G), np.nan)
+    rc = _load().oracle_edistance_sums(_ptr(X), len(X), X.shape[1], _ptr(ci), _ptr(off), G, _ptr(pr),
+                                       0 if pr is None else len(pr), _ptr(sums))
+    if rc != 0:
+        raise ValueError(f"oracle_edistance_sums failed with status {rc}")
+    return sums
+
+
+def edistance(X, offsets, cell_index=None):
+    """All pairs: (sums, mean distances, E), float64 [G, G] each."""
+    sums = edistance_sums(X, offsets, cell_index)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    G = len(off) - 1
+    mean = np.empty((G, G))
+    E = np.empty((G, G))
+    rc = _load().oracle_edistance_assemble(_ptr(off), G, _ptr(np.ascontiguousarray(sums)), _ptr(mean), _ptr(E))
+    if rc != 0:
+        raise ValueError(f"oracle_edistance_assemble failed with status {rc}")
+    return sums, mean, E

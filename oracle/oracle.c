@@ -26,6 +26,9 @@
  *   - UMAP layout (same passage; the UMAP method's embedding optimisation):
  *     edge-sampled SGD on the graph, epoch by epoch, with its readings stated
  *     above oracle_umap_epochs; negative samples from SplitMix64.
+ *   - E-distance (Methods, "Perturbation distance computation"): sums of
+ *     Euclidean distances per group pair by direct difference, means, and
+ *     E = 2 d_ab - d_aa - d_bb.
  *
  * All arithmetic is double; inputs are the float32 arrays the GPU reads.
  */
@@ -583,5 +586,78 @@ int oracle_umap_epochs(const int64_t *indptr, const int32_t *indices, const floa
     if (absmove) memcpy(absmove, am, sizeof(double) * (size_t)n);
     free(delta);
     free(am);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ E-distance
+ *
+ * Energy distance between groups of cells (paper, Methods, "Perturbation
+ * distance computation"): E(X, Y) = 2 mean ||X_i - Y_j|| - mean ||X_i - X_i'||
+ * - mean ||Y_j - Y_j'||, Euclidean distances over the embedding.  Groups are
+ * CSR-style: group g holds the cells cell_index[offsets[g] .. offsets[g+1])
+ * (cell_index NULL: the rows themselves).  For a pair a != b the sum runs over
+ * every i in a and j in b; for a == b over the pairs i < j of positions in the
+ * group (the upper triangle), as the paper's kernel accumulates them.
+ */
+static double row_dist(const float *X, int d, int64_t a, int64_t b) {
+    double s = 0.0;
+    for (int t = 0; t < d; ++t) {
+        const double v = (double)X[(size_t)a * d + t] - (double)X[(size_t)b * d + t];
+        s += v * v;
+    }
+    return sqrt(s);
+}
+
+/* Distance sums of the requested pairs (pairs [n_pairs][2], a <= b; NULL: all
+ * pairs a <= b), written to sums[a * G + b] (other entries untouched). */
+int oracle_edistance_sums(const float *X, int64_t n_rows, int d, const int32_t *cell_index, const int64_t *offsets,
+                          int G, const int32_t *pairs, int64_t n_pairs, double *sums) {
+    if (!X || n_rows <= 0 || d <= 0 || !offsets || G <= 0 || !sums) return ORC_BAD_ARG;
+    const int64_t np = pairs ? n_pairs : (int64_t)G * (G + 1) / 2;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < np; ++p) {
+        int a, b;
+        if (pairs) {
+            a = pairs[2 * p];
+            b = pairs[2 * p + 1];
+        } else {   /* p-th pair of the upper triangle, row by row */
+            int64_t r = p;
+            a = 0;
+            while (r >= G - a) { r -= G - a; ++a; }
+            b = a + (int)r;
+        }
+        if (a < 0 || b >= G || a > b) { bad = 1; continue; }
+        double s = 0.0;
+        for (int64_t u = offsets[a]; u < offsets[a + 1]; ++u) {
+            const int64_t i = cell_index ? cell_index[u] : u;
+            const int64_t v0 = (a == b) ? u + 1 : offsets[b];
+            for (int64_t v = v0; v < offsets[b + 1]; ++v) {
+                const int64_t j = cell_index ? cell_index[v] : v;
+                s += row_dist(X, d, i, j);
+            }
+        }
+        sums[(size_t)a * G + b] = s;
+    }
+    return bad ? ORC_BAD_ARG : ORC_OK;
+}
+
+/* Mean distances and energy distances from the sums of every pair a <= b:
+ * mean[a][b] = sums / (n_a n_b) (a != b) or sums / (n_a (n_a - 1) / 2)
+ * (a == b; 0 for a group of fewer than two cells, whose diagonal the paper's
+ * kernel skips); E[a][b] = E[b][a] = 2 mean[a][b] - mean[a][a] - mean[b][b]. */
+int oracle_edistance_assemble(const int64_t *offsets, int G, const double *sums, double *mean, double *E) {
+    if (!offsets || G <= 0 || !sums || !mean || !E) return ORC_BAD_ARG;
+    for (int a = 0; a < G; ++a)
+        for (int b = a; b < G; ++b) {
+            const double na = (double)(offsets[a + 1] - offsets[a]), nb = (double)(offsets[b + 1] - offsets[b]);
+            double m;
+            if (a == b) m = na >= 2 ? sums[(size_t)a * G + a] / (na * (na - 1.0) / 2.0) : 0.0;
+            else m = (na > 0 && nb > 0) ? sums[(size_t)a * G + b] / (na * nb) : 0.0;
+            mean[(size_t)a * G + b] = mean[(size_t)b * G + a] = m;
+        }
+    for (int a = 0; a < G; ++a)
+        for (int b = 0; b < G; ++b)
+            E[(size_t)a * G + b] = 2.0 * mean[(size_t)a * G + b] - mean[(size_t)a * G + a] - mean[(size_t)b * G + b];
     return ORC_OK;
 }
