@@ -514,6 +514,62 @@ rsc_status rsc_umap_layout(const int64_t *indptr, const int32_t *indices, const 
                            int64_t nnz, int32_t dim, float *embedding, const rsc_umap_opts *opts,
                            void *workspace, size_t workspace_bytes);
 
+/* ------------------------------------------------------------- E-distance
+ *
+ * Energy distance between groups of cells (paper, Methods, "Perturbation
+ * distance computation"): E(a, b) = 2 d(a, b) - d(a, a) - d(b, b), d the mean
+ * Euclidean distance between the cells of a and b (a != b: all n_a n_b pairs;
+ * a == b: the n_a (n_a - 1) / 2 pairs i < j, 0 for a group of fewer than two
+ * cells).  Groups are CSR-style: group g holds the cells
+ * cell_index[group_offsets[g] .. group_offsets[g + 1]) (the paper's category
+ * offsets and sorted cell index; cell_index NULL: rows group_offsets[g] ..
+ * group_offsets[g + 1] of X themselves).
+ */
+
+/*
+ * Minimum workspace for rsc_edistance with these groups and pairs (host-only
+ * query).  group_offsets and pairs are host arrays, as in rsc_edistance.
+ */
+rsc_status rsc_edistance_workspace_size(int64_t n_rows, int32_t d, const int64_t *group_offsets, int32_t n_groups,
+                                        const int32_t *pairs, int64_t n_pairs, size_t *bytes);
+
+/*
+ * Distance sums, mean distances and energy distances of group pairs.
+ *   X             [n_rows, d] float32 row-major (device), 1 <= d <= 58
+ *                 (RSC_ERR_UNSUPPORTED above: the three K blocks hold d + 6
+ *                 columns each).
+ *   cell_index    [group_offsets[G]] int32 device row ids, or NULL.
+ *   group_offsets [G + 1] int64 HOST array, group_offsets[0] = 0,
+ *                 non-decreasing, group_offsets[G] < 2^31; 1 <= G <= 65535.
+ *   pairs         [n_pairs, 2] int32 HOST array of requested pairs (a, b),
+ *                 a <= b (duplicates allowed), or NULL for every pair a <= b;
+ *                 explicit pairs need G <= 16384.  The paper's
+ *                 onesided_distances is the pairs (ref, b) and (b, b).
+ *   sums          [G, G] float64 device out: S[a][b] (a <= b) for the
+ *                 requested pairs, the sum of the pair's distances (upper
+ *                 triangle of the group on the diagonal); every other entry 0.
+ *   mean, E       [G, G] float64 device out, or NULL: for every (a, b) (both
+ *                 orders) whose pair was requested, the mean distance, and the
+ *                 energy distance where the pair and both diagonals were
+ *                 requested; NaN elsewhere.
+ * Distances are computed on tensor cores from BF16 operands split into high
+ * and low parts (three products per coordinate pair, FP32 accumulation, each
+ * row centred on a common point first), summed in FP32 per 64 columns and in
+ * FP64 beyond; expect about 1e-6 relative error in the sums.  Asynchronous on
+ * `stream`, except that the offsets, the work list and the pair mask are copied
+ * from host memory before the call returns.  Errors: RSC_ERR_INVALID_ARG for
+ * NULL pointers, bad offsets, pairs out of range or a > b, n_rows outside
+ * [1, 2^31) or cells beyond n_rows without a cell index; RSC_ERR_WORKSPACE
+ * when the workspace is missing or small.  A cell index outside [0, n_rows)
+ * is recorded as RSC_ERR_INVALID_ARG in the workspace status word
+ * (rsc_workspace_status); that cell then reads row 0.  Kernel waits that run
+ * out their budget record RSC_ERR_TIMEOUT there.
+ */
+rsc_status rsc_edistance(const float *X, int64_t n_rows, int32_t d, const int32_t *cell_index,
+                         const int64_t *group_offsets, int32_t n_groups, const int32_t *pairs, int64_t n_pairs,
+                         double *sums, double *mean, double *E, void *workspace, size_t workspace_bytes,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

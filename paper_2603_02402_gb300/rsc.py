@@ -99,6 +99,8 @@ SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_float)]),
     "rsc_umap_workspace_size": (_i32, [_i64, _i64, _i32, ctypes.POINTER(_sz)]),
     "rsc_umap_layout": (_i32, [_vp, _vp, _vp, _i64, _i64, _i32, _vp, ctypes.POINTER(rsc_umap_opts), _vp, _sz]),
+    "rsc_edistance_workspace_size": (_i32, [_i64, _i32, _vp, _i32, _vp, _i64, ctypes.POINTER(_sz)]),
+    "rsc_edistance": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
 }
 
 
@@ -543,3 +545,56 @@ def rsc_umap_layout(indptr: torch.Tensor, indices: torch.Tensor, data: torch.Ten
     _check(lib().rsc_umap_layout(_ptr(indptr), _ptr(indices), _ptr(data), n, nnz, dim, _ptr(embedding),
                                  ctypes.byref(o), _ptr(ws), ws.numel()))
     return embedding
+
+
+def _host_i64(a):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def _host_pairs(pairs):
+    import numpy as np
+    return None if pairs is None else np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+
+
+def rsc_edistance_workspace_size(n_rows, d, group_offsets, pairs=None) -> int:
+    off = _host_i64(group_offsets)
+    pr = _host_pairs(pairs)
+    out = _sz(0)
+    _check(lib().rsc_edistance_workspace_size(n_rows, d, off.ctypes.data, len(off) - 1,
+                                              None if pr is None else pr.ctypes.data,
+                                              0 if pr is None else len(pr), ctypes.byref(out)))
+    return int(out.value)
+
+
+def rsc_edistance(X: torch.Tensor, group_offsets, cell_index=None, pairs=None, with_mean=True, workspace=None,
+                  stream=None):
+    """Energy distances of cell groups: returns (sums, mean, E), float64 [G, G]
+    CUDA tensors (mean None without with_mean).  group_offsets and pairs are
+    host arrays (CSR offsets into cell_index, or into the rows of X)."""
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+        raise ValueError("X: float32 [n, d] CUDA tensor expected")
+    X = X.contiguous()
+    n_rows, d = X.shape
+    off = _host_i64(group_offsets)
+    G = len(off) - 1
+    pr = _host_pairs(pairs)
+    if cell_index is not None:
+        if not (cell_index.is_cuda and cell_index.dtype == torch.int32):
+            raise ValueError("cell_index: int32 CUDA tensor expected")
+        cell_index = cell_index.contiguous()
+    ws = _workspace(rsc_edistance_workspace_size(n_rows, d, off, pr), X.device, workspace)
+    sums = torch.empty((G, G), dtype=torch.float64, device=X.device)
+    mean = torch.empty((G, G), dtype=torch.float64, device=X.device) if with_mean else None
+    E = torch.empty((G, G), dtype=torch.float64, device=X.device)
+    _check(lib().rsc_edistance(_ptr(X), n_rows, d, _ptr(cell_index), off.ctypes.data, G,
+                               None if pr is None else pr.ctypes.data, 0 if pr is None else len(pr),
+                               _ptr(sums), _ptr(mean), _ptr(E), _ptr(ws), ws.numel(), _stream(stream)))
+    return sums, mean, E
+
+
+def edistance_onesided_pairs(n_groups: int, ref: int):
+    """Pairs of the paper's onesided_distances: (ref, b) for every b, and (b, b)."""
+    import numpy as np
+    pairs = [(min(ref, b), max(ref, b)) for b in range(n_groups)] + [(b, b) for b in range(n_groups)]
+    return np.array(pairs, dtype=np.int32)

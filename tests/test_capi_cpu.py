@@ -247,3 +247,25 @@ def test_umap_argument_errors(L):
         assert call(**kw) == rsc.RSC_ERR_INVALID_ARG, kw
     assert call(ws=16) == rsc.RSC_ERR_WORKSPACE
     assert call(wsp=None) == rsc.RSC_ERR_WORKSPACE
+
+
+def test_edistance_argument_errors(L):
+    import numpy as np
+    off = np.array([0, 10, 25, 40], np.int64)
+    assert rsc.rsc_edistance_workspace_size(40, 50, off) > 40 * 2 * 384
+    pairs = np.array([[0, 0], [0, 2]], np.int32)
+    assert rsc.rsc_edistance_workspace_size(40, 50, off, pairs) > rsc.rsc_edistance_workspace_size(40, 50, off) - 1
+    bad = [
+        (40, 0, off, None, rsc.RSC_ERR_INVALID_ARG),                                # d = 0
+        (40, 59, off, None, rsc.RSC_ERR_UNSUPPORTED),                               # d > 58
+        (0, 50, off, None, rsc.RSC_ERR_INVALID_ARG),                                # no rows
+        (40, 50, np.array([1, 10], np.int64), None, rsc.RSC_ERR_INVALID_ARG),       # offsets[0] != 0
+        (40, 50, np.array([0, 10, 5], np.int64), None, rsc.RSC_ERR_INVALID_ARG),    # decreasing
+        (40, 50, np.array([0, 0], np.int64), None, rsc.RSC_ERR_INVALID_ARG),        # no cells
+        (40, 50, off, np.array([[1, 0]], np.int32), rsc.RSC_ERR_INVALID_ARG),       # a > b
+        (40, 50, off, np.array([[0, 3]], np.int32), rsc.RSC_ERR_INVALID_ARG),       # b >= G
+    ]
+    for n, d, o, p, code in bad:
+        with pytest.raises(rsc.RscError) as e:
+            rsc.rsc_edistance_workspace_size(n, d, o, p)
+        assert e.value.status == code, (n, d, o, p)
