@@ -91,10 +91,12 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--candidates", type=int, default=0, help="candidates per row before the exact re-rank (0 = default)")
-    p.add_argument("--workload", choices=["graph", "batched", "partitioner", "cosine", "umap"], default="graph",
+    p.add_argument("--workload", choices=["graph", "batched", "partitioner", "cosine", "umap", "edistance"],
+                   default="graph",
                    help="graph: the 1M-cell neighbourhood graph (headline); batched: 64 samples, ~3M cells; "
                         "partitioner: learned-partition kNN graph of 5M cells; cosine: 11M-cell cosine graph, k=30; "
-                        "umap: 200-epoch UMAP layout of the 1M-cell graph")
+                        "umap: 200-epoch UMAP layout of the 1M-cell graph; edistance: all-pairs E-distance of a "
+                        "300k-cell, 2,000-group screen")
     p.add_argument("--epochs", type=int, default=200, help="UMAP layout epochs (umap workload)")
     return p.parse_args()
 
@@ -896,6 +898,117 @@ def run_umap(args):
         print(json.dumps(line), flush=True)
 
 
+ED_WORKLOAD = ("E-distance of a perturbation screen: 300,000 cells x 50 PCs fp32 (60-cluster mixture), 2,000 "
+               "groups of log-uniform sizes 20-2,000 in a permuted cell index, every group pair a <= b "
+               "(4.5e10 cell pairs), split-BF16 tensor-core distances")
+
+
+def run_edistance(args):
+    """E-distance workload: cell-pair distances per second of one all-pairs rsc_edistance call."""
+    import numpy as np
+    import torch
+    from paper_2603_02402_gb300 import rsc, synth
+
+    world, rank, local = setup_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rsc.lib()
+    n_cells = args.n if args.n != 1_000_000 else 300_000
+    G = 2000
+    sizes = synth.batched_sizes(G, lo=20, hi=2000, total=n_cells, seed=rank)
+    n = int(sizes.sum())
+    X = synth.mixture(n, 50, n_comp=60, seed=rank)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ci = np.random.default_rng(rank).permutation(n).astype(np.int32)
+    Xd, cd = torch.from_numpy(X).to(dev), torch.from_numpy(ci).to(dev)
+    ws = torch.empty(rsc.rsc_edistance_workspace_size(n, 50, off), dtype=torch.uint8, device=dev)
+    pairs = float(n) * (n - 1) / 2   # every cell pair lies in exactly one group pair a <= b
+
+    def step():
+        return rsc.rsc_edistance(Xd, off, cd, workspace=ws, with_mean=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert rsc.rsc_workspace_status(ws) == rsc.RSC_OK
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sampler = ClockSampler(_smi_id(dev))
+    sampler.__enter__()
+    ev[0].record()
+    for _ in range(args.steps):
+        sums, _, E = step()
+    ev[1].record()
+    torch.cuda.synchronize()
+    sampler.__exit__()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+
+    # end to end: rows and cell index in from pinned memory, E out
+    hX, hc = torch.from_numpy(X).pin_memory(), torch.from_numpy(ci).pin_memory()
+    hE = torch.empty((G, G), dtype=torch.float64).pin_memory()
+    gX, gc = torch.empty_like(Xd), torch.empty_like(cd)
+
+    def e2e_step():
+        gX.copy_(hX, non_blocking=True)
+        gc.copy_(hc, non_blocking=True)
+        _, _, Eo = rsc.rsc_edistance(gX, off, gc, workspace=ws, with_mean=False)
+        hE.copy_(Eo, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 5))
+    ev[0].record()
+    for _ in range(k):
+        e2e_step()
+    ev[1].record()
+    torch.cuda.synchronize()
+    e2e_ms = ev[0].elapsed_time(ev[1]) / k
+
+    peaks = _peaks()
+    clk = (sampler.summary() or {}).get("sm_mhz") or 2070.0
+    sfu_peak = 152 * 16 * clk * 1e6 / 1e12   # square roots per second (T/s): 16 per SM per clock
+    achieved = pairs / (ms / 1e3) / 1e12
+    tiles = 0
+    T = (n + 127) // 128
+    tiles = T * (T + 1) // 2
+    tflops = 2.0 * 128 * 128 * 192 * tiles / (ms / 1e3) / 1e12
+    line = {"metric": "E-distance cell-pair distances/s (300k cells, 2,000 groups, 50 PCs, all pairs)",
+            "value": pairs / (ms / 1e3), "unit": "distances/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": ED_WORKLOAD, "n": n, "groups": G, "d": 50, "cell_pairs": pairs,
+                       "tile_pairs": tiles,
+                       "l2": "operands (230 MB) stream from HBM/L2 per query tile; the G x G sums stay in L2"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tsqrt/s",
+                         "frac": achieved / sfu_peak, "traffic": None, "kernel": "edist.cu (edist_tc_kernel)",
+                         "peak_source": "derived: 152 SMs x 16 special-function results per clock x median SM clock",
+                         "algorithmic": "one square root per cell pair (n (n - 1) / 2) over the call's CUDA-event time",
+                         "tensor_tflops_executed": tflops,
+                         "tensor_frac_of_measured_bf16": tflops / (peaks.get("bf16_tflops_sustained") or 1729.0)},
+            "e2e": {"value": pairs / (e2e_ms / 1e3), "unit": "distances/s",
+                    "h2d_bytes_per_step": int(X.nbytes + ci.nbytes), "d2h_bytes_per_step": int(G * G * 8),
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": 4 * args.steps,
+            "clocks": sampler.summary()}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rng = np.random.default_rng(3)
+        a, b = rng.integers(0, G, 24), rng.integers(0, G, 24)
+        pl = np.stack([np.minimum(a, b), np.maximum(a, b)], 1).astype(np.int32)
+        cnt = sum(float(sizes[p]) * (sizes[q] if p != q else (sizes[p] - 1) / 2) for p, q in pl)
+        t0 = time.perf_counter()
+        ref = oracle.edistance_sums(X, off, ci, pairs=pl)
+        dt = time.perf_counter() - t0
+        got = sums.cpu().numpy()
+        rel = max(abs(got[p, q] - ref[p, q]) / abs(ref[p, q]) for p, q in pl if ref[p, q] != 0)
+        line["cpu_baseline"] = {"value": cnt / dt, "unit": "distances/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"24 seeded group pairs ({cnt:.3g} cell pairs, FP64 "
+                                                            "direct differences)",
+                                "max_rel_sum_diff": float(rel)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -908,6 +1021,8 @@ def main():
         run_cosine(args)
     elif args.workload == "umap":
         run_umap(args)
+    elif args.workload == "edistance":
+        run_edistance(args)
     else:
         run_ours(args)
 

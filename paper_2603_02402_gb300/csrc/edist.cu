@@ -20,11 +20,14 @@
 // Kernel: persistent, warp-specialised like the kNN search.  A TMA warp loads
 // the 128-row query tile (three K blocks) once per item and 128-row database
 // tiles through a ring of stages; one thread issues the 3 x 4 MMAs of
-// M = 128, N = 128, K = 16 per tile into one of two TMEM accumulators; eight
-// epilogue warps (four TMEM lane quarters x two 64-column halves) take
-// sqrt(max(0, v)) of every value and add it to the current (row group,
-// column group) sum.  A tile's columns split into runs of one group each
-// (warp-uniform); per run a thread adds its FP32 partial to an FP64 sum, and
+// M = 128, N = 128, K = 16 per tile into one of two TMEM accumulators;
+// sixteen epilogue warps (four TMEM lane quarters x four 32-column chunks)
+// take sqrt(max(0, v)) of every value and add it to the current (row group,
+// column group) sum.  A chunk table (the group of a chunk's first column and
+// the length of its run, loaded one tile ahead) gives the columns' groups; a
+// chunk of one group away from the diagonal is summed without predicates.
+// A chunk's columns split into runs of one group each (warp-uniform); per run
+// a thread adds its FP32 partial to an FP64 sum, and
 // when the column group changes the warp reduces the FP64 sums of rows of one
 // group (rows are in group order, so equal groups are adjacent lanes) and
 // one lane per run adds them to S with one double atomic.
@@ -48,9 +51,9 @@ namespace ed {
 constexpr int BM = 128;          // query rows per tile (TMEM lanes)
 constexpr int BN = 128;          // database rows per tile (accumulator columns)
 constexpr int KB = 3;            // 64-wide K blocks: h, l, h against h, h, l
-constexpr int kEpiWarps = 8;     // 4 lane quarters x 2 column halves
+constexpr int kEpiWarps = 16;    // 4 lane quarters x 4 column quarters
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kHalf = BN / 2;    // columns per epilogue warp
+constexpr int kCols = BN / 4;    // columns per epilogue warp (one 32-column chunk)
 constexpr int kQBlk = BM * 128;  // bytes of one 64-element bf16 block of the query tile
 constexpr int kDBlk = BN * 128;
 constexpr int kQBytes = KB * kQBlk;
@@ -154,6 +157,19 @@ __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ X, 
     group[p] = lo;
 }
 
+// Per 32-column chunk of the gathered order: the group of its first column and
+// the length of that group's run inside the chunk (32 when the chunk holds one
+// group), so an epilogue warp knows its columns' group with one load.
+__global__ void __launch_bounds__(256) chunk_kernel(const int32_t *__restrict__ group,
+                                                    const int64_t *__restrict__ offsets, int64_t n,
+                                                    int2 *__restrict__ chunk) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c0 = c * 32;
+    if (c0 >= n) return;
+    const int g = group[c0];
+    const int64_t end = std::min(std::min(offsets[g + 1], n), c0 + 32);
+    chunk[c] = make_int2(g, (int)(end - c0));
+}
 
 __device__ __forceinline__ float sqrt_fast(float x) {
     float r;
@@ -183,8 +199,8 @@ struct EdItem {
 __global__ void __launch_bounds__(kThreads, 1)
 edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const EdItem *__restrict__ items, int n_items, int64_t n, const int32_t *__restrict__ group,
-                const int64_t *__restrict__ offsets, int G, const uint32_t *__restrict__ pair_bits, double *S,
-                unsigned int *status, long long wait_budget) {
+                const int64_t *__restrict__ offsets, const int2 *__restrict__ chunk, int G,
+                const uint32_t *__restrict__ pair_bits, double *S, unsigned int *status, long long wait_budget) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = tck::align1024(smem_raw);
     uint8_t *sQ = smem;
@@ -322,7 +338,7 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     } else {
         // ---------------------------------------------------- epilogue
         const int e = warp - 2;
-        const int half = e >> 2;                 // 64-column half of every tile
+        const int part = e >> 2;                 // 32-column chunk of every tile
         const int quarter = warp & 3;            // TMEM lane quarter this warp may access
         const int r = quarter * 32 + lane;       // query row within the tile
         const uint32_t lane_bits = (uint32_t)(quarter * 32) << 16;
@@ -330,56 +346,77 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         bool ok = true;
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const EdItem wi = items[it];
-            const int64_t i = (int64_t)wi.qt * BM + r;   // gathered position of this thread's row
+            const int64_t q0 = (int64_t)wi.qt * BM;
+            const int64_t i = q0 + r;                    // gathered position of this thread's row
             const int grow = i < n ? group[i] : -1;
             int gc = -1;          // column group of the open sum (warp-uniform)
             double acc = 0.0;     // this row's sum for (grow, gc)
+            auto open = [&](int g) {   // make g the open column group (warp-uniform)
+                if (g != gc) {
+                    if (gc >= 0) flush_sums(acc, grow, gc, lane, G, S);
+                    gc = g;
+                    acc = 0.0;
+                }
+            };
+            auto wanted = [&](int g) -> bool {
+                bool w = grow >= 0 && grow <= g;
+                if (w && pair_bits) {
+                    const int64_t bit = (int64_t)grow * G + g;
+                    w = (pair_bits[bit >> 5] >> (bit & 31)) & 1u;
+                }
+                return w;
+            };
+            int64_t cbase = (int64_t)wi.dt0 * BN + part * kCols;
+            int2 ch = cbase < n ? chunk[cbase >> 5] : make_int2(0, 0);
             for (int dt = wi.dt0; dt < wi.dt1; ++dt, ++gt) {
                 const uint32_t b = gt & 1u;
                 ok = __all_sync(0xffffffffu, wait(&acc_full[b], (gt >> 1) & 1u));
                 if (!ok) break;
                 tc::tc_fence_after();
-                float v[64];
-                {
-                    float va[32], vb[32];
-                    const uint32_t tb = tmem_base + lane_bits + b * BN + half * kHalf;
-                    __syncwarp();
-                    tc::tmem_ld32(tb, va);
-                    tc::tmem_ld32(tb + 32, vb);
-                    tc::tmem_wait_ld();
-#pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        v[u] = sqrt_fast(fmaxf(va[u], 0.f));
-                        v[32 + u] = sqrt_fast(fmaxf(vb[u], 0.f));
-                    }
-                }
-                // the accumulator is in registers: hand it back to the MMA warp
+                float v[32];
+                __syncwarp();
+                tc::tmem_ld32(tmem_base + lane_bits + b * BN + part * kCols, v);
+                tc::tmem_wait_ld();
+                // the values are in registers: hand the accumulator back to the MMA warp
                 tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
-                const int64_t cbase = (int64_t)dt * BN + half * kHalf;
-                const int64_t cend = min(n, cbase + kHalf);
-                for (int64_t c = cbase; c < cend;) {   // runs of one column group (warp-uniform)
-                    const int g = group[c];
-                    const int64_t seg_end = min(cend, offsets[g + 1]);
-                    if (g != gc) {
-                        if (gc >= 0) flush_sums(acc, grow, gc, lane, G, S);
-                        gc = g;
-                        acc = 0.0;
-                    }
-                    bool want = grow >= 0 && grow <= g;
-                    if (want && pair_bits) {
-                        const int64_t bit = (int64_t)grow * G + g;
-                        want = (pair_bits[bit >> 5] >> (bit & 31)) & 1u;
-                    }
-                    if (want) {
-                        const int u0 = (int)(c - cbase), u1 = (int)(seg_end - cbase);
-                        const int64_t above = i - cbase;   // columns u with cbase + u > i count
-                        float part = 0.f;
+                const int2 cur = ch;
+                const int64_t cb = cbase;
+                cbase += BN;
+                if (dt + 1 < wi.dt1 && cbase < n) ch = chunk[cbase >> 5];   // next tile's chunk, loaded early
 #pragma unroll
-                        for (int u = 0; u < kHalf; ++u)
-                            if (u >= u0 && u < u1 && u > above) part += v[u];
-                        acc += (double)part;
+                for (int u = 0; u < 32; ++u) v[u] = sqrt_fast(fmaxf(v[u], 0.f));
+                if (cb >= n) continue;
+                const bool diag = cb < q0 + BM;          // some column may not lie above some row
+                const int64_t above = i - cb;            // columns u with cb + u > i count
+                if (cur.y == 32) {                       // one group over the whole chunk
+                    open(cur.x);
+                    if (wanted(cur.x)) {
+                        float sum = 0.f;
+                        if (!diag) {
+#pragma unroll
+                            for (int u = 0; u < 32; ++u) sum += v[u];
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 32; ++u) sum += (u > above) ? v[u] : 0.f;
+                        }
+                        acc += (double)sum;
+                    }
+                    continue;
+                }
+                const int64_t cend = min(n, cb + kCols);
+                for (int64_t c = cb; c < cend;) {        // runs of one column group (warp-uniform)
+                    const int g = c == cb ? cur.x : group[c];
+                    const int64_t seg_end = c == cb ? cb + cur.y : min(cend, offsets[g + 1]);
+                    open(g);
+                    if (wanted(g)) {
+                        const int u0 = (int)(c - cb), u1 = (int)(seg_end - cb);
+                        float sum = 0.f;
+#pragma unroll
+                        for (int u = 0; u < 32; ++u)
+                            sum += (u >= u0 && u < u1 && u > above) ? v[u] : 0.f;
+                        acc += (double)sum;
                     }
                     c = seg_end;
                 }
@@ -516,6 +553,7 @@ struct EdLayout {
     float *centre;
     __nv_bfloat16 *A, *B;
     int32_t *group;
+    int2 *chunk;
     int64_t *offsets;
     ed::EdItem *items;
     uint32_t *bits;
@@ -529,6 +567,7 @@ EdLayout carve_edistance(void *ws, const EdPlan &p, size_t *bytes) {
     L.A = cv.take<__nv_bfloat16>((size_t)p.n * 64 * ed::KB);
     L.B = cv.take<__nv_bfloat16>((size_t)p.n * 64 * ed::KB);
     L.group = cv.take<int32_t>((size_t)p.n);
+    L.chunk = cv.take<int2>((size_t)ceil_div(p.n, 32));
     L.offsets = cv.take<int64_t>((size_t)p.G + 1);
     L.items = cv.take<ed::EdItem>(std::max<size_t>(p.items.size(), 1));
     L.bits = p.bits.empty() ? nullptr : cv.take<uint32_t>(p.bits.size());
@@ -551,6 +590,8 @@ rsc_status run_edistance_sums(const float *X, int64_t n_rows, int32_t d, const i
     ed::centre_kernel<<<1, 256, 0, st>>>(X, cell, p.n, n_rows, d, L.centre);
     ed::prep_kernel<<<(unsigned)ceil_div(p.n, 256), 256, 0, st>>>(X, cell, p.n, n_rows, d, L.status, L.centre,
                                                                    L.offsets, p.G, L.A, L.B, L.group);
+    const int64_t chunks = ceil_div(p.n, 32);
+    ed::chunk_kernel<<<(unsigned)ceil_div(chunks, 256), 256, 0, st>>>(L.group, L.offsets, p.n, L.chunk);
     RSC_CUDA_TRY(cudaGetLastError());
     if (p.items.empty()) return RSC_OK;
     CUtensorMap ma, mb;
@@ -559,8 +600,8 @@ rsc_status run_edistance_sums(const float *X, int64_t n_rows, int32_t d, const i
     RSC_CUDA_TRY(cudaFuncSetAttribute(ed::edist_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ed::kSmem));
     const int n_items = (int)p.items.size();
     const int grid = std::min(n_items, sm_count());
-    ed::edist_tc_kernel<<<grid, ed::kThreads, ed::kSmem, st>>>(ma, mb, L.items, n_items, p.n, L.group, L.offsets, p.G,
-                                                               L.bits, S, L.status, tc_wait_budget());
+    ed::edist_tc_kernel<<<grid, ed::kThreads, ed::kSmem, st>>>(ma, mb, L.items, n_items, p.n, L.group, L.offsets,
+                                                               L.chunk, p.G, L.bits, S, L.status, tc_wait_budget());
     RSC_CUDA_TRY(cudaGetLastError());
     return RSC_OK;
 }
