@@ -21,6 +21,9 @@ neighbours step uses the UMAP smooth-kNN / fuzzy-union construction):
 * ``splitmix64`` / ``umap_negative`` -- the counter-based negative sampler.
 * ``edistance_sums`` / ``edistance`` -- group-pair sums of Euclidean distances
   and the energy distance (Methods, "Perturbation distance computation").
+* ``nndescent``    -- approximate kNN by synchronous NN-descent with
+  deterministic sampling (the paper's CPU neighbour search is PyNNDescent,
+  Methods, "Benchmarking"); list decisions on FP32 squared distances.
 
 Parity is pinned by tests/test_oracle_pins.py (brute force on tiny inputs,
 closed forms, a library kNN, invariants).
@@ -86,6 +89,8 @@ def _load():
             lib.oracle_edistance_sums.restype = i32
             lib.oracle_edistance_assemble.argtypes = [vp, i32, vp, vp, vp]
             lib.oracle_edistance_assemble.restype = i32
+            lib.oracle_nndescent.argtypes = [vp, i64, i32, i32, i32, i32, i32, i32, dbl, u64, vp, vp, vp, vp]
+            lib.oracle_nndescent.restype = i32
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i32
             _ = dbl
@@ -293,3 +298,22 @@ def edistance(X, offsets, cell_index=None):
     if rc != 0:
         raise ValueError(f"oracle_edistance_assemble failed with status {rc}")
     return sums, mean, E
+
+
+def nndescent(X, k, sample=None, rev_slots=32, cand_slots=64, iters=10, delta=0.0, seed=0):
+    """Synchronous NN-descent (definition above oracle_nndescent in oracle.c).
+
+    Returns (idx int32 [n, k], d2 float32 [n, k] FP32 squared distances in list
+    order, changes int64 [iters], iterations run)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n, d = X.shape
+    S = k if sample is None else sample
+    idx = np.empty((n, k), dtype=np.int32)
+    d2 = np.empty((n, k), dtype=np.float32)
+    ch = np.zeros(max(1, iters), dtype=np.int64)
+    run = ctypes.c_int(0)
+    rc = _load().oracle_nndescent(_ptr(X), n, d, k, S, rev_slots, cand_slots, iters, float(delta),
+                                  seed & (2**64 - 1), _ptr(idx), _ptr(d2), _ptr(ch), ctypes.byref(run))
+    if rc != 0:
+        raise ValueError(f"oracle_nndescent failed with status {rc}")
+    return idx, d2, ch[:iters], run.value

@@ -29,6 +29,12 @@
  *   - E-distance (Methods, "Perturbation distance computation"): sums of
  *     Euclidean distances per group pair by direct difference, means, and
  *     E = 2 d_ab - d_aa - d_bb.
+ *   - Approximate kNN by NN-descent (the paper's CPU neighbour search is
+ *     PyNNDescent, Methods, "Benchmarking"; the method is Dong, Charikar & Li,
+ *     WWW 2011): the synchronous variant stated above oracle_nndescent.  Its
+ *     list decisions are taken on FP32 squared distances (sequential fused
+ *     multiply-adds), the precision the GPU decides in, so that both sides
+ *     take the same integer decisions.
  *
  * All arithmetic is double; inputs are the float32 arrays the GPU reads.
  */
@@ -659,5 +665,269 @@ int oracle_edistance_assemble(const int64_t *offsets, int G, const double *sums,
     for (int a = 0; a < G; ++a)
         for (int b = 0; b < G; ++b)
             E[(size_t)a * G + b] = 2.0 * mean[(size_t)a * G + b] - mean[(size_t)a * G + a] - mean[(size_t)b * G + b];
+    return ORC_OK;
+}
+
+/*
+ * Approximate kNN by NN-descent (Dong, Charikar & Li, "Efficient k-nearest
+ * neighbor graph construction for generic similarity measures", WWW 2011):
+ * a neighbour of a neighbour is probably a neighbour, so every list is
+ * improved by joining, around each point v, the points v's list and reverse
+ * list name.  This is the synchronous form with deterministic sampling that
+ * the library runs (the paper names PyNNDescent as its CPU neighbour search,
+ * Methods, "Benchmarking", and prints no algorithm); every step below is a
+ * reading of the method and is the definition both sides follow.
+ *
+ *   delta2(a, b): FP32 squared Euclidean distance, acc = 0, then for
+ *     t = 0 .. d-1: u = x_a[t] - x_b[t] (FP32), acc = fmaf(u, u, acc).
+ *     (Symmetric bit for bit: x_b - x_a = -(x_a - x_b) exactly.)
+ *   key(x, id) = (bits of x) << 32 | id: lists are ordered by (delta2, id);
+ *     a non-negative float's bits order like its value.
+ *   G(i) = output i (i >= 1) of SplitMix64 seeded with `seed`.
+ *   slot_b(id) = (uint32)(id * 0x9E3779B1) >> (32 - b) (Fibonacci hashing).
+ *
+ * Initial lists: u itself, then the first k - 1 distinct values of
+ * (u + 1 + G(u 2k + j + 1) mod (n - 1)) mod n for j = 0 .. 2k - 1, then (if
+ * still short) u + 1, u + 2, ... mod n not yet present; ordered by key.  Every
+ * entry but u is flagged new.
+ *
+ * Iteration t (0-based), all steps reading the lists B_t as they were when
+ * the iteration began:
+ *   1. Forward samples.  new_f(u): the first S entries (list order) flagged
+ *      new, u itself excluded; their flags are cleared.  old_f(u): the
+ *      entries flagged old before that, u excluded.
+ *   2. Reverse samples.  R (power of two) slots per point for new and for
+ *      old: source u offers the key p(t, u) << 32 | u, p(t, u) the high 32
+ *      bits of G(((t + 1) << 40) | u), to slot slot_logR(u) of every w in
+ *      new_f(u) (resp. old_f(u)); a slot keeps its smallest key.  The ids in
+ *      w's new (resp. old) slots are w's reverse samples.
+ *   3. Join lists.  new(v) = new_f(v) united with v's new reverse samples;
+ *      old(v) = (old_f(v) united with v's old reverse samples) minus new(v).
+ *   4. Local join.  For every v and every unordered pair {a, b}, a != b,
+ *      with a in new(v) and b in new(v) or old(v): x = delta2(a, b); if
+ *      key(x, b) < thr(a) (the key of the last entry of B_t(a)) then
+ *      C(a)[slot_logC(b)] = min(C(a)[...], key(x, b)); the same for b with a.
+ *      (A candidate at or above thr(a) could never enter a's list, so the
+ *      test only spares slots.)  C slots per point start empty.
+ *   5. Merge.  B_{t+1}(u) = the k smallest distinct keys of B_t(u) and u's
+ *      non-empty candidate slots (equal keys are one entry: same id, same
+ *      distance); entries that were in B_t keep their flag, the others are
+ *      flagged new.  changes_t = number of entries not in B_t, summed over u.
+ *   6. Stop after iteration t when changes_t < delta n k.
+ * Output: ids in key order and dist = sqrtf(delta2).
+ */
+static float nd_delta2(const float *X, int d, int64_t a, int64_t b) {
+    float acc = 0.0f;
+    for (int t = 0; t < d; ++t) {
+        const float u = X[(size_t)a * d + t] - X[(size_t)b * d + t];
+        acc = fmaf(u, u, acc);
+    }
+    return acc;
+}
+
+static uint64_t nd_key(float x, int64_t id) {
+    uint32_t bits;
+    memcpy(&bits, &x, sizeof bits);
+    return ((uint64_t)bits << 32) | (uint32_t)id;
+}
+
+static uint32_t nd_slot(int64_t id, int bits) {
+    return (uint32_t)((uint32_t)id * 0x9E3779B1u) >> (32 - bits);
+}
+
+static int nd_log2(int v) {
+    int b = 0;
+    while ((1 << b) < v) ++b;
+    return (1 << b) == v ? b : -1;
+}
+
+static int cmp_u64(const void *a, const void *b) {
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* One pool entry of the merge: key, then 0 for a list entry / 1 for a
+ * candidate (so a list entry comes first among equal keys), and its flag. */
+typedef struct {
+    uint64_t key;
+    int src;
+    int isnew;
+} nd_item;
+
+static int cmp_item(const void *a, const void *b) {
+    const nd_item *x = (const nd_item *)a, *y = (const nd_item *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->src - y->src;
+}
+
+static int nd_has(const int64_t *v, int m, int64_t x) {
+    for (int i = 0; i < m; ++i)
+        if (v[i] == x) return 1;
+    return 0;
+}
+
+/*
+ * X [n, d] float32; k list length (self included), 2 <= k <= n; S new samples
+ * per list (1 <= S <= k); R reverse slots and C candidate slots (powers of
+ * two); T iterations at most; delta >= 0.  Outputs idx [n, k], d2 [n, k]
+ * (the FP32 squared distances), changes [T] (0 for iterations not run) and
+ * iters_run (nullable).
+ */
+int oracle_nndescent(const float *X, int64_t n, int d, int k, int S, int R, int C, int T, double delta,
+                     uint64_t seed, int32_t *idx, float *d2, int64_t *changes, int *iters_run) {
+    const int lr = nd_log2(R), lc = nd_log2(C);
+    if (!X || !idx || !d2 || n < 1 || d < 1 || k < 2 || k > n || S < 1 || S > k || lr < 0 || lc < 0 ||
+        T < 0 || delta < 0)
+        return ORC_BAD_ARG;
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n * k);
+    unsigned char *isnew = (unsigned char *)malloc((size_t)n * k);
+    int64_t *newf = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * S);
+    int *nnew = (int *)malloc(sizeof(int) * (size_t)n);
+    int64_t *oldf = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * k);
+    int *nold = (int *)malloc(sizeof(int) * (size_t)n);
+    uint64_t *rn = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n * R);
+    uint64_t *ro = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n * R);
+    uint64_t *cand = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n * C);
+    uint64_t *thr = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int64_t *jn = (int64_t *)malloc(sizeof(int64_t) * (size_t)(S + R));
+    int64_t *jo = (int64_t *)malloc(sizeof(int64_t) * (size_t)(k + R));
+    nd_item *pool = (nd_item *)malloc(sizeof(nd_item) * (size_t)(k + C));
+    int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    if (!key || !isnew || !newf || !nnew || !oldf || !nold || !rn || !ro || !cand || !thr || !jn || !jo || !pool ||
+        !ids) {
+        free(key); free(isnew); free(newf); free(nnew); free(oldf); free(nold); free(rn); free(ro);
+        free(cand); free(thr); free(jn); free(jo); free(pool); free(ids);
+        return ORC_NO_MEM;
+    }
+    /* initial lists */
+    for (int64_t u = 0; u < n; ++u) {
+        int m = 0;
+        ids[m++] = u;
+        for (int j = 0; j < 2 * k && m < k; ++j) {
+            const uint64_t g = oracle_splitmix64(seed, (uint64_t)u * (uint64_t)(2 * k) + (uint64_t)j + 1);
+            const int64_t r = (u + 1 + (int64_t)(g % (uint64_t)(n - 1))) % n;
+            if (!nd_has(ids, m, r)) ids[m++] = r;
+        }
+        for (int64_t s = 1; m < k; ++s) {
+            const int64_t r = (u + s) % n;
+            if (!nd_has(ids, m, r)) ids[m++] = r;
+        }
+        for (int c = 0; c < k; ++c) key[(size_t)u * k + c] = nd_key(nd_delta2(X, d, u, ids[c]), ids[c]);
+        qsort(key + (size_t)u * k, (size_t)k, sizeof(uint64_t), cmp_u64);
+        for (int c = 0; c < k; ++c)
+            isnew[(size_t)u * k + c] = (int64_t)(uint32_t)key[(size_t)u * k + c] != u;
+    }
+    if (changes)
+        for (int t = 0; t < T; ++t) changes[t] = 0;
+    int run = 0;
+    for (int t = 0; t < T; ++t) {
+        /* 1. forward samples */
+        for (int64_t u = 0; u < n; ++u) {
+            int a = 0, o = 0;
+            for (int c = 0; c < k; ++c) {
+                const size_t e = (size_t)u * k + c;
+                const int64_t id = (int64_t)(uint32_t)key[e];
+                if (id == u) continue;
+                if (isnew[e]) {
+                    if (a < S) {
+                        newf[(size_t)u * S + a++] = id;
+                        isnew[e] = 0;
+                    }
+                } else {
+                    oldf[(size_t)u * k + o++] = id;
+                }
+            }
+            nnew[u] = a;
+            nold[u] = o;
+        }
+        /* 2. reverse samples */
+        for (size_t e = 0; e < (size_t)n * R; ++e) rn[e] = ro[e] = UINT64_MAX;
+        for (int64_t u = 0; u < n; ++u) {
+            const uint64_t p = oracle_splitmix64(seed, ((uint64_t)(t + 1) << 40) | (uint64_t)u) >> 32;
+            const uint64_t pk = (p << 32) | (uint32_t)u;
+            const uint32_t s = nd_slot(u, lr);
+            for (int i = 0; i < nnew[u]; ++i) {
+                uint64_t *q = rn + (size_t)newf[(size_t)u * S + i] * R + s;
+                if (pk < *q) *q = pk;
+            }
+            for (int i = 0; i < nold[u]; ++i) {
+                uint64_t *q = ro + (size_t)oldf[(size_t)u * k + i] * R + s;
+                if (pk < *q) *q = pk;
+            }
+        }
+        /* 3-4. join lists and local join */
+        for (size_t e = 0; e < (size_t)n * C; ++e) cand[e] = UINT64_MAX;
+        for (int64_t u = 0; u < n; ++u) thr[u] = key[(size_t)u * k + k - 1];
+        for (int64_t v = 0; v < n; ++v) {
+            int a = 0, o = 0;
+            for (int i = 0; i < nnew[v]; ++i)
+                if (!nd_has(jn, a, newf[(size_t)v * S + i])) jn[a++] = newf[(size_t)v * S + i];
+            for (int s = 0; s < R; ++s) {
+                const uint64_t q = rn[(size_t)v * R + s];
+                if (q != UINT64_MAX && !nd_has(jn, a, (int64_t)(uint32_t)q)) jn[a++] = (int64_t)(uint32_t)q;
+            }
+            for (int i = 0; i < nold[v]; ++i) {
+                const int64_t id = oldf[(size_t)v * k + i];
+                if (!nd_has(jn, a, id) && !nd_has(jo, o, id)) jo[o++] = id;
+            }
+            for (int s = 0; s < R; ++s) {
+                const uint64_t q = ro[(size_t)v * R + s];
+                if (q == UINT64_MAX) continue;
+                const int64_t id = (int64_t)(uint32_t)q;
+                if (!nd_has(jn, a, id) && !nd_has(jo, o, id)) jo[o++] = id;
+            }
+            for (int i = 0; i < a; ++i)
+                for (int j = i + 1; j < a + o; ++j) {
+                    const int64_t pa = jn[i], pb = (j < a) ? jn[j] : jo[j - a];
+                    const float x = nd_delta2(X, d, pa, pb);
+                    const uint64_t ka = nd_key(x, pb), kb = nd_key(x, pa);
+                    if (ka < thr[pa]) {
+                        uint64_t *q = cand + (size_t)pa * C + nd_slot(pb, lc);
+                        if (ka < *q) *q = ka;
+                    }
+                    if (kb < thr[pb]) {
+                        uint64_t *q = cand + (size_t)pb * C + nd_slot(pa, lc);
+                        if (kb < *q) *q = kb;
+                    }
+                }
+        }
+        /* 5. merge */
+        int64_t ch = 0;
+        for (int64_t u = 0; u < n; ++u) {
+            int m = 0;
+            for (int c = 0; c < k; ++c) {
+                pool[m].key = key[(size_t)u * k + c];
+                pool[m].src = 0;
+                pool[m++].isnew = isnew[(size_t)u * k + c];
+            }
+            for (int s = 0; s < C; ++s) {
+                const uint64_t q = cand[(size_t)u * C + s];
+                if (q == UINT64_MAX) continue;
+                pool[m].key = q;
+                pool[m].src = 1;
+                pool[m++].isnew = 1;
+            }
+            qsort(pool, (size_t)m, sizeof(nd_item), cmp_item);
+            int w = 0;
+            for (int i = 0; i < m && w < k; ++i) {
+                if (i > 0 && pool[i].key == pool[i - 1].key) continue;
+                key[(size_t)u * k + w] = pool[i].key;
+                isnew[(size_t)u * k + w] = (unsigned char)pool[i].isnew;
+                ch += pool[i].src;
+                ++w;
+            }
+        }
+        if (changes) changes[t] = ch;
+        ++run;
+        if ((double)ch < delta * (double)n * (double)k) break;
+    }
+    for (size_t e = 0; e < (size_t)n * k; ++e) {
+        idx[e] = (int32_t)(uint32_t)key[e];
+        const uint32_t bits = (uint32_t)(key[e] >> 32);
+        memcpy(&d2[e], &bits, sizeof bits);
+    }
+    if (iters_run) *iters_run = run;
+    free(key); free(isnew); free(newf); free(nnew); free(oldf); free(nold); free(rn); free(ro);
+    free(cand); free(thr); free(jn); free(jo); free(pool); free(ids);
     return ORC_OK;
 }
