@@ -570,6 +570,75 @@ rsc_status rsc_edistance(const float *X, int64_t n_rows, int32_t d, const int32_
                          double *sums, double *mean, double *E, void *workspace, size_t workspace_bytes,
                          void *stream);
 
+/* ------------------------------------------------- approximate kNN (NN-descent)
+ *
+ * The paper's CPU neighbour search is PyNNDescent (Methods, "Benchmarking"), an
+ * approximate kNN by NN-descent (Dong, Charikar & Li, WWW 2011: a neighbour of
+ * a neighbour is probably a neighbour).  This is its synchronous form with
+ * deterministic sampling, a third speed / recall point beside the exact
+ * search.  Euclidean distance only.
+ */
+typedef struct {
+    int32_t sample;      /* S: entries flagged new sampled per list and
+                            iteration, 1 <= S <= k (0: k)                       */
+    int32_t rev_slots;   /* R: reverse-sample slots per point, a power of two
+                            in 1 .. 64 (0: 32)                                  */
+    int32_t cand_slots;  /* C: candidate slots per point, a power of two in
+                            1 .. 64 (0: 64)                                     */
+    int32_t max_iters;   /* T: iterations at most, 1 .. 64 (0: max(5,
+                            round(log2 n)), PyNNDescent's count)                 */
+    double delta;        /* stop after an iteration that changed fewer than
+                            delta n k list entries (0: run all T)               */
+    uint64_t seed;       /* generator seed of the initial lists and the
+                            reverse-sample priorities                           */
+    void *stream;        /* cudaStream_t, NULL = legacy default stream          */
+} rsc_nnd_opts;
+
+/* Minimum workspace for rsc_knn_descent: the lists (8 n k bytes), two masks
+ * per point, 2 n R + n C slots of 8 bytes, the change counters. */
+rsc_status rsc_knn_descent_workspace_size(int64_t n, int32_t d, int32_t k, const rsc_nnd_opts *opts, size_t *bytes);
+
+/*
+ * Approximate k-nearest-neighbour lists of every row of X by NN-descent.
+ *   X        [n, d] float32 row-major (device), 2 <= n < 2^31, d >= 1.
+ *   idx      [n, k] int32 out: each row's list, nearest first, the row itself
+ *            included (k <= min(64, n)); dist [n, k] float32 out: Euclidean
+ *            distance sqrtf(delta2) of each entry.
+ *   changes  [64] int64 device out or NULL: list entries changed by
+ *            iteration t (0 for iterations not run).
+ * Definition (every step on FP32 squared distances delta2(a, b): acc = 0,
+ * then acc = fmaf(x_a[t] - x_b[t], x_a[t] - x_b[t], acc) for t = 0 .. d-1;
+ * lists ordered by key = bits(delta2) << 32 | id; G(i) = output i >= 1 of
+ * SplitMix64 seeded with seed; slot_b(id) = (id * 0x9E3779B1 mod 2^32) >>
+ * (32 - b), 0 for b = 0):
+ *   initial list of u: u, then the first k - 1 distinct values of
+ *   (u + 1 + G(2ku + j + 1) mod (n - 1)) mod n, j = 0 .. 2k-1, then
+ *   u + 1, u + 2, ... mod n while short; all entries but u flagged new.
+ *   Iteration t, on the lists as they were when it began:
+ *   1. new_f(u) = the first S entries flagged new (u excluded), whose flags
+ *      are cleared; old_f(u) = the entries flagged old before (u excluded).
+ *   2. u offers key (G(((t+1) << 40) | u) >> 32) << 32 | u to slot
+ *      slot_log2R(u) of the new (old) reverse slots of every w in new_f(u)
+ *      (old_f(u)); a slot keeps its smallest key.
+ *   3. new(v) = new_f(v) and v's new reverse ids; old(v) = old_f(v) and v's
+ *      old reverse ids, minus new(v).
+ *   4. For every v and pair {a, b}, a != b, a in new(v), b in new(v) or
+ *      old(v): b is offered to a with key(delta2(a, b), b) if that is below
+ *      the key of a's last entry, into slot slot_log2C(b) of a's C candidate
+ *      slots (a slot keeps its smallest key); the same for a to b.
+ *   5. Each list becomes the k smallest distinct keys of itself and its
+ *      candidates; kept entries keep their flags, entered ones are new;
+ *      changes[t] counts the entered ones.
+ *   6. The run stops after an iteration with changes[t] < delta n k.
+ * The result is deterministic (the same bits on every run and launch shape).
+ * Asynchronous on opts->stream.  Errors: RSC_ERR_INVALID_ARG for NULL
+ * pointers, sizes or options outside the ranges above; RSC_ERR_WORKSPACE for
+ * a missing or small workspace; RSC_ERR_UNSUPPORTED when the join's shared
+ * memory (4 d (S + 2R + k) bytes and a little more) exceeds 200 KiB.
+ */
+rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, int32_t *idx, float *dist,
+                           int64_t *changes, const rsc_nnd_opts *opts, void *workspace, size_t workspace_bytes);
+
 #ifdef __cplusplus
 }
 #endif

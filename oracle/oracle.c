@@ -684,7 +684,8 @@ int oracle_edistance_assemble(const int64_t *offsets, int G, const double *sums,
  *   key(x, id) = (bits of x) << 32 | id: lists are ordered by (delta2, id);
  *     a non-negative float's bits order like its value.
  *   G(i) = output i (i >= 1) of SplitMix64 seeded with `seed`.
- *   slot_b(id) = (uint32)(id * 0x9E3779B1) >> (32 - b) (Fibonacci hashing).
+ *   slot_b(id) = (uint32)(id * 0x9E3779B1) >> (32 - b) (Fibonacci hashing;
+ *     0 when b = 0, a single slot).
  *
  * Initial lists: u itself, then the first k - 1 distinct values of
  * (u + 1 + G(u 2k + j + 1) mod (n - 1)) mod n for j = 0 .. 2k - 1, then (if
@@ -732,7 +733,7 @@ static uint64_t nd_key(float x, int64_t id) {
 }
 
 static uint32_t nd_slot(int64_t id, int bits) {
-    return (uint32_t)((uint32_t)id * 0x9E3779B1u) >> (32 - bits);
+    return bits == 0 ? 0u : (uint32_t)((uint32_t)id * 0x9E3779B1u) >> (32 - bits);
 }
 
 static int nd_log2(int v) {

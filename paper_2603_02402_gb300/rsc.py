@@ -50,6 +50,12 @@ class rsc_umap_opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
 
 
+class rsc_nnd_opts(ctypes.Structure):
+    _fields_ = [("sample", ctypes.c_int32), ("rev_slots", ctypes.c_int32), ("cand_slots", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("delta", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes); the full exported surface of include/rsc.h
 _vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
@@ -101,6 +107,8 @@ SIGNATURES = {
     "rsc_umap_layout": (_i32, [_vp, _vp, _vp, _i64, _i64, _i32, _vp, ctypes.POINTER(rsc_umap_opts), _vp, _sz]),
     "rsc_edistance_workspace_size": (_i32, [_i64, _i32, _vp, _i32, _vp, _i64, ctypes.POINTER(_sz)]),
     "rsc_edistance": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "rsc_knn_descent_workspace_size": (_i32, [_i64, _i32, _i32, ctypes.POINTER(rsc_nnd_opts), ctypes.POINTER(_sz)]),
+    "rsc_knn_descent": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(rsc_nnd_opts), _vp, _sz]),
 }
 
 
@@ -598,3 +606,35 @@ def edistance_onesided_pairs(n_groups: int, ref: int):
     import numpy as np
     pairs = [(min(ref, b), max(ref, b)) for b in range(n_groups)] + [(b, b) for b in range(n_groups)]
     return np.array(pairs, dtype=np.int32)
+
+
+def nnd_opts(sample=0, rev_slots=0, cand_slots=0, max_iters=0, delta=0.0, seed=0, stream=None) -> rsc_nnd_opts:
+    o = rsc_nnd_opts()
+    o.sample, o.rev_slots, o.cand_slots, o.max_iters = sample, rev_slots, cand_slots, max_iters
+    o.delta, o.seed = float(delta), seed & (2**64 - 1)
+    o.stream = _stream(stream) if torch.cuda.is_available() else None
+    return o
+
+
+def rsc_knn_descent_workspace_size(n: int, d: int, k: int, opts: rsc_nnd_opts | None = None) -> int:
+    out = _sz(0)
+    _check(lib().rsc_knn_descent_workspace_size(n, d, k, ctypes.byref(opts or rsc_nnd_opts()), ctypes.byref(out)))
+    return int(out.value)
+
+
+def rsc_knn_descent(X: torch.Tensor, k: int, sample=0, rev_slots=0, cand_slots=0, max_iters=0, delta=0.0, seed=0,
+                    workspace=None, stream=None, with_changes=False):
+    """Approximate kNN by NN-descent: returns (idx int32 [n, k], dist float32
+    [n, k]) CUDA tensors, and the int64 [64] change counts with_changes."""
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+        raise ValueError("X: float32 [n, d] CUDA tensor expected")
+    X = X.contiguous()
+    n, d = X.shape
+    o = nnd_opts(sample, rev_slots, cand_slots, max_iters, delta, seed, stream)
+    ws = _workspace(rsc_knn_descent_workspace_size(n, d, k, o), X.device, workspace)
+    idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((n, k), dtype=torch.float32, device=X.device)
+    ch = torch.zeros(64, dtype=torch.int64, device=X.device) if with_changes else None
+    _check(lib().rsc_knn_descent(_ptr(X), n, d, k, _ptr(idx), _ptr(dist), _ptr(ch), ctypes.byref(o), _ptr(ws),
+                                 ws.numel()))
+    return (idx, dist, ch) if with_changes else (idx, dist)

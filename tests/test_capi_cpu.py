@@ -269,3 +269,25 @@ def test_edistance_argument_errors(L):
         with pytest.raises(rsc.RscError) as e:
             rsc.rsc_edistance_workspace_size(n, d, o, p)
         assert e.value.status == code, (n, d, o, p)
+
+
+def test_knn_descent_argument_errors(L):
+    size = rsc.rsc_knn_descent_workspace_size(1000, 50, 15)
+    # lists, masks, 2 n R + n C slots (R = 32, C = 64), counters
+    assert size >= 1000 * (15 * 8 + 16 + (2 * 32 + 64) * 8)
+    assert rsc.rsc_knn_descent_workspace_size(2000, 50, 15) > size
+    bad = [((1, 5, 2), {}), ((100, 0, 15), {}), ((100, 5, 1), {}), ((10, 5, 11), {}), ((100, 5, 65), {}),
+           ((100, 5, 8), {"sample": 9}), ((100, 5, 8), {"rev_slots": 48}), ((100, 5, 8), {"cand_slots": 128}),
+           ((100, 5, 8), {"max_iters": 65}), ((100, 5, 8), {"delta": -0.5}), ((100, 5, 8), {"delta": float("nan")})]
+    for args, kw in bad:
+        with pytest.raises(rsc.RscError) as e:
+            rsc.rsc_knn_descent_workspace_size(*args, rsc.nnd_opts(**kw))
+        assert e.value.status == rsc.RSC_ERR_INVALID_ARG, (args, kw)
+    # the join's staged rows must fit in shared memory
+    with pytest.raises(rsc.RscError) as e:
+        rsc.rsc_knn_descent_workspace_size(1000, 4096, 64, rsc.nnd_opts(rev_slots=64))
+    assert e.value.status == rsc.RSC_ERR_UNSUPPORTED
+    # no workspace: refused on the host, before any launch
+    st = L.rsc_knn_descent(ctypes.c_void_p(16), 100, 5, 8, ctypes.c_void_p(16), ctypes.c_void_p(16), None,
+                           ctypes.byref(rsc.nnd_opts()), None, 0)
+    assert st == rsc.RSC_ERR_WORKSPACE
