@@ -21,6 +21,8 @@ neighbours step uses the UMAP smooth-kNN / fuzzy-union construction):
 * ``splitmix64`` / ``umap_negative`` -- the counter-based negative sampler.
 * ``edistance_sums`` / ``edistance`` -- group-pair sums of Euclidean distances
   and the energy distance (Methods, "Perturbation distance computation").
+* ``leiden``       -- Leiden communities on a CSR graph (synchronous rounds,
+  fixed-point weights; Methods, "Dimensionality reduction and graph analysis").
 * ``nndescent``    -- approximate kNN by synchronous NN-descent with
   deterministic sampling (the paper's CPU neighbour search is PyNNDescent,
   Methods, "Benchmarking"); list decisions on FP32 squared distances.
@@ -89,8 +91,10 @@ def _load():
             lib.oracle_edistance_sums.restype = i32
             lib.oracle_edistance_assemble.argtypes = [vp, i32, vp, vp, vp]
             lib.oracle_edistance_assemble.restype = i32
-            lib.oracle_nndescent.argtypes = [vp, i64, i32, i32, i32, i32, i32, i32, dbl, u64, vp, vp, vp, vp]
+            lib.oracle_nndescent.argtypes = [vp, i64, i32, i32, i32, i32, i32, i32, dbl, u64, vp, vp, vp, vp, vp, vp]
             lib.oracle_nndescent.restype = i32
+            lib.oracle_leiden.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp]
+            lib.oracle_leiden.restype = i32
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i32
             _ = dbl
@@ -300,20 +304,49 @@ def edistance(X, offsets, cell_index=None):
     return sums, mean, E
 
 
-def nndescent(X, k, sample=None, rev_slots=32, cand_slots=64, iters=10, delta=0.0, seed=0):
+def nndescent(X, k, sample=None, rev_slots=32, cand_slots=64, iters=10, delta=0.0, seed=0, init=None,
+              with_pairs=False):
     """Synchronous NN-descent (definition above oracle_nndescent in oracle.c).
 
+    init: caller lists int32 [n, k] the initial lists start from (or None).
     Returns (idx int32 [n, k], d2 float32 [n, k] FP32 squared distances in list
-    order, changes int64 [iters], iterations run)."""
+    order, changes int64 [iters], iterations run), and pairs joined per
+    iteration (int64 [iters]) last with_pairs."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     n, d = X.shape
     S = k if sample is None else sample
     idx = np.empty((n, k), dtype=np.int32)
     d2 = np.empty((n, k), dtype=np.float32)
     ch = np.zeros(max(1, iters), dtype=np.int64)
+    pr = np.zeros(max(1, iters), dtype=np.int64)
     run = ctypes.c_int(0)
+    ini = None if init is None else np.ascontiguousarray(init, dtype=np.int32).reshape(n, k)
     rc = _load().oracle_nndescent(_ptr(X), n, d, k, S, rev_slots, cand_slots, iters, float(delta),
-                                  seed & (2**64 - 1), _ptr(idx), _ptr(d2), _ptr(ch), ctypes.byref(run))
+                                  seed & (2**64 - 1), _ptr(ini), _ptr(idx), _ptr(d2), _ptr(ch), _ptr(pr),
+                                  ctypes.byref(run))
     if rc != 0:
         raise ValueError(f"oracle_nndescent failed with status {rc}")
+    if with_pairs:
+        return idx, d2, ch[:iters], run.value, pr[:iters]
     return idx, d2, ch[:iters], run.value
+
+
+def leiden(indptr, indices, data, resolution=1.0, n_iter=2, max_levels=32, max_rounds=64, init=None):
+    """Leiden communities (definition above oracle_leiden in oracle.c).
+
+    Returns (membership int32 [n] numbered by first appearance, number of
+    communities, modularity on the fixed-point weights, levels of the last run)."""
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.int32)
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    n = len(indptr) - 1
+    mem = np.empty(n, dtype=np.int32)
+    ini = None if init is None else np.ascontiguousarray(init, dtype=np.int32)
+    nc = ctypes.c_int64(0)
+    q = ctypes.c_double(0.0)
+    lv = ctypes.c_int(0)
+    rc = _load().oracle_leiden(_ptr(indptr), _ptr(indices), _ptr(data), n, float(resolution), n_iter, max_levels,
+                               max_rounds, _ptr(ini), _ptr(mem), ctypes.byref(nc), ctypes.byref(q), ctypes.byref(lv))
+    if rc != 0:
+        raise ValueError(f"oracle_leiden failed with status {rc}")
+    return mem, int(nc.value), float(q.value), int(lv.value)

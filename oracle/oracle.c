@@ -687,10 +687,12 @@ int oracle_edistance_assemble(const int64_t *offsets, int G, const double *sums,
  *   slot_b(id) = (uint32)(id * 0x9E3779B1) >> (32 - b) (Fibonacci hashing;
  *     0 when b = 0, a single slot).
  *
- * Initial lists: u itself, then the first k - 1 distinct values of
- * (u + 1 + G(u 2k + j + 1) mod (n - 1)) mod n for j = 0 .. 2k - 1, then (if
- * still short) u + 1, u + 2, ... mod n not yet present; ordered by key.  Every
- * entry but u is flagged new.
+ * Initial lists: u itself, then (with caller lists init [n, k]) the entries
+ * of init[u] in order that lie in [0, n) and are not yet present, then the
+ * distinct values of (u + 1 + G(u 2k + j + 1) mod (n - 1)) mod n for
+ * j = 0 .. 2k - 1, then u + 1, u + 2, ... mod n not yet present, each step
+ * only while the list is short of k; ordered by key.  Every entry but u is
+ * flagged new.
  *
  * Iteration t (0-based), all steps reading the lists B_t as they were when
  * the iteration began:
@@ -768,14 +770,16 @@ static int nd_has(const int64_t *v, int m, int64_t x) {
 }
 
 /*
- * X [n, d] float32; k list length (self included), 2 <= k <= n; S new samples
+ * X [n, d] float32; init [n, k] int32 caller lists or NULL; k list length
+ * (self included), 2 <= k <= n; S new samples
  * per list (1 <= S <= k); R reverse slots and C candidate slots (powers of
  * two); T iterations at most; delta >= 0.  Outputs idx [n, k], d2 [n, k]
- * (the FP32 squared distances), changes [T] (0 for iterations not run) and
- * iters_run (nullable).
+ * (the FP32 squared distances), changes [T] (0 for iterations not run),
+ * pairs [T] (pairs joined per iteration; nullable) and iters_run (nullable).
  */
 int oracle_nndescent(const float *X, int64_t n, int d, int k, int S, int R, int C, int T, double delta,
-                     uint64_t seed, int32_t *idx, float *d2, int64_t *changes, int *iters_run) {
+                     uint64_t seed, const int32_t *init, int32_t *idx, float *d2, int64_t *changes,
+                     int64_t *pairs, int *iters_run) {
     const int lr = nd_log2(R), lc = nd_log2(C);
     if (!X || !idx || !d2 || n < 1 || d < 1 || k < 2 || k > n || S < 1 || S > k || lr < 0 || lc < 0 ||
         T < 0 || delta < 0)
@@ -804,6 +808,11 @@ int oracle_nndescent(const float *X, int64_t n, int d, int k, int S, int R, int 
     for (int64_t u = 0; u < n; ++u) {
         int m = 0;
         ids[m++] = u;
+        if (init)
+            for (int c = 0; c < k && m < k; ++c) {
+                const int64_t r = init[(size_t)u * k + c];
+                if (r >= 0 && r < n && !nd_has(ids, m, r)) ids[m++] = r;
+            }
         for (int j = 0; j < 2 * k && m < k; ++j) {
             const uint64_t g = oracle_splitmix64(seed, (uint64_t)u * (uint64_t)(2 * k) + (uint64_t)j + 1);
             const int64_t r = (u + 1 + (int64_t)(g % (uint64_t)(n - 1))) % n;
@@ -820,6 +829,8 @@ int oracle_nndescent(const float *X, int64_t n, int d, int k, int S, int R, int 
     }
     if (changes)
         for (int t = 0; t < T; ++t) changes[t] = 0;
+    if (pairs)
+        for (int t = 0; t < T; ++t) pairs[t] = 0;
     int run = 0;
     for (int t = 0; t < T; ++t) {
         /* 1. forward samples */
@@ -877,6 +888,7 @@ int oracle_nndescent(const float *X, int64_t n, int d, int k, int S, int R, int 
                 const int64_t id = (int64_t)(uint32_t)q;
                 if (!nd_has(jn, a, id) && !nd_has(jo, o, id)) jo[o++] = id;
             }
+            if (pairs) pairs[t] += (int64_t)a * (a - 1) / 2 + (int64_t)a * o;
             for (int i = 0; i < a; ++i)
                 for (int j = i + 1; j < a + o; ++j) {
                     const int64_t pa = jn[i], pb = (j < a) ? jn[j] : jo[j - a];
@@ -931,4 +943,428 @@ int oracle_nndescent(const float *X, int64_t n, int d, int k, int S, int R, int 
     free(key); free(isnew); free(newf); free(nnew); free(oldf); free(nold); free(rn); free(ro);
     free(cand); free(thr); free(jn); free(jo); free(pool); free(ids);
     return ORC_OK;
+}
+
+/*
+ * Leiden community detection (Traag, Waltman & van Eck, "From Louvain to
+ * Leiden: guaranteeing well-connected communities", Sci. Rep. 2019), the
+ * clustering the paper runs on the stored graph (Methods, "Dimensionality
+ * reduction and graph analysis"), with the modularity quality function and a
+ * resolution gamma, as scanpy calls it.  The library runs it synchronously
+ * (every vertex decides on the state of the round before), so this is the
+ * same synchronous form; the readings (beside the paper's steps) are:
+ *
+ *   Weights in fixed point: W = rint(w * 2^32) as a 64-bit integer, so every
+ *   sum is exact and independent of its order; gamma enters as
+ *   G = rint(gamma * 2^16).  Strength k_v = sum of v's row (a self-loop entry
+ *   counted as stored), 2m = sum of all strengths, tot_c = sum of k over c.
+ *   Moving v from community a to c changes the quality by a positive
+ *   multiple of
+ *     g(c) = s_c 2m 2^16 - G k_v tot_c        (c != a),
+ *     g(a) = s_a 2m 2^16 - G k_v (tot_a - k_v) (staying),
+ *   s_c = weight of v's entries to other vertices of c; compared exactly
+ *   in 128-bit integers.  Entries whose fixed-point weight is 0 are skipped,
+ *   so a vertex's candidate communities are those with s_c > 0.
+ *   Labels are vertex ids; after each phase a community takes the smallest
+ *   id among its members.
+ *
+ * 1. Local moving (the paper's MoveNodesFast), in rounds r = 0, 1, ...: each
+ *    vertex picks the neighbouring community c != a with the largest g(c)
+ *    (ties: smallest c) and moves there if g(c) > g(a) and, in even rounds,
+ *    c < a, in odd rounds c > a (so two vertices never swap forever).  All
+ *    moves of a round apply together.  The phase ends after two rounds in a
+ *    row without a move, or after max_rounds rounds.
+ * 2. Refinement (RefinePartition / MergeNodesSubset): inside each community
+ *    C of step 1, every vertex starts alone.  A vertex v that is still alone
+ *    and well connected to C (s_{C-v} 2m 2^16 >= G k_v (tot_C - k_v)) looks at
+ *    the subcommunities S of its neighbours in C that are well connected
+ *    (ext_S 2m 2^16 >= G tot_S (tot_C - tot_S), ext_S the weight from S to
+ *    C - S) and picks the one with the largest g(S) = s_S 2m 2^16 -
+ *    G k_v tot_S >= 0 (ties: smallest label); the paper draws it at random
+ *    with probability growing with the gain, and the greedy choice is its
+ *    limit of zero randomness.  A vertex some other vertex picked stays (so
+ *    merges never chain within a round); all other picks apply together;
+ *    rounds repeat until none moves or max_rounds.
+ * 3. Aggregation (AggregateGraph): one node per refined subcommunity, in the
+ *    order of their smallest member; the weight between two nodes is the sum
+ *    of the weights between their members (a node's self-loop holds its
+ *    internal weight, both directions).  Each node starts in the community of
+ *    step 1 that holds its members.
+ * Levels repeat until step 1 leaves every community a single node, or the
+ * refinement merges nothing, or max_levels.  n_iter such runs are made, each
+ * starting from the previous partition (scanpy runs two).  Output: each
+ * vertex's community, numbered by first appearance over the vertices.
+ */
+typedef __int128 ld_i128;
+
+typedef struct {
+    int64_t nv;
+    int64_t *ip;
+    int32_t *col;
+    int64_t *wt;
+} ld_graph;
+
+static void ld_free(ld_graph *g) {
+    free(g->ip);
+    free(g->col);
+    free(g->wt);
+    g->ip = NULL;
+    g->col = NULL;
+    g->wt = NULL;
+}
+
+/* Relabels every community by its smallest member. */
+static void ld_canon(int64_t nv, int32_t *lab, int32_t *tmp) {
+    for (int64_t v = 0; v < nv; ++v) tmp[v] = INT32_MAX;
+    for (int64_t v = 0; v < nv; ++v)
+        if (v < tmp[lab[v]]) tmp[lab[v]] = (int32_t)v;
+    for (int64_t v = 0; v < nv; ++v) lab[v] = tmp[lab[v]];
+}
+
+/* Step 1.  Returns the number of moves made; comm is relabelled. */
+static int64_t ld_move(const ld_graph *g, const int64_t *k, int64_t m2, int64_t G, int max_rounds, int32_t *comm,
+                       int64_t *tot, int64_t *s, int32_t *touched, int32_t *next) {
+    const int64_t nv = g->nv;
+    int64_t total = 0;
+    int quiet = 0;
+    for (int r = 0; r < max_rounds && quiet < 2; ++r) {
+        for (int64_t c = 0; c < nv; ++c) tot[c] = 0;
+        for (int64_t v = 0; v < nv; ++v) tot[comm[v]] += k[v];
+        int64_t moves = 0;
+        for (int64_t v = 0; v < nv; ++v) {
+            const int32_t a = comm[v];
+            int nt = 0;
+            for (int64_t e = g->ip[v]; e < g->ip[v + 1]; ++e) {
+                const int32_t u = g->col[e];
+                if (u == v || g->wt[e] == 0) continue;
+                const int32_t c = comm[u];
+                if (s[c] == 0) touched[nt++] = c;
+                s[c] += g->wt[e];
+            }
+            const ld_i128 ga = (ld_i128)s[a] * m2 * 65536 - (ld_i128)G * k[v] * (tot[a] - k[v]);
+            int32_t best = -1;
+            ld_i128 gb = 0;
+            for (int i = 0; i < nt; ++i) {
+                const int32_t c = touched[i];
+                if (c == a) continue;
+                const ld_i128 gc = (ld_i128)s[c] * m2 * 65536 - (ld_i128)G * k[v] * tot[c];
+                if (best < 0 || gc > gb || (gc == gb && c < best)) {
+                    best = c;
+                    gb = gc;
+                }
+            }
+            for (int i = 0; i < nt; ++i) s[touched[i]] = 0;
+            next[v] = a;
+            if (best >= 0 && gb > ga && ((r % 2 == 0) ? best < a : best > a)) {
+                next[v] = best;
+                ++moves;
+            }
+        }
+        memcpy(comm, next, sizeof(int32_t) * (size_t)nv);
+        total += moves;
+        quiet = moves ? 0 : quiet + 1;
+    }
+    ld_canon(nv, comm, next);
+    for (int64_t c = 0; c < nv; ++c) tot[c] = 0;
+    for (int64_t v = 0; v < nv; ++v) tot[comm[v]] += k[v];
+    return total;
+}
+
+/* Step 2: ref (labels = vertex ids) refined inside comm; relabelled. */
+static void ld_refine(const ld_graph *g, const int64_t *k, int64_t m2, int64_t G, int max_rounds,
+                      const int32_t *comm, const int64_t *tot, int32_t *ref, int64_t *s, int32_t *touched,
+                      int32_t *target, int64_t *wC, int64_t *rtot, int64_t *ext, int32_t *size,
+                      unsigned char *picked, int32_t *tmp) {
+    const int64_t nv = g->nv;
+    for (int64_t v = 0; v < nv; ++v) {
+        ref[v] = (int32_t)v;
+        int64_t w = 0;
+        for (int64_t e = g->ip[v]; e < g->ip[v + 1]; ++e) {
+            const int32_t u = g->col[e];
+            if (u != v && comm[u] == comm[v]) w += g->wt[e];
+        }
+        wC[v] = w;
+    }
+    for (int r = 0; r < max_rounds; ++r) {
+        /* subcommunity totals, sizes, external weights at the round start */
+        for (int64_t S = 0; S < nv; ++S) {
+            rtot[S] = 0;
+            ext[S] = 0;
+            size[S] = 0;
+            picked[S] = 0;
+        }
+        for (int64_t v = 0; v < nv; ++v) {
+            rtot[ref[v]] += k[v];
+            size[ref[v]] += 1;
+            int64_t wS = 0;
+            for (int64_t e = g->ip[v]; e < g->ip[v + 1]; ++e) {
+                const int32_t u = g->col[e];
+                if (u != v && ref[u] == ref[v]) wS += g->wt[e];
+            }
+            ext[ref[v]] += wC[v] - wS;
+        }
+        for (int64_t v = 0; v < nv; ++v) {
+            target[v] = -1;
+            if (size[ref[v]] != 1) continue;   /* only vertices still alone move */
+            const int32_t C = comm[v];
+            if ((ld_i128)wC[v] * m2 * 65536 < (ld_i128)G * k[v] * (tot[C] - k[v])) continue;
+            int nt = 0;
+            for (int64_t e = g->ip[v]; e < g->ip[v + 1]; ++e) {
+                const int32_t u = g->col[e];
+                if (u == v || comm[u] != C || g->wt[e] == 0) continue;
+                const int32_t S = ref[u];
+                if (s[S] == 0) touched[nt++] = S;
+                s[S] += g->wt[e];
+            }
+            int32_t best = -1;
+            ld_i128 gb = 0;
+            for (int i = 0; i < nt; ++i) {
+                const int32_t S = touched[i];
+                if (S == ref[v]) continue;
+                if ((ld_i128)ext[S] * m2 * 65536 < (ld_i128)G * rtot[S] * (tot[C] - rtot[S])) continue;
+                const ld_i128 gS = (ld_i128)s[S] * m2 * 65536 - (ld_i128)G * k[v] * rtot[S];
+                if (gS < 0) continue;
+                if (best < 0 || gS > gb || (gS == gb && S < best)) {
+                    best = S;
+                    gb = gS;
+                }
+            }
+            for (int i = 0; i < nt; ++i) s[touched[i]] = 0;
+            target[v] = best;
+        }
+        for (int64_t v = 0; v < nv; ++v)
+            if (target[v] >= 0) picked[target[v]] = 1;
+        int64_t moves = 0;
+        for (int64_t v = 0; v < nv; ++v)
+            if (target[v] >= 0 && !picked[ref[v]]) {
+                ref[v] = target[v];
+                ++moves;
+            }
+        if (!moves) break;
+    }
+    ld_canon(nv, ref, tmp);
+}
+
+/* Step 3: the graph of the refined subcommunities.  node[v] (out) = new index
+ * of v's subcommunity; returns the node count (0 on allocation failure). */
+static int64_t ld_aggregate(const ld_graph *g, const int32_t *ref, int32_t *node, ld_graph *out, int64_t *acc,
+                            int32_t *touched) {
+    const int64_t nv = g->nv;
+    int64_t K = 0;
+    for (int64_t v = 0; v < nv; ++v)
+        if (ref[v] == v) node[v] = (int32_t)K++;   /* labels are smallest members: ascending order */
+    for (int64_t v = 0; v < nv; ++v) node[v] = node[ref[v]];
+    /* members of each node, in vertex order */
+    int64_t *moff = (int64_t *)calloc((size_t)K + 1, sizeof(int64_t));
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    out->ip = (int64_t *)calloc((size_t)K + 1, sizeof(int64_t));
+    if (!moff || !mem || !out->ip) {
+        free(moff);
+        free(mem);
+        return 0;
+    }
+    for (int64_t v = 0; v < nv; ++v) moff[node[v] + 1]++;
+    for (int64_t c = 0; c < K; ++c) moff[c + 1] += moff[c];
+    {
+        int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K > 0 ? K : 1));
+        if (!cur) {
+            free(moff);
+            free(mem);
+            return 0;
+        }
+        for (int64_t c = 0; c < K; ++c) cur[c] = moff[c];
+        for (int64_t v = 0; v < nv; ++v) mem[cur[node[v]]++] = (int32_t)v;
+        free(cur);
+    }
+    /* two passes: row lengths, then the rows (columns ascending) */
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t c = 0; c < K; ++c) {
+            int nt = 0;
+            for (int64_t i = moff[c]; i < moff[c + 1]; ++i) {
+                const int32_t v = mem[i];
+                for (int64_t e = g->ip[v]; e < g->ip[v + 1]; ++e) {
+                    if (g->wt[e] == 0) continue;
+                    const int32_t t = node[g->col[e]];
+                    if (acc[t] == 0) touched[nt++] = t;
+                    acc[t] += g->wt[e];
+                }
+            }
+            /* ascending columns: insertion sort of the touched list */
+            for (int i = 1; i < nt; ++i) {
+                const int32_t x = touched[i];
+                int j = i - 1;
+                while (j >= 0 && touched[j] > x) {
+                    touched[j + 1] = touched[j];
+                    --j;
+                }
+                touched[j + 1] = x;
+            }
+            if (pass == 0) {
+                out->ip[c + 1] = out->ip[c] + nt;
+            } else {
+                int64_t p = out->ip[c];
+                for (int i = 0; i < nt; ++i) {
+                    out->col[p] = touched[i];
+                    out->wt[p++] = acc[touched[i]];
+                }
+            }
+            for (int i = 0; i < nt; ++i) acc[touched[i]] = 0;
+        }
+        if (pass == 0) {
+            out->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(out->ip[K] > 0 ? out->ip[K] : 1));
+            out->wt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(out->ip[K] > 0 ? out->ip[K] : 1));
+            if (!out->col || !out->wt) {
+                free(moff);
+                free(mem);
+                return 0;
+            }
+        }
+    }
+    out->nv = K;
+    free(moff);
+    free(mem);
+    return K;
+}
+
+/*
+ * Symmetric CSR graph (indptr [n + 1], indices, data [nnz], data > 0
+ * expected; a zero weight adds nothing), resolution gamma, n_iter runs,
+ * max_levels, max_rounds.  init [n] (nullable): starting partition labels in
+ * [0, n).  Outputs membership [n] (communities numbered by first appearance),
+ * *n_comm, *quality = sum_c (in_c / 2m - gamma (tot_c / 2m)^2) on the
+ * fixed-point weights (nullable), *levels_run (levels of the last run).
+ */
+int oracle_leiden(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n, double gamma,
+                  int n_iter, int max_levels, int max_rounds, const int32_t *init, int32_t *membership,
+                  int64_t *n_comm, double *quality, int *levels_run) {
+    if (!indptr || !membership || n < 1 || n >= INT32_MAX || gamma <= 0 || gamma >= 32768 || n_iter < 1 ||
+        max_levels < 1 || max_rounds < 1)
+        return ORC_BAD_ARG;
+    const int64_t nnz = indptr[n];
+    for (int64_t v = 0; v < n; ++v)
+        if (indptr[v + 1] < indptr[v]) return ORC_BAD_ARG;
+    for (int64_t e = 0; e < nnz; ++e)
+        if (indices[e] < 0 || indices[e] >= n) return ORC_BAD_ARG;
+    const int64_t G = (int64_t)llrint(gamma * 65536.0);
+    ld_graph g0;
+    g0.nv = n;
+    g0.ip = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    g0.col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    g0.wt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    const size_t N = (size_t)n;
+    int64_t *k = (int64_t *)malloc(sizeof(int64_t) * N), *tot = (int64_t *)malloc(sizeof(int64_t) * N);
+    int64_t *s = (int64_t *)calloc(N, sizeof(int64_t)), *wC = (int64_t *)malloc(sizeof(int64_t) * N);
+    int64_t *rtot = (int64_t *)malloc(sizeof(int64_t) * N), *ext = (int64_t *)malloc(sizeof(int64_t) * N);
+    int32_t *comm = (int32_t *)malloc(sizeof(int32_t) * N), *next = (int32_t *)malloc(sizeof(int32_t) * N);
+    int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * N), *ref = (int32_t *)malloc(sizeof(int32_t) * N);
+    int32_t *target = (int32_t *)malloc(sizeof(int32_t) * N), *size = (int32_t *)malloc(sizeof(int32_t) * N);
+    int32_t *node = (int32_t *)malloc(sizeof(int32_t) * N), *top = (int32_t *)malloc(sizeof(int32_t) * N);
+    unsigned char *picked = (unsigned char *)malloc(N);
+    int rc = ORC_OK;
+    if (!g0.ip || !g0.col || !g0.wt || !k || !tot || !s || !wC || !rtot || !ext || !comm || !next || !touched ||
+        !ref || !target || !size || !node || !top || !picked) {
+        rc = ORC_NO_MEM;
+        goto done;
+    }
+    memcpy(g0.ip, indptr, sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t e = 0; e < nnz; ++e) {
+        g0.col[e] = indices[e];
+        g0.wt[e] = (int64_t)llrint((double)data[e] * 4294967296.0);
+    }
+    for (int64_t v = 0; v < n; ++v) membership[v] = init ? init[v] : (int32_t)v;
+    for (int64_t v = 0; v < n; ++v)
+        if (membership[v] < 0 || membership[v] >= n) {
+            rc = ORC_BAD_ARG;
+            goto done;
+        }
+    int64_t m2 = 0;
+    for (int it = 0; it < n_iter; ++it) {
+        ld_graph g = g0;   /* level 0 borrows the input graph */
+        int own = 0;       /* g owns its arrays from level 1 on */
+        for (int64_t v = 0; v < n; ++v) {
+            top[v] = (int32_t)v;   /* node of v at the current level */
+            comm[v] = membership[v];
+        }
+        ld_canon(n, comm, next);
+        int level = 0;
+        for (; level < max_levels; ++level) {
+            const int64_t nv = g.nv;
+            m2 = 0;
+            for (int64_t v = 0; v < nv; ++v) {
+                int64_t w = 0;
+                for (int64_t e = g.ip[v]; e < g.ip[v + 1]; ++e) w += g.wt[e];
+                k[v] = w;
+                m2 += w;
+            }
+            if (m2 == 0) break;
+            ld_move(&g, k, m2, G, max_rounds, comm, tot, s, touched, next);
+            int64_t ncomm = 0;
+            for (int64_t v = 0; v < nv; ++v) ncomm += comm[v] == v;
+            if (ncomm == nv) break;   /* every community is a single node */
+            ld_refine(&g, k, m2, G, max_rounds, comm, tot, ref, s, touched, target, wC, rtot, ext, size, picked,
+                      next);
+            ld_graph h = {0, NULL, NULL, NULL};
+            int64_t *acc = (int64_t *)calloc((size_t)nv, sizeof(int64_t));
+            if (!acc) {
+                rc = ORC_NO_MEM;
+                break;
+            }
+            const int64_t K = ld_aggregate(&g, ref, node, &h, acc, touched);
+            free(acc);
+            if (K == 0) {
+                ld_free(&h);
+                rc = ORC_NO_MEM;
+                break;
+            }
+            if (K == nv) {   /* the refinement merged nothing */
+                ld_free(&h);
+                break;
+            }
+            /* the aggregate's communities: node of each community's smallest member */
+            for (int64_t v = 0; v < nv; ++v) next[node[v]] = node[comm[v]];
+            for (int64_t v = 0; v < n; ++v) top[v] = node[top[v]];
+            if (own) ld_free(&g);
+            g = h;
+            own = 1;
+            memcpy(comm, next, sizeof(int32_t) * (size_t)K);
+        }
+        for (int64_t v = 0; v < n; ++v) membership[v] = comm[top[v]];
+        if (own) ld_free(&g);
+        if (levels_run) *levels_run = level;
+        if (rc != ORC_OK) goto done;
+    }
+    /* number by first appearance; quality on the input graph */
+    {
+        for (int64_t v = 0; v < n; ++v) next[v] = -1;
+        int32_t K = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            if (next[membership[v]] < 0) next[membership[v]] = K++;
+            membership[v] = next[membership[v]];
+        }
+        if (n_comm) *n_comm = K;
+        if (quality) {
+            for (int64_t c = 0; c < K; ++c) {
+                tot[c] = 0;
+                rtot[c] = 0;
+            }
+            int64_t M = 0;
+            for (int64_t v = 0; v < n; ++v)
+                for (int64_t e = g0.ip[v]; e < g0.ip[v + 1]; ++e) {
+                    tot[membership[v]] += g0.wt[e];
+                    M += g0.wt[e];
+                    if (membership[g0.col[e]] == membership[v]) rtot[membership[v]] += g0.wt[e];
+                }
+            double q = 0.0;
+            for (int64_t c = 0; c < K && M > 0; ++c) {
+                const double f = (double)tot[c] / (double)M;
+                q += (double)rtot[c] / (double)M - gamma * f * f;
+            }
+            *quality = q;
+        }
+    }
+done:
+    ld_free(&g0);
+    free(k); free(tot); free(s); free(wC); free(rtot); free(ext); free(comm); free(next); free(touched);
+    free(ref); free(target); free(size); free(node); free(top); free(picked);
+    return rc;
 }
