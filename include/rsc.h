@@ -601,6 +601,9 @@ rsc_status rsc_knn_descent_workspace_size(int64_t n, int32_t d, int32_t k, const
 /*
  * Approximate k-nearest-neighbour lists of every row of X by NN-descent.
  *   X        [n, d] float32 row-major (device), 2 <= n < 2^31, d >= 1.
+ *   init_idx [n, k] int32 (device) or NULL: lists to start from (for example
+ *            an earlier graph); entries outside [0, n), repeats and the row
+ *            itself are skipped, and hashed draws fill what is left.
  *   idx      [n, k] int32 out: each row's list, nearest first, the row itself
  *            included (k <= min(64, n)); dist [n, k] float32 out: Euclidean
  *            distance sqrtf(delta2) of each entry.
@@ -611,9 +614,10 @@ rsc_status rsc_knn_descent_workspace_size(int64_t n, int32_t d, int32_t k, const
  * lists ordered by key = bits(delta2) << 32 | id; G(i) = output i >= 1 of
  * SplitMix64 seeded with seed; slot_b(id) = (id * 0x9E3779B1 mod 2^32) >>
  * (32 - b), 0 for b = 0):
- *   initial list of u: u, then the first k - 1 distinct values of
- *   (u + 1 + G(2ku + j + 1) mod (n - 1)) mod n, j = 0 .. 2k-1, then
- *   u + 1, u + 2, ... mod n while short; all entries but u flagged new.
+ *   initial list of u: u, then the valid new entries of init_idx[u] in
+ *   order, then the new values of (u + 1 + G(2ku + j + 1) mod (n - 1)) mod n,
+ *   j = 0 .. 2k-1, then u + 1, u + 2, ... mod n, each only while the list is
+ *   short of k; all entries but u flagged new.
  *   Iteration t, on the lists as they were when it began:
  *   1. new_f(u) = the first S entries flagged new (u excluded), whose flags
  *      are cleared; old_f(u) = the entries flagged old before (u excluded).
@@ -636,8 +640,87 @@ rsc_status rsc_knn_descent_workspace_size(int64_t n, int32_t d, int32_t k, const
  * a missing or small workspace; RSC_ERR_UNSUPPORTED when the join's shared
  * memory (4 d (S + 2R + k) bytes and a little more) exceeds 200 KiB.
  */
-rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, int32_t *idx, float *dist,
-                           int64_t *changes, const rsc_nnd_opts *opts, void *workspace, size_t workspace_bytes);
+/*
+ * Pairs joined by each iteration of the last rsc_knn_descent call that used
+ * this workspace (a statistic for throughput accounting; the paper has no
+ * counterpart): pairs[t] = sum over points v of a (a - 1) / 2 + a o, a and o
+ * the sizes of v's new and old join lists.  pairs: HOST array of 64.
+ * Synchronises the device.
+ */
+rsc_status rsc_knn_descent_pairs(const void *workspace, size_t workspace_bytes, int64_t *pairs);
+
+rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, const int32_t *init_idx, int32_t *idx,
+                           float *dist, int64_t *changes, const rsc_nnd_opts *opts, void *workspace,
+                           size_t workspace_bytes);
+
+/* ---------------------------------------------------------------- Leiden
+ *
+ * Communities of the neighbourhood graph by the Leiden method (Traag, Waltman
+ * & van Eck, Sci. Rep. 2019), the clustering the paper runs on the stored
+ * graph (Methods, "Dimensionality reduction and graph analysis"), with the
+ * modularity quality function and a resolution gamma, as scanpy calls it.
+ */
+typedef struct {
+    double resolution;      /* gamma, in (0, 32768) (0: 1)                      */
+    int32_t n_iterations;   /* whole Leiden runs, each from the previous
+                               partition (0: 2, scanpy's count)                 */
+    int32_t max_levels;     /* aggregation levels per run at most (0: 32)       */
+    int32_t max_rounds;     /* rounds per moving or refinement phase (0: 64)    */
+    void *stream;           /* cudaStream_t, NULL = legacy default stream       */
+} rsc_leiden_opts;
+
+/* Minimum workspace for rsc_leiden (host-only query): two copies of the graph
+ * with 64-bit weights, hash tables of 4 nnz + 2 n slots (12 bytes each), a
+ * few arrays of n. */
+rsc_status rsc_leiden_workspace_size(int64_t n, int64_t nnz, size_t *bytes);
+
+/*
+ * Leiden communities of a graph.
+ *   indptr [n + 1] int64, indices [nnz] int32, data [nnz] float32 (device):
+ *              the graph as CSR, symmetric (rsc_connectivities' output);
+ *              weights >= 0; a diagonal entry is a self-loop.
+ *   init       [n] int32 (device) starting partition labels in [0, n), or NULL
+ *              (every vertex alone).
+ *   membership [n] int32 device out: each vertex's community, numbered
+ *              0, 1, ... in order of first appearance over the vertices.
+ *   n_communities, modularity: HOST out (nullable): the community count and
+ *              sum_c (in_c / 2m - gamma (tot_c / 2m)^2) of the result.
+ * Definition (every decision exact, on W = rint(w 2^32) as 64-bit integers
+ * and G = rint(gamma 2^16); k_v = the row sum of W, 2m = sum of k, tot_c =
+ * sum of k over c; labels are vertex ids and every phase ends by labelling a
+ * community with its smallest member; s_c = the weight of v's entries with
+ * W > 0 to other vertices of c):
+ *   1. Moving, in rounds r = 0, 1, ... on the state of the round's start:
+ *      v picks the neighbouring community c != a = comm(v) with the largest
+ *      g(c) = s_c 2m 2^16 - G k_v tot_c (ties: smaller c) and moves there if
+ *      g(c) > s_a 2m 2^16 - G k_v (tot_a - k_v) and c < a in even rounds,
+ *      c > a in odd ones; until two rounds in a row move nothing, or
+ *      max_rounds.
+ *   2. Refinement inside each community C: every vertex starts alone; a
+ *      vertex still alone with s_{C-v} 2m 2^16 >= G k_v (tot_C - k_v) picks,
+ *      among the subcommunities S of its neighbours in C with
+ *      ext_S 2m 2^16 >= G tot_S (tot_C - tot_S) (ext_S: the weight from S to
+ *      C - S), the one with the largest g(S) = s_S 2m 2^16 - G k_v tot_S >= 0
+ *      (ties: smaller label); vertices nobody picked join their pick, all at
+ *      once; until a round moves nothing, or max_rounds.  (The paper draws
+ *      the pick at random with a probability growing with the gain; this is
+ *      its limit without randomness.)
+ *   3. Aggregation: one node per subcommunity, numbered by smallest member;
+ *      node weights are sums of member weights (self-loops hold the internal
+ *      weight); each node starts in its community of step 1.
+ *   Levels repeat until step 1 leaves every community a single node, step 2
+ *   merges nothing, or max_levels; n_iterations runs.
+ * Deterministic: the same partition on every run (equal to the library's
+ * CPU statement of the same steps).  Synchronous: the host drives the rounds
+ * and reads each round's move count, so the call returns when the result is
+ * ready.  Errors: RSC_ERR_INVALID_ARG for NULL pointers, n outside
+ * [1, 2^31), options out of range, or (found on the device before any round)
+ * row pointers or columns outside the graph or starting labels outside
+ * [0, n); RSC_ERR_WORKSPACE for a missing or small workspace.
+ */
+rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n, int64_t nnz,
+                      const int32_t *init, int32_t *membership, int64_t *n_communities, double *modularity,
+                      const rsc_leiden_opts *opts, void *workspace, size_t workspace_bytes);
 
 #ifdef __cplusplus
 }

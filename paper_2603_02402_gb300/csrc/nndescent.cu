@@ -43,6 +43,7 @@ constexpr int kMaxK = 64;
 constexpr int kMaxSlots = 64;
 constexpr int kMaxIters = 64;
 constexpr int kJoinThreads = 64;
+constexpr int kPairSlots = 64;   // per-iteration pair counters, spread over slots
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
     uint64_t z = seed + i * kGolden;
@@ -115,14 +116,14 @@ __device__ __forceinline__ void warp_sort_u64(uint64_t (&v)[E]) {
 
 // ------------------------------------------------------------------ init
 
-// Warp per point: lane 0 draws the ids (the hashed draws, then consecutive
-// points if the draws repeat too often), every lane computes the distances
-// of its entries, the warp sorts the keys.
+// Warp per point: lane 0 picks the ids (the caller's list if any, the hashed
+// draws, then consecutive points if the draws repeat too often), every lane
+// computes the distances of its entries, the warp sorts the keys.
 constexpr int kInitWarps = 8;
 
 __global__ void __launch_bounds__(kInitWarps * 32)
-init_kernel(const float *__restrict__ X, int64_t n, int d, int k, uint64_t seed, uint64_t *__restrict__ key,
-            unsigned long long *__restrict__ flags) {
+init_kernel(const float *__restrict__ X, int64_t n, int d, int k, uint64_t seed, const int32_t *__restrict__ init,
+            uint64_t *__restrict__ key, unsigned long long *__restrict__ flags) {
     __shared__ int32_t s_ids[kInitWarps][kMaxK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t u = (int64_t)blockIdx.x * kInitWarps + warp;
@@ -131,6 +132,13 @@ init_kernel(const float *__restrict__ X, int64_t n, int d, int k, uint64_t seed,
     if (lane == 0) {
         int m = 0;
         ids[m++] = (int32_t)u;
+        if (init)
+            for (int c = 0; c < k && m < k; ++c) {
+                const int32_t r = init[u * k + c];
+                bool seen = r < 0 || (int64_t)r >= n;
+                for (int i = 0; i < m; ++i) seen |= ids[i] == r;
+                if (!seen) ids[m++] = r;
+            }
         for (int j = 0; j < 2 * k && m < k; ++j) {
             const uint64_t g = splitmix64(seed, (uint64_t)u * (uint64_t)(2 * k) + (uint64_t)j + 1);
             const int32_t r = (int32_t)((u + 1 + (int64_t)(g % (uint64_t)(n - 1))) % n);
@@ -237,7 +245,7 @@ join_kernel(const float *__restrict__ X, int64_t n, int d, int k, int lr, int lc
             const unsigned long long *__restrict__ ch, long long lim, const uint64_t *__restrict__ key,
             const unsigned long long *__restrict__ flags, const unsigned long long *__restrict__ smask,
             const unsigned long long *__restrict__ rn, const unsigned long long *__restrict__ ro,
-            unsigned long long *__restrict__ cand) {
+            unsigned long long *__restrict__ cand, unsigned long long *__restrict__ pairs) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_thr = reinterpret_cast<uint64_t *>(smem);       // [P]
     int32_t *s_id = reinterpret_cast<int32_t *>(s_thr + P);     // [P]
@@ -295,12 +303,34 @@ join_kernel(const float *__restrict__ X, int64_t n, int d, int k, int lr, int lc
     __syncthreads();
     const int a = s_cnt[0], m = a + s_cnt[1];
     if (a == 0) return;   // no new entry joins anything (block-uniform)
+    if (threadIdx.x == 0)  // pairs joined (a statistic: rsc_knn_descent_pairs)
+        atomicAdd(pairs + t * kPairSlots + (blockIdx.x & (kPairSlots - 1)),
+                  (unsigned long long)a * (a - 1) / 2 + (unsigned long long)a * (m - a));
+    // stage the rows: each warp takes four rows at a time, all their loads
+    // issued before the stores
     const int nwarps = kJoinThreads / 32;
-    for (int r = warp; r < m; r += nwarps) {
-        const int32_t id = s_id[r];
-        const float *xr = X + (int64_t)id * d;
-        for (int tt = lane; tt < d; tt += 32) s_x[tt * P + r] = __ldg(xr + tt);
-        if (lane == 0) s_thr[r] = key[(int64_t)id * k + k - 1];
+    for (int r0 = 4 * warp; r0 < m; r0 += 4 * nwarps) {
+        float v[4][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q;
+            const float *xr = X + (int64_t)(r < m ? s_id[r] : 0) * d;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int tt = lane + 32 * h;
+                v[q][h] = (r < m && tt < d) ? __ldg(xr + tt) : 0.f;
+            }
+        }
+        if (lane < 4 && r0 + lane < m) s_thr[r0 + lane] = key[(int64_t)s_id[r0 + lane] * k + k - 1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int tt = lane + 32 * h;
+                if (r0 + q < m && tt < d) s_x[tt * P + r0 + q] = v[q][h];
+            }
+        for (int tt = lane + 64; tt < d; tt += 32)   // d > 64: the rest, row by row
+            for (int q = 0; q < 4 && r0 + q < m; ++q) s_x[tt * P + r0 + q] = __ldg(X + (int64_t)s_id[r0 + q] * d + tt);
     }
     __syncthreads();
     const int TI = (a + 1) / 2, TJ = (m + 3) / 4;
@@ -334,14 +364,10 @@ join_kernel(const float *__restrict__ X, int64_t n, int d, int k, int lr, int lc
                 if (i >= a || j >= m || j <= i) continue;
                 const uint32_t ia = (uint32_t)s_id[i], ib = (uint32_t)s_id[j];
                 const unsigned long long ka = make_key(acc[p][q], ib), kb = make_key(acc[p][q], ia);
-                if (ka < s_thr[i]) {
-                    unsigned long long *sl = cand + (size_t)ia * C + slot_of(ib, lc);
-                    if (ka < *sl) atomicMin(sl, ka);
-                }
-                if (kb < s_thr[j]) {
-                    unsigned long long *sl = cand + (size_t)ib * C + slot_of(ia, lc);
-                    if (kb < *sl) atomicMin(sl, kb);
-                }
+                // the atomics' results are unused, so they issue as reductions
+                // the thread does not wait for
+                if (ka < s_thr[i]) atomicMin(cand + (size_t)ia * C + slot_of(ib, lc), ka);
+                if (kb < s_thr[j]) atomicMin(cand + (size_t)ib * C + slot_of(ia, lc), kb);
             }
         }
     }
@@ -541,7 +567,7 @@ rsc_status nnd_params(int64_t n, int32_t d, int32_t k, const rsc_nnd_opts *o, Nn
 struct NndLayout {
     unsigned int *status;
     uint64_t *key;
-    unsigned long long *flags, *smask, *rn, *ro, *cand, *ch;
+    unsigned long long *flags, *smask, *rn, *ro, *cand, *ch, *pairs;
 };
 
 NndLayout carve_nnd(void *ws, int64_t n, int k, const NndParams &p, size_t *bytes) {
@@ -549,6 +575,7 @@ NndLayout carve_nnd(void *ws, int64_t n, int k, const NndParams &p, size_t *byte
     NndLayout L;
     L.status = cv.take<unsigned int>(kStatusBytes / sizeof(unsigned int));
     L.ch = cv.take<unsigned long long>(nnd::kMaxIters);
+    L.pairs = cv.take<unsigned long long>((size_t)nnd::kMaxIters * nnd::kPairSlots);   // fixed offset: 768 bytes
     L.key = cv.take<uint64_t>((size_t)n * k);
     L.flags = cv.take<unsigned long long>((size_t)n);
     L.smask = cv.take<unsigned long long>((size_t)n);
@@ -566,6 +593,21 @@ using namespace rsc;
 
 extern "C" {
 
+rsc_status rsc_knn_descent_pairs(const void *workspace, size_t workspace_bytes, int64_t *pairs) {
+    constexpr size_t off = 768, cnt = (size_t)nnd::kMaxIters * nnd::kPairSlots;
+    if (!workspace || !pairs) return fail(RSC_ERR_INVALID_ARG, "workspace or pairs is NULL");
+    if (workspace_bytes < off + cnt * sizeof(unsigned long long))
+        return fail(RSC_ERR_WORKSPACE, "workspace of %zu bytes holds no counters", workspace_bytes);
+    unsigned long long h[cnt];
+    RSC_CUDA_TRY(cudaMemcpy(h, static_cast<const char *>(workspace) + off, sizeof h, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < nnd::kMaxIters; ++t) {
+        unsigned long long s = 0;
+        for (int j = 0; j < nnd::kPairSlots; ++j) s += h[t * nnd::kPairSlots + j];
+        pairs[t] = (int64_t)s;
+    }
+    return RSC_OK;
+}
+
 rsc_status rsc_knn_descent_workspace_size(int64_t n, int32_t d, int32_t k, const rsc_nnd_opts *opts, size_t *bytes) {
     if (!bytes) return fail(RSC_ERR_INVALID_ARG, "bytes is NULL");
     NndParams p;
@@ -575,8 +617,9 @@ rsc_status rsc_knn_descent_workspace_size(int64_t n, int32_t d, int32_t k, const
     return RSC_OK;
 }
 
-rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, int32_t *idx, float *dist,
-                           int64_t *changes, const rsc_nnd_opts *opts, void *workspace, size_t workspace_bytes) {
+rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, const int32_t *init_idx, int32_t *idx,
+                           float *dist, int64_t *changes, const rsc_nnd_opts *opts, void *workspace,
+                           size_t workspace_bytes) {
     NndParams p;
     rsc_status s = nnd_params(n, d, k, opts, &p);
     if (s != RSC_OK) return s;
@@ -592,11 +635,12 @@ rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, int3
     const uint64_t seed = opts ? opts->seed : 0;
     RSC_CUDA_TRY(cudaMemsetAsync(L.status, 0, kStatusBytes, st));
     RSC_CUDA_TRY(cudaMemsetAsync(L.ch, 0, sizeof(unsigned long long) * nnd::kMaxIters, st));
+    RSC_CUDA_TRY(cudaMemsetAsync(L.pairs, 0, sizeof(unsigned long long) * nnd::kMaxIters * nnd::kPairSlots, st));
     RSC_CUDA_TRY(cudaMemsetAsync(L.rn, 0xFF, sizeof(unsigned long long) * (size_t)n * p.R, st));
     RSC_CUDA_TRY(cudaMemsetAsync(L.ro, 0xFF, sizeof(unsigned long long) * (size_t)n * p.R, st));
     RSC_CUDA_TRY(cudaMemsetAsync(L.cand, 0xFF, sizeof(unsigned long long) * (size_t)n * p.C, st));
     nnd::init_kernel<<<(unsigned)ceil_div(n, nnd::kInitWarps), nnd::kInitWarps * 32, 0, st>>>(X, n, d, k, seed,
-                                                                                              L.key, L.flags);
+                                                                                              init_idx, L.key, L.flags);
     RSC_CUDA_TRY(cudaGetLastError());
     if (p.join_smem > 48 * 1024)
         RSC_CUDA_TRY(cudaFuncSetAttribute(nnd::join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -606,7 +650,7 @@ rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, int3
         nnd::sample_kernel<<<(unsigned)ceil_div(n, nnd::kSampleWarps), nnd::kSampleWarps * 32, 0, st>>>(
             n, k, p.S, p.lr, seed, t, L.ch, p.lim, L.key, L.flags, L.smask, L.rn, L.ro);
         nnd::join_kernel<<<(unsigned)n, nnd::kJoinThreads, p.join_smem, st>>>(
-            X, n, d, k, p.lr, p.lc, p.P, t, L.ch, p.lim, L.key, L.flags, L.smask, L.rn, L.ro, L.cand);
+            X, n, d, k, p.lr, p.lc, p.P, t, L.ch, p.lim, L.key, L.flags, L.smask, L.rn, L.ro, L.cand, L.pairs);
         nnd::merge_kernel<<<merge_grid, nnd::kMergeWarps * 32, 0, st>>>(n, k, p.lr, p.lc, t, L.ch, p.lim, L.key,
                                                                         L.flags, L.rn, L.ro, L.cand);
         RSC_CUDA_TRY(cudaGetLastError());

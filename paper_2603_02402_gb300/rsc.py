@@ -56,6 +56,11 @@ class rsc_nnd_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class rsc_leiden_opts(ctypes.Structure):
+    _fields_ = [("resolution", ctypes.c_double), ("n_iterations", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes); the full exported surface of include/rsc.h
 _vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
@@ -107,8 +112,12 @@ SIGNATURES = {
     "rsc_umap_layout": (_i32, [_vp, _vp, _vp, _i64, _i64, _i32, _vp, ctypes.POINTER(rsc_umap_opts), _vp, _sz]),
     "rsc_edistance_workspace_size": (_i32, [_i64, _i32, _vp, _i32, _vp, _i64, ctypes.POINTER(_sz)]),
     "rsc_edistance": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "rsc_knn_descent_pairs": (_i32, [_vp, _sz, _vp]),
+    "rsc_leiden_workspace_size": (_i32, [_i64, _i64, ctypes.POINTER(_sz)]),
+    "rsc_leiden": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(rsc_leiden_opts), _vp, _sz]),
     "rsc_knn_descent_workspace_size": (_i32, [_i64, _i32, _i32, ctypes.POINTER(rsc_nnd_opts), ctypes.POINTER(_sz)]),
-    "rsc_knn_descent": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(rsc_nnd_opts), _vp, _sz]),
+    "rsc_knn_descent": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(rsc_nnd_opts), _vp, _sz]),
 }
 
 
@@ -623,9 +632,10 @@ def rsc_knn_descent_workspace_size(n: int, d: int, k: int, opts: rsc_nnd_opts | 
 
 
 def rsc_knn_descent(X: torch.Tensor, k: int, sample=0, rev_slots=0, cand_slots=0, max_iters=0, delta=0.0, seed=0,
-                    workspace=None, stream=None, with_changes=False):
+                    init=None, workspace=None, stream=None, with_changes=False):
     """Approximate kNN by NN-descent: returns (idx int32 [n, k], dist float32
-    [n, k]) CUDA tensors, and the int64 [64] change counts with_changes."""
+    [n, k]) CUDA tensors, and the int64 [64] change counts with_changes.
+    init: int32 [n, k] CUDA tensor of lists to start from (or None)."""
     if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
         raise ValueError("X: float32 [n, d] CUDA tensor expected")
     X = X.contiguous()
@@ -635,6 +645,54 @@ def rsc_knn_descent(X: torch.Tensor, k: int, sample=0, rev_slots=0, cand_slots=0
     idx = torch.empty((n, k), dtype=torch.int32, device=X.device)
     dist = torch.empty((n, k), dtype=torch.float32, device=X.device)
     ch = torch.zeros(64, dtype=torch.int64, device=X.device) if with_changes else None
-    _check(lib().rsc_knn_descent(_ptr(X), n, d, k, _ptr(idx), _ptr(dist), _ptr(ch), ctypes.byref(o), _ptr(ws),
-                                 ws.numel()))
+    if init is not None:
+        if not (init.is_cuda and init.dtype == torch.int32 and tuple(init.shape) == (n, k)):
+            raise ValueError("init: int32 [n, k] CUDA tensor expected")
+        init = init.contiguous()
+    _check(lib().rsc_knn_descent(_ptr(X), n, d, k, _ptr(init), _ptr(idx), _ptr(dist), _ptr(ch), ctypes.byref(o),
+                                 _ptr(ws), ws.numel()))
     return (idx, dist, ch) if with_changes else (idx, dist)
+
+
+def rsc_knn_descent_pairs(workspace: torch.Tensor):
+    """Pairs joined per iteration by the last call on this workspace (int64 [64], host)."""
+    import numpy as np
+    out = np.zeros(64, dtype=np.int64)
+    _check(lib().rsc_knn_descent_pairs(_ptr(workspace), workspace.numel(), out.ctypes.data))
+    return out
+
+
+def rsc_leiden_workspace_size(n: int, nnz: int) -> int:
+    out = _sz(0)
+    _check(lib().rsc_leiden_workspace_size(n, nnz, ctypes.byref(out)))
+    return int(out.value)
+
+
+def leiden_opts(resolution=1.0, n_iterations=2, max_levels=32, max_rounds=64, stream=None) -> rsc_leiden_opts:
+    o = rsc_leiden_opts()
+    o.resolution, o.n_iterations, o.max_levels, o.max_rounds = float(resolution), n_iterations, max_levels, max_rounds
+    o.stream = _stream(stream) if torch.cuda.is_available() else None
+    return o
+
+
+def rsc_leiden(indptr: torch.Tensor, indices: torch.Tensor, data: torch.Tensor, resolution=1.0, n_iterations=2,
+               max_levels=32, max_rounds=64, init=None, workspace=None, stream=None):
+    """Leiden communities of a CSR graph: returns (membership int32 [n] CUDA
+    tensor, number of communities, modularity)."""
+    if not (indptr.is_cuda and indptr.dtype == torch.int64 and indices.dtype == torch.int32
+            and data.dtype == torch.float32):
+        raise ValueError("indptr int64, indices int32, data float32 CUDA tensors expected")
+    n = indptr.numel() - 1
+    nnz = indices.numel()
+    o = leiden_opts(resolution, n_iterations, max_levels, max_rounds, stream)
+    ws = _workspace(rsc_leiden_workspace_size(n, nnz), indptr.device, workspace)
+    mem = torch.empty(n, dtype=torch.int32, device=indptr.device)
+    if init is not None:
+        if not (init.is_cuda and init.dtype == torch.int32 and init.numel() == n):
+            raise ValueError("init: int32 [n] CUDA tensor expected")
+        init = init.contiguous()
+    K = _i64(0)
+    q = ctypes.c_double(0.0)
+    _check(lib().rsc_leiden(_ptr(indptr), _ptr(indices), _ptr(data), n, nnz, _ptr(init), _ptr(mem), ctypes.byref(K),
+                            ctypes.byref(q), ctypes.byref(o), _ptr(ws), ws.numel()))
+    return mem, int(K.value), float(q.value)

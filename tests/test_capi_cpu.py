@@ -288,6 +288,6 @@ def test_knn_descent_argument_errors(L):
         rsc.rsc_knn_descent_workspace_size(1000, 4096, 64, rsc.nnd_opts(rev_slots=64))
     assert e.value.status == rsc.RSC_ERR_UNSUPPORTED
     # no workspace: refused on the host, before any launch
-    st = L.rsc_knn_descent(ctypes.c_void_p(16), 100, 5, 8, ctypes.c_void_p(16), ctypes.c_void_p(16), None,
+    st = L.rsc_knn_descent(ctypes.c_void_p(16), 100, 5, 8, None, ctypes.c_void_p(16), ctypes.c_void_p(16), None,
                            ctypes.byref(rsc.nnd_opts()), None, 0)
     assert st == rsc.RSC_ERR_WORKSPACE

@@ -26,13 +26,14 @@ def rsc():
     return r
 
 
-def run_both(rsc, X, k, S=0, R=32, C=64, T=4, delta=0.0, seed=0):
+def run_both(rsc, X, k, S=0, R=32, C=64, T=4, delta=0.0, seed=0, init=None):
     dev = torch.device("cuda")
     gi, gd, gch = rsc.rsc_knn_descent(torch.from_numpy(X).to(dev), k, sample=S, rev_slots=R, cand_slots=C,
-                                      max_iters=T, delta=delta, seed=seed, with_changes=True)
+                                      max_iters=T, delta=delta, seed=seed, with_changes=True,
+                                      init=None if init is None else torch.from_numpy(init).to(dev))
     torch.cuda.synchronize()
     oi, od2, och, run = oracle.nndescent(X, k, sample=S or k, rev_slots=R, cand_slots=C, iters=T, delta=delta,
-                                         seed=seed)
+                                         seed=seed, init=init)
     return gi.cpu().numpy(), gd.cpu().numpy(), gch.cpu().numpy(), oi, od2, och, run
 
 
@@ -67,6 +68,18 @@ def test_k_equals_n_and_tiny_sets(rsc):
         assert_same(*run_both(rsc, X, k, T=3, seed=n)[:6], 3)
 
 
+def test_caller_lists(rsc):
+    """Seeded caller lists with out-of-range ids, repeats and the row itself."""
+    X = synth.mixture(3000, 24, n_comp=12, seed=14)
+    n, k = len(X), 12
+    rng = np.random.default_rng(15)
+    init = rng.integers(-50, n + 50, (n, k)).astype(np.int32)
+    init[::7, 3] = init[::7, 2]
+    init[::5, 0] = np.arange(0, n, 5)
+    for T in (1, 2, 4):
+        assert_same(*run_both(rsc, X, k, T=T, seed=6, init=init)[:6], T)
+
+
 def test_duplicate_points(rsc):
     rng = np.random.default_rng(12)
     P = rng.normal(0, 1, (400, 9)).astype(np.float32)
@@ -82,6 +95,19 @@ def test_early_stop_matches(rsc):
     assert_same(gi, gd, gch, oi, od2, och, 30)
     lim = delta * len(X) * k
     assert gch[run - 1] < lim and (gch[:run - 1] >= lim).all()
+
+
+def test_pair_counts(rsc):
+    """The join's pair counters equal the oracle's count of joined pairs."""
+    X = synth.mixture(2500, 16, n_comp=9, seed=16)
+    k, T = 12, 5
+    Xd = torch.from_numpy(X).cuda()
+    o = rsc.nnd_opts(max_iters=T, seed=7)
+    ws = torch.empty(rsc.rsc_knn_descent_workspace_size(len(X), 16, k, o), dtype=torch.uint8, device="cuda")
+    rsc.rsc_knn_descent(Xd, k, max_iters=T, seed=7, workspace=ws)
+    got = rsc.rsc_knn_descent_pairs(ws)
+    _, _, _, _, want = oracle.nndescent(X, k, iters=T, seed=7, with_pairs=True)
+    assert list(got[:T]) == list(want) and (got[T:] == 0).all()
 
 
 def test_runs_are_identical(rsc):
@@ -126,3 +152,4 @@ def test_full_size_workload_on_sampled_rows(rsc):
     want, _, _ = oracle.knn(X, k, queries=q)
     recall = np.mean([len(set(gi[u]) & set(want[r])) / k for r, u in enumerate(q)])
     assert recall >= 0.85, recall
+

@@ -229,3 +229,31 @@ def test_bad_arguments():
         oracle.nndescent(X, 3, rev_slots=12)   # not a power of two
     with pytest.raises(ValueError):
         oracle.nndescent(X, 3, sample=4)   # S > k
+
+
+def test_caller_lists_start_the_iterations():
+    """Initial lists from caller lists: the row itself, then the caller's valid
+    distinct entries in order, then hashed draws; k exact lists are a fixed point."""
+    rng = np.random.default_rng(13)
+    n, d, k = 60, 4, 6
+    X = rng.normal(0, 1, (n, d)).astype(np.float32)
+    ex = exact_sq(X)
+    exact = np.array([np.lexsort((np.arange(n), ex[u]))[:k] for u in range(n)], dtype=np.int32)
+    idx0, _, _, _ = oracle.nndescent(X, k, iters=0, init=exact)
+    assert (idx0 == exact).all()
+    idx5, _, ch, _ = oracle.nndescent(X, k, iters=5, init=exact)
+    assert (idx5 == exact).all() and (ch == 0).all()
+    # invalid, repeated and self entries are skipped; the rest keeps its order
+    init = np.full((n, k), -1, dtype=np.int32)
+    init[:, 0] = (np.arange(n) + 7) % n
+    init[:, 1] = (np.arange(n) + 7) % n
+    init[:, 2] = np.arange(n)
+    init[:, 3] = n + 5
+    init[:, 4] = (np.arange(n) + 3) % n
+    idx0, _, _, _ = oracle.nndescent(X, k, iters=0, init=init, seed=2)
+    plain, _, _, _ = oracle.nndescent(X, k, iters=0, seed=2)
+    for u in range(n):
+        s = set(idx0[u].tolist())
+        assert {u, (u + 7) % n, (u + 3) % n} <= s and len(s) == k
+        # the remaining entries are the hashed draws of the plain initial list
+        assert s - {(u + 7) % n, (u + 3) % n} <= set(plain[u].tolist())
