@@ -291,3 +291,23 @@ def test_knn_descent_argument_errors(L):
     st = L.rsc_knn_descent(ctypes.c_void_p(16), 100, 5, 8, None, ctypes.c_void_p(16), ctypes.c_void_p(16), None,
                            ctypes.byref(rsc.nnd_opts()), None, 0)
     assert st == rsc.RSC_ERR_WORKSPACE
+
+
+def test_leiden_argument_errors(L):
+    a = rsc.rsc_leiden_workspace_size(1000, 20000)
+    assert a > 20000 * (4 + 8) * 3 and rsc.rsc_leiden_workspace_size(2000, 40000) > a
+    for args in ((0, 10), (-1, 10), (10, -1)):
+        with pytest.raises(rsc.RscError) as e:
+            rsc.rsc_leiden_workspace_size(*args)
+        assert e.value.status == rsc.RSC_ERR_INVALID_ARG
+    o = rsc.leiden_opts()
+    vp = ctypes.c_void_p(256)
+    K, q = ctypes.c_int64(0), ctypes.c_double(0)
+    # refused on the host before any launch: no workspace, bad options, NULL pointers
+    assert L.rsc_leiden(vp, vp, vp, 10, 20, None, vp, ctypes.byref(K), ctypes.byref(q), ctypes.byref(o),
+                        None, 0) == rsc.RSC_ERR_WORKSPACE
+    for bad in (rsc.leiden_opts(resolution=-1.0), rsc.leiden_opts(n_iterations=-2), rsc.leiden_opts(max_rounds=-1)):
+        assert L.rsc_leiden(vp, vp, vp, 10, 20, None, vp, None, None, ctypes.byref(bad), vp, 1 << 30) == \
+            rsc.RSC_ERR_INVALID_ARG
+    assert L.rsc_leiden(None, vp, vp, 10, 20, None, vp, None, None, ctypes.byref(o), vp, 1 << 30) == \
+        rsc.RSC_ERR_INVALID_ARG
