@@ -92,7 +92,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--candidates", type=int, default=0, help="candidates per row before the exact re-rank (0 = default)")
     p.add_argument("--workload", choices=["graph", "batched", "partitioner", "cosine", "umap", "edistance",
-                                          "nndescent"],
+                                          "nndescent", "leiden"],
                    default="graph",
                    help="graph: the 1M-cell neighbourhood graph (headline); batched: 64 samples, ~3M cells; "
                         "partitioner: learned-partition kNN graph of 5M cells; cosine: 11M-cell cosine graph, k=30; "
@@ -1118,6 +1118,110 @@ def run_nndescent(args):
         print(json.dumps(line), flush=True)
 
 
+LD_WORKLOAD = ("Leiden communities of the headline neighbourhood graph: 1,000,000 cells x 50 PCs (100-cluster "
+               "mixture), k=15 BF16+re-rank kNN and fuzzy connectivities built untimed by the library "
+               "(22.8M entries), modularity, resolution 1, two runs (scanpy's count)")
+
+
+def run_leiden(args):
+    """Leiden workload: cells/s of one rsc_leiden call on the 1M-cell graph."""
+    import numpy as np
+    import torch
+    from paper_2603_02402_gb300 import rsc, synth
+
+    world, rank, local = setup_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rsc.lib()
+    n, k = args.n, args.k
+    X = synth.mixture(n, 50, n_comp=100, seed=rank)
+    idx, dist = rsc.rsc_knn(torch.from_numpy(X).to(dev), k, precision="bf16")
+    ip, ind, dat, _, _ = rsc.rsc_connectivities(idx, dist)
+    torch.cuda.synchronize()
+    nnz = int(ip[-1])
+    ind, dat = ind[:nnz].contiguous(), dat[:nnz].contiguous()
+    del idx, dist
+    ws = torch.empty(rsc.rsc_leiden_workspace_size(n, nnz), dtype=torch.uint8, device=dev)
+
+    def step():
+        return rsc.rsc_leiden(ip, ind, dat, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sampler = ClockSampler(_smi_id(dev))
+    sampler.__enter__()
+    ev[0].record()
+    for _ in range(args.steps):
+        mem, K, Q = step()
+    ev[1].record()
+    torch.cuda.synchronize()
+    sampler.__exit__()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    st = rsc.rsc_leiden_last_stats()
+
+    # end to end: the graph in from pinned memory, the membership out
+    hip, hind, hdat = ip.cpu().pin_memory(), ind.cpu().pin_memory(), dat.cpu().pin_memory()
+    hmem = torch.empty(n, dtype=torch.int32).pin_memory()
+    gip, gind, gdat = torch.empty_like(ip), torch.empty_like(ind), torch.empty_like(dat)
+
+    def e2e_step():
+        gip.copy_(hip, non_blocking=True)
+        gind.copy_(hind, non_blocking=True)
+        gdat.copy_(hdat, non_blocking=True)
+        m2, _, _ = rsc.rsc_leiden(gip, gind, gdat, workspace=ws)
+        hmem.copy_(m2, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    ke = max(1, min(args.steps, 3))
+    ev[0].record()
+    for _ in range(ke):
+        e2e_step()
+    ev[1].record()
+    torch.cuda.synchronize()
+    e2e_ms = ev[0].elapsed_time(ev[1]) / ke
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs") or 6787.6
+    moved = 16.0 * st["entries"] + 32.0 * st["vertices"]   # bytes the rounds read at least
+    achieved = moved / (ms / 1e3) / 1e9
+    line = {"metric": "Leiden cells/s (1M-cell neighbourhood graph, modularity, resolution 1)",
+            "value": n / (ms / 1e3), "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": LD_WORKLOAD, "n": n, "nnz": nnz, "communities": K, "modularity": Q,
+                       "work": st, "l2": "the level-0 graph (273 MB with 64-bit weights) exceeds L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "leiden.cu (move_kernel, inner/pick_kernel)",
+                         "peak_source": "hbm_gbs of measured",
+                         "algorithmic": "16 bytes per graph entry (column, 64-bit weight, the neighbour's label) and "
+                                        "32 per vertex (row pointers, strength, labels, totals) for every moving "
+                                        "round, twice per refinement round, over the call's CUDA-event time"},
+            "e2e": {"value": n / (e2e_ms / 1e3), "unit": "cells/s",
+                    "h2d_bytes_per_step": int(hip.numel() * 8 + hind.numel() * 4 + hdat.numel() * 4),
+                    "d2h_bytes_per_step": int(n * 4), "ms_per_step": e2e_ms},
+            "gpu_launches": int(st["launches"]) * args.steps,
+            "clocks": sampler.summary()}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        from scipy import spatial
+        oracle.build()
+        m = 100_000
+        Xs = synth.mixture(m, 8, n_comp=40, seed=11)
+        dd, ii = spatial.cKDTree(Xs.astype(np.float64)).query(Xs.astype(np.float64), k, workers=-1)
+        g = oracle.connectivities(ii.astype(np.int32), dd.astype(np.float32).astype(np.float64))
+        t0 = time.perf_counter()
+        oracle.leiden(g["indptr"], g["indices"], g["data"].astype(np.float32))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the oracle's Leiden on a {m}-cell graph (k-d tree lists of an "
+                                          "8-dimensional 40-cluster mixture, the oracle's connectivities)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1134,6 +1238,8 @@ def main():
         run_edistance(args)
     elif args.workload == "nndescent":
         run_nndescent(args)
+    elif args.workload == "leiden":
+        run_leiden(args)
     else:
         run_ours(args)
 

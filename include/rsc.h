@@ -554,8 +554,9 @@ rsc_status rsc_edistance_workspace_size(int64_t n_rows, int32_t d, const int64_t
  *                 requested; NaN elsewhere.
  * Distances are computed on tensor cores from BF16 operands split into high
  * and low parts (three products per coordinate pair, FP32 accumulation, each
- * row centred on a common point first), summed in FP32 per 64 columns and in
- * FP64 beyond; expect about 1e-6 relative error in the sums.  Asynchronous on
+ * row centred on a common point first), summed in FP32 per 32 columns and in
+ * float-float pairs (about 48 significant bits) beyond, each pair's total
+ * added in FP64; expect about 1e-6 relative error in the sums.  Asynchronous on
  * `stream`, except that the offsets, the work list and the pair mask are copied
  * from host memory before the call returns.  Errors: RSC_ERR_INVALID_ARG for
  * NULL pointers, bad offsets, pairs out of range or a > b, n_rows outside
@@ -718,6 +719,16 @@ rsc_status rsc_leiden_workspace_size(int64_t n, int64_t nnz, size_t *bytes);
  * row pointers or columns outside the graph or starting labels outside
  * [0, n); RSC_ERR_WORKSPACE for a missing or small workspace.
  */
+/*
+ * Work of the last successful rsc_leiden call made on this thread (a statistic
+ * for throughput accounting; the paper has no counterpart).  stats: HOST
+ * array of 6: levels run (over all runs), moving rounds, refinement rounds,
+ * graph entries read by those rounds (a moving round reads every entry of its
+ * level once, a refinement round twice), vertices visited likewise, and the
+ * kernels launched.
+ */
+rsc_status rsc_leiden_last_stats(int64_t *stats);
+
 rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n, int64_t nnz,
                       const int32_t *init, int32_t *membership, int64_t *n_communities, double *modularity,
                       const rsc_leiden_opts *opts, void *workspace, size_t workspace_bytes);

@@ -27,10 +27,10 @@
 // the length of its run, loaded one tile ahead) gives the columns' groups; a
 // chunk of one group away from the diagonal is summed without predicates.
 // A chunk's columns split into runs of one group each (warp-uniform); per run
-// a thread adds its FP32 partial to an FP64 sum, and
-// when the column group changes the warp reduces the FP64 sums of rows of one
-// group (rows are in group order, so equal groups are adjacent lanes) and
-// one lane per run adds them to S with one double atomic.
+// a thread adds its FP32 partial to a float-float sum (TwoSum: FP32 pipes
+// only), and when the column group changes the warp reduces the sums of rows
+// of one group (rows are in group order, so equal groups are adjacent lanes)
+// and one lane per run adds them to S with one double atomic.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
@@ -177,18 +177,38 @@ __device__ __forceinline__ float sqrt_fast(float x) {
     return r;
 }
 
-// Adds the FP64 sums of a warp's rows to S[g_row * G + gc]: rows are in group
-// order, so lanes of one group are adjacent; a segmented inclusive scan over
-// the lanes, then the last lane of each run adds the run's total.
-__device__ __forceinline__ void flush_sums(double acc, int grow, int gc, int lane, int G, double *__restrict__ S) {
+// hi + lo += x as a float-float pair: Knuth's TwoSum puts the rounding error
+// of hi + x into lo, so the pair carries about 48 significant bits (FP32
+// pipes only; the FP64 pipe is narrow on this part).
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// Adds the float-float sums of a warp's rows to S[g_row * G + gc]: rows are in
+// group order, so lanes of one group are adjacent; a segmented inclusive scan
+// over the lanes, then the last lane of each run adds the run's total (in
+// FP64) with one atomic.
+__device__ __forceinline__ void flush_sums(float hi, float lo, int grow, int gc, int lane, int G,
+                                           double *__restrict__ S) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const double v = __shfl_up_sync(0xffffffffu, acc, o);
+        const float vh = __shfl_up_sync(0xffffffffu, hi, o);
+        const float vl = __shfl_up_sync(0xffffffffu, lo, o);
         const int g = __shfl_up_sync(0xffffffffu, grow, o);
-        if (lane >= o && g == grow) acc += v;
+        if (lane >= o && g == grow) {
+            ff_add(hi, lo, vh);
+            lo = __fadd_rn(lo, vl);
+        }
     }
     const int gn = __shfl_down_sync(0xffffffffu, grow, 1);
-    if (grow >= 0 && (lane == 31 || gn != grow) && acc != 0.0) atomicAdd(&S[(int64_t)grow * G + gc], acc);
+    if (grow >= 0 && (lane == 31 || gn != grow)) {
+        const double v = (double)hi + (double)lo;
+        if (v != 0.0) atomicAdd(&S[(int64_t)grow * G + gc], v);
+    }
 }
 
 // Work item: query tile qt against database tiles [dt0, dt1).
@@ -350,12 +370,13 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const int64_t i = q0 + r;                    // gathered position of this thread's row
             const int grow = i < n ? group[i] : -1;
             int gc = -1;          // column group of the open sum (warp-uniform)
-            double acc = 0.0;     // this row's sum for (grow, gc)
+            float acc = 0.f, acc_lo = 0.f;   // this row's sum for (grow, gc), float-float
             auto open = [&](int g) {   // make g the open column group (warp-uniform)
                 if (g != gc) {
-                    if (gc >= 0) flush_sums(acc, grow, gc, lane, G, S);
+                    if (gc >= 0) flush_sums(acc, acc_lo, grow, gc, lane, G, S);
                     gc = g;
-                    acc = 0.0;
+                    acc = 0.f;
+                    acc_lo = 0.f;
                 }
             };
             auto wanted = [&](int g) -> bool {
@@ -401,7 +422,7 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
                             for (int u = 0; u < 32; ++u) sum += (u > above) ? v[u] : 0.f;
                         }
-                        acc += (double)sum;
+                        ff_add(acc, acc_lo, sum);
                     }
                     continue;
                 }
@@ -416,12 +437,12 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
                         for (int u = 0; u < 32; ++u)
                             sum += (u >= u0 && u < u1 && u > above) ? v[u] : 0.f;
-                        acc += (double)sum;
+                        ff_add(acc, acc_lo, sum);
                     }
                     c = seg_end;
                 }
             }
-            if (ok && gc >= 0) flush_sums(acc, grow, gc, lane, G, S);
+            if (ok && gc >= 0) flush_sums(acc, acc_lo, grow, gc, lane, G, S);
         }
     }
 

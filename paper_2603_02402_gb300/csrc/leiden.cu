@@ -6,10 +6,13 @@
 // Every vertex of a round decides on the state the round began with, so a
 // round is one launch over all vertices:
 //   move     warp per vertex: the weights to each neighbouring community are
-//            summed in the vertex's own open-addressing table (64-bit atomic
-//            adds, so the sums are exact and order-free), the table is read
-//            back and cleared, and the warp picks the community with the
-//            largest gain (128-bit integer gains, ties to the smaller label);
+//            summed exactly and in no particular order: for rows of up to 32
+//            entries in registers (lanes with equal labels found by
+//            match.any, their weights added by redux.sync in 16-bit pieces),
+//            for longer rows in the vertex's own open-addressing table (64-bit
+//            atomic adds; the table is read back and cleared); the warp picks
+//            the community with the largest gain (128-bit integer gains, ties
+//            to the smaller label);
 //            moves alternate direction between rounds (even: to a smaller
 //            label, odd: to a larger one);
 //   refine   inside each community, vertices that are still alone and well
@@ -95,6 +98,22 @@ __device__ __forceinline__ void warp_best(i128 &g, int32_t &c) {
             c = oc;
         }
     }
+}
+
+// Rows of at most 32 entries, without tables: lane l holds entry l's label c
+// (kNone when the entry is skipped) and weight w.  Lanes with equal labels
+// find each other (match.any) and add their weights exactly in four 16-bit
+// pieces (redux.sync.add over the lanes of the label); the label's first lane
+// is its leader.  Returns the label's total weight.
+__device__ __forceinline__ int64_t label_sum(int32_t c, int64_t w, bool &leader) {
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const uint64_t u = (uint64_t)w;
+    const uint64_t p0 = __reduce_add_sync(peers, (unsigned)(u & 0xFFFF));
+    const uint64_t p1 = __reduce_add_sync(peers, (unsigned)((u >> 16) & 0xFFFF));
+    const uint64_t p2 = __reduce_add_sync(peers, (unsigned)((u >> 32) & 0xFFFF));
+    const uint64_t p3 = __reduce_add_sync(peers, (unsigned)(u >> 48));
+    leader = c != kNone && (int)(__ffs(peers) - 1) == (int)(threadIdx.x & 31);
+    return (int64_t)(p0 + (p1 << 16) + (p2 << 32) + (p3 << 48));
 }
 
 __global__ void weights_kernel(const float *__restrict__ data, int64_t nnz, int64_t *__restrict__ wt) {
@@ -187,18 +206,38 @@ move_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restric
     if (v >= nv) return;   // warp-uniform
     const int32_t a = comm[v];
     const int64_t kv = k[v];
-    const int64_t T = toff[v], len = toff[v + 1] - T;
+    const int64_t e0 = ip[v], e1 = ip[v + 1];
+    int64_t sa = 0;
+    i128 gb = 0;
+    int32_t best = kNone;
+    if (e1 - e0 <= 32) {   // warp-uniform: sums in registers
+        int32_t c = kNone;
+        int64_t w = 0;
+        if (e0 + lane < e1) {
+            const int32_t u = col[e0 + lane];
+            w = wt[e0 + lane];
+            if (u != v && w != 0) c = comm[u];
+        }
+        bool leader;
+        const int64_t sc = label_sum(c, w, leader);
+        if (leader) {
+            if (c == a) {
+                sa = sc;
+            } else {
+                gb = (i128)sc * m2 * 65536 - (i128)G * kv * (int64_t)tot[c];
+                best = c;
+            }
+        }
+    }
+    const int64_t T = toff[v], len = e1 - e0 <= 32 ? 0 : toff[v + 1] - T;
     int32_t *key = hkey + T;
     u64 *sum = hsum + T;
-    for (int64_t e = ip[v] + lane; e < ip[v + 1]; e += 32) {
+    for (int64_t e = e0 + lane; e < e1 && len; e += 32) {
         const int32_t u = col[e];
         const int64_t w = wt[e];
         if (u != v && w != 0) table_add(key, sum, len, comm[u], w);
     }
     __syncwarp();
-    int64_t sa = 0;
-    i128 gb = 0;
-    int32_t best = kNone;
     for (int64_t s = lane; s < len; s += 32) {
         const int32_t c = __ldcg(key + s);
         if (c < 0) continue;
@@ -273,17 +312,39 @@ pick_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restric
         if (lane == 0) target[v] = -1;
         return;
     }
-    const int64_t T = toff[v], len = toff[v + 1] - T;
+    const int64_t e0 = ip[v], e1 = ip[v + 1];
+    i128 gb = 0;
+    int32_t best = kNone;
+    if (e1 - e0 <= 32) {   // warp-uniform: sums in registers
+        int32_t S = kNone;
+        int64_t w = 0;
+        if (e0 + lane < e1) {
+            const int32_t u = col[e0 + lane];
+            w = wt[e0 + lane];
+            if (u != v && w != 0 && comm[u] == C) S = ref[u];
+        }
+        bool leader;
+        const int64_t sS = label_sum(S, w, leader);
+        if (leader && S != own) {
+            const int64_t rS = (int64_t)rtot[S];
+            if ((i128)(int64_t)ext[S] * m2 * 65536 >= (i128)G * rS * (totC - rS)) {
+                const i128 g = (i128)sS * m2 * 65536 - (i128)G * kv * rS;
+                if (g >= 0) {
+                    gb = g;
+                    best = S;
+                }
+            }
+        }
+    }
+    const int64_t T = toff[v], len = e1 - e0 <= 32 ? 0 : toff[v + 1] - T;
     int32_t *key = hkey + T;
     u64 *sum = hsum + T;
-    for (int64_t e = ip[v] + lane; e < ip[v + 1]; e += 32) {
+    for (int64_t e = e0 + lane; e < e1 && len; e += 32) {
         const int32_t u = col[e];
         const int64_t w = wt[e];
         if (u != v && w != 0 && comm[u] == C) table_add(key, sum, len, ref[u], w);
     }
     __syncwarp();
-    i128 gb = 0;
-    int32_t best = kNone;
     for (int64_t s = lane; s < len; s += 32) {
         const int32_t S = __ldcg(key + s);
         if (S < 0) continue;
@@ -559,6 +620,12 @@ rsc_status leiden_params(int64_t n, int64_t nnz, const rsc_leiden_opts *o, LdPar
     return RSC_OK;
 }
 
+// Work of the last rsc_leiden call on this thread (rsc_leiden_last_stats).
+struct LdStats {
+    int64_t levels = 0, move_rounds = 0, refine_rounds = 0, entries = 0, vertices = 0, launches = 0;
+};
+thread_local LdStats g_last_stats;
+
 // One level's table offsets from tlen [nv].
 rsc_status table_offsets(const LdLayout &L, int64_t nv, cudaStream_t st) {
     RSC_CUDA_TRY(seg_scan::launch(L.tlen, nv, L.toff, L.ssum, st));
@@ -571,6 +638,17 @@ rsc_status table_offsets(const LdLayout &L, int64_t nv, cudaStream_t st) {
 using namespace rsc;
 
 extern "C" {
+
+rsc_status rsc_leiden_last_stats(int64_t *stats) {
+    if (!stats) return fail(RSC_ERR_INVALID_ARG, "stats is NULL");
+    stats[0] = g_last_stats.levels;
+    stats[1] = g_last_stats.move_rounds;
+    stats[2] = g_last_stats.refine_rounds;
+    stats[3] = g_last_stats.entries;
+    stats[4] = g_last_stats.vertices;
+    stats[5] = g_last_stats.launches;
+    return RSC_OK;
+}
 
 rsc_status rsc_leiden_workspace_size(int64_t n, int64_t nnz, size_t *bytes) {
     if (!bytes) return fail(RSC_ERR_INVALID_ARG, "bytes is NULL");
@@ -614,6 +692,9 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
         RSC_CUDA_TRY(cudaStreamSynchronize(st));
         if (bad) return fail(RSC_ERR_INVALID_ARG, "graph structure or starting labels out of range");
     }
+    LdStats stats;
+    g_last_stats = stats;
+    stats.launches = (nnz > 0 ? 3 : 2);   // weights, checks, starting labels
     RSC_CUDA_TRY(cudaMemsetAsync(L.hkey, 0xFF, sizeof(int32_t) * (size_t)L.hcap, st));
     RSC_CUDA_TRY(cudaMemsetAsync(L.hsum, 0, sizeof(u64) * (size_t)L.hcap, st));
     for (int it = 0; it < p.n_iter; ++it) {
@@ -625,7 +706,11 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
         ldn::iota_kernel<<<blocks(n), 256, 0, st>>>(L.top, n);
         RSC_CUDA_TRY(cudaMemcpyAsync(L.comm, L.mem, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
         if ((s = canon(L, n, L.comm, st)) != RSC_OK) return s;
+        stats.launches += 4 + 1;   // ids, relabelling; the membership at the end of the run
         for (int level = 0; level < p.max_levels; ++level) {
+            ++stats.levels;
+            int64_t level_nnz = 0;
+            RSC_CUDA_TRY(cudaMemcpyAsync(&level_nnz, ip + nv, sizeof level_nnz, cudaMemcpyDeviceToHost, st));
             // strengths, 2m, vertex tables
             const unsigned vb = blocks(nv * 32, ldn::kBlock);
             ldn::strength_kernel<<<vb, ldn::kBlock, 0, st>>>(nv, ip, wt, L.k, L.cnt, L.tlen);
@@ -633,7 +718,9 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
             u64 m2u = 0;
             if ((s = read_counter(L, st, &m2u)) != RSC_OK) return s;
             const int64_t m2 = (int64_t)m2u;
+            stats.launches += 1;
             if (m2 == 0) break;
+            stats.launches += 2 + 5;   // table offsets; relabelling, totals and count after moving
             if ((s = table_offsets(L, nv, st)) != RSC_OK) return s;
             // 1. local moving
             int quiet = 0;
@@ -644,6 +731,10 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
                 RSC_CUDA_TRY(cudaGetLastError());
                 u64 moves = 0;
                 if ((s = read_counter(L, st, &moves)) != RSC_OK) return s;
+                ++stats.move_rounds;
+                stats.launches += 2;
+                stats.entries += level_nnz;
+                stats.vertices += nv;
                 std::swap(L.comm, L.next);
                 quiet = moves ? 0 : quiet + 1;
             }
@@ -653,6 +744,7 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
             u64 ncomm = 0;
             if ((s = read_counter(L, st, &ncomm)) != RSC_OK) return s;
             if ((int64_t)ncomm == nv) break;
+            stats.launches += 2 + 3 + 3;   // refinement set-up; relabelling; head flags and their scan
             // 2. refinement
             ldn::inner_kernel<<<vb, ldn::kBlock, 0, st>>>(nv, ip, col, wt, L.k, L.comm, 0, L.wC, nullptr, nullptr,
                                                           nullptr);
@@ -671,6 +763,10 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
                 RSC_CUDA_TRY(cudaGetLastError());
                 u64 moves = 0;
                 if ((s = read_counter(L, st, &moves)) != RSC_OK) return s;
+                ++stats.refine_rounds;
+                stats.launches += 3;
+                stats.entries += 2 * level_nnz;   // the statistics pass and the picks
+                stats.vertices += 2 * nv;
                 if (!moves) break;
             }
             if ((s = canon(L, nv, L.ref, st)) != RSC_OK) return s;
@@ -681,6 +777,7 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
             RSC_CUDA_TRY(cudaMemcpyAsync(&K, L.pos + nv, sizeof K, cudaMemcpyDeviceToHost, st));
             RSC_CUDA_TRY(cudaStreamSynchronize(st));
             if (K == nv) break;   // the refinement merged nothing
+            stats.launches += 10;
             RSC_CUDA_TRY(cudaMemsetAsync(L.ndeg, 0, sizeof(u64) * (size_t)K, st));
             ldn::node_kernel<<<blocks(nv), 256, 0, st>>>(nv, L.ref, L.pos, L.comm, ip, L.node, L.next, L.ndeg);
             ldn::top_kernel<<<blocks(n), 256, 0, st>>>(n, L.node, L.top);
@@ -720,6 +817,8 @@ rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float
     RSC_CUDA_TRY(cudaMemcpyAsync(&K, L.pos + n, sizeof K, cudaMemcpyDeviceToHost, st));
     RSC_CUDA_TRY(cudaStreamSynchronize(st));
     if (n_communities) *n_communities = K;
+    stats.launches += 6 + (modularity ? 1 : 0);
+    g_last_stats = stats;
     if (modularity) {
         // per community inside weight and strength; summed on the host in
         // community order

@@ -113,6 +113,7 @@ SIGNATURES = {
     "rsc_edistance_workspace_size": (_i32, [_i64, _i32, _vp, _i32, _vp, _i64, ctypes.POINTER(_sz)]),
     "rsc_edistance": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
     "rsc_knn_descent_pairs": (_i32, [_vp, _sz, _vp]),
+    "rsc_leiden_last_stats": (_i32, [_vp]),
     "rsc_leiden_workspace_size": (_i32, [_i64, _i64, ctypes.POINTER(_sz)]),
     "rsc_leiden": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(rsc_leiden_opts), _vp, _sz]),
@@ -696,3 +697,11 @@ def rsc_leiden(indptr: torch.Tensor, indices: torch.Tensor, data: torch.Tensor, 
     _check(lib().rsc_leiden(_ptr(indptr), _ptr(indices), _ptr(data), n, nnz, _ptr(init), _ptr(mem), ctypes.byref(K),
                             ctypes.byref(q), ctypes.byref(o), _ptr(ws), ws.numel()))
     return mem, int(K.value), float(q.value)
+
+
+def rsc_leiden_last_stats() -> dict:
+    """Work of this thread's last rsc_leiden call."""
+    import numpy as np
+    out = np.zeros(6, dtype=np.int64)
+    _check(lib().rsc_leiden_last_stats(out.ctypes.data))
+    return dict(zip(("levels", "move_rounds", "refine_rounds", "entries", "vertices", "launches"), out.tolist()))
