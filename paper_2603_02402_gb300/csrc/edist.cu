@@ -22,7 +22,7 @@
 // tiles through a ring of stages; one thread issues the 3 x 4 MMAs of
 // M = 128, N = 128, K = 16 per tile into one of two TMEM accumulators;
 // sixteen epilogue warps (four TMEM lane quarters x four 32-column chunks)
-// take sqrt(max(0, v)) of every value and add it to the current (row group,
+// take sqrt(|v|) of every value and add it to the current (row group,
 // column group) sum.  A chunk table (the group of a chunk's first column and
 // the length of its run, loaded one tile ahead) gives the columns' groups; a
 // chunk of one group away from the diagonal is summed without predicates.
@@ -407,7 +407,11 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 cbase += BN;
                 if (dt + 1 < wi.dt1 && cbase < n) ch = chunk[cbase >> 5];   // next tile's chunk, loaded early
 #pragma unroll
-                for (int u = 0; u < 32; ++u) v[u] = sqrt_fast(fmaxf(v[u], 0.f));
+                // sqrt(|v|): v below 0 is rounding noise of a near-zero squared
+                // distance, |v| <= its error bound, so sqrt(|v|) stays within the
+                // distance error sqrt(bound) that sqrt(max(0, v)) has, without
+                // the comparison
+                for (int u = 0; u < 32; ++u) v[u] = sqrt_fast(fabsf(v[u]));
                 if (cb >= n) continue;
                 const bool diag = cb < q0 + BM;          // some column may not lie above some row
                 const int64_t above = i - cb;            // columns u with cb + u > i count

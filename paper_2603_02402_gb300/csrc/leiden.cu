@@ -195,7 +195,7 @@ __global__ void count_self_kernel(int64_t nv, const int32_t *__restrict__ lab, u
 
 // ---------------------------------------------------------------- moving
 
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 5)
 move_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restrict__ col,
             const int64_t *__restrict__ wt, const int64_t *__restrict__ k, const u64 *__restrict__ tot,
             const int32_t *__restrict__ comm, int32_t *__restrict__ next, int64_t m2, int64_t G, int parity,
@@ -295,7 +295,7 @@ inner_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restri
     }
 }
 
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 5)
 pick_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restrict__ col,
             const int64_t *__restrict__ wt, const int64_t *__restrict__ k, const u64 *__restrict__ tot,
             const int32_t *__restrict__ comm, const int32_t *__restrict__ ref, const int64_t *__restrict__ wC,
@@ -613,7 +613,7 @@ rsc_status leiden_params(int64_t n, int64_t nnz, const rsc_leiden_opts *o, LdPar
     p->G = (int64_t)llrint(gamma * 65536.0);
     p->n_iter = q.n_iterations ? q.n_iterations : 2;
     p->max_levels = q.max_levels ? q.max_levels : 32;
-    p->max_rounds = q.max_rounds ? q.max_rounds : 64;
+    p->max_rounds = q.max_rounds ? q.max_rounds : 16;
     if (p->n_iter < 1 || p->n_iter > 1000 || p->max_levels < 1 || p->max_levels > 1000 || p->max_rounds < 1 ||
         p->max_rounds > 100000)
         return fail(RSC_ERR_INVALID_ARG, "n_iterations, max_levels or max_rounds out of range");
