@@ -9,8 +9,10 @@
 //            summed exactly and in no particular order: for rows of up to 32
 //            entries in registers (lanes with equal labels found by
 //            match.any, their weights added by redux.sync in 16-bit pieces),
-//            for longer rows in the vertex's own open-addressing table (64-bit
-//            atomic adds; the table is read back and cleared); the warp picks
+//            for longer rows in an open-addressing table (64-bit atomic adds;
+//            the warp's own table in shared memory up to 128 entries, the
+//            vertex's table in global memory beyond; read back and cleared);
+//            the warp picks
 //            the community with the largest gain (128-bit integer gains, ties
 //            to the smaller label);
 //            moves alternate direction between rounds (even: to a smaller
@@ -44,6 +46,7 @@ constexpr int kWarps = 8;   // warps per block of the per-vertex kernels
 constexpr int kBlock = kWarps * 32;
 constexpr int kCounters = 64;   // spread counters (moves, community counts)
 constexpr int32_t kNone = INT32_MAX;
+constexpr int kSmemSlots = 256;   // per-warp shared-memory table: rows of up to 128 entries
 
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     x ^= x >> 16;
@@ -229,9 +232,30 @@ move_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restric
             }
         }
     }
-    const int64_t T = toff[v], len = e1 - e0 <= 32 ? 0 : toff[v + 1] - T;
-    int32_t *key = hkey + T;
-    u64 *sum = hsum + T;
+    // longer rows: a table in shared memory (up to 128 entries) or the
+    // vertex's own table in global memory
+    __shared__ int32_t s_key[kWarps][kSmemSlots];
+    __shared__ u64 s_sum[kWarps][kSmemSlots];
+    const int64_t deg = e1 - e0;
+    const bool in_smem = deg > 32 && deg <= kSmemSlots / 2;
+    int64_t len = 0;
+    int32_t *key;
+    u64 *sum;
+    if (in_smem) {
+        len = table_len(deg);
+        key = s_key[(threadIdx.x >> 5)];
+        sum = s_sum[(threadIdx.x >> 5)];
+        for (int64_t s = lane; s < len; s += 32) {
+            key[s] = -1;
+            sum[s] = 0;
+        }
+        __syncwarp();
+    } else {
+        const int64_t T = toff[v];
+        len = deg <= 32 ? 0 : toff[v + 1] - T;
+        key = hkey + T;
+        sum = hsum + T;
+    }
     for (int64_t e = e0 + lane; e < e1 && len; e += 32) {
         const int32_t u = col[e];
         const int64_t w = wt[e];
@@ -239,9 +263,9 @@ move_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restric
     }
     __syncwarp();
     for (int64_t s = lane; s < len; s += 32) {
-        const int32_t c = __ldcg(key + s);
+        const int32_t c = in_smem ? key[s] : __ldcg(key + s);
         if (c < 0) continue;
-        const int64_t sc = (int64_t)__ldcg(sum + s);
+        const int64_t sc = (int64_t)(in_smem ? sum[s] : __ldcg(sum + s));
         key[s] = -1;
         sum[s] = 0;
         if (c == a) {
@@ -336,9 +360,28 @@ pick_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restric
             }
         }
     }
-    const int64_t T = toff[v], len = e1 - e0 <= 32 ? 0 : toff[v + 1] - T;
-    int32_t *key = hkey + T;
-    u64 *sum = hsum + T;
+    __shared__ int32_t s_key[kWarps][kSmemSlots];
+    __shared__ u64 s_sum[kWarps][kSmemSlots];
+    const int64_t deg = e1 - e0;
+    const bool in_smem = deg > 32 && deg <= kSmemSlots / 2;
+    int64_t len = 0;
+    int32_t *key;
+    u64 *sum;
+    if (in_smem) {
+        len = table_len(deg);
+        key = s_key[(threadIdx.x >> 5)];
+        sum = s_sum[(threadIdx.x >> 5)];
+        for (int64_t s = lane; s < len; s += 32) {
+            key[s] = -1;
+            sum[s] = 0;
+        }
+        __syncwarp();
+    } else {
+        const int64_t T = toff[v];
+        len = deg <= 32 ? 0 : toff[v + 1] - T;
+        key = hkey + T;
+        sum = hsum + T;
+    }
     for (int64_t e = e0 + lane; e < e1 && len; e += 32) {
         const int32_t u = col[e];
         const int64_t w = wt[e];
@@ -346,9 +389,9 @@ pick_kernel(int64_t nv, const int64_t *__restrict__ ip, const int32_t *__restric
     }
     __syncwarp();
     for (int64_t s = lane; s < len; s += 32) {
-        const int32_t S = __ldcg(key + s);
+        const int32_t S = in_smem ? key[s] : __ldcg(key + s);
         if (S < 0) continue;
-        const int64_t sS = (int64_t)__ldcg(sum + s);
+        const int64_t sS = (int64_t)(in_smem ? sum[s] : __ldcg(sum + s));
         key[s] = -1;
         sum[s] = 0;
         if (S == own) continue;
