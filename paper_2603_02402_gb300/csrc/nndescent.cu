@@ -42,7 +42,7 @@ constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;   // SplitMix64 state increm
 constexpr int kMaxK = 64;
 constexpr int kMaxSlots = 64;
 constexpr int kMaxIters = 64;
-constexpr int kJoinThreads = 64;
+constexpr int kJoinThreads = 128;
 constexpr int kPairSlots = 64;   // per-iteration pair counters, spread over slots
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
