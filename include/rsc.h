@@ -555,8 +555,9 @@ rsc_status rsc_edistance_workspace_size(int64_t n_rows, int32_t d, const int64_t
  * Distances are computed on tensor cores from BF16 operands split into high
  * and low parts (three products per coordinate pair, FP32 accumulation, each
  * row centred on a common point first), summed in FP32 per 32 columns and in
- * float-float pairs (about 48 significant bits) beyond, each pair's total
- * added in FP64; expect about 1e-6 relative error in the sums.  Asynchronous on
+ * float-float pairs (about 48 significant bits) beyond, each pair's two parts
+ * added to the FP64 sums by atomics; expect about 1e-6 relative error in the
+ * sums.  Asynchronous on
  * `stream`, except that the offsets, the work list and the pair mask are copied
  * from host memory before the call returns.  Errors: RSC_ERR_INVALID_ARG for
  * NULL pointers, bad offsets, pairs out of range or a > b, n_rows outside

@@ -188,10 +188,21 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float x) {
     lo = __fadd_rn(lo, e);
 }
 
+// x as a double, built from its bits with integer operations (the FP64 pipe
+// is narrow on this part): exact for normal x; zero and subnormal x give 0
+// (below 2^-126, far under the sums' resolution); x is finite.
+__device__ __forceinline__ double float_bits_to_double(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e == 0) return 0.0;
+    const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 // Adds the float-float sums of a warp's rows to S[g_row * G + gc]: rows are in
 // group order, so lanes of one group are adjacent; a segmented inclusive scan
-// over the lanes, then the last lane of each run adds the run's total (in
-// FP64) with one atomic.
+// over the lanes, then the last lane of each run adds the run's two parts
+// to S with FP64 atomics.
 __device__ __forceinline__ void flush_sums(float hi, float lo, int grow, int gc, int lane, int G,
                                            double *__restrict__ S) {
 #pragma unroll
@@ -206,8 +217,10 @@ __device__ __forceinline__ void flush_sums(float hi, float lo, int grow, int gc,
     }
     const int gn = __shfl_down_sync(0xffffffffu, grow, 1);
     if (grow >= 0 && (lane == 31 || gn != grow)) {
-        const double v = (double)hi + (double)lo;
-        if (v != 0.0) atomicAdd(&S[(int64_t)grow * G + gc], v);
+        // the pair's two parts added to S separately (no FP64 arithmetic)
+        double *dst = &S[(int64_t)grow * G + gc];
+        if (hi != 0.f) atomicAdd(dst, float_bits_to_double(hi));
+        if (lo != 0.f) atomicAdd(dst, float_bits_to_double(lo));
     }
 }
 
@@ -414,7 +427,9 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 for (int u = 0; u < 32; ++u) v[u] = sqrt_fast(fabsf(v[u]));
                 if (cb >= n) continue;
                 const bool diag = cb < q0 + BM;          // some column may not lie above some row
-                const int64_t above = i - cb;            // columns u with cb + u > i count
+                // columns u with cb + u > i count: u > above, above clamped to
+                // [-1, 32] so that the tests are 32-bit
+                const int above = (int)max((int64_t)-1, min((int64_t)32, i - cb));
                 if (cur.y == 32) {                       // one group over the whole chunk
                     open(cur.x);
                     if (wanted(cur.x)) {
@@ -436,11 +451,12 @@ edist_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     const int64_t seg_end = c == cb ? cb + cur.y : min(cend, offsets[g + 1]);
                     open(g);
                     if (wanted(g)) {
-                        const int u0 = (int)(c - cb), u1 = (int)(seg_end - cb);
+                        // columns [lo, u1): one unsigned range test per column
+                        const int u1 = (int)(seg_end - cb), lo = max((int)(c - cb), above + 1);
+                        const unsigned span = u1 > lo ? (unsigned)(u1 - lo) : 0u;
                         float sum = 0.f;
 #pragma unroll
-                        for (int u = 0; u < 32; ++u)
-                            sum += (u >= u0 && u < u1 && u > above) ? v[u] : 0.f;
+                        for (int u = 0; u < 32; ++u) sum += ((unsigned)(u - lo) < span) ? v[u] : 0.f;
                         ff_add(acc, acc_lo, sum);
                     }
                     c = seg_end;
