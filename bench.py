@@ -47,7 +47,15 @@ TRAFFIC = {
     ("connectivities.cu", "graph"): {"bytes_per_launch": 1_800_462_336, "kernel_sha": "d6300e549cd22f3b"},
     # one UMAP epoch of the 1,000,000-cell k = 15 graph (profiles/umap_epoch_1m.md): 220.9 + 8.1 MB
     ("umap.cu", "epoch"): {"bytes_per_launch": 228_918_272, "kernel_sha": "3b64a6d38e4b0abd"},
+    # one edist_tc_kernel launch of the 300,000-cell, 2,000-group screen
+    # (profiles/edist_tc_groups_60k_300k.md): 17.45 GB + 24.63 MB as ncu rounds them
+    ("edist.cu", "screen"): {"bytes_per_launch": 17_474_630_000, "kernel_sha": "ac2c027fd5f2d4e2"},
+    # the eight join launches of one 1,000,000-cell rsc_knn_descent call
+    # (profiles/nndescent_join_1m_300k.md)
+    ("nndescent.cu", "call"): {"bytes_per_launch": 106_520_583_424, "kernel_sha": "05e7bb9d56782086"},
 }
+ED_SOURCES = ("edist.cu", "knn_tc.cuh", "tc_ptx.cuh")
+NND_SOURCES = ("nndescent.cu",)
 
 ORDER_MIN_ROWS = 16384   # automatic locality ordering from this many rows (BF16 path)
 
@@ -980,7 +988,11 @@ def run_edistance(args):
                        "tile_pairs": tiles,
                        "l2": "operands (230 MB) stream from HBM/L2 per query tile; the G x G sums stay in L2"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tsqrt/s",
-                         "frac": achieved / sfu_peak, "traffic": None, "kernel": "edist.cu (edist_tc_kernel)",
+                         "frac": achieved / sfu_peak,
+                         "traffic": (TRAFFIC[("edist.cu", "screen")]["bytes_per_launch"]
+                                     if n == 299977 and _kernel_sha(ED_SOURCES) == TRAFFIC[("edist.cu", "screen")]["kernel_sha"]
+                                     else None),
+                         "kernel": "edist.cu (edist_tc_kernel)",
                          "peak_source": "derived: 152 SMs x 16 special-function results per clock x median SM clock",
                          "algorithmic": "one square root per cell pair (n (n - 1) / 2) over the call's CUDA-event time",
                          "tensor_tflops_executed": tflops,
@@ -1086,7 +1098,12 @@ def run_nndescent(args):
                        "l2": "X (200 MB) exceeds L2; the slot arrays (768 MB) are touched at random"},
             "roofline": {"bound": "alu", "achieved": lane_ops / (ms / 1e3) / 1e12, "peak": lane_peak,
                          "unit": "T FP32 lane-ops/s", "frac": lane_ops / (ms / 1e3) / 1e12 / lane_peak,
-                         "traffic": None, "kernel": "nndescent.cu (join_kernel)",
+                         "traffic": (TRAFFIC[("nndescent.cu", "call")]["bytes_per_launch"]
+                                     if n == 1_000_000 and _kernel_sha(NND_SOURCES) == TRAFFIC[("nndescent.cu", "call")]["kernel_sha"]
+                                     else None),
+                         "traffic_note": "DRAM bytes of the call's eight join launches (ncu, cold cache): "
+                                         "1.8 TB/s over the call, the join's staged rows and slot offers",
+                         "kernel": "nndescent.cu (join_kernel)",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x median SM clock",
                          "algorithmic": "2 d lane operations (subtract, fused multiply-add) per joined pair, "
                                         "pairs counted by the kernel, over the whole call's CUDA-event time "
