@@ -49,10 +49,11 @@ TRAFFIC = {
     ("umap.cu", "epoch"): {"bytes_per_launch": 228_918_272, "kernel_sha": "3b64a6d38e4b0abd"},
     # one edist_tc_kernel launch of the 300,000-cell, 2,000-group screen
     # (profiles/edist_tc_groups_60k_300k.md): 17.45 GB + 24.63 MB as ncu rounds them
-    ("edist.cu", "screen"): {"bytes_per_launch": 17_474_630_000, "kernel_sha": "ac2c027fd5f2d4e2"},
+    # (hash taken after the entry point gained its trace range; the kernel is unchanged)
+    ("edist.cu", "screen"): {"bytes_per_launch": 17_474_630_000, "kernel_sha": "9948e3aed94fcac2"},
     # the eight join launches of one 1,000,000-cell rsc_knn_descent call
     # (profiles/nndescent_join_1m_300k.md)
-    ("nndescent.cu", "call"): {"bytes_per_launch": 106_520_583_424, "kernel_sha": "05e7bb9d56782086"},
+    ("nndescent.cu", "call"): {"bytes_per_launch": 106_520_583_424, "kernel_sha": "186c10799f37c1d6"},
 }
 ED_SOURCES = ("edist.cu", "knn_tc.cuh", "tc_ptx.cuh")
 NND_SOURCES = ("nndescent.cu",)

@@ -152,6 +152,7 @@ rsc_status rsc_autotune_workspace_size(int64_t n, int32_t d, int32_t k, int32_t 
 rsc_status rsc_autotune_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metric,
                             const rsc_knn_opts *opts, int32_t trials, int32_t *idx, float *dist,
                             rsc_knn_opts *best, float *best_ms, void *workspace, size_t workspace_bytes) {
+    RSC_TRACE("rsc_autotune_knn");
     if (!opts || !best || !X || !idx || !dist) return fail(RSC_ERR_INVALID_ARG, "NULL argument");
     if (trials < 1) return fail(RSC_ERR_INVALID_ARG, "trials must be >= 1");
     cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
@@ -192,6 +193,7 @@ rsc_status rsc_autotune_knn_batched(const float *X, int64_t n, int32_t d, const 
                                     const rsc_knn_opts *opts, int32_t trials, int32_t *idx_within,
                                     float *dist_within, int32_t *idx_cross, float *dist_cross, rsc_knn_opts *best,
                                     float *best_ms, void *workspace, size_t workspace_bytes) {
+    RSC_TRACE("rsc_autotune_knn_batched");
     if (!opts || !best) return fail(RSC_ERR_INVALID_ARG, "NULL argument");
     if (trials < 1) return fail(RSC_ERR_INVALID_ARG, "trials must be >= 1");
     cudaStream_t st = static_cast<cudaStream_t>(opts->stream);

@@ -482,6 +482,7 @@ rsc_status rsc_knn_workspace_size(int64_t n, int32_t d, int32_t k, int32_t metri
 
 rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metric, int32_t *idx,
                    float *dist, const rsc_knn_opts *opts, void *workspace, size_t workspace_bytes) {
+    RSC_TRACE("rsc_knn");
     if (!X || !idx || !dist) return fail(RSC_ERR_INVALID_ARG, "X/idx/dist is NULL");
     KnnPlan p;
     rsc_status s = plan_knn(n, d, k, metric, opts, &p);
@@ -587,6 +588,7 @@ rsc_status rsc_knn_batched(const float *X, int64_t n, int32_t d, const int64_t *
                            int32_t *idx_within, float *dist_within, int32_t *idx_cross,
                            float *dist_cross, const rsc_knn_opts *opts, void *workspace,
                            size_t workspace_bytes) {
+    RSC_TRACE("rsc_knn_batched");
     if (!X || !idx_within || !dist_within || !idx_cross || !dist_cross)
         return fail(RSC_ERR_INVALID_ARG, "NULL array argument");
     BatchedPlan p;
@@ -714,6 +716,7 @@ rsc_status rsc_connectivities(const int32_t *idx, const float *dist, int64_t n, 
                               int64_t *indptr, int32_t *indices, float *data, int64_t nnz_capacity,
                               float *rho, float *sigma, void *workspace, size_t workspace_bytes,
                               void *stream) {
+    RSC_TRACE("rsc_connectivities");
     rsc_status s = check_conn_args(idx, dist, n, k);
     if (s != RSC_OK) return s;
     if (!indptr) return fail(RSC_ERR_INVALID_ARG, "indptr is NULL");
@@ -741,6 +744,7 @@ rsc_status rsc_connectivities(const int32_t *idx, const float *dist, int64_t n, 
 rsc_status rsc_connectivities_nnz(const int32_t *idx, const float *dist, int64_t n, int32_t k,
                                   int64_t *nnz, void *workspace, size_t workspace_bytes,
                                   void *stream) {
+    RSC_TRACE("rsc_connectivities_nnz");
     rsc_status s = check_conn_args(idx, dist, n, k);
     if (s != RSC_OK) return s;
     if (!nnz) return fail(RSC_ERR_INVALID_ARG, "nnz is NULL");
@@ -867,6 +871,7 @@ rsc_status rsc_umap_workspace_size(int64_t n, int64_t nnz, int32_t dim, size_t *
 rsc_status rsc_umap_layout(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n,
                            int64_t nnz, int32_t dim, float *embedding, const rsc_umap_opts *o,
                            void *workspace, size_t workspace_bytes) {
+    RSC_TRACE("rsc_umap_layout");
     size_t need = 0;
     rsc_status s = rsc_umap_workspace_size(n, nnz, dim, &need);
     if (s != RSC_OK) return s;

@@ -2,11 +2,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "rsc.h"
 
 namespace rsc {
+
+// Names an entry point's span in profiler timelines (an NVTX range, pushed on
+// entry and popped on every return; nothing is recorded unless a profiler is
+// attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define RSC_TRACE(name) ::rsc::TraceRange rsc_trace_range_(name)
 
 // ---------------------------------------------------------------- host side
 

@@ -668,6 +668,7 @@ rsc_status rsc_edistance(const float *X, int64_t n_rows, int32_t d, const int32_
                          const int64_t *group_offsets, int32_t n_groups, const int32_t *pairs, int64_t n_pairs,
                          double *sums, double *mean, double *E, void *workspace, size_t workspace_bytes,
                          void *stream) {
+    RSC_TRACE("rsc_edistance");
     EdPlan p;
     rsc_status s = plan_edistance(n_rows, d, group_offsets, n_groups, pairs, n_pairs, &p);
     if (s != RSC_OK) return s;

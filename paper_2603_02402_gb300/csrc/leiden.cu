@@ -705,6 +705,7 @@ rsc_status rsc_leiden_workspace_size(int64_t n, int64_t nnz, size_t *bytes) {
 rsc_status rsc_leiden(const int64_t *indptr, const int32_t *indices, const float *data, int64_t n, int64_t nnz,
                       const int32_t *init, int32_t *membership, int64_t *n_communities, double *modularity,
                       const rsc_leiden_opts *opts, void *workspace, size_t workspace_bytes) {
+    RSC_TRACE("rsc_leiden");
     LdParams p;
     rsc_status s = leiden_params(n, nnz, opts, &p);
     if (s != RSC_OK) return s;

@@ -620,6 +620,7 @@ rsc_status rsc_knn_descent_workspace_size(int64_t n, int32_t d, int32_t k, const
 rsc_status rsc_knn_descent(const float *X, int64_t n, int32_t d, int32_t k, const int32_t *init_idx, int32_t *idx,
                            float *dist, int64_t *changes, const rsc_nnd_opts *opts, void *workspace,
                            size_t workspace_bytes) {
+    RSC_TRACE("rsc_knn_descent");
     NndParams p;
     rsc_status s = nnd_params(n, d, k, opts, &p);
     if (s != RSC_OK) return s;

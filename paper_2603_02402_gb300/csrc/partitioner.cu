@@ -743,6 +743,7 @@ rsc_status rsc_partitioner_loss_grad_workspace_size(const rsc_partitioner *p, in
 rsc_status rsc_partitioner_loss_grad(rsc_partitioner *p, const float *Xb, const float *T, int32_t batch,
                                      float *loss_host, float *grad, void *workspace, size_t workspace_bytes,
                                      void *stream) {
+    RSC_TRACE("rsc_partitioner_loss_grad");
     rsc_status s = check_handle(p);
     if (s != RSC_OK) return s;
     if (!Xb || !T || batch < 1 || !loss_host) return fail(RSC_ERR_INVALID_ARG, "bad arguments");
@@ -956,6 +957,7 @@ rsc_status rsc_partitioner_workspace_size(const rsc_partitioner *p, int64_t n, i
 
 rsc_status rsc_partitioner_build_index(rsc_partitioner *p, const float *X, int64_t n, void *workspace,
                                        size_t workspace_bytes, void *stream) {
+    RSC_TRACE("rsc_partitioner_build_index");
     rsc_status s = check_handle(p);
     if (s != RSC_OK) return s;
     if (!X || n < 1 || n >= (int64_t(1) << 31)) return fail(RSC_ERR_INVALID_ARG, "X / n");
@@ -994,6 +996,7 @@ rsc_status rsc_partitioner_build_index(rsc_partitioner *p, const float *X, int64
 rsc_status rsc_partitioner_train(rsc_partitioner *p, const float *X, int64_t n, const int32_t *train_rows,
                                  int64_t n_train, int32_t k, int32_t kmeans_iters, int32_t epochs, int32_t batch,
                                  float lr, float *final_loss, void *workspace, size_t workspace_bytes, void *stream) {
+    RSC_TRACE("rsc_partitioner_train");
     rsc_status s = check_handle(p);
     if (s != RSC_OK) return s;
     if (!X || !train_rows || n < 1 || n >= (int64_t(1) << 31) || n_train < p->P || n_train > n)
@@ -1080,6 +1083,7 @@ rsc_status rsc_partitioner_train(rsc_partitioner *p, const float *X, int64_t n, 
 rsc_status rsc_knn_partitioned(rsc_partitioner *p, const float *X, int64_t n, int32_t k, int32_t n_probe,
                                int32_t routing, const int32_t *query_rows, int64_t n_queries, int32_t *idx,
                                float *dist, void *workspace, size_t workspace_bytes, void *stream) {
+    RSC_TRACE("rsc_knn_partitioned");
     rsc_status s = check_handle(p);
     if (s != RSC_OK) return s;
     if (!X || !idx || !dist || n != p->n_db) return fail(RSC_ERR_INVALID_ARG, "X / outputs / n (index built for n=%lld)",
