@@ -83,6 +83,15 @@ def test_knn_graphs_match_oracle(rsc, n, d, comps, seed):
     assert r[1] > 1
 
 
+def test_cosine_k30_graph(rsc):
+    """The oracle's cosine kNN (k = 30) and connectivities of a 5,000-cell mixture."""
+    X = synth.mixture(5000, 40, n_comp=25, seed=12)
+    i, dist, _ = oracle.knn(X, 30, metric=oracle.COSINE)
+    g = oracle.connectivities(i.astype(np.int32), dist)
+    graph = (g["indptr"].astype(np.int64), g["indices"].astype(np.int32), g["data"].astype(np.float32))
+    assert_same(*run_both(rsc, graph))
+
+
 @pytest.mark.parametrize("gamma", [0.1, 0.3, 2.5, 7.0])
 def test_resolutions(rsc, gamma):
     assert_same(*run_both(rsc, knn_graph(3000, 20, 12, 4), resolution=gamma))

@@ -54,6 +54,7 @@ def assert_same(gi, gd, gch, oi, od2, och, T):
     (800, 3, 2, 1, 1, 1, 5, 5),          # one reverse and one candidate slot
     (300, 64, 10, 10, 64, 64, 8, 6),     # d = 64
     (257, 1, 5, 3, 4, 8, 6, 7),          # d = 1: many equal distances, ties by id
+    (1500, 100, 20, 0, 32, 64, 3, 8),    # d = 100: rows beyond one tensor-core K block (the join is FP32 SIMT)
 ])
 def test_iterations_bit_exact(rsc, n, d, k, S, R, C, T, seed):
     X = synth.mixture(n, d, n_comp=7, seed=seed) if d > 1 else \
