@@ -179,6 +179,30 @@ def setup_dist(args):
     return world, rank, local
 
 
+def rank_barrier(world):
+    """Barrier over the ranks of the job (no-op for one rank)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks (one rank: x itself)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank processes its own units)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, timed on bounded query samples."""
     world, rank, _ = setup_dist(args)
@@ -282,15 +306,10 @@ def run_ours(args):
             ev[4].record(stream)
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        rank_barrier(world)
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ms(x):
+        return max_over_ranks(x, world, dev)
 
     def timed(prec, steps, warmup, clocks=False, prune=args.prune):
         ws_knn = buffers(prec, prune)
@@ -314,7 +333,7 @@ def run_ours(args):
             sampler.__exit__()
         if rsc.rsc_workspace_status(ws_knn) != rsc.RSC_OK or rsc.rsc_workspace_status(ws_conn) != rsc.RSC_OK:
             raise RuntimeError("a kernel recorded a failure status")
-        ms = max_over_ranks(start.elapsed_time(end) / steps)
+        ms = max_ms(start.elapsed_time(end) / steps)
         search = [p[1].elapsed_time(p[2]) for p in phase]
         rerank = [p[2].elapsed_time(p[3]) for p in phase]
         prep = [p[0].elapsed_time(p[1]) for p in phase]
@@ -371,14 +390,14 @@ def run_ours(args):
     e_end.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_ms = max_over_ranks(e_start.elapsed_time(e_end) / e2e_steps)
+    e2e_ms = max_ms(e_start.elapsed_time(e_end) / e2e_steps)
     h2d = X_pin.numel() * 4
     d2h = sum(t.numel() * t.element_size() for t in out_host.values())
 
     fp32 = None
     if precision != "fp32" and args.fp32_steps > 0:
         f_ms, f_ph, _, _ = timed("fp32", args.fp32_steps, 1)
-        fp32 = {"value": world * n / (f_ms / 1e3), "ms_per_step": f_ms, "search_ms": f_ph["search_ms"]}
+        fp32 = {"value": job_rate(n, world, f_ms), "ms_per_step": f_ms, "search_ms": f_ph["search_ms"]}
 
     # roofline of the dominant kernel (candidate search): algorithmic flops =
     # 2 * d per (query, database row) pair computed.  The full scan computes
@@ -395,7 +414,7 @@ def run_ours(args):
     if precision == "bf16" and scanned < pairs_total and args.full_scan_steps > 0:
         fs_ms, fs_ph, _, _ = timed("bf16", args.full_scan_steps, 1, prune="off")
         fs_ach = 2.0 * d * full_pairs / (fs_ph["search_ms"] / 1e3) / 1e12
-        full_scan = {"ms_per_step": fs_ms, "search_ms": fs_ph["search_ms"], "value": world * n / (fs_ms / 1e3),
+        full_scan = {"ms_per_step": fs_ms, "search_ms": fs_ph["search_ms"], "value": job_rate(n, world, fs_ms),
                      "achieved_tflops": fs_ach,
                      "frac": fs_ach / (peaks.get("bf16_tflops_sustained") or 1700.0),
                      "note": "same workload with pruning off (every tile pair scanned)"}
@@ -440,7 +459,7 @@ def run_ours(args):
         cpu = cpu_baseline(X, idx_main.cpu().numpy(), dist_main.cpu().numpy(), k, args.cpu_seconds)
 
     if rank == 0:
-        value = world * n / (ms / 1e3)
+        value = job_rate(n, world, ms)
         line = {
             "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -456,7 +475,7 @@ def run_ours(args):
             "roofline": roofline,
             "roofline_connectivities": roofline_conn,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(n, world, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step(metric, precision, n) * args.steps,
             "clocks": clocks,
