@@ -331,7 +331,7 @@ def nndescent(X, k, sample=None, rev_slots=32, cand_slots=64, iters=10, delta=0.
     return idx, d2, ch[:iters], run.value
 
 
-def leiden(indptr, indices, data, resolution=1.0, n_iter=2, max_levels=32, max_rounds=16, init=None):
+def leiden(indptr, indices, data, resolution=1.0, n_iter=2, max_levels=32, max_rounds=8, init=None):
     """Leiden communities (definition above oracle_leiden in oracle.c).
 
     Returns (membership int32 [n] numbered by first appearance, number of

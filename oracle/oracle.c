@@ -973,7 +973,7 @@ int oracle_nndescent(const float *X, int64_t n, int d, int k, int S, int R, int 
  *    (ties: smallest c) and moves there if g(c) > g(a) and, in even rounds,
  *    c < a, in odd rounds c > a (so two vertices never swap forever).  All
  *    moves of a round apply together.  The phase ends after two rounds in a
- *    row without a move, or after max_rounds rounds (16 by default).
+ *    row without a move, or after max_rounds rounds (8 by default).
  * 2. Refinement (RefinePartition / MergeNodesSubset): inside each community
  *    C of step 1, every vertex starts alone.  A vertex v that is still alone
  *    and well connected to C (s_{C-v} 2m 2^16 >= G k_v (tot_C - k_v)) looks at

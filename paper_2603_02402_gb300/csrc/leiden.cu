@@ -656,7 +656,7 @@ rsc_status leiden_params(int64_t n, int64_t nnz, const rsc_leiden_opts *o, LdPar
     p->G = (int64_t)llrint(gamma * 65536.0);
     p->n_iter = q.n_iterations ? q.n_iterations : 2;
     p->max_levels = q.max_levels ? q.max_levels : 32;
-    p->max_rounds = q.max_rounds ? q.max_rounds : 16;
+    p->max_rounds = q.max_rounds ? q.max_rounds : 8;
     if (p->n_iter < 1 || p->n_iter > 1000 || p->max_levels < 1 || p->max_levels > 1000 || p->max_rounds < 1 ||
         p->max_rounds > 100000)
         return fail(RSC_ERR_INVALID_ARG, "n_iterations, max_levels or max_rounds out of range");

@@ -669,7 +669,7 @@ def rsc_leiden_workspace_size(n: int, nnz: int) -> int:
     return int(out.value)
 
 
-def leiden_opts(resolution=1.0, n_iterations=2, max_levels=32, max_rounds=16, stream=None) -> rsc_leiden_opts:
+def leiden_opts(resolution=1.0, n_iterations=2, max_levels=32, max_rounds=8, stream=None) -> rsc_leiden_opts:
     o = rsc_leiden_opts()
     o.resolution, o.n_iterations, o.max_levels, o.max_rounds = float(resolution), n_iterations, max_levels, max_rounds
     o.stream = _stream(stream) if torch.cuda.is_available() else None
@@ -677,7 +677,7 @@ def leiden_opts(resolution=1.0, n_iterations=2, max_levels=32, max_rounds=16, st
 
 
 def rsc_leiden(indptr: torch.Tensor, indices: torch.Tensor, data: torch.Tensor, resolution=1.0, n_iterations=2,
-               max_levels=32, max_rounds=16, init=None, workspace=None, stream=None):
+               max_levels=32, max_rounds=8, init=None, workspace=None, stream=None):
     """Leiden communities of a CSR graph: returns (membership int32 [n] CUDA
     tensor, number of communities, modularity)."""
     if not (indptr.is_cuda and indptr.dtype == torch.int64 and indices.dtype == torch.int32

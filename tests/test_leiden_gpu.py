@@ -49,7 +49,7 @@ def run_both(rsc, graph, init=None, **kw):
                                torch.from_numpy(dat).to(dev),
                                init=None if init is None else torch.from_numpy(init).to(dev), **kw)
     okw = {"resolution": kw.get("resolution", 1.0), "n_iter": kw.get("n_iterations", 2),
-           "max_levels": kw.get("max_levels", 32), "max_rounds": kw.get("max_rounds", 16)}
+           "max_levels": kw.get("max_levels", 32), "max_rounds": kw.get("max_rounds", 8)}
     om, oK, oQ, _ = oracle.leiden(ip, ind, dat, init=init, **okw)
     return mem.cpu().numpy(), K, Q, om, oK, oQ
 
@@ -101,7 +101,7 @@ def test_resolutions(rsc, gamma):
 def test_iterations_levels_rounds(rsc):
     g = knn_graph(4000, 30, 15, 5)
     for kw in ({"n_iterations": 1}, {"n_iterations": 3}, {"max_levels": 1}, {"max_rounds": 2},
-               {"max_rounds": 1, "n_iterations": 1}, {"max_rounds": 64}):
+               {"max_rounds": 1, "n_iterations": 1}, {"max_rounds": 16}, {"max_rounds": 64}):
         assert_same(*run_both(rsc, g, **kw))
 
 
