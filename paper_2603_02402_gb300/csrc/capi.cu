@@ -163,12 +163,30 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
             return fail(RSC_ERR_UNSUPPORTED, "no SIMT kernel for DP=%d KC=%d", p->DP, p->KC);
     }
     // database splits: enough CTAs to fill the GPU when there are few queries
-    const int64_t qrows = 128;                        // query rows per CTA work unit
+    const bool tiled = !tc && p->KC <= 32;            // register-tiled FP32 kernel: 256 queries, 64-row tiles
+    const int64_t qrows = tiled ? 256 : 128;          // query rows per CTA work unit
     const int64_t target = tc ? 152 : 1024;           // work units wanted (persistent CTAs / blocks)
-    const int64_t align = tc ? knn_tc_split_align() : 32;
+    const int64_t align = tc ? knn_tc_split_align() : tiled ? 64 : 32;
     const int64_t qblocks = ceil_div(n, qrows);
     const int per_split = p->parts * p->KC;           // candidate ids per row and split
     int splits = o->db_splits;
+    if (splits == 0 && tiled) {
+        // one CTA per SM: the fewest splits whose waves are at least 94 % full
+        // (each split adds a candidate list per row), else the fullest
+        double best = -1.0;
+        for (int s = 1; s <= 8; ++s) {
+            const int64_t ctas = qblocks * s, waves = ceil_div(ctas, (int64_t)152);
+            const double fill = (double)ctas / (double)(152 * waves);
+            if (fill >= 0.94) {
+                splits = s;
+                break;
+            }
+            if (fill > best + 1e-9) {
+                best = fill;
+                splits = s;
+            }
+        }
+    }
     if (splits == 0) splits = (int)std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(target, qblocks)));
     while (splits > 1 && splits * per_split > 1024) --splits;
     if (splits * per_split > 1024) return fail(RSC_ERR_INVALID_ARG, "db_splits * candidates above 1024");
@@ -521,7 +539,8 @@ rsc_status rsc_knn(const float *X, int64_t n, int32_t d, int32_t k, int32_t metr
                                        p.order ? kOrderWindow : 0, L.cand, L.status, st));
     } else {
         if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[1], st));
-        RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, p.KC, p.splits, p.split_len, L.cand, st));
+        RSC_CUDA_TRY(launch_knn_simt(L.Y, L.ny, n, p.DP, d + (metric == RSC_COSINE ? 1 : 0), p.KC, p.splits,
+                                     p.split_len, L.cand, st));
     }
     if (ev) RSC_CUDA_TRY(cudaEventRecord(ev[2], st));
     // exact re-rank reads the caller's rows (Euclidean) or the normalised rows (cosine)

@@ -19,8 +19,9 @@ cudaError_t launch_prep_fp32(const float *X, int64_t n, int d, int DP, int metri
 // FP32 SIMT candidate search: for every query row and database split s,
 // cand[(s * n + q) * KC + c] = the KC columns with the smallest
 // ny_j - 2 * Y_q . Y_j inside the split (ties keep the earlier column).
+// Columns width .. DP - 1 of Y are zero (DP - 7 <= width <= DP).
 bool knn_simt_supported(int DP, int KC);
-cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, int KC,
+cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, int width, int KC,
                             int splits, int64_t split_len, int32_t *cand, cudaStream_t st);
 
 // ---- knn_tc.cu ------------------------------------------------------------

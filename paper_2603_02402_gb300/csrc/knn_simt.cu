@@ -9,12 +9,13 @@ bool knn_simt_supported(int DP, int KC) {
     return dp_ok && kc_ok;
 }
 
-cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, int KC,
+cudaError_t launch_knn_simt(const float *Y, const float *ny, int64_t n, int DP, int width, int KC,
                             int splits, int64_t split_len, int32_t *cand, cudaStream_t st) {
+    if (width < DP - 7 || width > DP) return cudaErrorInvalidValue;
     switch (KC) {
-        case 16: return launch_knn_simt_kc<16>(DP, Y, ny, n, splits, split_len, cand, st);
-        case 32: return launch_knn_simt_kc<32>(DP, Y, ny, n, splits, split_len, cand, st);
-        case 64: return launch_knn_simt_kc<64>(DP, Y, ny, n, splits, split_len, cand, st);
+        case 16: return launch_knn_simt_kc<16>(DP, Y, ny, n, width, splits, split_len, cand, st);
+        case 32: return launch_knn_simt_kc<32>(DP, Y, ny, n, width, splits, split_len, cand, st);
+        case 64: return launch_knn_simt_kc<64>(DP, Y, ny, n, width, splits, split_len, cand, st);
     }
     return cudaErrorInvalidValue;
 }

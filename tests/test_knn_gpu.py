@@ -102,6 +102,21 @@ def test_exact_ties_and_duplicates_integer_grid(rsc, precision):
         check_knn(X, gi, gd, oi, od, on, allow_miss=MISS[precision])
 
 
+@pytest.mark.parametrize("metric,n,d", [("euclidean", 3001, 50), ("euclidean", 700, 7), ("euclidean", 5000, 64),
+                                         ("cosine", 3001, 50), ("cosine", 700, 7), ("cosine", 5000, 63)])
+def test_fp32_tiled_and_per_query_kernels_agree(rsc, metric, n, d):
+    # FP32 candidate lists of 32 come from the register-tiled kernel, lists of
+    # 64 from the one-query-per-thread kernel; both must give the exact lists
+    X = synth.mixture(n, d, n_comp=8, seed=d + 1)
+    om = oracle.COSINE if metric == "cosine" else oracle.EUCLIDEAN
+    oi, od, on = oracle.knn(X, 15, metric=om)
+    ai, ad = run_knn(rsc, X, 15, metric=metric, precision="fp32", candidates=24)
+    bi, bd = run_knn(rsc, X, 15, metric=metric, precision="fp32", candidates=40)
+    check_knn(X, ai, ad, oi, od, on, metric=metric, allow_miss=0.0)
+    np.testing.assert_array_equal(ai, bi)
+    np.testing.assert_array_equal(ad, bd)
+
+
 def test_large_offset_is_translation_invariant(rsc):
     # a common offset of 1e3 leaves Euclidean distances unchanged; the
     # centring in the prep pass keeps the candidate search accurate
