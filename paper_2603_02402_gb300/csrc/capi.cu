@@ -163,14 +163,13 @@ rsc_status plan_knn(int64_t n, int32_t d, int32_t k, int32_t metric, const rsc_k
             return fail(RSC_ERR_UNSUPPORTED, "no SIMT kernel for DP=%d KC=%d", p->DP, p->KC);
     }
     // database splits: enough CTAs to fill the GPU when there are few queries
-    const bool tiled = !tc && p->KC <= 32;            // register-tiled FP32 kernel: 256 queries, 64-row tiles
-    const int64_t qrows = tiled ? 256 : 128;          // query rows per CTA work unit
-    const int64_t target = tc ? 152 : 1024;           // work units wanted (persistent CTAs / blocks)
-    const int64_t align = tc ? knn_tc_split_align() : tiled ? 64 : 32;
+    const int64_t qrows = tc ? 128 : 256;             // query rows per CTA work unit
+    const int64_t target = 152;                       // work units wanted (persistent CTAs)
+    const int64_t align = tc ? knn_tc_split_align() : 64;
     const int64_t qblocks = ceil_div(n, qrows);
     const int per_split = p->parts * p->KC;           // candidate ids per row and split
     int splits = o->db_splits;
-    if (splits == 0 && tiled) {
+    if (splits == 0 && !tc) {
         // one CTA per SM: the fewest splits whose waves are at least 94 % full
         // (each split adds a candidate list per row), else the fullest
         double best = -1.0;

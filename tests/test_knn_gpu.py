@@ -104,9 +104,10 @@ def test_exact_ties_and_duplicates_integer_grid(rsc, precision):
 
 @pytest.mark.parametrize("metric,n,d", [("euclidean", 3001, 50), ("euclidean", 700, 7), ("euclidean", 5000, 64),
                                          ("cosine", 3001, 50), ("cosine", 700, 7), ("cosine", 5000, 63)])
-def test_fp32_tiled_and_per_query_kernels_agree(rsc, metric, n, d):
-    # FP32 candidate lists of 32 come from the register-tiled kernel, lists of
-    # 64 from the one-query-per-thread kernel; both must give the exact lists
+def test_fp32_list_widths_agree(rsc, metric, n, d):
+    # FP32 candidate lists of 32 come from 8 x 8 register blocks over 64-row
+    # tiles, lists of 64 from 8 x 4 blocks over 32-row tiles; both must give
+    # the exact lists
     X = synth.mixture(n, d, n_comp=8, seed=d + 1)
     om = oracle.COSINE if metric == "cosine" else oracle.EUCLIDEAN
     oi, od, on = oracle.knn(X, 15, metric=om)
