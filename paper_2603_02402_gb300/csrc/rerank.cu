@@ -30,9 +30,11 @@ constexpr int kWarps = 16;   // queries per block: neighbouring queries share ca
 // row): the gathers are bound by the L1's line lookups, not by bytes.
 // E = (candidate slots rounded up to a power of two) / 32 (key, id) pairs per
 // lane, element v = e * 32 + lane, sorted ascending by (key, id) with a
-// bitonic network held in registers.
+// bitonic network held in registers.  Up to 64 candidates fit in 32 registers
+// a thread, so four blocks (all 64 warps) stay resident to hide the gathers'
+// latency.
 template <int E>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, E <= 2 ? 4 : 1)
 rerank_kernel(const float *__restrict__ R, int64_t rs, int64_t n, int d, int metric, bool vec,
               const int32_t *__restrict__ cand, int KC, int C, int k, const int32_t *__restrict__ perm,
               bool r_by_pos, int32_t *__restrict__ idx, float *__restrict__ dist) {
