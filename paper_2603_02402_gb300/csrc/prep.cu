@@ -17,7 +17,7 @@ namespace {
 
 constexpr int kRowsPerWarp = 32;
 constexpr int kWarps = 4;
-constexpr int kColBlocks = 256;
+constexpr int kColBlocks = 1216;   // 8 per SM: enough loads in flight to stream X near the HBM rate
 constexpr int kColTile = 64;   // rows staged in shared memory at a time
 
 // Column sums, deterministic: block b owns a fixed row range (a multiple of 4
@@ -56,18 +56,24 @@ colsum_partials_kernel(const float *__restrict__ X, int64_t n, int d, float *__r
     if (g == 0 && c < d) part[(int64_t)blockIdx.x * 64 + c] = (red[0][c] + red[1][c]) + (red[2][c] + red[3][c]);
 }
 
-__global__ void colmean_final_kernel(const float *__restrict__ part, int nb, int64_t n, int d,
-                                     float *__restrict__ mu) {
-    const int c = threadIdx.x;
-    if (c >= d) return;
+// Thread (g, c) adds column c of partials g, g + 4, ... with Kahan
+// compensation; the four sums are added in a fixed order.
+__global__ void __launch_bounds__(256) colmean_final_kernel(const float *__restrict__ part, int nb, int64_t n,
+                                                            int d, float *__restrict__ mu) {
+    __shared__ float red[4][64];
+    const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
     float s = 0.f, comp = 0.f;
-    for (int b = 0; b < nb; ++b) {
-        const float y = part[b * 64 + c] - comp;
-        const float t = s + y;
-        comp = (t - s) - y;
-        s = t;
+    if (c < d) {
+        for (int b = g; b < nb; b += 4) {
+            const float y = part[b * 64 + c] - comp;
+            const float t = s + y;
+            comp = (t - s) - y;
+            s = t;
+        }
     }
-    mu[c] = (float)((double)(s - comp) / (double)n);
+    red[g][c] = s - comp;
+    __syncthreads();
+    if (g == 0 && c < d) mu[c] = (float)((double)((red[0][c] + red[1][c]) + (red[2][c] + red[3][c])) / (double)n);
 }
 
 // A warp stages 32 consecutive rows (contiguous in X) through shared memory so
@@ -141,7 +147,7 @@ cudaError_t launch_prep_fp32(const float *X, int64_t n, int d, int DP, int metri
     float *mu = scratch + (size_t)kColBlocks * 64;
     if (metric == RSC_EUCLIDEAN) {
         colsum_partials_kernel<<<kColBlocks, 256, 0, st>>>(X, n, d, scratch);
-        colmean_final_kernel<<<1, 64, 0, st>>>(scratch, kColBlocks, n, d, mu);
+        colmean_final_kernel<<<1, 256, 0, st>>>(scratch, kColBlocks, n, d, mu);
     }
     const int64_t rows_per_block = (int64_t)kWarps * kRowsPerWarp;
     const int64_t blocks = ceil_div(n, rows_per_block);
