@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kWarps = 16;   // queries per block: neighbouring queries share candidate rows in L1
 
-// Warp per query, 8 lanes per candidate row.  In round g, lanes 8 r + s
+// Warp per query, 8 lanes per candidate row.  In step g, lanes 8 r + s
 // (r < 4, s < 8) score candidate 4 g + r of the current 32: lane s takes
 // components 4 s .. 4 s + 3 and 32 + 4 s .. 32 + 4 s + 3 (two 16-byte loads
 // when rows start on 16-byte boundaries, else scalar loads; the same sums
