@@ -281,6 +281,27 @@ def test_input_rows_off_16_byte_boundary(rsc, precision):
     np.testing.assert_array_equal(gd, ad)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_rerank_vector_and_scalar_loads_agree(rsc, precision):
+    # d = 48: rows of an aligned X are re-ranked with 16-byte loads, rows of a
+    # copy placed 4 bytes off a 16-byte boundary with scalar loads; the partial
+    # sums are the same either way, so the results are identical (below the
+    # ordering's size, the re-rank reads the caller's rows)
+    n, d, k = 6000, 48, 15
+    X = synth.mixture(n, d, n_comp=12, seed=41)
+    flat = torch.zeros(n * d + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(X.reshape(-1)).cuda()
+    Xv = flat[1:].view(n, d)
+    assert Xv.data_ptr() % 16 != 0
+    ws = torch.empty(rsc.rsc_knn_workspace_size(n, d, k, "euclidean", precision), dtype=torch.uint8, device="cuda")
+    gi, gd = [t.cpu().numpy() for t in rsc.rsc_knn(Xv, k, "euclidean", precision, workspace=ws)]
+    ai, ad = run_knn(rsc, X, k, precision=precision)
+    np.testing.assert_array_equal(gi, ai)
+    np.testing.assert_array_equal(gd, ad)
+    oi, od, on = oracle.knn(X, k)
+    check_knn(X, gi, gd, oi, od, on, allow_miss=MISS[precision])
+
+
 def test_fp8_on_ordered_rows(rsc):
     # 30,000 rows take the locality ordering (window first, no pruning for
     # FP8); default candidates (8k, at most 128)
