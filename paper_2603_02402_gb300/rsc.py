@@ -677,14 +677,18 @@ def leiden_opts(resolution=1.0, n_iterations=2, max_levels=32, max_rounds=8, str
 
 
 def rsc_leiden(indptr: torch.Tensor, indices: torch.Tensor, data: torch.Tensor, resolution=1.0, n_iterations=2,
-               max_levels=32, max_rounds=8, init=None, workspace=None, stream=None):
+               max_levels=32, max_rounds=8, init=None, workspace=None, stream=None, nnz=None):
     """Leiden communities of a CSR graph: returns (membership int32 [n] CUDA
-    tensor, number of communities, modularity)."""
+    tensor, number of communities, modularity).  nnz defaults to indptr[-1]
+    (read back), so rsc_connectivities' capacity-sized outputs can be passed
+    as they are."""
     if not (indptr.is_cuda and indptr.dtype == torch.int64 and indices.dtype == torch.int32
             and data.dtype == torch.float32):
         raise ValueError("indptr int64, indices int32, data float32 CUDA tensors expected")
     n = indptr.numel() - 1
-    nnz = indices.numel()
+    nnz = int(indptr[-1].item()) if nnz is None else int(nnz)
+    if nnz > indices.numel() or nnz > data.numel():
+        raise ValueError("indices / data shorter than nnz")
     o = leiden_opts(resolution, n_iterations, max_levels, max_rounds, stream)
     ws = _workspace(rsc_leiden_workspace_size(n, nnz), indptr.device, workspace)
     mem = torch.empty(n, dtype=torch.int32, device=indptr.device)
